@@ -1,0 +1,256 @@
+/*
+ * fdc.h -- C ABI of the GB300 track-repeating proton dose engine.
+ *
+ * The engine implements the track-repeating algorithm of Yepes, Mirkovic &
+ * Taddei, "A GPU implementation of a track-repeating algorithm for proton
+ * radiotherapy dose calculations":
+ *   Sec. 2.2  a database of proton tracks pre-generated in water, stored step
+ *             by step, is re-traced through a voxel phantom by scaling each
+ *             step length and each scattering angle with the local material;
+ *   Sec. 2.3  the problem statement the calls below follow: load the material
+ *             scaling tables and the voxel geometry, load the track database,
+ *             simulate N incident protons drawn from a phase space, tally the
+ *             deposited energy in a grid shaped like the phantom and convert
+ *             it to dose by dividing by the voxel mass;
+ *   Sec. 2.4  batch statistics, eq. (1).
+ *
+ * Conventions shared by every call:
+ *   - Units: cm, MeV, g/cm^3, Gy.  The beam travels along +z and enters the
+ *     phantom at its upstream face z = z0.
+ *   - Voxel (ix, iy, iz) has linear index v = ix + nx * (iy + ny * iz)
+ *     (x fastest); every per-voxel array uses that order.
+ *   - "host" pointers are ordinary CPU memory, read during the call and not
+ *     retained; "device" pointers are CUDA global memory on the context's
+ *     device, owned by the caller unless stated otherwise.
+ *   - Streams are cudaStream_t values passed as void * (NULL = legacy default
+ *     stream).  Device work is asynchronous on that stream; argument errors
+ *     are returned synchronously; errors found on the device are latched in
+ *     a status word returned by fdc_sync.  Nothing traps.
+ *   - Return value: FDC_OK (0) or one of the FDC_ERR_* codes below;
+ *     fdc_last_error gives a one-line message.
+ *   - Determinism: for the same database, phantom, beam, seed and history
+ *     range the integer energy tally, and hence the dose, is bitwise
+ *     identical whatever the launch schedule or the split of the history
+ *     range into calls.
+ */
+#ifndef FDC_H
+#define FDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FDC_OK = 0,
+    FDC_ERR_INVALID = 1,     /* bad argument or input data */
+    FDC_ERR_NOT_LOADED = 2,  /* database or phantom missing */
+    FDC_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    FDC_ERR_OOM = 4,         /* device allocation failed */
+    FDC_ERR_STEP_LIMIT = 5,  /* device: a step crossed more voxels than the grid allows */
+    FDC_ERR_OVERFLOW = 6,    /* fixed-point headroom would be exceeded */
+    FDC_ERR_TIMEOUT = 7      /* a bounded device wait gave up */
+};
+
+enum { FDC_PROFILE_GAUSS = 0, FDC_PROFILE_RECT = 1, FDC_PROFILE_DISK = 2 };
+
+/* Energy tally unit: the dose grid accumulates int64 multiples of
+ * 2^-FDC_TALLY_SHIFT MeV. */
+#define FDC_TALLY_SHIFT 28
+
+typedef struct fdc_ctx fdc_ctx;
+
+/* Water track database (Sec. 2.2), host arrays in CSR form.
+ *   energy[n_energies]        bin energies (MeV), strictly increasing;
+ *   track_begin[n_energies+1] tracks of bin b are [track_begin[b], track_begin[b+1]),
+ *                             every bin holds at least one track;
+ *   step_begin[n_tracks+1]    steps of track t are [step_begin[t], step_begin[t+1]);
+ *   per step k, in track order:
+ *     dE[k]    energy lost along the step (MeV, >= 0);
+ *     len[k]   step length in water (cm, > 0);
+ *     theta[k] polar deflection applied at the end of the step (rad, [0, pi]);
+ *     phi[k]   its azimuth (rad);
+ *     esec[k]  energy deposited locally at the end of the step (MeV, >= 0).
+ * Storage: theta is kept as IEEE half precision and phi as a multiple of
+ * 2 pi / 65536 (one 16-byte record per step); values already on those grids
+ * are stored exactly. */
+typedef struct fdc_database {
+    int32_t n_energies;
+    const float *energy;
+    const int64_t *track_begin;
+    const int64_t *step_begin;
+    const float *dE, *len, *theta, *phi, *esec;
+} fdc_database;
+
+/* Voxel phantom (Sec. 2.3: material index per voxel plus per-material
+ * scaling parameters).  host arrays:
+ *   material[nvox] in [0, n_mat); density[nvox] (g/cm^3, >= 0);
+ *   s_rel[n_mat]   mass stopping-power ratio to water: a geometric length g in
+ *                  voxel v consumes g * density[v] * s_rel[material[v]] of the
+ *                  water step length;
+ *   k_theta[n_mat] scattering-power ratio to water: a step's deflection is
+ *                  theta * sqrt(sum_i w_i k_theta_i^2) over the voxels it
+ *                  crossed, w_i the water-equivalent fraction in each.
+ * Geometry: nx, ny, nz voxels of dx, dy, dz cm; (x0, y0, z0) is the corner of
+ * voxel (0, 0, 0).  n_mat <= 256. */
+typedef struct fdc_phantom {
+    int32_t nx, ny, nz, n_mat;
+    double dx, dy, dz, x0, y0, z0;
+    const uint8_t *material;
+    const float *density;
+    const float *s_rel;
+    const float *k_theta;
+} fdc_phantom;
+
+/* One beam spot (phase-space source, Sec. 2.3).  The spot's histories have
+ * consecutive global indices, spots in array order.  Per history:
+ *   entry (x, y): GAUSS: centre + a * N(0,1) per axis; RECT: uniform over
+ *   a x b around the centre; DISK: uniform over a disk of radius a;
+ *   energy: energy + sigma_e * N(0,1) (sigma_e = 0: mono-energetic);
+ *   layer: index of the per-layer tally the history scores into. */
+typedef struct fdc_spot {
+    double x, y, energy, sigma_e, a, b;
+    int32_t profile, layer;
+    uint64_t n_histories;
+} fdc_spot;
+
+typedef struct fdc_beam {
+    int32_t n_spots;
+    const fdc_spot *spots;   /* host [n_spots] */
+} fdc_beam;
+
+/* Launch schedule of the replay kernel.  Zero fields take the context's
+ * tuned (or built-in) value. */
+typedef struct fdc_schedule {
+    int32_t ctas_per_sm;     /* persistent CTAs per SM */
+    int32_t warps_per_cta;
+    int32_t chunk;           /* 32-history groups a warp claims per atomic */
+    int32_t aggregate;       /* 1: warp-aggregate tally atomics, 2: plain atomics */
+} fdc_schedule;
+
+/* Options of fdc_run_ex.  Zero-initialise for the defaults. */
+typedef struct fdc_run_opts {
+    uint64_t history_offset; /* first global history index of this call */
+    int32_t track_group;     /* histories h with equal h / track_group draw the same
+                                track (0 or 1: independent draws) */
+    int32_t no_rotation;     /* 1: replay every track unrotated (psi = 0) */
+    int32_t scaling_mode;    /* 0: per-voxel water-equivalent scaling; 1: the
+                                voxel where a step starts scales the whole step */
+    int32_t fp64_geometry;   /* 1: step geometry in FP64 instead of FP32 */
+    int32_t n_batches;       /* >= 2: split the histories into equal batches and
+                                accumulate the per-voxel batch dose sum and sum of
+                                squares (eq. (1)); 0 or 1: one batch */
+    int32_t pad;
+    fdc_schedule schedule;
+} fdc_run_opts;
+
+/* Outputs of fdc_run_ex; any pointer may be NULL.  device arrays, written
+ * (not accumulated) by the call:
+ *   dose[nvox]                  total dose (Gy);
+ *   layer_dose[n_layers * nvox] dose per layer, n_layers = 1 + max spot layer;
+ *   batch_sum[nvox], batch_sumsq[nvox]
+ *                               sum over batches of the batch dose and of its
+ *                               square (needs n_batches >= 2);
+ *   tally[nvox]                 raw int64 energy tally of the whole call
+ *                               (units of 2^-FDC_TALLY_SHIFT MeV). */
+typedef struct fdc_outputs {
+    double *dose;
+    double *layer_dose;
+    double *batch_sum;
+    double *batch_sumsq;
+    int64_t *tally;
+} fdc_outputs;
+
+/* Counters of the last run, valid after fdc_sync.  Energies are in tally
+ * units: replayed = energy of the replayed steps, escaped = the part that left
+ * the grid; the tally holds replayed - escaped exactly. */
+typedef struct fdc_counters {
+    uint64_t histories, steps, segments;
+    int64_t replayed, escaped;
+    int32_t status;
+    int32_t pad;
+    uint64_t bad_history;    /* first history that raised a device error */
+} fdc_counters;
+
+/* Create a context on CUDA device `device`.  *out receives the handle. */
+int fdc_create(fdc_ctx **out, int device);
+/* Free every device buffer of the context (waits for its work first). */
+void fdc_destroy(fdc_ctx *ctx);
+/* Message of the last error on this context (static storage of the context). */
+const char *fdc_last_error(const fdc_ctx *ctx);
+
+/* Sec. 2.2: validate and copy the database to the device (replaces any
+ * previous one).  Synchronous. */
+int fdc_load_database(fdc_ctx *ctx, const fdc_database *db);
+/* Sec. 2.3: validate and copy the phantom and material tables to the device
+ * (replaces any previous one).  Synchronous. */
+int fdc_load_phantom(fdc_ctx *ctx, const fdc_phantom *ph);
+
+/* Sec. 2.3: simulate histories [0, n_histories) of `beam` with random stream
+ * `seed` and write the dose (Gy) to device array dose_out[nvox].
+ * n_histories = 0 means all histories of the beam; more than the beam holds
+ * is FDC_ERR_INVALID.  Asynchronous on `stream`. */
+int fdc_run(fdc_ctx *ctx, const fdc_beam *beam, uint64_t n_histories, uint64_t seed,
+            double *dose_out, void *stream);
+
+/* As fdc_run, for histories [opts->history_offset, opts->history_offset +
+ * n_histories) with the options and outputs above. */
+int fdc_run_ex(fdc_ctx *ctx, const fdc_beam *beam, uint64_t n_histories, uint64_t seed,
+               const fdc_run_opts *opts, const fdc_outputs *out, void *stream);
+
+/* As fdc_run with a HOST dose buffer: copies the beam in, runs, copies the
+ * dose out and waits.  Returns the device status as fdc_sync does. */
+int fdc_run_host(fdc_ctx *ctx, const fdc_beam *beam, uint64_t n_histories, uint64_t seed,
+                 double *dose_host);
+
+/* Wait for `stream`, read the device status word of the last run and its
+ * counters.  Returns FDC_OK or the first device error (FDC_ERR_STEP_LIMIT,
+ * ...); `counters` (host, may be NULL) receives the counters. */
+int fdc_sync(fdc_ctx *ctx, void *stream, fdc_counters *counters);
+
+/* Eq. (1) on the device: from batch_sum/batch_sumsq over n_batches (>= 2)
+ * write mean[nvox] and sigma[nvox] (device, Gy), and to *mean_rel (host) the
+ * average of sigma/mean over voxels whose mean exceeds frac * max(mean)
+ * (Sec. 2.4 uses frac = 0.5).  Synchronous. */
+int fdc_batch_stats(fdc_ctx *ctx, const double *batch_sum, const double *batch_sumsq,
+                    int32_t n_batches, double frac, double *mean, double *sigma,
+                    double *mean_rel, void *stream);
+
+/* Pick the replay schedule for this beam by timing candidates on the device
+ * (runs the beam's first n_histories histories several times; results are
+ * discarded).  The choice becomes the context's default; *best (host, may be
+ * NULL) receives it.  Synchronous. */
+int fdc_autotune(fdc_ctx *ctx, const fdc_beam *beam, uint64_t n_histories, uint64_t seed,
+                 fdc_schedule *best);
+
+/* Measurement.  fdc_set_timing(ctx, 1) makes later runs record CUDA events
+ * on their stream around the replay kernel(s) and the finalize kernel;
+ * fdc_last_kernel_ms waits for them and returns the last run's replay time
+ * (first to last replay launch) and finalize time in milliseconds. */
+int fdc_set_timing(fdc_ctx *ctx, int32_t enable);
+int fdc_last_kernel_ms(fdc_ctx *ctx, double *replay_ms, double *finalize_ms);
+
+/* L2 atomic throughput probe (roofline denominator of the tally updates):
+ * n_ops 64-bit atomic adds of 1 spread by a hash over the n_slots counters of
+ * device array slots[n_slots] (zeroed by the call), issued by a full grid;
+ * *ms (host) receives the kernel time.  Synchronous on `stream`. */
+int fdc_probe_atomics(uint64_t *slots, uint64_t n_slots, uint64_t n_ops, double *ms, void *stream);
+
+/* Test hooks.  fdc_debug_philox: Philox4x64-10 (Salmon et al., SC'11) with
+ * key (key0, key1) on n device counters ctr[n][4], writing out[n][4] (device).
+ * fdc_debug_sample: task 1 of histories [h_begin, h_begin + n) -- entry x, y,
+ * energy and rotation psi (device xyEpsi[n][4]) and energy bin, track and
+ * start step (device btk[n][3]). */
+int fdc_debug_philox(uint64_t key0, uint64_t key1, const uint64_t *ctr, uint64_t n,
+                     uint64_t *out, void *stream);
+int fdc_debug_sample(fdc_ctx *ctx, const fdc_beam *beam, uint64_t seed, uint64_t h_begin,
+                     uint64_t n, int32_t track_group, int32_t no_rotation, float *xyEpsi,
+                     int64_t *btk, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDC_H */

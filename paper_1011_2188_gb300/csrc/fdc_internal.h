@@ -1,0 +1,92 @@
+// Internal declarations shared by the host library (fdc_api.cu) and the
+// kernels (fdc_kernels.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fdc.h"
+
+namespace fdc {
+
+// One step of a track, 16 bytes, loaded with a single 128-bit load:
+//   x: len (float bits, cm of water)   y: dE (float bits, MeV)
+//   z: esec (float bits, MeV)          w: theta as IEEE half (low 16 bits) |
+//                                         phi code in units of 2 pi / 65536 (high 16)
+// Per-step side arrays: eres (float residual energy at step start, used by
+// the start-step search) and tail (int64: tally units of all later steps of
+// the track, used to book escaped energy exactly).
+static_assert(sizeof(uint4) == 16, "step record must be 16 bytes");
+
+constexpr double kTallyUnitsPerMeV = 268435456.0;  // 2^FDC_TALLY_SHIFT
+constexpr double kMeVToJ = 1.602176634e-13;
+
+struct DeviceCounters {  // same layout as fdc_counters
+    unsigned long long histories, steps, segments;
+    long long replayed, escaped;
+    int status;
+    int pad;
+    unsigned long long bad_history;
+};
+static_assert(sizeof(DeviceCounters) == sizeof(fdc_counters), "counter layout");
+
+struct ReplayArgs {
+    // database (device)
+    const uint4 *rec;
+    const float *eres;
+    const long long *tail;
+    const long long *step_begin;
+    const float *bin_energy;
+    const long long *bin_track_begin;
+    int n_bins;
+    // phantom (device): per voxel (S_rel = density * s_rel[m], k_theta[m]^2)
+    const float2 *vox;
+    int nx, ny, nz;
+    double dx, dy, dz, x0, y0, z0;
+    // beam (device)
+    const fdc_spot *spots;
+    const unsigned long long *spot_cum;  // [n_spots + 1]
+    int n_spots;
+    // run
+    unsigned long long *tally;  // [n_tallies][nvox], int64 two's complement
+    long long nvox;
+    int per_layer;
+    unsigned long long h_begin, n;  // histories [h_begin, h_begin + n)
+    unsigned long long seed;
+    int track_group, rotate, scaling_mode;
+    int chunk;
+    unsigned long long *work;     // work counter (zeroed before launch)
+    DeviceCounters *counters;
+};
+
+struct FinalizeArgs {
+    long long *tally;        // [n_tallies][nvox], read (and zeroed if zero_after)
+    int n_tallies;
+    long long nvox;
+    const float *density;
+    double scale;            // Gy per tally unit per (g/cm^3)
+    double *dose;            // [nvox] or null: dose of the summed tally
+    double *layer_dose;      // [n_tallies][nvox] or null
+    long long *tally_out;    // [nvox] or null: summed tally
+    double *batch_sum;       // [nvox] or null: += dose
+    double *batch_sumsq;     // [nvox] or null: += dose^2
+    long long *accum;        // [n_tallies][nvox] or null: += tally
+    int zero_after;          // 1: tally := 0 after reading
+};
+
+cudaError_t launch_replay(const ReplayArgs &a, const fdc_schedule &s, int fp64, int sm_count,
+                          cudaStream_t st);
+cudaError_t launch_finalize(const FinalizeArgs &a, int sm_count, cudaStream_t st);
+cudaError_t launch_batch_stats(const double *sum, const double *sumsq, int n_batches, long long nvox,
+                               double frac, double *mean, double *sigma, double *partials,
+                               int n_partials, double *result, cudaStream_t st);
+cudaError_t launch_debug_philox(unsigned long long k0, unsigned long long k1,
+                                const unsigned long long *ctr, unsigned long long n,
+                                unsigned long long *out, cudaStream_t st);
+cudaError_t launch_debug_sample(const ReplayArgs &a, float *xyEpsi, long long *btk,
+                                cudaStream_t st);
+int replay_max_ctas_per_sm(int warps_per_cta, int fp64, int aggregate);
+cudaError_t launch_probe_atomics(unsigned long long *slots, unsigned long long n_slots,
+                                 unsigned long long n_ops, int sm_count, cudaStream_t st);
+
+}  // namespace fdc

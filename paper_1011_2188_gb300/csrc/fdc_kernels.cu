@@ -1,0 +1,601 @@
+// Device code of the track-repeating dose engine (sm_103a).
+//
+// replay_kernel: persistent grid; every warp claims groups of 32 histories
+// from a global counter and each lane re-traces one history at a time
+// (Sec. 2.3, tasks 1 and 2):
+//   task 1  Philox4x64-10 draws the entry point, energy and track rotation;
+//           the energy picks the database bin and the start step (first step
+//           whose residual energy is <= the proton energy);
+//   task 2  for every step: one 128-bit load of the step record, an
+//           Amanatides-Woo march over the voxels the step crosses in which
+//           the water step length is consumed as water-equivalent length
+//           (Sec. 2.2 step scaling), energy shared over the segments in
+//           proportion, the deflection at the end scaled by the crossed
+//           materials' scattering-power ratios (Sec. 2.2 angle scaling).
+// Energy goes to an int64 fixed-point tally (2^-28 MeV units) with integer
+// atomics, so the sum is independent of the order of the updates: the paper's
+// blocking tally update (Sec. 2.3) becomes a single L2 reduction, optionally
+// combined across the lanes of a warp that hit the same voxel.
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fdc_internal.h"
+
+namespace fdc {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kUnitsF = 268435456.0f;  // 2^28
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr float kPhiQuantumF = 9.58737992428525e-05f;  // 2 pi / 65536
+constexpr double kPhiQuantumD = 9.587379924285257e-05;
+
+// ---------------------------------------------------------------- Philox
+// Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 64x64->128 multiplications and a key-dependent mix, the key bumped by the
+// Weyl constants between rounds.
+struct U64x4 {
+    unsigned long long v0, v1, v2, v3;
+};
+
+__device__ __forceinline__ U64x4 philox(unsigned long long c0, unsigned long long c1,
+                                        unsigned long long c2, unsigned long long c3,
+                                        unsigned long long k0, unsigned long long k1) {
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const unsigned long long hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        const unsigned long long hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        const unsigned long long n0 = hi1 ^ c1 ^ k0;
+        const unsigned long long n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// (0,1) uniform from the top 53 bits, centred in its cell.
+__device__ __forceinline__ double u01(unsigned long long r) {
+    return __dmul_rn(__dadd_rn((double)(r >> 11), 0.5), 0x1p-53);
+}
+
+// ---------------------------------------------------------------- task 1
+struct Start {
+    float x, y, E, psi;
+    int bin, layer;
+    long long track, s0, k0, n;  // steps [s0 + k0, s0 + n) are replayed
+};
+
+// Per-history draws in FP64 with explicit rounding (no contraction), then
+// rounded to the single-precision per-proton state.
+__device__ Start sample_start(const ReplayArgs &P, unsigned long long h) {
+    Start st;
+    const U64x4 A = philox(h, 1, 0, 0, P.seed, 0);
+    const U64x4 B = philox(h, 2, 0, 0, P.seed, 0);
+    const unsigned long long g = P.track_group > 1 ? h / (unsigned long long)P.track_group : h;
+    const U64x4 C = philox(g, 3, 0, 0, P.seed, 0);
+
+    // spot: largest s with cum[s] <= h
+    int lo = 0, hi = P.n_spots - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.spot_cum[mid] <= h) lo = mid; else hi = mid - 1;
+    }
+    const fdc_spot sp = P.spots[lo];
+    st.layer = sp.layer;
+
+    double x, y;
+    if (sp.profile == FDC_PROFILE_GAUSS) {
+        const double r = __dsqrt_rn(__dmul_rn(-2.0, log(u01(A.v0))));
+        double s, c;
+        sincos(__dmul_rn(kTwoPi, u01(A.v1)), &s, &c);
+        x = __dadd_rn(sp.x, __dmul_rn(sp.a, __dmul_rn(r, c)));
+        y = __dadd_rn(sp.y, __dmul_rn(sp.a, __dmul_rn(r, s)));
+    } else if (sp.profile == FDC_PROFILE_RECT) {
+        x = __dadd_rn(sp.x, __dmul_rn(sp.a, __dsub_rn(u01(A.v0), 0.5)));
+        y = __dadd_rn(sp.y, __dmul_rn(sp.b, __dsub_rn(u01(A.v1), 0.5)));
+    } else {
+        const double r = __dmul_rn(sp.a, __dsqrt_rn(u01(A.v0)));
+        double s, c;
+        sincos(__dmul_rn(kTwoPi, u01(A.v1)), &s, &c);
+        x = __dadd_rn(sp.x, __dmul_rn(r, c));
+        y = __dadd_rn(sp.y, __dmul_rn(r, s));
+    }
+    double E = sp.energy;
+    if (sp.sigma_e > 0.0) {
+        const double r = __dsqrt_rn(__dmul_rn(-2.0, log(u01(A.v2))));
+        const double n0 = __dmul_rn(r, cos(__dmul_rn(kTwoPi, u01(A.v3))));
+        E = __dadd_rn(sp.energy, __dmul_rn(sp.sigma_e, n0));
+    }
+    st.x = (float)x;
+    st.y = (float)y;
+    st.E = (float)E;
+    st.psi = P.rotate ? (float)__dmul_rn(kTwoPi, u01(B.v0)) : 0.0f;
+
+    // energy bin: first bin energy >= E, else the top bin
+    int b0 = 0, b1 = P.n_bins - 1;
+    while (b0 < b1) {
+        const int mid = (b0 + b1) >> 1;
+        if (P.bin_energy[mid] >= st.E) b1 = mid; else b0 = mid + 1;
+    }
+    st.bin = b0;
+    const long long tb = P.bin_track_begin[b0];
+    const unsigned long long nb = (unsigned long long)(P.bin_track_begin[b0 + 1] - tb);
+    st.track = tb + (long long)__umul64hi(C.v0, nb);
+    st.s0 = P.step_begin[st.track];
+    st.n = P.step_begin[st.track + 1] - st.s0;
+    // start step: first k with eres[k] <= E (eres is non-increasing)
+    long long k0 = st.n;
+    if (st.E > 0.0f) {
+        long long l = 0, r = st.n;
+        while (l < r) {
+            const long long mid = (l + r) >> 1;
+            if (__ldg(P.eres + st.s0 + mid) <= st.E) r = mid; else l = mid + 1;
+        }
+        k0 = l;
+    }
+    st.k0 = k0;
+    return st;
+}
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ void sincos_(float a, float *s, float *c) { sincosf(a, s, c); }
+__device__ __forceinline__ void sincos_(double a, double *s, double *c) { sincos(a, s, c); }
+__device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
+__device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
+__device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
+__device__ __forceinline__ double rsqrt_(double a) { return rsqrt(a); }
+__device__ __forceinline__ long long to_units(float e) { return __float2ll_rn(e * kUnitsF); }
+__device__ __forceinline__ long long to_units(double e) { return __double2ll_rn(e * 268435456.0); }
+template <typename R> __device__ __forceinline__ R inf_();
+template <> __device__ __forceinline__ float inf_<float>() { return __int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ double inf_<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
+
+// Tally update.  AGG: lanes of the warp that add to the same voxel are
+// combined first (match on the index, add the four 16-bit limbs of the
+// two's-complement value with redux.sync inside each group, one atomic per
+// group); otherwise one atomic per lane.
+template <bool AGG>
+__device__ __forceinline__ void tally_add(unsigned long long *tally, long long idx, long long units) {
+    if (!AGG) {
+        atomicAdd(tally + idx, (unsigned long long)units);
+        return;
+    }
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned mask = __activemask();
+    const unsigned peers = __match_any_sync(mask, (unsigned long long)idx);
+    if (peers == (1u << lane)) {
+        atomicAdd(tally + idx, (unsigned long long)units);
+        return;
+    }
+    const unsigned long long u = (unsigned long long)units;
+    const unsigned l0 = __reduce_add_sync(peers, (unsigned)(u & 0xffffu));
+    const unsigned l1 = __reduce_add_sync(peers, (unsigned)((u >> 16) & 0xffffu));
+    const unsigned l2 = __reduce_add_sync(peers, (unsigned)((u >> 32) & 0xffffu));
+    const unsigned l3 = __reduce_add_sync(peers, (unsigned)(u >> 48));
+    if (lane == (unsigned)(__ffs(peers) - 1)) {
+        const unsigned long long s = (unsigned long long)l0 + ((unsigned long long)l1 << 16) +
+                                     ((unsigned long long)l2 << 32) + ((unsigned long long)l3 << 48);
+        atomicAdd(tally + idx, s);
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ void raise_status(DeviceCounters *c, int code, unsigned long long h) {
+    if (atomicCAS(&c->status, 0, code) == 0) c->bad_history = h;
+}
+
+// ---------------------------------------------------------------- task 2
+// Re-trace one history.  Geometry in grid units: u = (position - origin) /
+// spacing per axis, so voxel faces sit at integers; distances along the ray
+// are in cm.  Returns nothing; per-lane counters are updated in place.
+template <typename R, bool AGG>
+__device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start &st,
+                                               unsigned long long h, unsigned long long &steps,
+                                               unsigned long long &segs, long long &replayed,
+                                               long long &escaped) {
+    if (st.k0 >= st.n) return;
+    const long long s_first = st.s0 + st.k0, s_end = st.s0 + st.n;
+    // energy of the replayed steps, in tally units
+    long long rep;
+    {
+        const uint4 r0 = __ldg(P.rec + s_first);
+        rep = to_units(__uint_as_float(r0.y)) + to_units(__uint_as_float(r0.z)) + __ldg(P.tail + s_first);
+    }
+    replayed += rep;
+    // entry on the upstream face; inside test and voxel in FP64 (the
+    // per-proton state is FP32, the comparison is exact in FP64)
+    const double xe = (double)st.x, ye = (double)st.y;
+    if (!(xe >= P.x0 && xe < P.x0 + P.nx * P.dx && ye >= P.y0 && ye < P.y0 + P.ny * P.dy)) {
+        escaped += rep;  // misses the phantom: the whole history escapes
+        return;
+    }
+    const double gx = (xe - P.x0) / P.dx, gy = (ye - P.y0) / P.dy;
+    int ix = min((int)floor(gx), P.nx - 1), iy = min((int)floor(gy), P.ny - 1), iz = 0;
+    R ux = (R)gx, uy = (R)gy, uz = (R)0;
+    R dx = (R)0, dy = (R)0, dz = (R)1;
+    const R ihx = (R)(1.0 / P.dx), ihy = (R)(1.0 / P.dy), ihz = (R)(1.0 / P.dz);
+    const long long sy = P.nx, sz = (long long)P.nx * P.ny;
+    long long v = ix + sy * iy;
+    const long long tbase = P.per_layer ? (long long)st.layer * P.nvox : 0ll;
+    unsigned long long *const tally = P.tally + tbase;
+    const R psi = (R)st.psi;
+    const int seg_cap = P.nx + P.ny + P.nz + 8;
+    const R INF = inf_<R>();
+
+    for (long long s = s_first; s < s_end; ++s) {
+        const uint4 rec = __ldg(P.rec + s);
+        const float dE_f = __uint_as_float(rec.y);
+        const R len = (R)__uint_as_float(rec.x), dE = (R)dE_f;
+        const long long Qk = to_units(dE_f);
+        const long long Qs = to_units(__uint_as_float(rec.z));
+        const R inv_len = (R)1 / len;
+        ++steps;
+
+        // ray in grid units per cm, distances to the next faces (cm)
+        const R rx = dx * ihx, ry = dy * ihy, rz = dz * ihz;
+        R tmx, tmy, tmz, tdx, tdy, tdz;
+        int stx, sty, stz;
+        if (rx > (R)0) { tmx = ((R)(ix + 1) - ux) / rx; tdx = (R)1 / rx; stx = 1; }
+        else if (rx < (R)0) { tmx = ((R)ix - ux) / rx; tdx = (R)-1 / rx; stx = -1; }
+        else { tmx = INF; tdx = INF; stx = 0; }
+        if (ry > (R)0) { tmy = ((R)(iy + 1) - uy) / ry; tdy = (R)1 / ry; sty = 1; }
+        else if (ry < (R)0) { tmy = ((R)iy - uy) / ry; tdy = (R)-1 / ry; sty = -1; }
+        else { tmy = INF; tdy = INF; sty = 0; }
+        if (rz > (R)0) { tmz = ((R)(iz + 1) - uz) / rz; tdz = (R)1 / rz; stz = 1; }
+        else if (rz < (R)0) { tmz = ((R)iz - uz) / rz; tdz = (R)-1 / rz; stz = -1; }
+        else { tmz = INF; tdz = INF; stz = 0; }
+        tmx = tmx > (R)0 ? tmx : (R)0;
+        tmy = tmy > (R)0 ? tmy : (R)0;
+        tmz = tmz > (R)0 ? tmz : (R)0;
+
+        R rem = len, t = (R)0, acc = (R)0;
+        long long dep = 0;
+        R S_fix = (R)0, k2_fix = (R)0;
+        if (P.scaling_mode == 1) {
+            const float2 sk = __ldg(P.vox + v);
+            S_fix = (R)sk.x;
+            k2_fix = (R)sk.y;
+        }
+        int nseg = 0;
+        bool gone = false;
+        for (;;) {
+            R S, k2;
+            if (P.scaling_mode == 1) { S = S_fix; k2 = k2_fix; }
+            else { const float2 sk = __ldg(P.vox + v); S = (R)sk.x; k2 = (R)sk.y; }
+            // nearest face; ties go to x, then y, then z
+            int a = 0;
+            R tm = tmx;
+            if (tmy < tm) { a = 1; tm = tmy; }
+            if (tmz < tm) { a = 2; tm = tmz; }
+            R seg = tm - t;
+            seg = seg > (R)0 ? seg : (R)0;
+            const R wexit = seg * S;
+            ++segs;
+            if (wexit >= rem) {  // the step ends in this voxel
+                const long long units = Qk - dep;
+                if (units) tally_add<AGG>(tally, v, units);
+                acc += rem * k2;
+                t += rem / S;
+                break;
+            }
+            const long long units = to_units(dE * (wexit * inv_len));
+            dep += units;
+            if (units) tally_add<AGG>(tally, v, units);
+            acc += wexit * k2;
+            rem -= wexit;
+            t = tm;
+            bool out;
+            if (a == 0) { ix += stx; v += stx; out = (unsigned)ix >= (unsigned)P.nx; tmx += tdx; }
+            else if (a == 1) { iy += sty; v += sty * sy; out = (unsigned)iy >= (unsigned)P.ny; tmy += tdy; }
+            else { iz += stz; v += stz * sz; out = (unsigned)iz >= (unsigned)P.nz; tmz += tdz; }
+            if (out) {  // left the grid: the rest of the history escapes
+                escaped += (Qk - dep) + Qs + __ldg(P.tail + s);
+                gone = true;
+                break;
+            }
+            if (++nseg > seg_cap) {
+                raise_status(P.counters, FDC_ERR_STEP_LIMIT, h);
+                gone = true;
+                break;
+            }
+        }
+        if (gone) return;
+        ux += t * rx;
+        uy += t * ry;
+        uz += t * rz;
+        if (Qs) tally_add<AGG>(tally, v, Qs);
+
+        // deflection at the end of the step, scaled by the crossed materials
+        const R theta = (R)__half2float(__ushort_as_half((unsigned short)(rec.w & 0xffffu))) *
+                        sqrt_(acc * inv_len);
+        R phi = (R)(rec.w >> 16) * (sizeof(R) == 4 ? (R)kPhiQuantumF : (R)kPhiQuantumD);
+        R st_, ct_;
+        sincos_(theta, &st_, &ct_);
+        const R p2 = dx * dx + dy * dy;
+        R nx_, ny_, nz_;
+        if (p2 > (R)0) {
+            R sp_, cp_;
+            sincos_(phi, &sp_, &cp_);
+            const R ip = rsqrt_(p2), p = p2 * ip;
+            const R a = st_ * cp_, b = st_ * sp_;
+            // e1 = (dx dz, dy dz, -p^2)/p, e2 = (-dy, dx, 0)/p
+            nx_ = a * (dx * dz * ip) - b * (dy * ip) + ct_ * dx;
+            ny_ = a * (dy * dz * ip) + b * (dx * ip) + ct_ * dy;
+            nz_ = -a * p + ct_ * dz;
+        } else {
+            // along the beam axis: the frame is (x, y) turned by psi, which
+            // makes the replay a rigid rotation of the track
+            const R sgn = dz > (R)0 ? (R)1 : (R)-1;
+            R sp_, cp_;
+            sincos_(phi + sgn * psi, &sp_, &cp_);
+            nx_ = st_ * cp_;
+            ny_ = sgn * st_ * sp_;
+            nz_ = sgn * ct_;
+        }
+        const R inorm = rsqrt_(nx_ * nx_ + ny_ * ny_ + nz_ * nz_);
+        dx = nx_ * inorm;
+        dy = ny_ * inorm;
+        dz = nz_ * inorm;
+    }
+}
+
+template <typename R, bool AGG>
+__global__ void __launch_bounds__(256) replay_kernel(const ReplayArgs P) {
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned long long steps = 0, segs = 0, hist = 0;
+    long long replayed = 0, escaped = 0;
+    const unsigned long long claim = 32ull * (unsigned long long)P.chunk;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(P.work, claim);
+        base = __shfl_sync(kFull, base, 0);
+        if (base >= P.n) break;
+        for (int c = 0; c < P.chunk; ++c) {
+            const unsigned long long li = base + 32ull * c + lane;
+            if (li < P.n) {
+                const unsigned long long h = P.h_begin + li;
+                const Start st = sample_start(P, h);
+                replay_history<R, AGG>(P, st, h, steps, segs, replayed, escaped);
+                ++hist;
+            }
+        }
+    }
+    hist = warp_sum_u64(hist);
+    steps = warp_sum_u64(steps);
+    segs = warp_sum_u64(segs);
+    replayed = (long long)warp_sum_u64((unsigned long long)replayed);
+    escaped = (long long)warp_sum_u64((unsigned long long)escaped);
+    if (lane == 0) {
+        atomicAdd(&P.counters->histories, hist);
+        atomicAdd(&P.counters->steps, steps);
+        atomicAdd(&P.counters->segments, segs);
+        atomicAdd((unsigned long long *)&P.counters->replayed, (unsigned long long)replayed);
+        atomicAdd((unsigned long long *)&P.counters->escaped, (unsigned long long)escaped);
+    }
+}
+
+// ---------------------------------------------------------------- finalize
+// Sec. 2.3: energy per voxel divided by the voxel mass; FP64.
+__global__ void finalize_kernel(const FinalizeArgs A) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < A.nvox; v += stride) {
+        const double rho = (double)A.density[v];
+        const double f = rho > 0.0 ? A.scale / rho : 0.0;
+        long long tot = 0;
+        for (int l = 0; l < A.n_tallies; ++l) {
+            const long long t = A.tally[l * A.nvox + v];
+            tot += t;
+            if (A.layer_dose) A.layer_dose[l * A.nvox + v] = (double)t * f;
+            if (A.accum) A.accum[l * A.nvox + v] += t;
+            if (A.zero_after) A.tally[l * A.nvox + v] = 0;
+        }
+        const double d = (double)tot * f;
+        if (A.dose) A.dose[v] = d;
+        if (A.tally_out) A.tally_out[v] = tot;
+        if (A.batch_sum) A.batch_sum[v] += d;
+        if (A.batch_sumsq) A.batch_sumsq[v] += d * d;
+    }
+}
+
+// ---------------------------------------------------------------- statistics
+// Eq. (1) per voxel from batch sums, then a deterministic two-level
+// reduction: per-block partials (max of the mean; then masked sum and count
+// of sigma/mean), combined by one block in a fixed order.
+__global__ void stats_pass1(const double *sum, const double *sumsq, int n, long long nvox, double *mean,
+                            double *sigma, double *part_max) {
+    __shared__ double sm[256];
+    double mx = 0.0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long long)gridDim.x * blockDim.x) {
+        const double s = sum[v], m = s / n;
+        const double ss = sumsq[v] - s * s / n;
+        const double sg = sqrt((ss > 0.0 ? ss : 0.0) / ((double)n * (n - 1)));
+        mean[v] = m;
+        sigma[v] = sg;
+        mx = m > mx ? m : mx;
+    }
+    sm[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part_max[blockIdx.x] = sm[0];
+}
+
+__global__ void stats_pass2(const double *mean, const double *sigma, long long nvox, double frac,
+                            const double *part_max, int n_parts, double *part_sum, double *part_cnt) {
+    __shared__ double s1[256], s2[256];
+    double mx = 0.0;
+    for (int i = 0; i < n_parts; ++i) mx = fmax(mx, part_max[i]);
+    const double thr = frac * mx;
+    double acc = 0.0, cnt = 0.0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long long)gridDim.x * blockDim.x) {
+        if (mean[v] > thr) {
+            acc += sigma[v] / mean[v];
+            cnt += 1.0;
+        }
+    }
+    s1[threadIdx.x] = acc;
+    s2[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part_sum[blockIdx.x] = s1[0];
+        part_cnt[blockIdx.x] = s2[0];
+    }
+}
+
+__global__ void stats_pass3(const double *part_sum, const double *part_cnt, int n_parts, double *result) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0.0, c = 0.0;
+        for (int i = 0; i < n_parts; ++i) {
+            a += part_sum[i];
+            c += part_cnt[i];
+        }
+        result[0] = c > 0.0 ? a / c : __longlong_as_double(0x7ff8000000000000ll);
+    }
+}
+
+// ---------------------------------------------------------------- test hooks
+__global__ void debug_philox_kernel(unsigned long long k0, unsigned long long k1,
+                                    const unsigned long long *ctr, unsigned long long n,
+                                    unsigned long long *out) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const U64x4 r = philox(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], k0, k1);
+        out[4 * i] = r.v0;
+        out[4 * i + 1] = r.v1;
+        out[4 * i + 2] = r.v2;
+        out[4 * i + 3] = r.v3;
+    }
+}
+
+__global__ void debug_sample_kernel(const ReplayArgs P, float *xyEpsi, long long *btk) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < P.n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const Start st = sample_start(P, P.h_begin + i);
+        xyEpsi[4 * i] = st.x;
+        xyEpsi[4 * i + 1] = st.y;
+        xyEpsi[4 * i + 2] = st.E;
+        xyEpsi[4 * i + 3] = st.psi;
+        btk[3 * i] = st.bin;
+        btk[3 * i + 1] = st.track;
+        btk[3 * i + 2] = st.k0;
+    }
+}
+
+// 64-bit atomic adds to hashed addresses (every thread its own stream of
+// slots), the access pattern of the dose tally without the transport.
+__global__ void probe_atomics_kernel(unsigned long long *slots, unsigned long long n_slots,
+                                     unsigned long long n_ops) {
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = tid; i < n_ops; i += nth) {
+        unsigned long long x = i * 0x9E3779B97F4A7C15ull;
+        x ^= x >> 29;
+        atomicAdd(slots + (x % n_slots), 1ull);
+    }
+}
+
+template <typename R, bool AGG>
+cudaError_t launch_replay_t(const ReplayArgs &a, int ctas, int threads, cudaStream_t st) {
+    replay_kernel<R, AGG><<<ctas, threads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename R, bool AGG>
+int max_ctas_t(int threads) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, replay_kernel<R, AGG>, threads, 0) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+}  // namespace
+
+cudaError_t launch_replay(const ReplayArgs &a, const fdc_schedule &s, int fp64, int sm_count,
+                          cudaStream_t st) {
+    const int threads = 32 * s.warps_per_cta;
+    const int ctas = sm_count * s.ctas_per_sm;
+    const bool agg = s.aggregate != 2;
+    if (fp64) return agg ? launch_replay_t<double, true>(a, ctas, threads, st)
+                         : launch_replay_t<double, false>(a, ctas, threads, st);
+    return agg ? launch_replay_t<float, true>(a, ctas, threads, st)
+               : launch_replay_t<float, false>(a, ctas, threads, st);
+}
+
+int replay_max_ctas_per_sm(int warps_per_cta, int fp64, int aggregate) {
+    const int threads = 32 * warps_per_cta;
+    const bool agg = aggregate != 2;
+    if (fp64) return agg ? max_ctas_t<double, true>(threads) : max_ctas_t<double, false>(threads);
+    return agg ? max_ctas_t<float, true>(threads) : max_ctas_t<float, false>(threads);
+}
+
+cudaError_t launch_probe_atomics(unsigned long long *slots, unsigned long long n_slots,
+                                 unsigned long long n_ops, int sm_count, cudaStream_t st) {
+    probe_atomics_kernel<<<sm_count * 8, 256, 0, st>>>(slots, n_slots, n_ops);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const FinalizeArgs &a, int sm_count, cudaStream_t st) {
+    long long blocks = (a.nvox + 255) / 256;
+    const long long cap = (long long)sm_count * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    finalize_kernel<<<(int)blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_stats(const double *sum, const double *sumsq, int n_batches, long long nvox,
+                               double frac, double *mean, double *sigma, double *partials,
+                               int n_partials, double *result, cudaStream_t st) {
+    // partials: [3][n_partials]
+    stats_pass1<<<n_partials, 256, 0, st>>>(sum, sumsq, n_batches, nvox, mean, sigma, partials);
+    stats_pass2<<<n_partials, 256, 0, st>>>(mean, sigma, nvox, frac, partials, n_partials,
+                                            partials + n_partials, partials + 2 * n_partials);
+    stats_pass3<<<1, 32, 0, st>>>(partials + n_partials, partials + 2 * n_partials, n_partials, result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_philox(unsigned long long k0, unsigned long long k1,
+                                const unsigned long long *ctr, unsigned long long n,
+                                unsigned long long *out, cudaStream_t st) {
+    unsigned long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    debug_philox_kernel<<<(unsigned)blocks, 256, 0, st>>>(k0, k1, ctr, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_sample(const ReplayArgs &a, float *xyEpsi, long long *btk, cudaStream_t st) {
+    unsigned long long blocks = (a.n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    debug_sample_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, xyEpsi, btk);
+    return cudaGetLastError();
+}
+
+}  // namespace fdc

@@ -45,6 +45,7 @@ STEP_CM = 0.1
 
 PHI_CODES = 65536
 PHI_QUANTUM = 2.0 * math.pi / PHI_CODES
+_PHI_TABLE = (np.arange(PHI_CODES, dtype=np.float64) * PHI_QUANTUM).astype(np.float32)
 
 # Synthetic material table: (name, mass stopping-power ratio to water,
 # radiation-length ratio X_water/X_material (mass units)).  These are this
@@ -187,6 +188,8 @@ def water_database(energies, n_tracks, seed, step_cm=STEP_CM, scatter=True,
     if np.any(np.diff(energies) <= 0):
         raise ValueError("energies must be strictly increasing")
     rng = np.random.Generator(np.random.PCG64(seed))
+    if not straggling and not nuclear:
+        return _water_database_csda(energies, n_tracks, rng, step_cm, scatter)
     per_bin = []
     total_steps = 0
     for E0 in energies:
@@ -213,6 +216,64 @@ def water_database(energies, n_tracks, seed, step_cm=STEP_CM, scatter=True,
         t0 += n_tracks
     track_begin = np.arange(len(energies) + 1, dtype=np.int64) * n_tracks
     return Database(energy=energies.astype(np.float32), track_begin=track_begin,
+                    step_begin=step_begin, **arrays)
+
+
+def _csda_steps(E0, step_cm):
+    """Deterministic continuous-slowing-down steps of a proton of energy E0:
+    (energy at step start, length, energy loss) per step."""
+    e_start, lens, des = [], [], []
+    e = float(E0)
+    while True:
+        R = BK_ALPHA * e ** BK_P
+        ln = min(step_cm, R)
+        last = ln >= R
+        e_new = 0.0 if last else ((R - ln) / BK_ALPHA) ** (1.0 / BK_P)
+        e_start.append(e)
+        lens.append(ln)
+        des.append(e - e_new)
+        if last:
+            break
+        e = e_new
+    return np.array(e_start), np.array(lens), np.array(des)
+
+
+def _water_database_csda(energies, n_tracks, rng, step_cm, scatter, chunk=20000):
+    """Fast path without straggling or local deposits: every track of a bin
+    has the same lengths and energy losses; only the deflections differ."""
+    per_bin = [_csda_steps(float(np.float32(E0)), step_cm) for E0 in energies]
+    n_steps = [len(b[0]) for b in per_bin]
+    total = sum(n * n_tracks for n in n_steps)
+    arrays = {k: np.empty(total, dtype=np.float32) for k in ("dE", "len", "theta", "phi", "esec")}
+    arrays["esec"][:] = 0.0
+    step_begin = np.empty(len(energies) * n_tracks + 1, dtype=np.int64)
+    pos = 0
+    t0 = 0
+    for (e_start, lens, des), n in zip(per_bin, n_steps):
+        step_begin[t0:t0 + n_tracks] = pos + n * np.arange(n_tracks, dtype=np.int64)
+        blk = slice(pos, pos + n * n_tracks)
+        arrays["dE"][blk] = np.tile(des.astype(np.float32), n_tracks)
+        arrays["len"][blk] = np.tile(lens.astype(np.float32), n_tracks)
+        th0 = highland_theta0(e_start, lens)
+        for c0 in range(0, n_tracks, chunk):
+            c1 = min(n_tracks, c0 + chunk)
+            sub = slice(pos + c0 * n, pos + c1 * n)
+            if scatter:
+                th0f = th0.astype(np.float32)[None, :]
+                tx = rng.standard_normal((c1 - c0, n), dtype=np.float32) * th0f
+                ty = rng.standard_normal((c1 - c0, n), dtype=np.float32) * th0f
+                th = np.minimum(np.hypot(tx, ty), np.float32(math.pi))
+                arrays["theta"][sub] = th.astype(np.float16).astype(np.float32).reshape(-1)
+                code = np.rint(np.arctan2(ty, tx) * np.float32(1.0 / PHI_QUANTUM)).astype(np.int32) & (PHI_CODES - 1)
+                arrays["phi"][sub] = _PHI_TABLE[code].reshape(-1)
+            else:
+                arrays["theta"][sub] = 0.0
+                arrays["phi"][sub] = 0.0
+        pos += n * n_tracks
+        t0 += n_tracks
+    step_begin[-1] = pos
+    track_begin = np.arange(len(energies) + 1, dtype=np.int64) * n_tracks
+    return Database(energy=np.asarray(energies, np.float64).astype(np.float32), track_begin=track_begin,
                     step_begin=step_begin, **arrays)
 
 

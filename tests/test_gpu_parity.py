@@ -1,0 +1,267 @@
+"""GPU parity tests: the CUDA path through the C ABI against the CPU oracle on
+identical random streams (GB300 only)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import stats
+from paper_1011_2188_gb300 import synth
+import tiny_cases
+from gpu_helpers import assert_conservation, assert_parity, engine, gpu_energy
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    assert torch.cuda.is_available()
+
+
+# ------------------------------------------------------------------ task 1
+
+def test_philox_bitwise_1m_counters():
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    rng = np.random.default_rng(1)
+    n = 1 << 20
+    ctr = rng.integers(0, 2**63, size=(n, 4), dtype=np.int64).view(np.uint64)
+    ctr[:, 1] = rng.integers(0, 4, n).astype(np.uint64)
+    key = (0x0123456789ABCDEF, 7)
+    dev = fdc.philox(torch.from_numpy(ctr.view(np.int64)).cuda(), key)
+    got = dev.cpu().numpy().view(np.uint64)
+    ref = oracle.philox4x64_10(ctr, np.array(key, np.uint64))
+    assert np.array_equal(got, ref)
+
+
+def _beams(db):
+    return {
+        "gauss_spread": synth.make_spots([dict(x=0.3, y=-0.2, energy=140.0, sigma_e=6.0, a=0.4, profile=0,
+                                               layer=0, n_histories=30000)]),
+        "rect": synth.field_beam(30000, energy=150.0, width=10.0, height=6.0, sigma_e_rel=0.01),
+        "disk": synth.disk_beam(30000, energy=121.0, radius=4.0),
+        "spots": synth.spot_plan(seed=3, n_layers=5, spots_per_layer=8, total=30000,
+                                 count_range=(100, 4000)),
+    }
+
+
+@pytest.mark.parametrize("G", [1, 32])
+@pytest.mark.parametrize("rotate", [True, False])
+def test_sampling_matches_oracle(G, rotate):
+    db = synth.water_database(synth.database_energies(24), 40, seed=5)
+    eng = engine(db, synth.slab_phantom(n=8))
+    for name, beam in _beams(db).items():
+        f, i = eng.debug_sample(beam, 99, 17, 20000, track_group=G, rotate=rotate)
+        rf, ri = oracle.sample(db, beam, 99, 17, 20000, track_group=G, rotate=rotate)
+        f = f.cpu().numpy()
+        i = i.cpu().numpy()
+        # discrete choices exact; floats identical up to a rare last-bit
+        # difference of the FP64 transcendentals before rounding to FP32
+        same = np.all(f == rf, axis=1)
+        assert same.mean() >= 0.9999, (name, same.mean())
+        bad = ~same
+        np.testing.assert_allclose(f[bad], rf[bad], rtol=2e-7, atol=1e-6)
+        assert np.mean(np.all(i == ri, axis=1)) >= 0.9999, name
+    eng.close()
+
+
+# ------------------------------------------------------------------ tiny cases
+
+@pytest.mark.parametrize("name", sorted(tiny_cases.CASES))
+@pytest.mark.parametrize("fp64", [False, True])
+def test_tiny_cases(name, fp64):
+    db, ph, beam, opts, exp = tiny_cases.CASES[name]()
+    eng = engine(db, ph)
+    layers = bool(opts.get("per_layer"))
+    kw = {k: v for k, v in opts.items() if k != "per_layer"}
+    r = gpu_energy(eng, ph, beam, 1, layers=layers, rotate=False, fp64_geometry=fp64, **kw)
+    assert_conservation(r)
+    c = r["counters"]
+    scale = 1.0 / float(1 << 28)
+    if layers:
+        ld = r["layer_dose"].reshape(r["layer_dose"].shape[0], -1)
+        # back to energy: dose * mass / (MeV -> J)
+        mass = ph.density.reshape(-1).astype(np.float64) * 1.0 * 1e-3
+        edep = ld * mass[None, :] / 1.602176634e-13
+    else:
+        edep = r["energy"].reshape(-1)
+    tiny_cases.check(edep, c["escaped"] * scale, c["replayed"] * scale, exp, atol=2e-5)
+    eng.close()
+
+
+# ------------------------------------------------------------------ transport parity
+
+def test_parity_slab_pencil():
+    db = synth.water_database([150.0], 2000, seed=1)
+    ph = synth.slab_phantom()
+    beam = synth.pencil_beam(100000, energy=150.0, sigma_cm=0.3)
+    eng = engine(db, ph)
+    r = gpu_energy(eng, ph, beam, 42)
+    ref = oracle.run(db, ph, beam, seed=42)
+    assert_conservation(r)
+    assert_parity(r["energy"], ref.edep, "slab")
+    assert r["counters"]["steps"] == ref.n_steps
+    d = oracle.dose(ph, ref.edep)
+    assert np.abs(r["dose"] - d).max() <= 1e-3 * d.max()
+    # escaped energy agrees with the oracle's bookkeeping
+    esc = r["counters"]["escaped"] / float(1 << 28)
+    assert abs(esc - ref.escaped) <= 1e-6 * ref.replayed
+    eng.close()
+
+
+def test_parity_slab_121mev_disk_grouped():
+    db = synth.water_database([121.0], 500, seed=2, nuclear=True)
+    assert db.esec.max() > 0
+    ph = synth.slab_phantom()
+    beam = synth.disk_beam(60000, energy=121.0, radius=4.0)
+    eng = engine(db, ph)
+    r = gpu_energy(eng, ph, beam, 7, track_group=32)
+    ref = oracle.run(db, ph, beam, seed=7, track_group=32)
+    assert_conservation(r)
+    assert_parity(r["energy"], ref.edep, "slab 121 MeV, G=32")
+    eng.close()
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_parity_thorax(fp64):
+    db = synth.water_database(synth.database_energies(24), 300, seed=2)
+    ph = synth.thorax_phantom(seed=7)
+    beam = synth.field_beam(30000, energy=150.0, width=10.0, height=10.0, sigma_e_rel=0.01)
+    eng = engine(db, ph)
+    r = gpu_energy(eng, ph, beam, 11, fp64_geometry=fp64)
+    ref = oracle.run(db, ph, beam, seed=11)
+    assert_conservation(r)
+    assert_parity(r["energy"], ref.edep, "thorax")
+    eng.close()
+
+
+def test_parity_thorax_start_voxel_scaling():
+    db = synth.water_database(synth.database_energies(6, 120, 180), 200, seed=2)
+    ph = synth.thorax_phantom(seed=7, shape=(96, 96, 64))
+    beam = synth.field_beam(20000, energy=150.0, width=8.0, height=8.0, sigma_e_rel=0.01)
+    eng = engine(db, ph)
+    r = gpu_energy(eng, ph, beam, 3, scaling_mode=1)
+    ref = oracle.run(db, ph, beam, seed=3, scaling_mode=1)
+    assert_conservation(r)
+    assert_parity(r["energy"], ref.edep, "start-voxel scaling")
+    eng.close()
+
+
+def test_parity_spots_per_layer():
+    db = synth.water_database(synth.database_energies(24), 100, seed=2)
+    ph = synth.slab_phantom()
+    beam = synth.spot_plan(seed=5, n_layers=6, spots_per_layer=12, total=40000, count_range=(50, 3000))
+    eng = engine(db, ph)
+    r = gpu_energy(eng, ph, beam, 5, layers=True)
+    ref = oracle.run(db, ph, beam, seed=5, per_layer=True)
+    assert_conservation(r)
+    # layer doses from the oracle's per-layer energies
+    for l in range(ref.edep.shape[0]):
+        d_ref = oracle.dose(ph, ref.edep[l])
+        d = r["layer_dose"][l]
+        assert np.abs(d - d_ref).max() <= 1e-3 * d_ref.max(), l
+    assert_parity(r["energy"], ref.edep.sum(axis=0), "spots total")
+    np.testing.assert_allclose(r["layer_dose"].sum(axis=0), r["dose"], rtol=1e-12, atol=1e-30)
+    eng.close()
+
+
+# ------------------------------------------------------------------ determinism, sharding
+
+def test_schedule_independent_bitwise():
+    db = synth.water_database([150.0], 300, seed=1)
+    ph = synth.slab_phantom()
+    beam = synth.pencil_beam(50000, energy=150.0, sigma_cm=0.3)
+    eng = engine(db, ph)
+    base = gpu_energy(eng, ph, beam, 9)["tally"]
+    for sched in [(1, 4, 1, 1), (2, 8, 4, 2), (0, 16, 2, 1), (0, 8, 1, 2), (1, 32, 16, 1)]:
+        t = gpu_energy(eng, ph, beam, 9, schedule=sched)["tally"]
+        assert np.array_equal(t, base), sched
+    eng.close()
+
+
+def test_sharded_runs_add_up_bitwise():
+    db = synth.water_database(synth.database_energies(24), 100, seed=2)
+    ph = synth.thorax_phantom(seed=7, shape=(96, 96, 64))
+    beam = synth.field_beam(60000, energy=150.0, width=8.0, height=8.0)
+    eng = engine(db, ph)
+    full = gpu_energy(eng, ph, beam, 4)
+    parts = [gpu_energy(eng, ph, beam, 4, n=hi - lo, history_offset=lo)
+             for lo, hi in [(0, 12345), (12345, 40000), (40000, 60000)]]
+    assert np.array_equal(sum(p["tally"] for p in parts), full["tally"])
+    assert sum(p["counters"]["escaped"] for p in parts) == full["counters"]["escaped"]
+    eng.close()
+
+
+# ------------------------------------------------------------------ batches and eq. (1)
+
+def test_batches_match_separate_runs_and_eq1():
+    import torch
+    db = synth.water_database([121.0], 300, seed=4)
+    ph = synth.slab_phantom(n=32, voxel_cm=0.4)
+    n_b, per = 8, 4000
+    beam = synth.disk_beam(n_b * per, energy=121.0, radius=1.5)
+    eng = engine(db, ph)
+    shape = ph.shape[::-1]
+    s = torch.zeros(shape, dtype=torch.float64, device="cuda:0")
+    s2 = torch.zeros_like(s)
+    dose = torch.zeros_like(s)
+    eng.run_ex(beam, 0, 100, n_batches=n_b, batch_sum=s, batch_sumsq=s2, dose=dose)
+    eng.sync()
+    # each batch equals a separate run over its history range
+    sep = []
+    for b in range(n_b):
+        sep.append(gpu_energy(eng, ph, beam, 100, n=per, history_offset=b * per)["dose"])
+    sep = np.array(sep)
+    np.testing.assert_allclose(s.cpu().numpy(), sep.sum(0), rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(s2.cpu().numpy(), (sep ** 2).sum(0), rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(dose.cpu().numpy(), sep.sum(0), rtol=1e-12, atol=1e-300)
+    # eq. (1) on the device vs the FP64 statistics of the oracle package
+    mean, sigma, rel = eng.batch_stats(s, s2, n_b)
+    m_ref, sg_ref = stats.batch_sigma(sep)
+    np.testing.assert_allclose(mean.cpu().numpy(), m_ref, rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(sigma.cpu().numpy(), sg_ref, rtol=1e-6, atol=1e-12 * sg_ref.max())
+    assert rel == pytest.approx(stats.mean_relative_uncertainty(m_ref, sg_ref), rel=1e-6)
+    # and the oracle agrees on the batch doses
+    for b in (0, 5):
+        ref = oracle.run(db, ph, beam, seed=100, h_begin=b * per, h_end=(b + 1) * per)
+        d_ref = oracle.dose(ph, ref.edep)
+        assert np.abs(sep[b] - d_ref).max() <= 1e-3 * d_ref.max()
+    eng.close()
+
+
+# ------------------------------------------------------------------ errors
+
+def test_argument_errors():
+    from paper_1011_2188_gb300 import fdc
+    db = synth.water_database([100.0], 4, seed=1)
+    ph = synth.slab_phantom(n=8)
+    e = fdc.Engine(0)
+    beam = synth.pencil_beam(10, energy=100.0)
+    with pytest.raises(fdc.FdcError) as ex:
+        e.run(beam, 0, 1)
+    assert ex.value.code == 2  # not loaded
+    bad = synth.water_database([100.0], 4, seed=1)
+    bad.len[3] = -1.0
+    with pytest.raises(fdc.FdcError) as ex:
+        e.load_database(bad)
+    assert ex.value.code == 1
+    huge = synth.database_from_tracks([100.0], [[[(5.0e6, 0.1, 0.0, 0.0, 0.0)]]])
+    with pytest.raises(fdc.FdcError) as ex:
+        e.load_database(huge)
+    assert ex.value.code == 6  # fixed-point headroom
+    e.load_database(db)
+    e.load_phantom(ph)
+    with pytest.raises(fdc.FdcError) as ex:
+        e.run(beam, 11, 1)  # more histories than the beam holds
+    assert ex.value.code == 1
+    badbeam = beam.copy()
+    badbeam["profile"] = 7
+    with pytest.raises(fdc.FdcError):
+        e.run(badbeam, 0, 1)
+    e.run(beam, 0, 1)
+    assert e.sync()["histories"] == 10
+    e.close()
