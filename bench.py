@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--tracks", type=int, default=100_000, help="database tracks per energy")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--schedule", default="", help="ctas_per_sm,warps_per_cta,chunk,aggregate")
+    ap.add_argument("--quick", action="store_true", help="device timing only (sweeps)")
     return ap.parse_args()
 
 
@@ -153,6 +155,41 @@ def cpu_baseline(db, ph, beam, seed, target_s=12.0):
             "track_steps_per_s": r.n_steps / dt, "seconds": dt}
 
 
+def time_to_sigma(eng, beam, ph, seed, target=0.02, n_batches=10, n0=200_000, local=0):
+    """Plain method: device time to reach a mean relative batch uncertainty
+    (eq. (1), n_batches batches) of ``target`` over voxels above half the
+    maximum dose (Sec. 2.4) and, separately, above 0.9 of it (the Bragg-peak
+    region).  The history count is predicted from a pilot run (sigma ~ N^-1/2)
+    and then run and timed."""
+    import torch
+    shape = ph.shape[::-1]
+    s1 = torch.zeros(shape, dtype=torch.float64, device=f"cuda:{local}")
+    s2 = torch.zeros_like(s1)
+    total = int(beam["n_histories"].sum())
+
+    def measure(n):
+        n = min(total, max(n_batches, (n // n_batches) * n_batches))
+        eng.run_ex(beam, n, seed, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2)  # warm / capture
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        eng.run_ex(beam, n, seed, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2)
+        e1.record()
+        e1.synchronize()
+        _, _, rel = eng.batch_stats(s1, s2, n_batches, 0.5)
+        _, _, rel9 = eng.batch_stats(s1, s2, n_batches, 0.9)
+        return n, e0.elapsed_time(e1) * 1e-3, rel, rel9
+
+    n, _, rel, rel9 = measure(n0)
+    out = {}
+    for key, r in (("half_max", rel), ("bragg_peak_0.9max", rel9)):
+        want = int(n * (r / target) ** 2 * 1.05) + n_batches
+        m, sec, rel_m, rel9_m = measure(want)
+        got = rel_m if key == "half_max" else rel9_m
+        out[key] = {"histories": m, "seconds": sec, "mean_rel_sigma": got, "target": target,
+                    "n_batches": n_batches, "reached": bool(got <= target)}
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -219,17 +256,26 @@ def main():
     eng.load_phantom(ph)
     t_load = time.perf_counter() - t_load
     seed = 1234
-    offset = rank * n
+    from paper_1011_2188_gb300.shard import weak_shard
+    offset, _ = weak_shard(n, rank)
     sched = None
+    if args.schedule:
+        sched = tuple(int(x) for x in args.schedule.split(","))
     if args.autotune:
         sched = eng.autotune(beam, min(n, 1_000_000), seed)
     dose = torch.empty(ph.shape[::-1], dtype=torch.float64, device=f"cuda:{local}")
+    layer_dose = None
+    if args.workload == "spots":  # total dose plus the dose of every energy layer
+        n_layers = int(beam["layer"].max()) + 1
+        layer_dose = torch.empty((n_layers,) + tuple(ph.shape[::-1]), dtype=torch.float64,
+                                 device=f"cuda:{local}")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
     eng.set_timing(True)
 
     def one_step():
-        eng.run_ex(beam, n, seed, history_offset=offset, dose=dose, stream=stream)
+        eng.run_ex(beam, n, seed, history_offset=offset, dose=dose, layer_dose=layer_dose, stream=stream,
+                   schedule=sched)
 
     for _ in range(max(args.warmup, 0)):
         one_step()
@@ -268,6 +314,12 @@ def main():
         ms = float(t[0])
     value = n * world / (ms * 1e-3)
     rep_ms = statistics.median(replay_ms)
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"value": value, "ms_per_step": ms, "replay_ms": rep_ms, "schedule": sched,
+                              "track_steps_per_s": steps_per_run * world / (ms * 1e-3), "clocks": clk,
+                              "flags": os.environ.get("FDC_NVCC_FLAGS", "")}), flush=True)
+        return
 
     # ---- end to end through the C ABI with host buffers (beam in, dose out)
     host_dose = torch.empty(ph.shape[::-1], dtype=torch.float64).pin_memory().numpy()
@@ -318,6 +370,8 @@ def main():
         "clocks": clk,
         "load_s": t_load,
     }
+    if rank == 0:
+        line["time_to_2pct_sigma_plain"] = time_to_sigma(eng, beam, ph, seed + 99, local=local)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(db, ph, beam, seed)
     if rank == 0:

@@ -125,9 +125,11 @@ typedef struct fdc_beam {
  * tuned (or built-in) value. */
 typedef struct fdc_schedule {
     int32_t ctas_per_sm;     /* persistent CTAs per SM */
-    int32_t warps_per_cta;
+    int32_t warps_per_cta;   /* 1..8 */
     int32_t chunk;           /* 32-history groups a warp claims per atomic */
-    int32_t aggregate;       /* 1: warp-aggregate tally atomics, 2: plain atomics */
+    int32_t aggregate;       /* 1: combine the tally atomics of warp lanes that hit the same
+                                voxel; 2: one atomic per lane (default).  Either way a lane
+                                sums its consecutive deposits into one voxel first. */
 } fdc_schedule;
 
 /* Options of fdc_run_ex.  Zero-initialise for the defaults. */
@@ -142,7 +144,9 @@ typedef struct fdc_run_opts {
     int32_t n_batches;       /* >= 2: split the histories into equal batches and
                                 accumulate the per-voxel batch dose sum and sum of
                                 squares (eq. (1)); 0 or 1: one batch */
-    int32_t pad;
+    int32_t no_graph;        /* 1: issue the launches directly; 0: run them as a CUDA
+                                graph, captured once and relaunched while the launch
+                                configuration repeats */
     fdc_schedule schedule;
 } fdc_run_opts;
 

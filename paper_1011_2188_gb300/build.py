@@ -30,8 +30,9 @@ def nvcc():
 
 
 def flags(extra=()):
+    env = os.environ.get("FDC_NVCC_FLAGS", "").split()
     return ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xcompiler",
-            "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC, *extra]
+            "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC, *env, *extra]
 
 
 def _stale():
@@ -39,6 +40,10 @@ def _stale():
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, s) for s in SOURCES] + HEADERS + [os.path.abspath(__file__)]
+    stamp = LIB + ".flags"
+    flags_now = os.environ.get("FDC_NVCC_FLAGS", "")
+    if (open(stamp).read() if os.path.exists(stamp) else "") != flags_now:
+        return True
     return any(os.path.getmtime(d) > t for d in deps)
 
 
@@ -67,6 +72,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(LIB + ".flags", "w") as f:
+        f.write(os.environ.get("FDC_NVCC_FLAGS", ""))
     return LIB
 
 

@@ -47,6 +47,16 @@ struct DevBuf {
 
 }  // namespace
 
+namespace {
+// Everything a captured run depends on; compared bytewise (zero-filled first).
+struct GraphKey {
+    fdc::ReplayArgs a;
+    fdc_schedule sched;
+    fdc_outputs out;
+    int n_batches, n_tallies, fp64, timing;
+};
+}  // namespace
+
 struct fdc_ctx {
     int device = 0;
     int sm_count = 0;
@@ -86,6 +96,10 @@ struct fdc_ctx {
     bool timing = false;
     bool timed = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // captured run sequence
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    GraphKey graph_key;
     // schedule
     fdc_schedule tuned = {0, 0, 0, 0};
     int last_fp64 = 0;
@@ -133,8 +147,11 @@ int resolve_schedule(fdc_ctx *c, const fdc_schedule *req, int fp64, fdc_schedule
     if (req) s = *req;
     if (!s.warps_per_cta) s.warps_per_cta = c->tuned.warps_per_cta ? c->tuned.warps_per_cta : 8;
     if (!s.chunk) s.chunk = c->tuned.chunk ? c->tuned.chunk : 1;
-    if (!s.aggregate) s.aggregate = c->tuned.aggregate ? c->tuned.aggregate : 1;
-    if (s.warps_per_cta < 1 || s.warps_per_cta > 32 || s.chunk < 1 || s.chunk > 1024 || s.aggregate < 1 ||
+    // plain atomics by default: on GB300 the L2 absorbs the tally updates
+    // faster than a match/redux combine across the warp
+    if (!s.aggregate) s.aggregate = c->tuned.aggregate ? c->tuned.aggregate : 2;
+    // the replay kernel is compiled for at most 256 threads per CTA
+    if (s.warps_per_cta < 1 || s.warps_per_cta > 8 || s.chunk < 1 || s.chunk > 1024 || s.aggregate < 1 ||
         s.aggregate > 2 || s.ctas_per_sm < 0)
         return fail(c, FDC_ERR_INVALID, "invalid schedule");
     const int maxc = fdc::replay_max_ctas_per_sm(s.warps_per_cta, fp64, s.aggregate);
@@ -278,6 +295,8 @@ void fdc_destroy(fdc_ctx *c) {
     if (c->beam_copied) cudaEventDestroy(c->beam_copied);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
@@ -475,13 +494,6 @@ int run_impl(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t se
     if (n_batches > 1) FDC_CUDA(c, c->accum.ensure(tsize));
     rc = upload_beam(c, beam, st, force_upload);
     if (rc) return rc;
-    FDC_CUDA(c, cudaMemsetAsync(c->counters.p, 0, sizeof(DeviceCounters), st));
-    FDC_CUDA(c, cudaMemsetAsync(c->tally.p, 0, sizeof(long long) * tsize, st));
-    if (n_batches > 1) {
-        FDC_CUDA(c, cudaMemsetAsync(c->accum.p, 0, sizeof(long long) * tsize, st));
-        if (out.batch_sum) FDC_CUDA(c, cudaMemsetAsync(out.batch_sum, 0, sizeof(double) * c->nvox, st));
-        if (out.batch_sumsq) FDC_CUDA(c, cudaMemsetAsync(out.batch_sumsq, 0, sizeof(double) * c->nvox, st));
-    }
     fdc::ReplayArgs a = base_args(c);
     a.tally = (unsigned long long *)c->tally.p;
     a.per_layer = n_tallies > 1 ? 1 : 0;
@@ -491,50 +503,116 @@ int run_impl(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t se
     a.rotate = opts.no_rotation ? 0 : 1;
     a.scaling_mode = opts.scaling_mode;
     a.chunk = sched.chunk;
+    a.h_begin = opts.history_offset;
+    a.n = n;
     const double scale = fdc::kMeVToJ / (fdc::kTallyUnitsPerMeV * c->dx * c->dy * c->dz * 1e-3);
-    c->timed = false;
-    if (c->timing) FDC_CUDA(c, cudaEventRecord(c->ev[0], st));
-    for (int b = 0; b < n_batches; ++b) {
-        const unsigned long long lo = n * (unsigned long long)b / n_batches;
-        const unsigned long long hi = n * (unsigned long long)(b + 1) / n_batches;
-        a.h_begin = opts.history_offset + lo;
-        a.n = hi - lo;
-        FDC_CUDA(c, cudaMemsetAsync(c->work.p, 0, sizeof(unsigned long long), st));
-        if (a.n) FDC_CUDA(c, fdc::launch_replay(a, sched, opts.fp64_geometry, c->sm_count, st));
+
+    // The whole run as one sequence of stream operations: zero the counters
+    // and tallies, per batch one replay launch (plus the fold of the batch
+    // into the FP64 sums), then the dose.
+    auto issue = [&](cudaStream_t s) -> int {
+        FDC_CUDA(c, cudaMemsetAsync(c->counters.p, 0, sizeof(DeviceCounters), s));
+        FDC_CUDA(c, cudaMemsetAsync(c->tally.p, 0, sizeof(long long) * tsize, s));
         if (n_batches > 1) {
+            FDC_CUDA(c, cudaMemsetAsync(c->accum.p, 0, sizeof(long long) * tsize, s));
+            if (out.batch_sum) FDC_CUDA(c, cudaMemsetAsync(out.batch_sum, 0, sizeof(double) * c->nvox, s));
+            if (out.batch_sumsq) FDC_CUDA(c, cudaMemsetAsync(out.batch_sumsq, 0, sizeof(double) * c->nvox, s));
+        }
+        if (c->timing) FDC_CUDA(c, cudaEventRecord(c->ev[0], s));
+        fdc::ReplayArgs ab = a;
+        for (int b = 0; b < n_batches; ++b) {
+            const unsigned long long lo = n * (unsigned long long)b / n_batches;
+            const unsigned long long hi = n * (unsigned long long)(b + 1) / n_batches;
+            ab.h_begin = opts.history_offset + lo;
+            ab.n = hi - lo;
+            FDC_CUDA(c, cudaMemsetAsync(c->work.p, 0, sizeof(unsigned long long), s));
+            if (ab.n) FDC_CUDA(c, fdc::launch_replay(ab, sched, opts.fp64_geometry, c->sm_count, s));
+            if (n_batches > 1) {
+                fdc::FinalizeArgs f;
+                std::memset(&f, 0, sizeof f);
+                f.tally = c->tally.p;
+                f.n_tallies = n_tallies;
+                f.nvox = c->nvox;
+                f.density = c->density.p;
+                f.scale = scale;
+                f.batch_sum = out.batch_sum;
+                f.batch_sumsq = out.batch_sumsq;
+                f.accum = c->accum.p;
+                f.zero_after = 1;
+                FDC_CUDA(c, fdc::launch_finalize(f, c->sm_count, s));
+            }
+        }
+        if (c->timing) FDC_CUDA(c, cudaEventRecord(c->ev[1], s));
+        if (c->timing) FDC_CUDA(c, cudaEventRecord(c->ev[2], s));
+        if (out.dose || out.layer_dose || out.tally) {
             fdc::FinalizeArgs f;
             std::memset(&f, 0, sizeof f);
-            f.tally = c->tally.p;
+            f.tally = n_batches > 1 ? c->accum.p : c->tally.p;
             f.n_tallies = n_tallies;
             f.nvox = c->nvox;
             f.density = c->density.p;
             f.scale = scale;
-            f.batch_sum = out.batch_sum;
-            f.batch_sumsq = out.batch_sumsq;
-            f.accum = c->accum.p;
-            f.zero_after = 1;
-            FDC_CUDA(c, fdc::launch_finalize(f, c->sm_count, st));
+            f.dose = out.dose;
+            f.layer_dose = out.layer_dose;
+            f.tally_out = (long long *)out.tally;
+            FDC_CUDA(c, fdc::launch_finalize(f, c->sm_count, s));
         }
+        if (c->timing) FDC_CUDA(c, cudaEventRecord(c->ev[3], s));
+        return FDC_OK;
+    };
+
+    c->timed = false;
+    if (opts.no_graph) {
+        rc = issue(st);
+        if (rc) return rc;
+    } else {
+        // CUDA graph of the sequence, captured on the context's own stream and
+        // relaunched on the caller's stream while the launch configuration
+        // (every kernel argument, buffer and schedule) stays the same.
+        GraphKey key;
+        std::memset(&key, 0, sizeof key);
+        key.a = a;
+        key.sched = sched;
+        key.out = out;
+        key.n_batches = n_batches;
+        key.n_tallies = n_tallies;
+        key.fp64 = opts.fp64_geometry;
+        key.timing = c->timing ? 1 : 0;
+        if (!c->graph_exec || std::memcmp(&key, &c->graph_key, sizeof key) != 0) {
+            if (!c->cap_stream) FDC_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+            FDC_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            rc = issue(c->cap_stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (ec != cudaSuccess) return cuda_fail(c, ec, "cudaStreamEndCapture");
+            bool updated = false;
+            if (c->graph_exec) {
+                cudaGraphExecUpdateResultInfo info;
+                updated = cudaGraphExecUpdate(c->graph_exec, g, &info) == cudaSuccess;
+                if (!updated) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(c->graph_exec);
+                    c->graph_exec = nullptr;
+                }
+            }
+            if (!updated) {
+                cudaError_t ei = cudaGraphInstantiate(&c->graph_exec, g, 0);
+                if (ei != cudaSuccess) {
+                    cudaGraphDestroy(g);
+                    c->graph_exec = nullptr;
+                    return cuda_fail(c, ei, "cudaGraphInstantiate");
+                }
+            }
+            cudaGraphDestroy(g);
+            c->graph_key = key;
+        }
+        FDC_CUDA(c, cudaGraphLaunch(c->graph_exec, st));
     }
-    if (c->timing) FDC_CUDA(c, cudaEventRecord(c->ev[1], st));
-    if (c->timing) FDC_CUDA(c, cudaEventRecord(c->ev[2], st));
-    if (out.dose || out.layer_dose || out.tally) {
-        fdc::FinalizeArgs f;
-        std::memset(&f, 0, sizeof f);
-        f.tally = n_batches > 1 ? c->accum.p : c->tally.p;
-        f.n_tallies = n_tallies;
-        f.nvox = c->nvox;
-        f.density = c->density.p;
-        f.scale = scale;
-        f.dose = out.dose;
-        f.layer_dose = out.layer_dose;
-        f.tally_out = (long long *)out.tally;
-        FDC_CUDA(c, fdc::launch_finalize(f, c->sm_count, st));
-    }
-    if (c->timing) {
-        FDC_CUDA(c, cudaEventRecord(c->ev[3], st));
-        c->timed = true;
-    }
+    if (c->timing) c->timed = true;
     c->last_fp64 = opts.fp64_geometry;
     return FDC_OK;
 }
@@ -614,7 +692,7 @@ int fdc_autotune(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int warps_opts[] = {4, 8, 16};
+    const int warps_opts[] = {2, 4, 8};
     const int chunk_opts[] = {1, 4};
     const int agg_opts[] = {1, 2};
     fdc_schedule best_s = {0, 0, 0, 0};

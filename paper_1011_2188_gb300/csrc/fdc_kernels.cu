@@ -27,6 +27,11 @@ namespace fdc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// 1: a lane sums consecutive deposits into one voxel before its atomic.
+#ifndef FDC_LANE_COALESCE
+#define FDC_LANE_COALESCE 1
+#endif
 constexpr float kUnitsF = 268435456.0f;  // 2^28
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr float kPhiQuantumF = 9.58737992428525e-05f;  // 2 pi / 65536
@@ -160,21 +165,23 @@ template <typename R> __device__ __forceinline__ R inf_();
 template <> __device__ __forceinline__ float inf_<float>() { return __int_as_float(0x7f800000); }
 template <> __device__ __forceinline__ double inf_<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
 
-// Tally update.  AGG: lanes of the warp that add to the same voxel are
-// combined first (match on the index, add the four 16-bit limbs of the
-// two's-complement value with redux.sync inside each group, one atomic per
-// group); otherwise one atomic per lane.
+// Tally update.  AGG: lanes of the warp that add to the same tally word are
+// combined first (match on the word's address -- not on the voxel index, since
+// lanes may score into different layer tallies -- then add the four 16-bit
+// limbs of the two's-complement value with redux.sync inside each group, one
+// atomic per group); otherwise one atomic per lane.
 template <bool AGG>
 __device__ __forceinline__ void tally_add(unsigned long long *tally, long long idx, long long units) {
+    unsigned long long *const addr = tally + idx;
     if (!AGG) {
-        atomicAdd(tally + idx, (unsigned long long)units);
+        atomicAdd(addr, (unsigned long long)units);
         return;
     }
     const unsigned lane = threadIdx.x & 31u;
     const unsigned mask = __activemask();
-    const unsigned peers = __match_any_sync(mask, (unsigned long long)idx);
+    const unsigned peers = __match_any_sync(mask, (unsigned long long)addr);
     if (peers == (1u << lane)) {
-        atomicAdd(tally + idx, (unsigned long long)units);
+        atomicAdd(addr, (unsigned long long)units);
         return;
     }
     const unsigned long long u = (unsigned long long)units;
@@ -185,9 +192,38 @@ __device__ __forceinline__ void tally_add(unsigned long long *tally, long long i
     if (lane == (unsigned)(__ffs(peers) - 1)) {
         const unsigned long long s = (unsigned long long)l0 + ((unsigned long long)l1 << 16) +
                                      ((unsigned long long)l2 << 32) + ((unsigned long long)l3 << 48);
-        atomicAdd(tally + idx, s);
+        atomicAdd(addr, s);
     }
 }
+
+// Lane-local coalescing of tally updates: consecutive deposits of one lane
+// into the same tally word are summed in registers and written with one
+// atomic when the lane moves to another word (or finishes the history).
+// Integer sums, so the tally is the same bit for bit.
+template <bool AGG>
+struct PendingTally {
+    unsigned long long *addr = nullptr;
+    long long units = 0;
+    __device__ __forceinline__ void add(unsigned long long *tally, long long idx, long long u) {
+        unsigned long long *const a = tally + idx;
+        if (!FDC_LANE_COALESCE) {
+            if (u) tally_add<AGG>(a, 0, u);
+            return;
+        }
+        if (a == addr) {
+            units += u;
+            return;
+        }
+        flush();
+        addr = a;
+        units = u;
+    }
+    __device__ __forceinline__ void flush() {
+        if (addr && units) tally_add<AGG>(addr, 0, units);
+        addr = nullptr;
+        units = 0;
+    }
+};
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
@@ -200,9 +236,45 @@ __device__ void raise_status(DeviceCounters *c, int code, unsigned long long h) 
 }
 
 // ---------------------------------------------------------------- task 2
-// Re-trace one history.  Geometry in grid units: u = (position - origin) /
-// spacing per axis, so voxel faces sit at integers; distances along the ray
-// are in cm.  Returns nothing; per-lane counters are updated in place.
+// Energy (MeV) to tally units.  Shares below 2^31 units (8 MeV) take the
+// 32-bit conversion; larger ones the 64-bit one.  Both round to nearest even,
+// so the result equals the 64-bit conversion of the same value.
+__device__ __forceinline__ long long units_of(float scaled) {
+    return fabsf(scaled) < 2147483520.0f ? (long long)__float2int_rn(scaled) : __float2ll_rn(scaled);
+}
+__device__ __forceinline__ long long units_of(double scaled) { return __double2ll_rn(scaled); }
+__device__ __forceinline__ float unit_scale(float) { return kUnitsF; }
+__device__ __forceinline__ double unit_scale(double) { return 268435456.0; }
+
+// sin and cos of a polar deflection.  Below 0.25 rad (almost every step) the
+// Taylor series to theta^9 / theta^10 (truncation < 1e-11); above, sincos.
+template <typename R>
+__device__ __forceinline__ void sincos_theta(R th, R *s, R *c) {
+    if (th < (R)0.25) {
+        const R t2 = th * th;
+        *s = th * ((R)1 - t2 * ((R)(1.0 / 6) - t2 * ((R)(1.0 / 120) - t2 * ((R)(1.0 / 5040) - t2 * (R)(1.0 / 362880)))));
+        *c = (R)1 - t2 * ((R)0.5 - t2 * ((R)(1.0 / 24) - t2 * ((R)(1.0 / 720) - t2 * (R)(1.0 / 40320))));
+    } else {
+        sincos_(th, s, c);
+    }
+}
+
+// sin and cos of an azimuth given as a 16-bit code of 2 pi / 65536: the code
+// is read as a signed value so the angle lies in [-pi, pi), where the
+// hardware approximation has an absolute error below 1e-6 (FP32 path).
+__device__ __forceinline__ void sincos_phi(unsigned code, float *s, float *c) {
+    const float a = (float)(short)(unsigned short)code * kPhiQuantumF;
+    __sincosf(a, s, c);
+}
+__device__ __forceinline__ void sincos_phi(unsigned code, double *s, double *c) {
+    sincos((double)(short)(unsigned short)code * kPhiQuantumD, s, c);
+}
+
+// Re-trace one history.  Positions are kept as the voxel index plus the
+// fractional position inside the voxel, f in [0, 1] per axis (grid units:
+// faces at integers), which keeps FP32 rounding relative to the voxel rather
+// than to the whole grid; distances along the ray are in cm.  Per-lane
+// counters are updated in place.
 template <typename R, bool AGG>
 __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start &st,
                                                unsigned long long h, unsigned long long &steps,
@@ -210,12 +282,10 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
                                                long long &escaped) {
     if (st.k0 >= st.n) return;
     const long long s_first = st.s0 + st.k0, s_end = st.s0 + st.n;
+    uint4 rec = __ldg(P.rec + s_first);
     // energy of the replayed steps, in tally units
-    long long rep;
-    {
-        const uint4 r0 = __ldg(P.rec + s_first);
-        rep = to_units(__uint_as_float(r0.y)) + to_units(__uint_as_float(r0.z)) + __ldg(P.tail + s_first);
-    }
+    const long long rep = units_of(__uint_as_float(rec.y) * kUnitsF) +
+                          units_of(__uint_as_float(rec.z) * kUnitsF) + __ldg(P.tail + s_first);
     replayed += rep;
     // entry on the upstream face; inside test and voxel in FP64 (the
     // per-proton state is FP32, the comparison is exact in FP64)
@@ -226,7 +296,7 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
     }
     const double gx = (xe - P.x0) / P.dx, gy = (ye - P.y0) / P.dy;
     int ix = min((int)floor(gx), P.nx - 1), iy = min((int)floor(gy), P.ny - 1), iz = 0;
-    R ux = (R)gx, uy = (R)gy, uz = (R)0;
+    R fx = (R)(gx - ix), fy = (R)(gy - iy), fz = (R)0;
     R dx = (R)0, dy = (R)0, dz = (R)1;
     const R ihx = (R)(1.0 / P.dx), ihy = (R)(1.0 / P.dy), ihz = (R)(1.0 / P.dz);
     const long long sy = P.nx, sz = (long long)P.nx * P.ny;
@@ -236,47 +306,45 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
     const R psi = (R)st.psi;
     const int seg_cap = P.nx + P.ny + P.nz + 8;
     const R INF = inf_<R>();
+    const R US = unit_scale((R)0);
+    // material of the current voxel, carried from one step to the next
+    float2 sk = __ldg(P.vox + v);
+    PendingTally<AGG> pend;
 
-    for (long long s = s_first; s < s_end; ++s) {
-        const uint4 rec = __ldg(P.rec + s);
+    for (long long s = s_first;;) {
         const float dE_f = __uint_as_float(rec.y);
         const R len = (R)__uint_as_float(rec.x), dE = (R)dE_f;
-        const long long Qk = to_units(dE_f);
-        const long long Qs = to_units(__uint_as_float(rec.z));
+        const long long Qk = units_of(dE_f * kUnitsF);
+        const long long Qs = units_of(__uint_as_float(rec.z) * kUnitsF);
         const R inv_len = (R)1 / len;
+        const R dEu = dE * inv_len * US;  // tally units per cm of water-equivalent length
         ++steps;
 
-        // ray in grid units per cm, distances to the next faces (cm)
+        // ray in grid units per cm; distances to the next faces (cm)
         const R rx = dx * ihx, ry = dy * ihy, rz = dz * ihz;
-        R tmx, tmy, tmz, tdx, tdy, tdz;
-        int stx, sty, stz;
-        if (rx > (R)0) { tmx = ((R)(ix + 1) - ux) / rx; tdx = (R)1 / rx; stx = 1; }
-        else if (rx < (R)0) { tmx = ((R)ix - ux) / rx; tdx = (R)-1 / rx; stx = -1; }
-        else { tmx = INF; tdx = INF; stx = 0; }
-        if (ry > (R)0) { tmy = ((R)(iy + 1) - uy) / ry; tdy = (R)1 / ry; sty = 1; }
-        else if (ry < (R)0) { tmy = ((R)iy - uy) / ry; tdy = (R)-1 / ry; sty = -1; }
-        else { tmy = INF; tdy = INF; sty = 0; }
-        if (rz > (R)0) { tmz = ((R)(iz + 1) - uz) / rz; tdz = (R)1 / rz; stz = 1; }
-        else if (rz < (R)0) { tmz = ((R)iz - uz) / rz; tdz = (R)-1 / rz; stz = -1; }
-        else { tmz = INF; tdz = INF; stz = 0; }
+        const R irx = rx != (R)0 ? (R)1 / rx : INF;
+        const R iry = ry != (R)0 ? (R)1 / ry : INF;
+        const R irz = rz != (R)0 ? (R)1 / rz : INF;
+        const int stx = rx > (R)0 ? 1 : (rx < (R)0 ? -1 : 0);
+        const int sty = ry > (R)0 ? 1 : (ry < (R)0 ? -1 : 0);
+        const int stz = rz > (R)0 ? 1 : (rz < (R)0 ? -1 : 0);
+        R tmx = stx ? ((R)(stx > 0) - fx) * irx : INF;
+        R tmy = sty ? ((R)(sty > 0) - fy) * iry : INF;
+        R tmz = stz ? ((R)(stz > 0) - fz) * irz : INF;
+        const int ix0 = ix, iy0 = iy, iz0 = iz;
+        const R tdx = fabs(irx), tdy = fabs(iry), tdz = fabs(irz);
         tmx = tmx > (R)0 ? tmx : (R)0;
         tmy = tmy > (R)0 ? tmy : (R)0;
         tmz = tmz > (R)0 ? tmz : (R)0;
 
         R rem = len, t = (R)0, acc = (R)0;
         long long dep = 0;
-        R S_fix = (R)0, k2_fix = (R)0;
-        if (P.scaling_mode == 1) {
-            const float2 sk = __ldg(P.vox + v);
-            S_fix = (R)sk.x;
-            k2_fix = (R)sk.y;
-        }
+        const bool fixed = P.scaling_mode == 1;
+        const R S_fix = (R)sk.x, k2_fix = (R)sk.y;
         int nseg = 0;
         bool gone = false;
         for (;;) {
-            R S, k2;
-            if (P.scaling_mode == 1) { S = S_fix; k2 = k2_fix; }
-            else { const float2 sk = __ldg(P.vox + v); S = (R)sk.x; k2 = (R)sk.y; }
+            const R S = fixed ? S_fix : (R)sk.x, k2 = fixed ? k2_fix : (R)sk.y;
             // nearest face; ties go to x, then y, then z
             int a = 0;
             R tm = tmx;
@@ -288,14 +356,14 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
             ++segs;
             if (wexit >= rem) {  // the step ends in this voxel
                 const long long units = Qk - dep;
-                if (units) tally_add<AGG>(tally, v, units);
+                pend.add(tally, v, units);
                 acc += rem * k2;
                 t += rem / S;
                 break;
             }
-            const long long units = to_units(dE * (wexit * inv_len));
+            const long long units = units_of(wexit * dEu);
             dep += units;
-            if (units) tally_add<AGG>(tally, v, units);
+            pend.add(tally, v, units);
             acc += wexit * k2;
             rem -= wexit;
             t = tm;
@@ -313,34 +381,46 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
                 gone = true;
                 break;
             }
+            sk = __ldg(P.vox + v);
         }
-        if (gone) return;
-        ux += t * rx;
-        uy += t * ry;
-        uz += t * rz;
-        if (Qs) tally_add<AGG>(tally, v, Qs);
+        if (gone) {
+            pend.flush();
+            return;
+        }
+        // fractional position in the end voxel
+        fx = ((R)(ix0 - ix) + fx) + t * rx;
+        fy = ((R)(iy0 - iy) + fy) + t * ry;
+        fz = ((R)(iz0 - iz) + fz) + t * rz;
+        if (Qs) pend.add(tally, v, Qs);
+        if (++s >= s_end) {
+            pend.flush();
+            return;
+        }
+        const unsigned ang = rec.w;
+        rec = __ldg(P.rec + s);  // next record: issued before the deflection arithmetic
 
         // deflection at the end of the step, scaled by the crossed materials
-        const R theta = (R)__half2float(__ushort_as_half((unsigned short)(rec.w & 0xffffu))) *
+        const R theta = (R)__half2float(__ushort_as_half((unsigned short)(ang & 0xffffu))) *
                         sqrt_(acc * inv_len);
-        R phi = (R)(rec.w >> 16) * (sizeof(R) == 4 ? (R)kPhiQuantumF : (R)kPhiQuantumD);
         R st_, ct_;
-        sincos_(theta, &st_, &ct_);
+        sincos_theta(theta, &st_, &ct_);
         const R p2 = dx * dx + dy * dy;
         R nx_, ny_, nz_;
         if (p2 > (R)0) {
             R sp_, cp_;
-            sincos_(phi, &sp_, &cp_);
+            sincos_phi(ang >> 16, &sp_, &cp_);
             const R ip = rsqrt_(p2), p = p2 * ip;
             const R a = st_ * cp_, b = st_ * sp_;
             // e1 = (dx dz, dy dz, -p^2)/p, e2 = (-dy, dx, 0)/p
-            nx_ = a * (dx * dz * ip) - b * (dy * ip) + ct_ * dx;
-            ny_ = a * (dy * dz * ip) + b * (dx * ip) + ct_ * dy;
+            const R az = a * dz * ip;
+            nx_ = az * dx - b * (dy * ip) + ct_ * dx;
+            ny_ = az * dy + b * (dx * ip) + ct_ * dy;
             nz_ = -a * p + ct_ * dz;
         } else {
             // along the beam axis: the frame is (x, y) turned by psi, which
             // makes the replay a rigid rotation of the track
             const R sgn = dz > (R)0 ? (R)1 : (R)-1;
+            const R phi = (R)(ang >> 16) * (sizeof(R) == 4 ? (R)kPhiQuantumF : (R)kPhiQuantumD);
             R sp_, cp_;
             sincos_(phi + sgn * psi, &sp_, &cp_);
             nx_ = st_ * cp_;
@@ -354,8 +434,15 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
     }
 }
 
+// Minimum resident CTAs of 256 threads per SM requested from the register
+// allocator (4 caps the kernel at 64 registers).
+#ifndef FDC_REPLAY_MIN_CTAS
+#define FDC_REPLAY_MIN_CTAS 4
+#endif
+
 template <typename R, bool AGG>
-__global__ void __launch_bounds__(256) replay_kernel(const ReplayArgs P) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? FDC_REPLAY_MIN_CTAS : 2)
+    replay_kernel(const ReplayArgs P) {
     const unsigned lane = threadIdx.x & 31u;
     unsigned long long steps = 0, segs = 0, hist = 0;
     long long replayed = 0, escaped = 0;

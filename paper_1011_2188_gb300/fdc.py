@@ -74,7 +74,7 @@ class Schedule(C.Structure):
 class RunOpts(C.Structure):
     _fields_ = [("history_offset", C.c_uint64), ("track_group", C.c_int32), ("no_rotation", C.c_int32),
                 ("scaling_mode", C.c_int32), ("fp64_geometry", C.c_int32), ("n_batches", C.c_int32),
-                ("pad", C.c_int32), ("schedule", Schedule)]
+                ("no_graph", C.c_int32), ("schedule", Schedule)]
 
 
 class Outputs(C.Structure):
@@ -217,7 +217,9 @@ class Engine:
         """Dose (Gy) of histories [0, n_histories) into a float64 CUDA tensor."""
         import torch
         if dose is None:
-            dose = torch.empty(self.shape, dtype=torch.float64, device=f"cuda:{self.device}")
+            # without a phantom the library reports FDC_ERR_NOT_LOADED
+            shape = self.shape if self.shape is not None else (1,)
+            dose = torch.empty(shape, dtype=torch.float64, device=f"cuda:{self.device}")
         k = _Keep()
         b = beam_struct(spots, k)
         self._check(self._lib.fdc_run(self.h, C.byref(b), int(n_histories), int(seed), _ptr(dose),
@@ -226,12 +228,12 @@ class Engine:
 
     def run_ex(self, spots, n_histories=0, seed=0, history_offset=0, track_group=1, rotate=True,
                scaling_mode=0, fp64_geometry=False, n_batches=0, schedule=None, dose=None,
-               layer_dose=None, batch_sum=None, batch_sumsq=None, tally=None, stream=None):
+               layer_dose=None, batch_sum=None, batch_sumsq=None, tally=None, stream=None, graph=True):
         k = _Keep()
         b = beam_struct(spots, k)
         sch = Schedule(*(schedule or (0, 0, 0, 0)))
         o = RunOpts(int(history_offset), int(track_group), 0 if rotate else 1, int(scaling_mode),
-                    1 if fp64_geometry else 0, int(n_batches), 0, sch)
+                    1 if fp64_geometry else 0, int(n_batches), 0 if graph else 1, sch)
         out = Outputs(_ptr(dose), _ptr(layer_dose), _ptr(batch_sum), _ptr(batch_sumsq), _ptr(tally))
         self._check(self._lib.fdc_run_ex(self.h, C.byref(b), int(n_histories), int(seed), C.byref(o),
                                          C.byref(out), _stream_handle(stream)), "run_ex")
