@@ -128,8 +128,7 @@ typedef struct fdc_schedule {
     int32_t warps_per_cta;   /* 1..8 */
     int32_t chunk;           /* 32-history groups a warp claims per atomic */
     int32_t aggregate;       /* 1: combine the tally atomics of warp lanes that hit the same
-                                voxel; 2: one atomic per lane (default).  Either way a lane
-                                sums its consecutive deposits into one voxel first. */
+                                voxel; 2: one atomic per lane (default) */
 } fdc_schedule;
 
 /* Options of fdc_run_ex.  Zero-initialise for the defaults. */
@@ -230,7 +229,8 @@ int fdc_autotune(fdc_ctx *ctx, const fdc_beam *beam, uint64_t n_histories, uint6
                  fdc_schedule *best);
 
 /* Measurement.  fdc_set_timing(ctx, 1) makes later runs record CUDA events
- * on their stream around the replay kernel(s) and the finalize kernel;
+ * on their stream around the replay kernel(s) and the finalize kernel (timed
+ * runs launch their kernels directly instead of through a CUDA graph);
  * fdc_last_kernel_ms waits for them and returns the last run's replay time
  * (first to last replay launch) and finalize time in milliseconds. */
 int fdc_set_timing(fdc_ctx *ctx, int32_t enable);

@@ -562,7 +562,9 @@ int run_impl(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t se
     };
 
     c->timed = false;
-    if (opts.no_graph) {
+    // timed runs issue their launches directly: events recorded inside a
+    // stream capture only order the capture and cannot be read back
+    if (opts.no_graph || c->timing) {
         rc = issue(st);
         if (rc) return rc;
     } else {
