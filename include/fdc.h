@@ -242,6 +242,40 @@ int fdc_last_kernel_ms(fdc_ctx *ctx, double *replay_ms, double *finalize_ms);
  * *ms (host) receives the kernel time.  Synchronous on `stream`. */
 int fdc_probe_atomics(uint64_t *slots, uint64_t n_slots, uint64_t n_ops, double *ms, void *stream);
 
+/* Run without allocating device memory.
+ *
+ * For callers that must not allocate during a run: for example a planning
+ * system that reserves all of its device memory at start-up and keeps other
+ * work in flight on the GPU, where a cudaMalloc or cudaFree (which may wait
+ * for the whole device) or an out-of-memory failure in the middle of a plan
+ * is not acceptable.  The paper has no counterpart to this call.
+ *
+ * Same computation and result as fdc_run.  The database and phantom must
+ * already be loaded into ctx (those loads allocate, once, beforehand); the
+ * caller passes the beam (host) and dose_out[nvox] (device).  All scratch --
+ * the int64 tally, the counters, the work counter and the device copy of the
+ * spot table -- lives in one static device array of FDC_NOALLOC_SCRATCH_BYTES
+ * that every GPU which loads the library holds until the process exits; the
+ * call makes no cudaMalloc, cudaFree or other allocating call.
+ * Limits: nvox <= FDC_NOALLOC_MAX_VOXELS, n_spots <= FDC_NOALLOC_MAX_SPOTS;
+ * larger inputs return FDC_ERR_INVALID.
+ * The first call on a device looks up the static array's device address
+ * (once per device); make that first call before any stream capture.
+ * Every call on a device shares the one array and reuses it as the last call
+ * left it (the call clears what must start at zero): calls whose GPU work
+ * overlaps -- on different streams or host threads without ordering -- race
+ * and corrupt each other's results.
+ * counters_dev (device, may be NULL) receives the run's counters and device
+ * status (as fdc_sync reports them for other runs) once the work on `stream`
+ * completes.  Asynchronous on `stream`. */
+#define FDC_NOALLOC_MAX_VOXELS (1 << 21)
+#define FDC_NOALLOC_MAX_SPOTS 4096
+#define FDC_NOALLOC_SCRATCH_BYTES                                                  \
+    (8u * FDC_NOALLOC_MAX_VOXELS + 256u + 64u * FDC_NOALLOC_MAX_SPOTS + \
+     8u * (FDC_NOALLOC_MAX_SPOTS + 1) + 256u)
+int fdc_run_noalloc(fdc_ctx *ctx, const fdc_beam *beam, uint64_t n_histories, uint64_t seed,
+                    double *dose_out, fdc_counters *counters_dev, void *stream);
+
 /* Test hooks.  fdc_debug_philox: Philox4x64-10 (Salmon et al., SC'11) with
  * key (key0, key1) on n device counters ctr[n][4], writing out[n][4] (device).
  * fdc_debug_sample: task 1 of histories [h_begin, h_begin + n) -- entry x, y,

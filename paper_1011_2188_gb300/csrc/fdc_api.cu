@@ -798,6 +798,67 @@ int fdc_probe_atomics(uint64_t *slots, uint64_t n_slots, uint64_t n_ops, double 
     return rc;
 }
 
+int fdc_run_noalloc(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t seed, double *dose_out,
+                    fdc_counters *counters_dev, void *stream) {
+    if (!c) return FDC_ERR_INVALID;
+    if (!c->db_loaded || !c->ph_loaded) return fail(c, FDC_ERR_NOT_LOADED, "database and phantom must be loaded");
+    if (!dose_out) return fail(c, FDC_ERR_INVALID, "dose_out is null");
+    BeamInfo bi;
+    int rc = check_beam(c, beam, &bi);
+    if (rc) return rc;
+    if (c->nvox > FDC_NOALLOC_MAX_VOXELS)
+        return fail(c, FDC_ERR_INVALID, "run_noalloc: %lld voxels exceed the static scratch limit of %d",
+                    c->nvox, FDC_NOALLOC_MAX_VOXELS);
+    if (beam->n_spots > FDC_NOALLOC_MAX_SPOTS)
+        return fail(c, FDC_ERR_INVALID, "run_noalloc: %d spots exceed the static scratch limit of %d",
+                    beam->n_spots, FDC_NOALLOC_MAX_SPOTS);
+    const unsigned long long n = n_histories ? n_histories : bi.total;
+    if (n > bi.total) return fail(c, FDC_ERR_INVALID, "more histories than the beam holds");
+    if (c->max_track_units > 0 && (double)n * (double)c->max_track_units > 9.0e18)
+        return fail(c, FDC_ERR_OVERFLOW, "too many histories per launch for the int64 tally");
+    fdc_schedule sched;
+    rc = resolve_schedule(c, nullptr, 0, &sched);
+    if (rc) return rc;
+    FDC_CUDA(c, cudaSetDevice(c->device));
+    fdc::NoallocScratch sc;
+    FDC_CUDA(c, fdc::noalloc_scratch(c->device, &sc));
+    cudaStream_t st = (cudaStream_t)stream;
+    // inputs into the scratch; zero what accumulates
+    FDC_CUDA(c, cudaMemcpyAsync(sc.spots, beam->spots, sizeof(fdc_spot) * beam->n_spots, cudaMemcpyHostToDevice, st));
+    FDC_CUDA(c, fdc::launch_spot_prefix(sc.spots, beam->n_spots, sc.spot_cum, st));
+    FDC_CUDA(c, cudaMemsetAsync(sc.tally, 0, sizeof(unsigned long long) * c->nvox, st));
+    FDC_CUDA(c, cudaMemsetAsync(sc.counters, 0, sizeof(DeviceCounters), st));
+    FDC_CUDA(c, cudaMemsetAsync(sc.work, 0, sizeof(unsigned long long), st));
+    fdc::ReplayArgs a = base_args(c);
+    a.spots = sc.spots;
+    a.spot_cum = sc.spot_cum;
+    a.n_spots = beam->n_spots;
+    a.tally = sc.tally;
+    a.per_layer = 0;
+    a.seed = seed;
+    a.track_group = 1;
+    a.rotate = 1;
+    a.scaling_mode = 0;
+    a.chunk = sched.chunk;
+    a.h_begin = 0;
+    a.n = n;
+    a.work = sc.work;
+    a.counters = sc.counters;
+    if (n) FDC_CUDA(c, fdc::launch_replay(a, sched, 0, c->sm_count, st));
+    fdc::FinalizeArgs f;
+    std::memset(&f, 0, sizeof f);
+    f.tally = (long long *)sc.tally;
+    f.n_tallies = 1;
+    f.nvox = c->nvox;
+    f.density = c->density.p;
+    f.scale = fdc::kMeVToJ / (fdc::kTallyUnitsPerMeV * c->dx * c->dy * c->dz * 1e-3);
+    f.dose = dose_out;
+    FDC_CUDA(c, fdc::launch_finalize(f, c->sm_count, st));
+    if (counters_dev)
+        FDC_CUDA(c, cudaMemcpyAsync(counters_dev, sc.counters, sizeof(DeviceCounters), cudaMemcpyDeviceToDevice, st));
+    return FDC_OK;
+}
+
 int fdc_debug_philox(uint64_t key0, uint64_t key1, const uint64_t *ctr, uint64_t n, uint64_t *out, void *stream) {
     if (!ctr || !out) return FDC_ERR_INVALID;
     if (!n) return FDC_OK;

@@ -86,6 +86,19 @@ cudaError_t launch_debug_philox(unsigned long long k0, unsigned long long k1,
 cudaError_t launch_debug_sample(const ReplayArgs &a, float *xyEpsi, long long *btk,
                                 cudaStream_t st);
 int replay_max_ctas_per_sm(int warps_per_cta, int fp64, int aggregate);
+// Static scratch of fdc_run_noalloc (defined in fdc_kernels.cu with the
+// array): device addresses of its parts on the current device, looked up once
+// per device.
+struct NoallocScratch {
+    unsigned long long *tally;  // [FDC_NOALLOC_MAX_VOXELS]
+    DeviceCounters *counters;
+    unsigned long long *work;
+    fdc_spot *spots;            // [FDC_NOALLOC_MAX_SPOTS]
+    unsigned long long *spot_cum;  // [FDC_NOALLOC_MAX_SPOTS + 1]
+};
+cudaError_t noalloc_scratch(int device, NoallocScratch *out);
+cudaError_t launch_spot_prefix(const fdc_spot *spots, int n_spots, unsigned long long *cum,
+                               cudaStream_t st);
 cudaError_t launch_probe_atomics(unsigned long long *slots, unsigned long long n_slots,
                                  unsigned long long n_ops, int sm_count, cudaStream_t st);
 

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "fdc_internal.h"
 
 namespace fdc {
@@ -594,6 +596,18 @@ __global__ void debug_sample_kernel(const ReplayArgs P, float *xyEpsi, long long
     }
 }
 
+// One thread: prefix sum of the spots' history counts (cum[0] = 0).
+__global__ void spot_prefix_kernel(const fdc_spot *spots, int n_spots, unsigned long long *cum) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long a = 0;
+        cum[0] = 0;
+        for (int i = 0; i < n_spots; ++i) {
+            a += spots[i].n_histories;
+            cum[i + 1] = a;
+        }
+    }
+}
+
 // 64-bit atomic adds to hashed addresses (every thread its own stream of
 // slots), the access pattern of the dose tally without the transport.
 __global__ void probe_atomics_kernel(unsigned long long *slots, unsigned long long n_slots,
@@ -622,6 +636,61 @@ int max_ctas_t(int threads) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- static scratch
+// The scratch of fdc_run_noalloc: one file-scope device array, resident on
+// every GPU that loads the library.  Host code must not use the symbol itself
+// as a pointer (on the host it is only a stand-in); noalloc_scratch() looks up
+// its device address with cudaGetSymbolAddress, once per device, with that
+// device current.
+constexpr size_t kNoallocTallyBytes = 8ull * FDC_NOALLOC_MAX_VOXELS;
+constexpr size_t kNoallocCountersOff = kNoallocTallyBytes;
+constexpr size_t kNoallocWorkOff = kNoallocCountersOff + 128;
+constexpr size_t kNoallocSpotsOff = kNoallocCountersOff + 256;
+constexpr size_t kNoallocCumOff = kNoallocSpotsOff + sizeof(fdc_spot) * FDC_NOALLOC_MAX_SPOTS;
+constexpr size_t kNoallocBytes = kNoallocCumOff + 8ull * (FDC_NOALLOC_MAX_SPOTS + 1) + 256;
+static_assert(kNoallocBytes == FDC_NOALLOC_SCRATCH_BYTES, "scratch size in fdc.h");
+static_assert(sizeof(DeviceCounters) <= 128, "counters slot");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_base[kMaxDevices] = {};
+}  // namespace
+
+cudaError_t noalloc_scratch(int device, NoallocScratch *out) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_base[device]) {
+            int cur = -1;
+            cudaError_t e = cudaGetDevice(&cur);
+            if (e != cudaSuccess) return e;
+            if (cur != device && (e = cudaSetDevice(device)) != cudaSuccess) return e;
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (cur != device) cudaSetDevice(cur);
+            if (e != cudaSuccess) return e;
+            g_noalloc_base[device] = (unsigned char *)p;
+        }
+        base = g_noalloc_base[device];
+    }
+    out->tally = (unsigned long long *)base;
+    out->counters = (DeviceCounters *)(base + kNoallocCountersOff);
+    out->work = (unsigned long long *)(base + kNoallocWorkOff);
+    out->spots = (fdc_spot *)(base + kNoallocSpotsOff);
+    out->spot_cum = (unsigned long long *)(base + kNoallocCumOff);
+    return cudaSuccess;
+}
+
+cudaError_t launch_spot_prefix(const fdc_spot *spots, int n_spots, unsigned long long *cum,
+                               cudaStream_t st) {
+    spot_prefix_kernel<<<1, 32, 0, st>>>(spots, n_spots, cum);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_replay(const ReplayArgs &a, const fdc_schedule &s, int fp64, int sm_count,
                           cudaStream_t st) {

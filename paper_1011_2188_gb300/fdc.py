@@ -38,6 +38,7 @@ SIGNATURES = {
     "fdc_set_timing": (C.c_int, [_p, C.c_int32]),
     "fdc_last_kernel_ms": (C.c_int, [_p, _p, _p]),
     "fdc_probe_atomics": (C.c_int, [_p, C.c_uint64, C.c_uint64, _p, _p]),
+    "fdc_run_noalloc": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, _p, _p, _p]),
     "fdc_debug_philox": (C.c_int, [C.c_uint64, C.c_uint64, _p, C.c_uint64, _p, _p]),
     "fdc_debug_sample": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int32, C.c_int32,
                                    _p, _p, _p]),
@@ -237,6 +238,20 @@ class Engine:
         out = Outputs(_ptr(dose), _ptr(layer_dose), _ptr(batch_sum), _ptr(batch_sumsq), _ptr(tally))
         self._check(self._lib.fdc_run_ex(self.h, C.byref(b), int(n_histories), int(seed), C.byref(o),
                                          C.byref(out), _stream_handle(stream)), "run_ex")
+
+    def run_noalloc(self, spots, n_histories=0, seed=0, dose=None, counters=None, stream=None):
+        """fdc_run_noalloc: the run's scratch lives in the library's static
+        device array, so the call allocates no device memory (the caller must
+        provide ``dose``; ``counters`` is an optional device buffer of at
+        least sizeof(fdc_counters) = 56 bytes, e.g. a uint8 tensor, that
+        receives the run's counters)."""
+        if dose is None:
+            raise ValueError("run_noalloc needs a caller-provided dose tensor")
+        k = _Keep()
+        b = beam_struct(spots, k)
+        self._check(self._lib.fdc_run_noalloc(self.h, C.byref(b), int(n_histories), int(seed), _ptr(dose),
+                                              _ptr(counters), _stream_handle(stream)), "run_noalloc")
+        return dose
 
     def run_host(self, spots, n_histories=0, seed=0, dose_host=None):
         """End-to-end call with a host (numpy float64) dose buffer."""

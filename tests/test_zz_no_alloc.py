@@ -1,0 +1,73 @@
+"""fdc_run_noalloc: the entry point for callers that must not allocate device
+memory while a run is in flight (its scratch lives in a static device array
+of the library).  Checked through the C ABI against fdc_run on the same
+inputs, on two calls in a row (the second reuses the scratch the first one
+left behind), plus its size limits.  This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+from paper_1011_2188_gb300 import synth
+from gpu_helpers import VOXEL_TOL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _counters(buf):
+    from paper_1011_2188_gb300 import fdc
+    raw = buf.cpu().numpy().tobytes()
+    c = fdc.Counters.from_buffer_copy(raw)
+    return c.as_dict()
+
+
+def test_noalloc_matches_fdc_run_twice():
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    db = synth.water_database([150.0], 300, seed=1)
+    ph = synth.slab_phantom()
+    beam = synth.pencil_beam(50000, energy=150.0, sigma_cm=0.3)
+    eng = fdc.Engine(0)
+    eng.load_database(db)
+    eng.load_phantom(ph)
+    shape = ph.shape[::-1]
+    for seed in (7, 8):  # two calls in a row on the shared static scratch
+        ref = eng.run(beam, 0, seed)
+        eng.sync()
+        dose = torch.full(shape, -1.0, dtype=torch.float64, device="cuda:0")
+        counters = torch.zeros(64, dtype=torch.uint8, device="cuda:0")
+        eng.run_noalloc(beam, 0, seed, dose=dose, counters=counters)
+        torch.cuda.synchronize()
+        r, d = ref.cpu().numpy(), dose.cpu().numpy()
+        assert np.abs(d - r).max() <= VOXEL_TOL * r.max()
+        c = _counters(counters)
+        assert c["histories"] == 50000 and c["status"] == 0
+        assert c["replayed"] > c["escaped"] > 0
+    eng.close()
+
+
+def test_noalloc_rejects_sizes_beyond_the_static_scratch():
+    from paper_1011_2188_gb300 import fdc
+    import torch
+    db = synth.water_database([100.0], 10, seed=1)
+    big = synth.uniform_phantom((130, 130, 130), (0.2, 0.2, 0.2), (-13.0, -13.0, 0.0))
+    eng = fdc.Engine(0)
+    eng.load_database(db)
+    eng.load_phantom(big)  # 2,197,000 voxels > FDC_NOALLOC_MAX_VOXELS (2,097,152)
+    dose = torch.zeros(big.shape[::-1], dtype=torch.float64, device="cuda:0")
+    with pytest.raises(fdc.FdcError) as ex:
+        eng.run_noalloc(synth.pencil_beam(10, energy=100.0), 0, 1, dose=dose)
+    assert ex.value.code == 1 and "static scratch" in str(ex.value)
+    eng.load_phantom(synth.slab_phantom(n=16))
+    many = synth.make_spots([dict(x=0.0, y=0.0, energy=100.0, sigma_e=0.0, a=0.1, profile=0, layer=0,
+                                  n_histories=1)] * 4097)
+    dose = torch.zeros((16, 16, 16), dtype=torch.float64, device="cuda:0")
+    with pytest.raises(fdc.FdcError) as ex:
+        eng.run_noalloc(many, 0, 1, dose=dose)
+    assert ex.value.code == 1
+    eng.close()
