@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--workload", default="thorax", choices=["thorax", "slab", "spots"])
     ap.add_argument("--histories", type=int, default=0, help="override histories per step")
     ap.add_argument("--tracks", type=int, default=100_000, help="database tracks per energy")
+    ap.add_argument("--track-group", type=int, default=32,
+                    help="histories sharing one database track: 32 (default) is the paper's scheme of "
+                         "feeding one history to a thread group; 1 draws a track per history")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--schedule", default="", help="ctas_per_sm,warps_per_cta,chunk,aggregate")
@@ -160,110 +163,51 @@ def cpu_baseline(db, ph, beam, seed, target_s=12.0):
 
 def time_to_sigma(eng, beam, ph, seed, target=0.02, n_batches=10, n0=200_000, local=0):
     """Plain method: device time to reach a mean relative batch uncertainty
-    (eq. (1), n_batches batches) of ``target`` over voxels above half the
-    maximum dose (Sec. 2.4) and, separately, above 0.9 of it (the Bragg-peak
-    region).  The history count is predicted from a pilot run (sigma ~ N^-1/2)
-    and then run and timed."""
+    (eq. (1)) of ``target`` over voxels above half the maximum dose (Sec. 2.4)
+    and, separately, above 0.9 of it (the Bragg-peak region)."""
+    from paper_1011_2188_gb300.measure import time_to_sigma as tts
+    shape = ph.shape[::-1]
+    return {"half_max": tts(eng, beam, shape, seed, target, 0.5, n_batches, n0, local),
+            "bragg_peak_0.9max": tts(eng, beam, shape, seed, target, 0.9, n_batches, n0, local)}
+
+
+def history_vs_batch(eng, beam, ph, n, seed, n_batches=10, local=0, track_group=1):
+    """Sec. 2.4 / Fig. 5 analogue on the bench workload: one run of n
+    histories in n_batches batches that also keeps the second (squared) tally;
+    mean relative uncertainty over D > D_max/2 from eq. (1) and from eq. (2),
+    and the device-time cost of keeping the squares (the paper: +18 %)."""
     import torch
     shape = ph.shape[::-1]
-    s1 = torch.zeros(shape, dtype=torch.float64, device=f"cuda:{local}")
-    s2 = torch.zeros_like(s1)
-    total = int(beam["n_histories"].sum())
+    dev = f"cuda:{local}"
+    dose = torch.zeros(shape, dtype=torch.float64, device=dev)
+    s1, s2, sq = torch.zeros_like(dose), torch.zeros_like(dose), torch.zeros_like(dose)
 
-    def measure(n):
-        n = min(total, max(n_batches, (n // n_batches) * n_batches))
-        eng.run_ex(beam, n, seed, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2)  # warm / capture
+    def timed(**kw):
+        kw["track_group"] = track_group
+        eng.run_ex(beam, n, seed, dose=dose, **kw)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        eng.run_ex(beam, n, seed, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2)
-        e1.record()
-        e1.synchronize()
-        _, _, rel = eng.batch_stats(s1, s2, n_batches, 0.5)
-        _, _, rel9 = eng.batch_stats(s1, s2, n_batches, 0.9)
-        return n, e0.elapsed_time(e1) * 1e-3, rel, rel9
-
-    n, _, rel, rel9 = measure(n0)
-    out = {}
-    for key, r in (("half_max", rel), ("bragg_peak_0.9max", rel9)):
-        want = int(n * (r / target) ** 2 * 1.05) + n_batches
-        m, sec, rel_m, rel9_m = measure(want)
-        got = rel_m if key == "half_max" else rel9_m
-        out[key] = {"histories": m, "seconds": sec, "mean_rel_sigma": got, "target": target,
-                    "n_batches": n_batches, "reached": bool(got <= target)}
-    return out
-
-
-def precision_study(args):
-    """Slab phantom (64^3 x 2 mm, bone slab), 150 MeV pencil (and 121 MeV):
-    10^8 histories in 100 batches with FP32 and with FP64 step geometry;
-    dose differences FP32 vs FP64 on the device, both against the FP64 oracle
-    on a history subset, per-voxel batch uncertainty from the FP64 batch sums,
-    and the device time to 2 % mean uncertainty in the Bragg-peak region."""
-    import numpy as np
-    import torch
-    import oracle
-    from paper_1011_2188_gb300 import fdc, synth
-    oracle.build()
-    n_total = args.histories or 100_000_000
-    n_batches = 100
-    res = {"study": "precision", "histories": n_total, "n_batches": n_batches}
-    for E in (150.0, 121.0):
-        db = synth.water_database([E], 10_000, seed=1)
-        ph = synth.slab_phantom()
-        beam = synth.pencil_beam(n_total, energy=E, sigma_cm=0.3)
-        eng = fdc.Engine(0)
-        eng.load_database(db)
-        eng.load_phantom(ph)
-        shape = ph.shape[::-1]
-        out = {}
-        doses = {}
-        for fp64 in (False, True):
-            s1 = torch.zeros(shape, dtype=torch.float64, device="cuda:0")
-            s2 = torch.zeros_like(s1)
-            dose = torch.zeros_like(s1)
-            eng.run_ex(beam, n_total, 5, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2, dose=dose,
-                       fp64_geometry=fp64)
-            eng.sync()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = None
+        for _ in range(3):
             e0.record()
-            eng.run_ex(beam, n_total, 5, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2, dose=dose,
-                       fp64_geometry=fp64)
+            eng.run_ex(beam, n, seed, dose=dose, **kw)
             e1.record()
             e1.synchronize()
-            cnt = eng.sync()
-            mean, sigma, rel_half = eng.batch_stats(s1, s2, n_batches, 0.5)
-            _, _, rel_peak = eng.batch_stats(s1, s2, n_batches, 0.9)
-            key = "fp64" if fp64 else "fp32"
-            sec = e0.elapsed_time(e1) * 1e-3
-            # histories to reach 2 % in the Bragg-peak region, from sigma ~ N^-1/2
-            n2 = n_total * (rel_peak / 0.02) ** 2
-            out[key] = {"seconds": sec, "histories_per_s": n_total / sec,
-                        "track_steps_per_s": cnt["steps"] / sec,
-                        "mean_rel_sigma_half_max": rel_half, "mean_rel_sigma_peak": rel_peak,
-                        "histories_for_2pct_peak": n2, "seconds_for_2pct_peak": sec * n2 / n_total}
-            doses[key] = dose.cpu().numpy()
-        d32, d64 = doses["fp32"], doses["fp64"]
-        mx = d64.max()
-        out["fp32_vs_fp64_device"] = {"max_abs_over_max": float(np.abs(d32 - d64).max() / mx),
-                                      "mean_abs_over_max": float(np.abs(d32 - d64).mean() / mx)}
-        # against the FP64 oracle on the first n_sub histories
-        n_sub = 300_000
-        ref = oracle.run(db, ph, beam, seed=5, h_begin=0, h_end=n_sub)
-        d_ref = oracle.dose(ph, ref.edep)
-        sub = {}
-        for fp64 in (False, True):
-            d = torch.zeros(shape, dtype=torch.float64, device="cuda:0")
-            eng.run_ex(beam, n_sub, 5, dose=d, fp64_geometry=fp64)
-            eng.sync()
-            dd = d.cpu().numpy()
-            sub["fp64" if fp64 else "fp32"] = {
-                "max_abs_over_max": float(np.abs(dd - d_ref).max() / d_ref.max()),
-                "mean_abs_over_max": float(np.abs(dd - d_ref).mean() / d_ref.max()),
-                "total_energy_rel": float(abs(dd.sum() - d_ref.sum()) / d_ref.sum())}
-        out["vs_oracle_first_%d" % n_sub] = sub
-        res[f"{E:g}MeV"] = out
-        eng.close()
-    print(json.dumps(res), flush=True)
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best
+
+    t_plain = timed()
+    t_sq = timed(history_sumsq=sq)
+    eng.run_ex(beam, n, seed, dose=dose, history_sumsq=sq, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2,
+               track_group=track_group)
+    eng.sync()
+    _, _, rel_b = eng.batch_stats(s1, s2, n_batches, 0.5)
+    _, _, rel_h = eng.history_stats(dose, sq, n, 0.5)
+    # eq. (2) gives the uncertainty of the mean per-history dose, eq. (1) of
+    # the mean batch dose; relative values compare directly
+    return {"histories": n, "track_group": track_group, "mean_rel_sigma_batch_eq1": rel_b, "mean_rel_sigma_history_eq2": rel_h,
+            "history_over_batch": rel_h / rel_b, "ms_plain": t_plain, "ms_with_squares": t_sq,
+            "squares_overhead": t_sq / t_plain - 1.0}
 
 
 def run_reference(args, rank, world):
@@ -355,7 +299,7 @@ def main():
 
     def one_step():
         eng.run_ex(beam, n, seed, history_offset=offset, dose=dose, layer_dose=layer_dose, stream=stream,
-                   schedule=sched)
+                   schedule=sched, track_group=args.track_group)
 
     for _ in range(max(args.warmup, 0)):
         one_step()
@@ -397,9 +341,26 @@ def main():
     if args.quick:
         if rank == 0:
             print(json.dumps({"value": value, "ms_per_step": ms, "replay_ms": rep_ms, "schedule": sched,
+                              "tracks": args.tracks, "track_group": args.track_group,
                               "track_steps_per_s": steps_per_run * world / (ms * 1e-3), "clocks": clk,
                               "flags": os.environ.get("FDC_NVCC_FLAGS", "")}), flush=True)
         return
+
+    # ---- ablation: a separate track per history (Sec. 4: +50 % time on the GTX 295)
+    indep = None
+    if args.track_group != 1 and not args.quick:
+        t_ind = []
+        for i in range(3 + 3):
+            ev0.record(stream)
+            eng.run_ex(beam, n, seed, history_offset=offset, dose=dose, layer_dose=layer_dose, stream=stream,
+                       schedule=sched, track_group=1)
+            ev1.record(stream)
+            ev1.synchronize()
+            if i >= 3:
+                t_ind.append(ev0.elapsed_time(ev1))
+        ms_ind = sum(t_ind) / len(t_ind)
+        indep = {"track_group": 1, "histories_per_s": n / (ms_ind * 1e-3), "ms_per_step": ms_ind,
+                 "time_ratio_vs_shared": ms_ind / ms}
 
     # ---- end to end through the C ABI with host buffers (beam in, dose out)
     host_dose = torch.empty(ph.shape[::-1], dtype=torch.float64).pin_memory().numpy()
@@ -431,7 +392,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "histories_per_step": n, "tally": "int64 fixed point 2^-28 MeV",
                    "l2": "flushed between timed steps (512 MB write); track working set > L2",
-                   "schedule": list(sched) if sched else "default", "parallelism": f"replicas x{world}"},
+                   "schedule": list(sched) if sched else "default", "parallelism": f"replicas x{world}",
+                   "track_group": args.track_group},
         "track_steps_per_s": steps_per_run * world / (ms * 1e-3),
         "segments_per_s": segs_per_run * world / (ms * 1e-3),
         "steps_per_history": steps_per_run / hist_per_run,
@@ -447,11 +409,14 @@ def main():
         "e2e": {"value": n / e2e_s, "unit": "histories/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,
+        "ablation_independent_tracks": indep,
         "clocks": clk,
         "load_s": t_load,
     }
-    if rank == 0:
+    if rank == 0 and args.workload != "spots":  # batches of a spot plan would cover different spots
         line["time_to_2pct_sigma_plain"] = time_to_sigma(eng, beam, ph, seed + 99, local=local)
+        line["history_by_history"] = history_vs_batch(eng, beam, ph, n, seed + 7, local=local,
+                                                      track_group=args.track_group)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(db, ph, beam, seed)
     if rank == 0:

@@ -164,6 +164,10 @@ typedef struct fdc_outputs {
     double *batch_sum;
     double *batch_sumsq;
     int64_t *tally;
+    double *history_sumsq;   /* [nvox]: sum over histories of the square of the history's
+                                dose in the voxel (Gy^2), the second tally of Sec. 2.3 for
+                                eq. (2); squared per voxel visit, so a history that leaves a
+                                voxel and re-enters it later adds two squares */
 } fdc_outputs;
 
 /* Counters of the last run, valid after fdc_sync.  Energies are in tally
@@ -220,6 +224,15 @@ int fdc_sync(fdc_ctx *ctx, void *stream, fdc_counters *counters);
 int fdc_batch_stats(fdc_ctx *ctx, const double *batch_sum, const double *batch_sumsq,
                     int32_t n_batches, double frac, double *mean, double *sigma,
                     double *mean_rel, void *stream);
+
+/* Eq. (2) on the device: from dose_sum[nvox] (the run's dose, i.e. the sum of
+ * the N per-history doses) and history_sumsq[nvox] write the mean dose per
+ * history mean[nvox] and its uncertainty sigma[nvox] (device, Gy), and to
+ * *mean_rel (host) the average sigma/mean over voxels above frac * max(mean).
+ * Synchronous. */
+int fdc_history_stats(fdc_ctx *ctx, const double *dose_sum, const double *history_sumsq,
+                      uint64_t n_histories, double frac, double *mean, double *sigma,
+                      double *mean_rel, void *stream);
 
 /* Pick the replay schedule for this beam by timing candidates on the device
  * (runs the beam's first n_histories histories several times; results are

@@ -1,0 +1,110 @@
+/*
+ * fdc_unet.h -- C ABI of the learned denoiser's kernels.
+ *
+ * The denoiser is not part of the paper: it is a small 3-D U-Net that maps a
+ * dose computed from few histories (plus the phantom density) to the dose of
+ * many histories; the track-repeating engine of fdc.h generates its training
+ * pairs and stays the fallback and the judge of its error.  These calls are
+ * the building blocks the network is trained and run with: BF16 tensor-core
+ * convolutions with FP32 accumulation and their gradients, plus the
+ * element-wise pieces.
+ *
+ * Conventions: all pointers are device memory owned by the caller; tensors
+ * are channels-last [batch][d][h][w][c]; "bf16" arrays hold IEEE bfloat16
+ * values (uint16 storage); weights are [c_out][k][k][k][c_in] (bf16) and
+ * their transposed copy for the data gradient [c_in][k][k][k][c_out].
+ * Calls are asynchronous on `stream` (cudaStream_t as void *, NULL = legacy
+ * default stream) and return FDC_OK, FDC_ERR_INVALID (bad shapes: channel
+ * counts must be multiples of 16, sizes positive and consistent) or
+ * FDC_ERR_CUDA (launch failure).
+ */
+#ifndef FDC_UNET_H
+#define FDC_UNET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A 3-D convolution: kernel ksize^3 (1, 2 or 3), stride, zero padding pad;
+ * out = (in + 2 pad - ksize) / stride + 1 per axis.  relu = 1 applies
+ * max(0, .) to the forward output. */
+typedef struct fdc_conv3d {
+    int32_t batch, in_d, in_h, in_w, out_d, out_h, out_w, c_in, c_out, ksize, stride, pad, relu;
+} fdc_conv3d;
+
+/* y[b][o][co] = act(bias[co] + sum_{tap, ci} x[b][o * stride - pad + tap][ci] w[co][tap][ci]).
+ * x bf16 [batch][in...][c_in]; w bf16; bias FP32 [c_out] or NULL; outputs
+ * y_bf16 [batch][out...][c_out] and/or y_f32 (either may be NULL). */
+int fdc_conv3d_forward(const fdc_conv3d *g, const void *x, const void *w, const float *bias, void *y_bf16,
+                       float *y_f32, void *stream);
+/* dx[b][i][ci] = sum over (tap, co) with i + pad - tap = stride * o of dy[b][o][co] w[co][tap][ci]
+ * (the gradient of the forward map with respect to x, without the ReLU).
+ * dy bf16 [batch][out...][c_out]; w_t bf16 [c_in][tap][c_out]; dx bf16. */
+int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_t, void *dx, void *stream);
+/* dw[co][tap][ci] += sum_o dy[o][co] x[o * stride - pad + tap][ci] and, if db is not NULL,
+ * db[co] += sum_o dy[o][co]; dw, db FP32 (accumulated: zero them first). */
+int fdc_conv3d_backward_weights(const fdc_conv3d *g, const void *x, const void *dy, float *dw, float *db,
+                                void *stream);
+/* w_t[ci][tap][co] = w[co][tap][ci] (bf16). */
+int fdc_conv3d_transpose_weights(const fdc_conv3d *g, const void *w, void *w_t, void *stream);
+
+/* dx = dy where y > 0, else 0 (bf16, n elements). */
+int fdc_relu_backward(const void *y, const void *dy, void *dx, int64_t n, void *stream);
+/* Nearest-neighbour x2 upsampling of x [b][d][h][w][c] into y [b][2d][2h][2w][c]
+ * (backward = 0), or its adjoint: dx[b][d][h][w][c] = sum of the 8 children of dy
+ * (backward = 1, x = dy, y = dx).  bf16. */
+int fdc_upsample2(const void *x, void *y, int32_t b, int32_t d, int32_t h, int32_t w, int32_t c,
+                  int32_t backward, void *stream);
+/* split = 0: out[r] = concat(a[r] (ca channels), b[r] (cb channels)); split = 1:
+ * the inverse, a[r] and b[r] from out[r].  bf16, rows r. */
+int fdc_concat_channels(void *a, int32_t ca, void *b, int32_t cb, void *out, int64_t rows, int32_t split,
+                        void *stream);
+/* Mean squared error of channel 0 of pred [rows][c] (FP32) against target [rows]:
+ * adds mean((pred - target)^2) to *loss (FP32, device) and, if grad is not NULL,
+ * writes d loss / d pred into grad [rows][c] (bf16, zero outside channel 0). */
+int fdc_mse(const float *pred, int32_t c, const float *target, int64_t rows, void *grad, float *loss,
+            void *stream);
+/* One Adam step (Kingma & Ba 2015) at step number `step` (>= 1) on n FP32 parameters p with
+ * gradient g and moments m, v; also writes the bf16 copy p_bf16 if not NULL. */
+int fdc_adam(float *p, const float *g, float *m, float *v, void *p_bf16, int64_t n, float lr, float beta1,
+             float beta2, float eps, int32_t step, void *stream);
+/* y = bf16(x), n elements. */
+int fdc_f32_to_bf16(const float *x, void *y, int64_t n, void *stream);
+/* out = a + b (bf16, n elements; out may alias a or b). */
+int fdc_add_bf16(const void *a, const void *b, void *out, int64_t n, void *stream);
+
+/* Network input from a dose grid of n voxels (FP64, Gy) and its density
+ * (FP32): x [n][16] bf16 with channel 0 = dose / dose_scale, channel 1 =
+ * density * density_scale, channels 2..15 zero; dose_in [n] FP32 = channel 0.
+ * With dose_high (a high-history dose of the same field) and target not NULL,
+ * target [n] FP32 = dose_high / dose_scale - dose_in, the correction the
+ * network is trained to predict. */
+int fdc_unet_prepare(const double *dose, const float *density, const double *dose_high, int64_t n,
+                     double dose_scale, float density_scale, void *x, float *dose_in, float *target,
+                     void *stream);
+/* Denoised dose: dose_out [n] (FP64, Gy) = max(0, (head[n][16] channel 0 + dose_in) * dose_scale). */
+int fdc_unet_finish(const float *head, const float *dose_in, int64_t n, double dose_scale, double *dose_out,
+                    void *stream);
+
+/* Gamma index (Low, Harms, Mutic & Purdy 1998) of an evaluated dose against a
+ * reference dose on the same d x h x w grid (spacing sd, sh, sw cm; FP64,
+ * x fastest): for every reference voxel above threshold * max(ref),
+ * gamma = min over evaluated voxels within the search radius of
+ * sqrt(distance^2 / dta^2 + (eval - ref)^2 / (dose_frac * max(ref))^2)
+ * (global dose difference, voxel-centre sampling, no interpolation; search
+ * radius ceil(1.5 dta / min spacing) voxels, at most 8).  gamma [n] FP32
+ * (may be NULL) receives the values (-1 outside the threshold); scratch is a
+ * device buffer of 3 uint64; *pass_rate (host, may be NULL) receives the
+ * fraction of evaluated voxels with gamma <= 1 (the call then waits for the
+ * stream). */
+int fdc_gamma(const double *ref, const double *eval, int32_t d, int32_t h, int32_t w, double sd, double sh,
+              double sw, double dose_frac, double dta, double threshold, float *gamma, uint64_t *scratch,
+              double *pass_rate, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDC_UNET_H */

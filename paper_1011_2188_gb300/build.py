@@ -17,8 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libfdc.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["fdc_kernels.cu", "fdc_api.cu"]
-HEADERS = [os.path.join(CSRC, "fdc_internal.h"), os.path.join(INCLUDE, "fdc.h")]
+SOURCES = ["fdc_kernels.cu", "fdc_api.cu", "unet_kernels.cu"]
+HEADERS = [os.path.join(CSRC, "fdc_internal.h"), os.path.join(INCLUDE, "fdc.h"), os.path.join(INCLUDE, "fdc_unet.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -80,7 +80,7 @@ struct fdc_ctx {
     DevBuf<float2> vox;
     DevBuf<float> density;
     // run scratch
-    DevBuf<long long> tally, accum;
+    DevBuf<long long> tally, accum, sumsq;
     DevBuf<fdc_spot> spots;
     DevBuf<unsigned long long> spot_cum;
     DevBuf<DeviceCounters> counters;
@@ -239,6 +239,13 @@ fdc::ReplayArgs base_args(fdc_ctx *c) {
     a.x0 = c->x0;
     a.y0 = c->y0;
     a.z0 = c->z0;
+    a.x1 = c->x0 + c->nx * c->dx;
+    a.y1 = c->y0 + c->ny * c->dy;
+    a.idx_ = 1.0 / c->dx;
+    a.idy_ = 1.0 / c->dy;
+    a.ihx = (float)(1.0 / c->dx);
+    a.ihy = (float)(1.0 / c->dy);
+    a.ihz = (float)(1.0 / c->dz);
     a.spots = c->spots.p;
     a.spot_cum = c->spot_cum.p;
     a.nvox = c->nvox;
@@ -285,6 +292,7 @@ void fdc_destroy(fdc_ctx *c) {
     c->density.release();
     c->tally.release();
     c->accum.release();
+    c->sumsq.release();
     c->spots.release();
     c->spot_cum.release();
     c->counters.release();
@@ -417,7 +425,7 @@ int fdc_load_phantom(fdc_ctx *c, const fdc_phantom *ph) {
         !std::isfinite(ph->dz) || !std::isfinite(ph->x0) || !std::isfinite(ph->y0) || !std::isfinite(ph->z0))
         return fail(c, FDC_ERR_INVALID, "phantom: bad spacing or origin");
     const long long nvox = (long long)ph->nx * ph->ny * ph->nz;
-    if (nvox > (1ll << 34)) return fail(c, FDC_ERR_INVALID, "phantom: too many voxels");
+    if (nvox >= (1ll << 31)) return fail(c, FDC_ERR_INVALID, "phantom: more than 2^31 - 1 voxels");
     for (int m = 0; m < ph->n_mat; ++m)
         if (!finite_f(ph->s_rel[m]) || ph->s_rel[m] < 0 || !finite_f(ph->k_theta[m]) || ph->k_theta[m] < 0)
             return fail(c, FDC_ERR_INVALID, "phantom: bad material %d", m);
@@ -492,6 +500,7 @@ int run_impl(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t se
     const long long tsize = (long long)n_tallies * c->nvox;
     FDC_CUDA(c, c->tally.ensure(tsize));
     if (n_batches > 1) FDC_CUDA(c, c->accum.ensure(tsize));
+    if (out.history_sumsq) FDC_CUDA(c, c->sumsq.ensure(tsize));
     rc = upload_beam(c, beam, st, force_upload);
     if (rc) return rc;
     fdc::ReplayArgs a = base_args(c);
@@ -505,6 +514,7 @@ int run_impl(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t se
     a.chunk = sched.chunk;
     a.h_begin = opts.history_offset;
     a.n = n;
+    a.sumsq = out.history_sumsq ? (unsigned long long *)c->sumsq.p : nullptr;
     const double scale = fdc::kMeVToJ / (fdc::kTallyUnitsPerMeV * c->dx * c->dy * c->dz * 1e-3);
 
     // The whole run as one sequence of stream operations: zero the counters
@@ -513,6 +523,7 @@ int run_impl(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t se
     auto issue = [&](cudaStream_t s) -> int {
         FDC_CUDA(c, cudaMemsetAsync(c->counters.p, 0, sizeof(DeviceCounters), s));
         FDC_CUDA(c, cudaMemsetAsync(c->tally.p, 0, sizeof(long long) * tsize, s));
+        if (a.sumsq) FDC_CUDA(c, cudaMemsetAsync(c->sumsq.p, 0, sizeof(long long) * tsize, s));
         if (n_batches > 1) {
             FDC_CUDA(c, cudaMemsetAsync(c->accum.p, 0, sizeof(long long) * tsize, s));
             if (out.batch_sum) FDC_CUDA(c, cudaMemsetAsync(out.batch_sum, 0, sizeof(double) * c->nvox, s));
@@ -544,10 +555,12 @@ int run_impl(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t se
         }
         if (c->timing) FDC_CUDA(c, cudaEventRecord(c->ev[1], s));
         if (c->timing) FDC_CUDA(c, cudaEventRecord(c->ev[2], s));
-        if (out.dose || out.layer_dose || out.tally) {
+        if (out.dose || out.layer_dose || out.tally || out.history_sumsq) {
             fdc::FinalizeArgs f;
             std::memset(&f, 0, sizeof f);
             f.tally = n_batches > 1 ? c->accum.p : c->tally.p;
+            f.sumsq = a.sumsq ? c->sumsq.p : nullptr;
+            f.hist_sumsq = out.history_sumsq;
             f.n_tallies = n_tallies;
             f.nvox = c->nvox;
             f.density = c->density.p;
@@ -675,8 +688,27 @@ int fdc_batch_stats(fdc_ctx *c, const double *batch_sum, const double *batch_sum
     const int parts = std::max(1, std::min<int>(c->sm_count * 2, (int)((c->nvox + 255) / 256)));
     FDC_CUDA(c, c->stats_part.ensure(3 * parts + 1));
     cudaStream_t st = (cudaStream_t)stream;
-    FDC_CUDA(c, fdc::launch_batch_stats(batch_sum, batch_sumsq, n_batches, c->nvox, frac, mean, sigma,
+    FDC_CUDA(c, fdc::launch_batch_stats(batch_sum, batch_sumsq, n_batches, 0, c->nvox, frac, mean, sigma,
                                         c->stats_part.p, parts, c->stats_part.p + 3 * parts, st));
+    double r = 0;
+    FDC_CUDA(c, cudaMemcpyAsync(&r, c->stats_part.p + 3 * parts, sizeof r, cudaMemcpyDeviceToHost, st));
+    FDC_CUDA(c, cudaStreamSynchronize(st));
+    if (mean_rel) *mean_rel = r;
+    return FDC_OK;
+}
+
+int fdc_history_stats(fdc_ctx *c, const double *dose_sum, const double *history_sumsq, uint64_t n_histories,
+                      double frac, double *mean, double *sigma, double *mean_rel, void *stream) {
+    if (!c) return FDC_ERR_INVALID;
+    if (!c->ph_loaded) return fail(c, FDC_ERR_NOT_LOADED, "phantom must be loaded");
+    if (!dose_sum || !history_sumsq || !mean || !sigma || n_histories < 2 || !(frac >= 0.0))
+        return fail(c, FDC_ERR_INVALID, "history stats: bad arguments");
+    FDC_CUDA(c, cudaSetDevice(c->device));
+    const int parts = std::max(1, std::min<int>(c->sm_count * 2, (int)((c->nvox + 255) / 256)));
+    FDC_CUDA(c, c->stats_part.ensure(3 * parts + 1));
+    cudaStream_t st = (cudaStream_t)stream;
+    FDC_CUDA(c, fdc::launch_batch_stats(dose_sum, history_sumsq, (long long)n_histories, 1, c->nvox, frac, mean,
+                                        sigma, c->stats_part.p, parts, c->stats_part.p + 3 * parts, st));
     double r = 0;
     FDC_CUDA(c, cudaMemcpyAsync(&r, c->stats_part.p + 3 * parts, sizeof r, cudaMemcpyDeviceToHost, st));
     FDC_CUDA(c, cudaStreamSynchronize(st));

@@ -43,12 +43,16 @@ struct ReplayArgs {
     const float2 *vox;
     int nx, ny, nz;
     double dx, dy, dz, x0, y0, z0;
+    double x1, y1;            // x0 + nx * dx, y0 + ny * dy (entry test)
+    double idx_, idy_;        // 1 / dx, 1 / dy (entry voxel, FP64)
+    float ihx, ihy, ihz;      // 1 / spacing in FP32 (grid units per cm)
     // beam (device)
     const fdc_spot *spots;
     const unsigned long long *spot_cum;  // [n_spots + 1]
     int n_spots;
     // run
     unsigned long long *tally;  // [n_tallies][nvox], int64 two's complement
+    unsigned long long *sumsq;  // null, or [n_tallies][nvox]: sum of squared voxel visits (2^-28 MeV^2)
     long long nvox;
     int per_layer;
     unsigned long long h_begin, n;  // histories [h_begin, h_begin + n)
@@ -72,12 +76,15 @@ struct FinalizeArgs {
     double *batch_sumsq;     // [nvox] or null: += dose^2
     long long *accum;        // [n_tallies][nvox] or null: += tally
     int zero_after;          // 1: tally := 0 after reading
+    const long long *sumsq;  // [n_tallies][nvox] or null: squared-visit tally ...
+    double *hist_sumsq;      // ... summed over tallies and converted to Gy^2 here
 };
 
 cudaError_t launch_replay(const ReplayArgs &a, const fdc_schedule &s, int fp64, int sm_count,
                           cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeArgs &a, int sm_count, cudaStream_t st);
-cudaError_t launch_batch_stats(const double *sum, const double *sumsq, int n_batches, long long nvox,
+// mode 0: eq. (1) from n batch sums; mode 1: eq. (2) from sums over n histories
+cudaError_t launch_batch_stats(const double *sum, const double *sumsq, long long n, int mode, long long nvox,
                                double frac, double *mean, double *sigma, double *partials,
                                int n_partials, double *result, cudaStream_t st);
 cudaError_t launch_debug_philox(unsigned long long k0, unsigned long long k1,
@@ -86,6 +93,35 @@ cudaError_t launch_debug_philox(unsigned long long k0, unsigned long long k1,
 cudaError_t launch_debug_sample(const ReplayArgs &a, float *xyEpsi, long long *btk,
                                 cudaStream_t st);
 int replay_max_ctas_per_sm(int warps_per_cta, int fp64, int aggregate);
+// Denoiser convolutions (layout in fdc_unet.h).
+struct Conv3dArgs {
+    int batch, in_d, in_h, in_w, out_d, out_h, out_w, c_in, c_out, ksize, stride, pad, relu;
+};
+cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const void *wt, const float *bias,
+                        void *out_bf16, float *out_f32, cudaStream_t st);
+cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy, float *dw, float *db,
+                              cudaStream_t st);
+cudaError_t launch_transpose_weights(const void *w, void *wt, int co, int taps, int ci, cudaStream_t st);
+cudaError_t launch_relu_bwd(const void *y, const void *dy, void *dx, long long n, cudaStream_t st);
+cudaError_t launch_upsample2(const void *x, void *y, int B, int D, int H, int W, int C, int backward,
+                             cudaStream_t st);
+cudaError_t launch_concat(const void *a, int Ca, const void *b, int Cb, void *out, long long rows, int inverse,
+                          cudaStream_t st);
+cudaError_t launch_mse(const float *pred, int C, const float *target, long long rows, void *grad, float *loss,
+                       cudaStream_t st);
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, void *p_bf16, long long n, float lr, float b1,
+                        float b2, float eps, float bc1, float bc2, cudaStream_t st);
+cudaError_t launch_f32_to_bf16(const float *x, void *y, long long n, cudaStream_t st);
+cudaError_t launch_add_bf16(const void *a, const void *b, void *out, long long n, cudaStream_t st);
+cudaError_t launch_prepare(const double *dose, const float *density, const double *dose_high, long long n,
+                           double inv_scale, float density_scale, void *x, float *dose_in, float *target,
+                           cudaStream_t st);
+cudaError_t launch_finish(const float *head, const float *dose_in, long long n, double scale, double *dose_out,
+                          cudaStream_t st);
+cudaError_t launch_gamma(const double *ref, const double *eval, int D, int H, int W, double sd, double sh, double sw,
+                         double dd, double dta, double thr, int radius, float *gamma, unsigned long long *scratch,
+                         cudaStream_t st);
+
 // Static scratch of fdc_run_noalloc (defined in fdc_kernels.cu with the
 // array): device addresses of its parts on the current device, looked up once
 // per device.

@@ -157,11 +157,53 @@ __device__ Start sample_start(const ReplayArgs &P, unsigned long long h) {
 }
 
 // ---------------------------------------------------------------- helpers
+// Step records stream through L2 once per use; loading them with an
+// evict-first L2 policy keeps the L2-resident tally and phantom words from
+// being displaced by the stream.
+#ifndef FDC_RECORD_EVICT_FIRST
+#define FDC_RECORD_EVICT_FIRST 0
+#endif
+// A lane reads its track's records in order, eight to a 128-byte line; when
+// it enters a line, the next line is prefetched into L2 (some eight steps of
+// lead over its use).
+#ifndef FDC_RECORD_PREFETCH
+#define FDC_RECORD_PREFETCH 1
+#endif
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ unsigned long long evict_first_policy() {
+    unsigned long long pol = 0;
+#if FDC_RECORD_EVICT_FIRST
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+#endif
+    return pol;
+}
+
+__device__ __forceinline__ uint4 load_record(const uint4 *p, unsigned long long pol) {
+#if FDC_RECORD_EVICT_FIRST
+    uint4 r;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+#else
+    (void)pol;
+    return __ldg(p);
+#endif
+}
+
 __device__ __forceinline__ void sincos_(float a, float *s, float *c) { sincosf(a, s, c); }
 __device__ __forceinline__ void sincos_(double a, double *s, double *c) { sincos(a, s, c); }
 __device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
 __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
 __device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
+// Reciprocal: hardware approximation in FP32 (relative error ~1e-7, used for
+// segment geometry only), IEEE in FP64.
+__device__ __forceinline__ float rcp_(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ double rcp_(double a) { return 1.0 / a; }
 __device__ __forceinline__ double rsqrt_(double a) { return rsqrt(a); }
 template <typename R> __device__ __forceinline__ R inf_();
 template <> __device__ __forceinline__ float inf_<float>() { return __int_as_float(0x7f800000); }
@@ -202,27 +244,46 @@ __device__ __forceinline__ void tally_add(unsigned long long *tally, long long i
 // into the same tally word are summed in registers and written with one
 // atomic when the lane moves to another word (or finishes the history).
 // Integer sums, so the tally is the same bit for bit.
-template <bool AGG>
+// Energy (MeV) to tally units.  Shares below 2^31 units (8 MeV) take the
+// 32-bit conversion; larger ones the 64-bit one.  Both round to nearest even,
+// so the result equals the 64-bit conversion of the same value.
+__device__ __forceinline__ long long units_of(float scaled) {
+    return fabsf(scaled) < 2147483520.0f ? (long long)__float2int_rn(scaled) : __float2ll_rn(scaled);
+}
+__device__ __forceinline__ long long units_of(double scaled) { return __double2ll_rn(scaled); }
+__device__ __forceinline__ float unit_scale(float) { return kUnitsF; }
+__device__ __forceinline__ double unit_scale(double) { return 268435456.0; }
+
+template <bool AGG, bool SQ>
 struct PendingTally {
-    unsigned long long *addr = nullptr;
+    long long idx = -1;  // tally word (layer offset included)
     long long units = 0;
-    __device__ __forceinline__ void add(unsigned long long *tally, long long idx, long long u) {
-        unsigned long long *const a = tally + idx;
-        if (!FDC_LANE_COALESCE) {
-            if (u) tally_add<AGG>(a, 0, u);
+    __device__ __forceinline__ void add(const ReplayArgs &P, long long i, long long u) {
+        if (!SQ && !FDC_LANE_COALESCE) {
+            if (u) tally_add<AGG>(P.tally, i, u);
             return;
         }
-        if (a == addr) {
+        if (i == idx) {
             units += u;
             return;
         }
-        flush();
-        addr = a;
+        flush(P);
+        idx = i;
         units = u;
     }
-    __device__ __forceinline__ void flush() {
-        if (addr && units) tally_add<AGG>(addr, 0, units);
-        addr = nullptr;
+    // With SQ the pending sum is one whole visit of the history to the voxel;
+    // its square goes to the second tally (2^-28 MeV^2 units):
+    // (u * 2^-14)^2 = u^2 * 2^-28.
+    __device__ __forceinline__ void flush(const ReplayArgs &P) {
+        if (idx >= 0 && units) {
+            tally_add<AGG>(P.tally, idx, units);
+            if (SQ) {
+                const float e = (float)units * 6.103515625e-05f;
+                const long long q = units_of(e * e);
+                if (q) atomicAdd(P.sumsq + idx, (unsigned long long)q);
+            }
+        }
+        idx = -1;
         units = 0;
     }
 };
@@ -238,16 +299,6 @@ __device__ void raise_status(DeviceCounters *c, int code, unsigned long long h) 
 }
 
 // ---------------------------------------------------------------- task 2
-// Energy (MeV) to tally units.  Shares below 2^31 units (8 MeV) take the
-// 32-bit conversion; larger ones the 64-bit one.  Both round to nearest even,
-// so the result equals the 64-bit conversion of the same value.
-__device__ __forceinline__ long long units_of(float scaled) {
-    return fabsf(scaled) < 2147483520.0f ? (long long)__float2int_rn(scaled) : __float2ll_rn(scaled);
-}
-__device__ __forceinline__ long long units_of(double scaled) { return __double2ll_rn(scaled); }
-__device__ __forceinline__ float unit_scale(float) { return kUnitsF; }
-__device__ __forceinline__ double unit_scale(double) { return 268435456.0; }
-
 // sin and cos of a polar deflection.  Below 0.25 rad (almost every step) the
 // Taylor series to theta^9 / theta^10 (truncation < 1e-11); above, sincos.
 template <typename R>
@@ -277,14 +328,18 @@ __device__ __forceinline__ void sincos_phi(unsigned code, double *s, double *c) 
 // faces at integers), which keeps FP32 rounding relative to the voxel rather
 // than to the whole grid; distances along the ray are in cm.  Per-lane
 // counters are updated in place.
-template <typename R, bool AGG>
+template <typename R, bool AGG, bool SQ>
 __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start &st,
                                                unsigned long long h, unsigned long long &steps,
                                                unsigned long long &segs, long long &replayed,
                                                long long &escaped) {
     if (st.k0 >= st.n) return;
     const long long s_first = st.s0 + st.k0, s_end = st.s0 + st.n;
-    uint4 rec = __ldg(P.rec + s_first);
+    const unsigned long long pol = evict_first_policy();
+    uint4 rec = load_record(P.rec + s_first, pol);
+#if FDC_RECORD_PREFETCH
+    if (s_first + 8 < s_end) prefetch_l2(P.rec + ((s_first + 8) & ~7ll));
+#endif
     // energy of the replayed steps, in tally units
     const long long rep = units_of(__uint_as_float(rec.y) * kUnitsF) +
                           units_of(__uint_as_float(rec.z) * kUnitsF) + __ldg(P.tail + s_first);
@@ -292,44 +347,47 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
     // entry on the upstream face; inside test and voxel in FP64 (the
     // per-proton state is FP32, the comparison is exact in FP64)
     const double xe = (double)st.x, ye = (double)st.y;
-    if (!(xe >= P.x0 && xe < P.x0 + P.nx * P.dx && ye >= P.y0 && ye < P.y0 + P.ny * P.dy)) {
+    if (!(xe >= P.x0 && xe < P.x1 && ye >= P.y0 && ye < P.y1)) {
         escaped += rep;  // misses the phantom: the whole history escapes
         return;
     }
-    const double gx = (xe - P.x0) / P.dx, gy = (ye - P.y0) / P.dy;
+    const double gx = (xe - P.x0) * P.idx_, gy = (ye - P.y0) * P.idy_;
     int ix = min((int)floor(gx), P.nx - 1), iy = min((int)floor(gy), P.ny - 1), iz = 0;
     R fx = (R)(gx - ix), fy = (R)(gy - iy), fz = (R)0;
     R dx = (R)0, dy = (R)0, dz = (R)1;
-    const R ihx = (R)(1.0 / P.dx), ihy = (R)(1.0 / P.dy), ihz = (R)(1.0 / P.dz);
-    const long long sy = P.nx, sz = (long long)P.nx * P.ny;
-    long long v = ix + sy * iy;
+    const R ihx = sizeof(R) == 4 ? (R)P.ihx : (R)(1.0 / P.dx);
+    const R ihy = sizeof(R) == 4 ? (R)P.ihy : (R)(1.0 / P.dy);
+    const R ihz = sizeof(R) == 4 ? (R)P.ihz : (R)(1.0 / P.dz);
+    const int sy = P.nx, sz = P.nx * P.ny;  // fewer than 2^31 voxels
+    int v = ix + sy * iy;
     const long long tbase = P.per_layer ? (long long)st.layer * P.nvox : 0ll;
-    unsigned long long *const tally = P.tally + tbase;
     const R psi = (R)st.psi;
     const int seg_cap = P.nx + P.ny + P.nz + 8;
     const R INF = inf_<R>();
     const R US = unit_scale((R)0);
     // material of the current voxel, carried from one step to the next
     float2 sk = __ldg(P.vox + v);
-    PendingTally<AGG> pend;
+    PendingTally<AGG, SQ> pend;
 
     for (long long s = s_first;;) {
         const float dE_f = __uint_as_float(rec.y);
         const R len = (R)__uint_as_float(rec.x), dE = (R)dE_f;
         const long long Qk = units_of(dE_f * kUnitsF);
         const long long Qs = units_of(__uint_as_float(rec.z) * kUnitsF);
-        const R inv_len = (R)1 / len;
+        const R inv_len = rcp_(len);
         const R dEu = dE * inv_len * US;  // tally units per cm of water-equivalent length
         ++steps;
 
         // ray in grid units per cm; distances to the next faces (cm)
         const R rx = dx * ihx, ry = dy * ihy, rz = dz * ihz;
-        const R irx = rx != (R)0 ? (R)1 / rx : INF;
-        const R iry = ry != (R)0 ? (R)1 / ry : INF;
-        const R irz = rz != (R)0 ? (R)1 / rz : INF;
-        const int stx = rx > (R)0 ? 1 : (rx < (R)0 ? -1 : 0);
-        const int sty = ry > (R)0 ? 1 : (ry < (R)0 ? -1 : 0);
-        const int stz = rz > (R)0 ? 1 : (rz < (R)0 ? -1 : 0);
+        // components below 1e-30 grid units per cm never reach a face
+        const R tiny = (R)1e-30;
+        const int stx = rx > tiny ? 1 : (rx < -tiny ? -1 : 0);
+        const int sty = ry > tiny ? 1 : (ry < -tiny ? -1 : 0);
+        const int stz = rz > tiny ? 1 : (rz < -tiny ? -1 : 0);
+        const R irx = stx ? rcp_(rx) : INF;
+        const R iry = sty ? rcp_(ry) : INF;
+        const R irz = stz ? rcp_(rz) : INF;
         R tmx = stx ? ((R)(stx > 0) - fx) * irx : INF;
         R tmy = sty ? ((R)(sty > 0) - fy) * iry : INF;
         R tmz = stz ? ((R)(stz > 0) - fz) * irz : INF;
@@ -358,14 +416,14 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
             ++segs;
             if (wexit >= rem) {  // the step ends in this voxel
                 const long long units = Qk - dep;
-                pend.add(tally, v, units);
+                pend.add(P, tbase + v, units);
                 acc += rem * k2;
-                t += rem / S;
+                t += rem * rcp_(S);
                 break;
             }
             const long long units = units_of(wexit * dEu);
             dep += units;
-            pend.add(tally, v, units);
+            pend.add(P, tbase + v, units);
             acc += wexit * k2;
             rem -= wexit;
             t = tm;
@@ -386,20 +444,23 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
             sk = __ldg(P.vox + v);
         }
         if (gone) {
-            pend.flush();
+            pend.flush(P);
             return;
         }
         // fractional position in the end voxel
         fx = ((R)(ix0 - ix) + fx) + t * rx;
         fy = ((R)(iy0 - iy) + fy) + t * ry;
         fz = ((R)(iz0 - iz) + fz) + t * rz;
-        if (Qs) pend.add(tally, v, Qs);
+        if (Qs) pend.add(P, tbase + v, Qs);
         if (++s >= s_end) {
-            pend.flush();
+            pend.flush(P);
             return;
         }
         const unsigned ang = rec.w;
-        rec = __ldg(P.rec + s);  // next record: issued before the deflection arithmetic
+        rec = load_record(P.rec + s, pol);  // next record: issued before the deflection arithmetic
+#if FDC_RECORD_PREFETCH
+        if ((s & 7) == 0 && s + 8 < s_end) prefetch_l2(P.rec + s + 8);
+#endif
 
         // deflection at the end of the step, scaled by the crossed materials
         const R theta = (R)__half2float(__ushort_as_half((unsigned short)(ang & 0xffffu))) *
@@ -442,7 +503,7 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
 #define FDC_REPLAY_MIN_CTAS 4
 #endif
 
-template <typename R, bool AGG>
+template <typename R, bool AGG, bool SQ>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? FDC_REPLAY_MIN_CTAS : 2)
     replay_kernel(const ReplayArgs P) {
     const unsigned lane = threadIdx.x & 31u;
@@ -459,7 +520,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? FDC_REPLAY_MIN_CTAS : 2)
             if (li < P.n) {
                 const unsigned long long h = P.h_begin + li;
                 const Start st = sample_start(P, h);
-                replay_history<R, AGG>(P, st, h, steps, segs, replayed, escaped);
+                replay_history<R, AGG, SQ>(P, st, h, steps, segs, replayed, escaped);
                 ++hist;
             }
         }
@@ -494,6 +555,12 @@ __global__ void finalize_kernel(const FinalizeArgs A) {
             if (A.zero_after) A.tally[l * A.nvox + v] = 0;
         }
         const double d = (double)tot * f;
+        if (A.hist_sumsq) {
+            long long q = 0;
+            for (int l = 0; l < A.n_tallies; ++l) q += A.sumsq[l * A.nvox + v];
+            // squared tally units are 2^-28 MeV^2; f converts 2^-28 MeV to Gy
+            A.hist_sumsq[v] = (double)q * f * (f * 268435456.0);
+        }
         if (A.dose) A.dose[v] = d;
         if (A.tally_out) A.tally_out[v] = tot;
         if (A.batch_sum) A.batch_sum[v] += d;
@@ -505,15 +572,24 @@ __global__ void finalize_kernel(const FinalizeArgs A) {
 // Eq. (1) per voxel from batch sums, then a deterministic two-level
 // reduction: per-block partials (max of the mean; then masked sum and count
 // of sigma/mean), combined by one block in a fixed order.
-__global__ void stats_pass1(const double *sum, const double *sumsq, int n, long long nvox, double *mean,
-                            double *sigma, double *part_max) {
+// mode 0, eq. (1): n batch doses, sigma = sqrt(sum (D_b - mean)^2 / (n (n-1)));
+// mode 1, eq. (2): n histories, sigma = sqrt((s2/n - mean^2) / (n - 1)).
+__global__ void stats_pass1(const double *sum, const double *sumsq, long long n, int mode, long long nvox,
+                            double *mean, double *sigma, double *part_max) {
     __shared__ double sm[256];
     double mx = 0.0;
+    const double dn = (double)n;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
          v += (long long)gridDim.x * blockDim.x) {
-        const double s = sum[v], m = s / n;
-        const double ss = sumsq[v] - s * s / n;
-        const double sg = sqrt((ss > 0.0 ? ss : 0.0) / ((double)n * (n - 1)));
+        const double s = sum[v], m = s / dn;
+        double sg;
+        if (mode == 0) {
+            const double ss = sumsq[v] - s * s / dn;
+            sg = sqrt((ss > 0.0 ? ss : 0.0) / (dn * (dn - 1.0)));
+        } else {
+            const double var = sumsq[v] / dn - m * m;
+            sg = sqrt((var > 0.0 ? var : 0.0) / (dn - 1.0));
+        }
         mean[v] = m;
         sigma[v] = sg;
         mx = m > mx ? m : mx;
@@ -621,16 +697,16 @@ __global__ void probe_atomics_kernel(unsigned long long *slots, unsigned long lo
     }
 }
 
-template <typename R, bool AGG>
+template <typename R, bool AGG, bool SQ>
 cudaError_t launch_replay_t(const ReplayArgs &a, int ctas, int threads, cudaStream_t st) {
-    replay_kernel<R, AGG><<<ctas, threads, 0, st>>>(a);
+    replay_kernel<R, AGG, SQ><<<ctas, threads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename R, bool AGG>
+template <typename R, bool AGG, bool SQ>
 int max_ctas_t(int threads) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, replay_kernel<R, AGG>, threads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, replay_kernel<R, AGG, SQ>, threads, 0) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
@@ -696,18 +772,21 @@ cudaError_t launch_replay(const ReplayArgs &a, const fdc_schedule &s, int fp64, 
                           cudaStream_t st) {
     const int threads = 32 * s.warps_per_cta;
     const int ctas = sm_count * s.ctas_per_sm;
-    const bool agg = s.aggregate != 2;
-    if (fp64) return agg ? launch_replay_t<double, true>(a, ctas, threads, st)
-                         : launch_replay_t<double, false>(a, ctas, threads, st);
-    return agg ? launch_replay_t<float, true>(a, ctas, threads, st)
-               : launch_replay_t<float, false>(a, ctas, threads, st);
+    if (a.sumsq)  // history-by-history squares: per-visit sums, plain atomics
+        return fp64 ? launch_replay_t<double, false, true>(a, ctas, threads, st)
+                    : launch_replay_t<float, false, true>(a, ctas, threads, st);
+    const bool agg = s.aggregate == 1;
+    if (fp64) return agg ? launch_replay_t<double, true, false>(a, ctas, threads, st)
+                         : launch_replay_t<double, false, false>(a, ctas, threads, st);
+    return agg ? launch_replay_t<float, true, false>(a, ctas, threads, st)
+               : launch_replay_t<float, false, false>(a, ctas, threads, st);
 }
 
 int replay_max_ctas_per_sm(int warps_per_cta, int fp64, int aggregate) {
     const int threads = 32 * warps_per_cta;
-    const bool agg = aggregate != 2;
-    if (fp64) return agg ? max_ctas_t<double, true>(threads) : max_ctas_t<double, false>(threads);
-    return agg ? max_ctas_t<float, true>(threads) : max_ctas_t<float, false>(threads);
+    const bool agg = aggregate == 1;
+    if (fp64) return agg ? max_ctas_t<double, true, false>(threads) : max_ctas_t<double, false, false>(threads);
+    return agg ? max_ctas_t<float, true, false>(threads) : max_ctas_t<float, false, false>(threads);
 }
 
 cudaError_t launch_probe_atomics(unsigned long long *slots, unsigned long long n_slots,
@@ -725,11 +804,11 @@ cudaError_t launch_finalize(const FinalizeArgs &a, int sm_count, cudaStream_t st
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_stats(const double *sum, const double *sumsq, int n_batches, long long nvox,
+cudaError_t launch_batch_stats(const double *sum, const double *sumsq, long long n, int mode, long long nvox,
                                double frac, double *mean, double *sigma, double *partials,
                                int n_partials, double *result, cudaStream_t st) {
     // partials: [3][n_partials]
-    stats_pass1<<<n_partials, 256, 0, st>>>(sum, sumsq, n_batches, nvox, mean, sigma, partials);
+    stats_pass1<<<n_partials, 256, 0, st>>>(sum, sumsq, n, mode, nvox, mean, sigma, partials);
     stats_pass2<<<n_partials, 256, 0, st>>>(mean, sigma, nvox, frac, partials, n_partials,
                                             partials + n_partials, partials + 2 * n_partials);
     stats_pass3<<<1, 32, 0, st>>>(partials + n_partials, partials + 2 * n_partials, n_partials, result);

@@ -1,0 +1,783 @@
+// Kernels of the learned denoiser (3-D U-Net over dose grids): BF16
+// tensor-core convolutions as implicit GEMMs with FP32 accumulation, their
+// data and weight gradients, and the element-wise pieces of the network and
+// its training (ReLU gradient, nearest upsampling, channel concatenation,
+// mean-squared error, Adam).  Activations are channels-last,
+// [batch][d][h][w][c] in BF16; weights [c_out][k^3][c_in].
+//
+// conv_igemm_kernel computes out[r][n] = sum_k A[r][k] * B[n][k] with
+//   forward: r = output voxel, n = output channel, k = (tap, input channel),
+//            A gathered from the input at voxel r * stride - pad + tap;
+//   data gradient: r = input voxel, n = input channel, k = (tap, output
+//            channel), A gathered from the output gradient at
+//            (r + pad - tap) / stride when that divides exactly.
+// Tiles: 128 rows x NT columns per CTA of four warps, K in steps of 16 channels
+// of one tap, operands staged through shared memory with cp.async (zero fill
+// for padding), mma.sync m16n8k16 BF16 -> FP32.
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fdc_internal.h"
+
+namespace fdc {
+namespace {
+
+constexpr int kRows = 128;       // rows (voxels) per CTA
+constexpr int kRowBytes = 48;    // 16 BF16 (32 B) padded to 48 B: conflict-free fragment loads
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
+
+__device__ __forceinline__ void mma_bf16(float c[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned lds32(const unsigned char *p) { return *(const unsigned *)p; }
+
+struct RowCoord {
+    int b, d, h, w;
+    bool valid;
+};
+
+__device__ __forceinline__ RowCoord row_coord(long long r, long long rows, int D, int H, int W) {
+    RowCoord c;
+    c.valid = r < rows;
+    if (!c.valid) r = 0;
+    c.w = (int)(r % W);
+    long long q = r / W;
+    c.h = (int)(q % H);
+    q /= H;
+    c.d = (int)(q % D);
+    c.b = (int)(q / D);
+    return c;
+}
+
+// Source voxel of row c for tap (kd, kh, kw); -1 when outside (padding).
+template <int MODE>
+__device__ __forceinline__ long long src_voxel(const RowCoord &c, int kd, int kh, int kw, const Conv3dArgs &g) {
+    int sd, sh, sw, Ds, Hs, Ws;
+    if (MODE == 0) {
+        Ds = g.in_d; Hs = g.in_h; Ws = g.in_w;
+        sd = c.d * g.stride - g.pad + kd;
+        sh = c.h * g.stride - g.pad + kh;
+        sw = c.w * g.stride - g.pad + kw;
+    } else {
+        Ds = g.out_d; Hs = g.out_h; Ws = g.out_w;
+        int td = c.d + g.pad - kd, th = c.h + g.pad - kh, tw = c.w + g.pad - kw;
+        if (td < 0 || th < 0 || tw < 0 || td % g.stride || th % g.stride || tw % g.stride) return -1;
+        sd = td / g.stride; sh = th / g.stride; sw = tw / g.stride;
+    }
+    if (!c.valid || sd < 0 || sh < 0 || sw < 0 || sd >= Ds || sh >= Hs || sw >= Ws) return -1;
+    return (((long long)c.b * Ds + sd) * Hs + sh) * (long long)Ws + sw;
+}
+
+template <int MODE, int NT>
+__global__ void __launch_bounds__(128) conv_igemm_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
+                                                         const __nv_bfloat16 *wt, const float *bias,
+                                                         __nv_bfloat16 *out_bf16, float *out_f32) {
+    __shared__ __align__(16) unsigned char sA[2][kRows * kRowBytes];
+    __shared__ __align__(16) unsigned char sB[2][NT * kRowBytes];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int grp = lane >> 2, tig = lane & 3;
+    // row space and source channels per mode
+    const int Dr = MODE == 0 ? g.out_d : g.in_d, Hr = MODE == 0 ? g.out_h : g.in_h;
+    const int Wr = MODE == 0 ? g.out_w : g.in_w;
+    const int Cs = MODE == 0 ? g.c_in : g.c_out;   // gathered channels (K per tap)
+    const int Nn = MODE == 0 ? g.c_out : g.c_in;   // output channels
+    const long long rows = (long long)g.batch * Dr * Hr * Wr;
+    const long long r0 = (long long)blockIdx.x * kRows;
+    const int n0 = blockIdx.y * NT;
+    const int taps = g.ksize * g.ksize * g.ksize;
+    const int csteps = Cs / 16;
+    const int ksteps = taps * csteps;
+    // this thread gathers row r0 + tid
+    const RowCoord rc = row_coord(r0 + tid, rows, Dr, Hr, Wr);
+
+    auto load_stage = [&](int buf, int ks) {
+        const int tap = ks / csteps, c0 = (ks % csteps) * 16;
+        const int kd = tap / (g.ksize * g.ksize), kh = (tap / g.ksize) % g.ksize, kw = tap % g.ksize;
+        const long long sv = src_voxel<MODE>(rc, kd, kh, kw, g);
+        const __nv_bfloat16 *p = sv >= 0 ? src + sv * Cs + c0 : src;
+        unsigned char *dst = sA[buf] + tid * kRowBytes;
+        cp_async16(dst, p, sv >= 0);
+        cp_async16(dst + 16, p + 8, sv >= 0);
+        for (int i = tid; i < NT * 2; i += 128) {
+            const int n = i >> 1, half = i & 1;
+            const bool ok = n0 + n < Nn;
+            const __nv_bfloat16 *q = ok ? wt + ((long long)(n0 + n) * taps + tap) * Cs + c0 + half * 8 : wt;
+            cp_async16(sB[buf] + n * kRowBytes + half * 16, q, ok);
+        }
+    };
+
+    float acc[2][NT / 8][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < NT / 8; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+
+    load_stage(0, 0);
+    cp_async_commit();
+    for (int ks = 0; ks < ksteps; ++ks) {
+        const int buf = ks & 1;
+        if (ks + 1 < ksteps) load_stage(buf ^ 1, ks + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const unsigned char *A = sA[buf];
+        const unsigned char *B = sB[buf];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int ra = warp * 32 + mt * 16 + grp;
+            const unsigned a0 = lds32(A + ra * kRowBytes + tig * 4);
+            const unsigned a1 = lds32(A + (ra + 8) * kRowBytes + tig * 4);
+            const unsigned a2 = lds32(A + ra * kRowBytes + 16 + tig * 4);
+            const unsigned a3 = lds32(A + (ra + 8) * kRowBytes + 16 + tig * 4);
+#pragma unroll
+            for (int nt = 0; nt < NT / 8; ++nt) {
+                const int nb = nt * 8 + grp;
+                const unsigned b0 = lds32(B + nb * kRowBytes + tig * 4);
+                const unsigned b1 = lds32(B + nb * kRowBytes + 16 + tig * 4);
+                mma_bf16(acc[mt][nt], a0, a1, a2, a3, b0, b1);
+            }
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+
+    // epilogue: bias, ReLU, store
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const long long r = r0 + warp * 32 + mt * 16 + grp + half * 8;
+            if (r >= rows) continue;
+#pragma unroll
+            for (int nt = 0; nt < NT / 8; ++nt) {
+                const int n = n0 + nt * 8 + tig * 2;
+                if (n >= Nn) continue;
+                float v0 = acc[mt][nt][half * 2], v1 = acc[mt][nt][half * 2 + 1];
+                if (bias) {
+                    v0 += bias[n];
+                    if (n + 1 < Nn) v1 += bias[n + 1];
+                }
+                if (g.relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                if (out_f32) {
+                    out_f32[r * Nn + n] = v0;
+                    if (n + 1 < Nn) out_f32[r * Nn + n + 1] = v1;
+                }
+                if (out_bf16) {
+                    if (n + 1 < Nn) {
+                        *(__nv_bfloat162 *)(out_bf16 + r * Nn + n) = __floats2bfloat162_rn(v0, v1);
+                    } else {
+                        out_bf16[r * Nn + n] = __float2bfloat16_rn(v0);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Weight gradient: dW[co][tap][ci] += sum_v dy[v][co] * x[src(v, tap)][ci]
+// over a chunk of output voxels v, as a GEMM with M = output channels,
+// N = input channels and K = voxels; FP32 partial sums are added atomically.
+constexpr int kWgVox = 16;        // voxels per K step
+constexpr int kWgRowBytes = 144;  // 64 BF16 (128 B) padded to 144 B
+
+__global__ void __launch_bounds__(128) conv_wgrad_kernel(const Conv3dArgs g, const __nv_bfloat16 *x,
+                                                         const __nv_bfloat16 *dy, float *dw, int chunk) {
+    __shared__ __align__(16) unsigned char sDy[2][kWgVox * kWgRowBytes];
+    __shared__ __align__(16) unsigned char sX[2][kWgVox * kWgRowBytes];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int grp = lane >> 2, tig = lane & 3;
+    const int taps = g.ksize * g.ksize * g.ksize;
+    const int tap = blockIdx.y;
+    const int kd = tap / (g.ksize * g.ksize), kh = (tap / g.ksize) % g.ksize, kw = tap % g.ksize;
+    const int co_tiles = (g.c_out + 63) / 64;
+    const int co0 = (blockIdx.x % co_tiles) * 64, ci0 = (blockIdx.x / co_tiles) * 64;
+    const long long rows = (long long)g.batch * g.out_d * g.out_h * g.out_w;
+    const long long v_begin = (long long)blockIdx.z * chunk;
+    long long v_end = v_begin + chunk;
+    if (v_end > rows) v_end = rows;
+    const int ksteps = (int)((v_end - v_begin + kWgVox - 1) / kWgVox);
+
+    // 16 voxels x 64 channels per operand: 128 chunks of 16 B each
+    auto load_stage = [&](int buf, int ks) {
+        const int vi = tid >> 3, part = tid & 7;  // voxel row, 8-channel part
+        const long long v = v_begin + (long long)ks * kWgVox + vi;
+        const bool vin = v < v_end;
+        // dy row
+        const int co = co0 + part * 8;
+        const bool okd = vin && co < g.c_out;
+        cp_async16(sDy[buf] + vi * kWgRowBytes + part * 16, okd ? dy + v * g.c_out + co : dy, okd);
+        // x at the tap's source voxel
+        long long sv = -1;
+        if (vin) {
+            const RowCoord rc = row_coord(v, rows, g.out_d, g.out_h, g.out_w);
+            sv = src_voxel<0>(rc, kd, kh, kw, g);
+        }
+        const int ci = ci0 + part * 8;
+        const bool okx = sv >= 0 && ci < g.c_in;
+        cp_async16(sX[buf] + vi * kWgRowBytes + part * 16, okx ? x + sv * g.c_in + ci : x, okx);
+    };
+    auto ld16 = [](const unsigned char *base, int row, int col) -> unsigned {
+        return (unsigned)*(const unsigned short *)(base + row * kWgRowBytes + col * 2);
+    };
+
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[j][k] = 0.f;
+    if (ksteps > 0) {
+        load_stage(0, 0);
+        cp_async_commit();
+    }
+    for (int ks = 0; ks < ksteps; ++ks) {
+        const int buf = ks & 1;
+        if (ks + 1 < ksteps) load_stage(buf ^ 1, ks + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const unsigned char *Dy = sDy[buf];
+        const unsigned char *X = sX[buf];
+        // A[m = co][k = v]: warp rows co = warp * 16 + grp (+8); k = 2 tig (+1), (+8)
+        const int m = warp * 16 + grp;
+        const int k = tig * 2;
+        const unsigned a0 = ld16(Dy, k, m) | (ld16(Dy, k + 1, m) << 16);
+        const unsigned a1 = ld16(Dy, k, m + 8) | (ld16(Dy, k + 1, m + 8) << 16);
+        const unsigned a2 = ld16(Dy, k + 8, m) | (ld16(Dy, k + 9, m) << 16);
+        const unsigned a3 = ld16(Dy, k + 8, m + 8) | (ld16(Dy, k + 9, m + 8) << 16);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int n = nt * 8 + grp;
+            const unsigned b0 = ld16(X, k, n) | (ld16(X, k + 1, n) << 16);
+            const unsigned b1 = ld16(X, k + 8, n) | (ld16(X, k + 9, n) << 16);
+            mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int co = co0 + warp * 16 + grp + half * 8;
+            const int ci = ci0 + nt * 8 + tig * 2;
+            if (co >= g.c_out) continue;
+            float *p = dw + ((long long)co * taps + tap) * g.c_in + ci;
+            if (ci < g.c_in && acc[nt][half * 2] != 0.f) atomicAdd(p, acc[nt][half * 2]);
+            if (ci + 1 < g.c_in && acc[nt][half * 2 + 1] != 0.f) atomicAdd(p + 1, acc[nt][half * 2 + 1]);
+        }
+    }
+}
+
+// db[c] += sum over rows of dy[row][c]
+__global__ void bias_grad_kernel(const __nv_bfloat16 *dy, long long rows, int C, float *db, int chunk) {
+    const int c = threadIdx.x % C;
+    const int lanes = blockDim.x / C;
+    const int sub = threadIdx.x / C;
+    if (sub >= lanes) return;
+    const long long r0 = (long long)blockIdx.x * chunk;
+    long long r1 = r0 + chunk;
+    if (r1 > rows) r1 = rows;
+    float s = 0.f;
+    for (long long r = r0 + sub; r < r1; r += lanes) s += __bfloat162float(dy[r * C + c]);
+    atomicAdd(db + c, s);
+}
+
+// [ci][tap][co] <- [co][tap][ci]
+__global__ void transpose_weights_kernel(const __nv_bfloat16 *w, __nv_bfloat16 *wt, int co_n, int taps, int ci_n) {
+    const long long n = (long long)co_n * taps * ci_n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)(i % ci_n);
+        const long long q = i / ci_n;
+        const int tap = (int)(q % taps), co = (int)(q / taps);
+        wt[((long long)ci * taps + tap) * co_n + co] = w[i];
+    }
+}
+
+__global__ void relu_bwd_kernel(const __nv_bfloat16 *y, const __nv_bfloat16 *dy, __nv_bfloat16 *dx, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dx[i] = __bfloat162float(y[i]) > 0.f ? dy[i] : __float2bfloat16_rn(0.f);
+}
+
+// nearest x2 upsampling of [b][d][h][w][c] to [b][2d][2h][2w][c]
+__global__ void upsample2_fwd_kernel(const __nv_bfloat16 *x, __nv_bfloat16 *y, int B, int D, int H, int W, int C) {
+    const long long n = (long long)B * 8 * D * H * W * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long q = i / C;
+        const int w = (int)(q % (2 * W)); q /= 2 * W;
+        const int h = (int)(q % (2 * H)); q /= 2 * H;
+        const int d = (int)(q % (2 * D));
+        const int b = (int)(q / (2 * D));
+        y[i] = x[((((long long)b * D + d / 2) * H + h / 2) * W + w / 2) * C + c];
+    }
+}
+
+__global__ void upsample2_bwd_kernel(const __nv_bfloat16 *dy, __nv_bfloat16 *dx, int B, int D, int H, int W, int C) {
+    const long long n = (long long)B * D * H * W * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long q = i / C;
+        const int w = (int)(q % W); q /= W;
+        const int h = (int)(q % H); q /= H;
+        const int d = (int)(q % D);
+        const int b = (int)(q / D);
+        float s = 0.f;
+        for (int k = 0; k < 8; ++k) {
+            const int dd = 2 * d + (k >> 2), hh = 2 * h + ((k >> 1) & 1), ww = 2 * w + (k & 1);
+            s += __bfloat162float(dy[((((long long)b * 2 * D + dd) * 2 * H + hh) * 2 * W + ww) * C + c]);
+        }
+        dx[i] = __float2bfloat16_rn(s);
+    }
+}
+
+// out[r] = [a[r] | b[r]] along channels; split is the inverse (with da, db)
+__global__ void concat_kernel(const __nv_bfloat16 *a, int Ca, const __nv_bfloat16 *b, int Cb, __nv_bfloat16 *out,
+                              long long rows, int inverse) {
+    const int C = Ca + Cb;
+    const long long n = rows * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / C;
+        const int c = (int)(i % C);
+        if (!inverse) {
+            out[i] = c < Ca ? a[r * Ca + c] : b[r * Cb + (c - Ca)];
+        } else {
+            if (c < Ca) ((__nv_bfloat16 *)a)[r * Ca + c] = out[i];
+            else ((__nv_bfloat16 *)b)[r * Cb + (c - Ca)] = out[i];
+        }
+    }
+}
+
+// Mean squared error over rows of channel 0 of pred[rows][C] (FP32) against
+// target[rows]; writes the BF16 gradient [rows][C] (zero outside channel 0)
+// and adds the loss to *loss (per-block partial sums).
+__global__ void mse_kernel(const float *pred, int C, const float *target, long long rows, float scale,
+                           __nv_bfloat16 *grad, float *loss) {
+    __shared__ float sm[256];
+    float s = 0.f;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
+        const float e = pred[r * C] - target[r];
+        s += e * e;
+        if (grad) {
+            grad[r * C] = __float2bfloat16_rn(2.f * e * scale);
+            for (int c = 1; c < C; ++c) grad[r * C + c] = __float2bfloat16_rn(0.f);
+        }
+    }
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, sm[0] * scale);
+}
+
+// Adam (Kingma & Ba) on FP32 master weights; writes the BF16 copy.
+__global__ void adam_kernel(float *p, const float *g, float *m, float *v, __nv_bfloat16 *p_bf16, long long n,
+                            float lr, float b1, float b2, float eps, float bc1, float bc2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float upd = lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        const float pi = p[i] - upd;
+        p[i] = pi;
+        if (p_bf16) p_bf16[i] = __float2bfloat16_rn(pi);
+    }
+}
+
+__global__ void f32_to_bf16_kernel(const float *x, __nv_bfloat16 *y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+__global__ void add_bf16_kernel(const __nv_bfloat16 *a, const __nv_bfloat16 *b, __nv_bfloat16 *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(__bfloat162float(a[i]) + __bfloat162float(b[i]));
+}
+
+// Network input [n][16]: channel 0 = dose / dose_scale, channel 1 = density *
+// density_scale, the rest zero; dose_in keeps channel 0 in FP32 and, with a
+// high-history dose, target = dose_high / dose_scale - dose_in (the network
+// predicts the correction to its input).
+__global__ void prepare_kernel(const double *dose, const float *density, const double *dose_high, long long n,
+                               double inv_scale, float density_scale, __nv_bfloat16 *x, float *dose_in,
+                               float *target) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float d = (float)(dose[i] * inv_scale);
+        dose_in[i] = d;
+        __nv_bfloat16 *row = x + i * 16;
+        row[0] = __float2bfloat16_rn(d);
+        row[1] = __float2bfloat16_rn(density[i] * density_scale);
+        for (int c = 2; c < 16; ++c) row[c] = __float2bfloat16_rn(0.f);
+        if (target) target[i] = (float)(dose_high[i] * inv_scale) - d;
+    }
+}
+
+__global__ void finish_kernel(const float *head, const float *dose_in, long long n, double scale, double *dose_out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = ((double)head[i * 16] + (double)dose_in[i]) * scale;
+        dose_out[i] = v > 0.0 ? v : 0.0;
+    }
+}
+
+// ---- gamma index (Low et al. 1998), global dose difference
+// gamma(v) = min over evaluated points u within the search radius of
+// sqrt(|u - v|^2 / dta^2 + (eval(u) - ref(v))^2 / (dd * ref_max)^2),
+// for reference voxels with ref(v) > threshold * ref_max.
+__global__ void max_kernel(const double *x, long long n, unsigned long long *out) {
+    __shared__ double sm[256];
+    double m = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmax(m, x[i]);
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+        __syncthreads();
+    }
+    // non-negative doubles order like their bit patterns
+    if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(sm[0]));
+}
+
+__global__ void gamma_kernel(const double *ref, const double *eval, int D, int H, int W, double sd, double sh,
+                             double sw, double dd, double dta, double thr, int radius,
+                             const unsigned long long *ref_max_bits, float *gamma, unsigned long long *counts) {
+    const double ref_max = __longlong_as_double((long long)*ref_max_bits);
+    const double dmax = dd * ref_max;
+    const long long n = (long long)D * H * W;
+    unsigned long long evaluated = 0, passed = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double r = ref[i];
+        if (!(r > thr * ref_max)) {
+            if (gamma) gamma[i] = -1.f;
+            continue;
+        }
+        const int w = (int)(i % W), h = (int)((i / W) % H), d = (int)(i / ((long long)W * H));
+        double best = 1e300;
+        for (int a = -radius; a <= radius; ++a) {
+            const int dz = d + a;
+            if (dz < 0 || dz >= D) continue;
+            for (int b = -radius; b <= radius; ++b) {
+                const int hy = h + b;
+                if (hy < 0 || hy >= H) continue;
+                for (int c = -radius; c <= radius; ++c) {
+                    const int wx = w + c;
+                    if (wx < 0 || wx >= W) continue;
+                    const double dist2 = (a * sd) * (a * sd) + (b * sh) * (b * sh) + (c * sw) * (c * sw);
+                    const double de = eval[((long long)dz * H + hy) * W + wx] - r;
+                    const double g2 = dist2 / (dta * dta) + de * de / (dmax * dmax);
+                    best = fmin(best, g2);
+                }
+            }
+        }
+        const double gm = sqrt(best);
+        if (gamma) gamma[i] = (float)gm;
+        ++evaluated;
+        if (gm <= 1.0) ++passed;
+    }
+    atomicAdd(counts, evaluated);
+    atomicAdd(counts + 1, passed);
+}
+
+int grid_for(long long n, int threads = 256) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 16384) b = 16384;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const void *wt, const float *bias,
+                        void *out_bf16, float *out_f32, cudaStream_t st) {
+    const int Nn = mode == 0 ? g.c_out : g.c_in;
+    const long long rows = (long long)g.batch * (mode == 0 ? (long long)g.out_d * g.out_h * g.out_w
+                                                          : (long long)g.in_d * g.in_h * g.in_w);
+    const int nt = Nn >= 64 ? 64 : (Nn >= 32 ? 32 : 16);
+    dim3 grid((unsigned)((rows + kRows - 1) / kRows), (unsigned)((Nn + nt - 1) / nt));
+    auto s = (const __nv_bfloat16 *)src;
+    auto w = (const __nv_bfloat16 *)wt;
+    auto ob = (__nv_bfloat16 *)out_bf16;
+    if (mode == 0) {
+        if (nt == 64) conv_igemm_kernel<0, 64><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32);
+        else if (nt == 32) conv_igemm_kernel<0, 32><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32);
+        else conv_igemm_kernel<0, 16><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32);
+    } else {
+        if (nt == 64) conv_igemm_kernel<1, 64><<<grid, 128, 0, st>>>(g, s, w, nullptr, ob, out_f32);
+        else if (nt == 32) conv_igemm_kernel<1, 32><<<grid, 128, 0, st>>>(g, s, w, nullptr, ob, out_f32);
+        else conv_igemm_kernel<1, 16><<<grid, 128, 0, st>>>(g, s, w, nullptr, ob, out_f32);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy, float *dw, float *db,
+                              cudaStream_t st) {
+    const long long rows = (long long)g.batch * g.out_d * g.out_h * g.out_w;
+    const int taps = g.ksize * g.ksize * g.ksize;
+    const int tiles = ((g.c_out + 63) / 64) * ((g.c_in + 63) / 64);
+    // enough CTAs to fill the GPU, K chunks of whole 16-voxel steps
+    long long chunks = (152ll * 16 + (long long)tiles * taps - 1) / ((long long)tiles * taps);
+    if (chunks < 1) chunks = 1;
+    long long chunk = (rows + chunks - 1) / chunks;
+    chunk = ((chunk + kWgVox - 1) / kWgVox) * kWgVox;
+    if (chunk < 256) chunk = 256;
+    chunks = (rows + chunk - 1) / chunk;
+    dim3 grid((unsigned)tiles, (unsigned)taps, (unsigned)chunks);
+    conv_wgrad_kernel<<<grid, 128, 0, st>>>(g, (const __nv_bfloat16 *)x, (const __nv_bfloat16 *)dy, dw, (int)chunk);
+    if (db) {
+        const int C = g.c_out;
+        const int threads = (256 / C) * C;
+        const int ch = 4096;
+        bias_grad_kernel<<<(unsigned)((rows + ch - 1) / ch), threads, 0, st>>>((const __nv_bfloat16 *)dy, rows, C, db,
+                                                                                ch);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_weights(const void *w, void *wt, int co, int taps, int ci, cudaStream_t st) {
+    const long long n = (long long)co * taps * ci;
+    transpose_weights_kernel<<<grid_for(n), 256, 0, st>>>((const __nv_bfloat16 *)w, (__nv_bfloat16 *)wt, co, taps, ci);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relu_bwd(const void *y, const void *dy, void *dx, long long n, cudaStream_t st) {
+    relu_bwd_kernel<<<grid_for(n), 256, 0, st>>>((const __nv_bfloat16 *)y, (const __nv_bfloat16 *)dy,
+                                                 (__nv_bfloat16 *)dx, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upsample2(const void *x, void *y, int B, int D, int H, int W, int C, int backward,
+                             cudaStream_t st) {
+    const long long n = (long long)B * D * H * W * C * (backward ? 1 : 8);
+    if (backward)
+        upsample2_bwd_kernel<<<grid_for(n), 256, 0, st>>>((const __nv_bfloat16 *)x, (__nv_bfloat16 *)y, B, D, H, W, C);
+    else
+        upsample2_fwd_kernel<<<grid_for(n), 256, 0, st>>>((const __nv_bfloat16 *)x, (__nv_bfloat16 *)y, B, D, H, W, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_concat(const void *a, int Ca, const void *b, int Cb, void *out, long long rows, int inverse,
+                          cudaStream_t st) {
+    concat_kernel<<<grid_for(rows * (Ca + Cb)), 256, 0, st>>>((const __nv_bfloat16 *)a, Ca, (const __nv_bfloat16 *)b,
+                                                             Cb, (__nv_bfloat16 *)out, rows, inverse);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mse(const float *pred, int C, const float *target, long long rows, void *grad, float *loss,
+                       cudaStream_t st) {
+    mse_kernel<<<grid_for(rows), 256, 0, st>>>(pred, C, target, rows, 1.0f / (float)rows, (__nv_bfloat16 *)grad, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, void *p_bf16, long long n, float lr, float b1,
+                        float b2, float eps, float bc1, float bc2, cudaStream_t st) {
+    adam_kernel<<<grid_for(n), 256, 0, st>>>(p, g, m, v, (__nv_bfloat16 *)p_bf16, n, lr, b1, b2, eps, bc1, bc2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_bf16(const void *a, const void *b, void *out, long long n, cudaStream_t st) {
+    add_bf16_kernel<<<grid_for(n), 256, 0, st>>>((const __nv_bfloat16 *)a, (const __nv_bfloat16 *)b,
+                                                 (__nv_bfloat16 *)out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare(const double *dose, const float *density, const double *dose_high, long long n,
+                           double inv_scale, float density_scale, void *x, float *dose_in, float *target,
+                           cudaStream_t st) {
+    prepare_kernel<<<grid_for(n), 256, 0, st>>>(dose, density, dose_high, n, inv_scale, density_scale,
+                                                (__nv_bfloat16 *)x, dose_in, target);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const float *head, const float *dose_in, long long n, double scale, double *dose_out,
+                          cudaStream_t st) {
+    finish_kernel<<<grid_for(n), 256, 0, st>>>(head, dose_in, n, scale, dose_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gamma(const double *ref, const double *eval, int D, int H, int W, double sd, double sh, double sw,
+                         double dd, double dta, double thr, int radius, float *gamma, unsigned long long *scratch,
+                         cudaStream_t st) {
+    const long long n = (long long)D * H * W;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 3 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    max_kernel<<<grid_for(n), 256, 0, st>>>(ref, n, scratch);
+    gamma_kernel<<<grid_for(n, 128), 128, 0, st>>>(ref, eval, D, H, W, sd, sh, sw, dd, dta, thr, radius, scratch,
+                                                  gamma, scratch + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_bf16(const float *x, void *y, long long n, cudaStream_t st) {
+    f32_to_bf16_kernel<<<grid_for(n), 256, 0, st>>>(x, (__nv_bfloat16 *)y, n);
+    return cudaGetLastError();
+}
+
+}  // namespace fdc
+
+// ---------------------------------------------------------------- C ABI
+#include <cmath>
+
+#include "fdc_unet.h"
+
+namespace {
+
+bool conv_ok(const fdc_conv3d *g) {
+    if (!g || g->batch < 1 || g->c_in < 16 || g->c_out < 16 || g->c_in % 16 || g->c_out % 16) return false;
+    if (g->ksize < 1 || g->ksize > 3 || g->stride < 1 || g->pad < 0) return false;
+    const int in[3] = {g->in_d, g->in_h, g->in_w}, out[3] = {g->out_d, g->out_h, g->out_w};
+    for (int a = 0; a < 3; ++a) {
+        if (in[a] < 1 || out[a] < 1) return false;
+        if (out[a] != (in[a] + 2 * g->pad - g->ksize) / g->stride + 1) return false;
+    }
+    return true;
+}
+
+fdc::Conv3dArgs to_args(const fdc_conv3d *g) {
+    fdc::Conv3dArgs a;
+    a.batch = g->batch;
+    a.in_d = g->in_d; a.in_h = g->in_h; a.in_w = g->in_w;
+    a.out_d = g->out_d; a.out_h = g->out_h; a.out_w = g->out_w;
+    a.c_in = g->c_in; a.c_out = g->c_out;
+    a.ksize = g->ksize; a.stride = g->stride; a.pad = g->pad; a.relu = g->relu ? 1 : 0;
+    return a;
+}
+
+int rc(cudaError_t e) { return e == cudaSuccess ? FDC_OK : FDC_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+int fdc_conv3d_forward(const fdc_conv3d *g, const void *x, const void *w, const float *bias, void *y_bf16,
+                       float *y_f32, void *stream) {
+    if (!conv_ok(g) || !x || !w || (!y_bf16 && !y_f32)) return FDC_ERR_INVALID;
+    return rc(fdc::launch_conv(to_args(g), 0, x, w, bias, y_bf16, y_f32, (cudaStream_t)stream));
+}
+
+int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_t, void *dx, void *stream) {
+    if (!conv_ok(g) || !dy || !w_t || !dx) return FDC_ERR_INVALID;
+    fdc::Conv3dArgs a = to_args(g);
+    a.relu = 0;
+    return rc(fdc::launch_conv(a, 1, dy, w_t, nullptr, dx, nullptr, (cudaStream_t)stream));
+}
+
+int fdc_conv3d_backward_weights(const fdc_conv3d *g, const void *x, const void *dy, float *dw, float *db,
+                                void *stream) {
+    if (!conv_ok(g) || !x || !dy || !dw) return FDC_ERR_INVALID;
+    return rc(fdc::launch_conv_wgrad(to_args(g), x, dy, dw, db, (cudaStream_t)stream));
+}
+
+int fdc_conv3d_transpose_weights(const fdc_conv3d *g, const void *w, void *w_t, void *stream) {
+    if (!conv_ok(g) || !w || !w_t) return FDC_ERR_INVALID;
+    return rc(fdc::launch_transpose_weights(w, w_t, g->c_out, g->ksize * g->ksize * g->ksize, g->c_in,
+                                            (cudaStream_t)stream));
+}
+
+int fdc_relu_backward(const void *y, const void *dy, void *dx, int64_t n, void *stream) {
+    if (!y || !dy || !dx || n < 0) return FDC_ERR_INVALID;
+    if (!n) return FDC_OK;
+    return rc(fdc::launch_relu_bwd(y, dy, dx, n, (cudaStream_t)stream));
+}
+
+int fdc_upsample2(const void *x, void *y, int32_t b, int32_t d, int32_t h, int32_t w, int32_t c, int32_t backward,
+                  void *stream) {
+    if (!x || !y || b < 1 || d < 1 || h < 1 || w < 1 || c < 1) return FDC_ERR_INVALID;
+    return rc(fdc::launch_upsample2(x, y, b, d, h, w, c, backward, (cudaStream_t)stream));
+}
+
+int fdc_concat_channels(void *a, int32_t ca, void *b, int32_t cb, void *out, int64_t rows, int32_t split,
+                        void *stream) {
+    if (!a || !b || !out || ca < 1 || cb < 1 || rows < 0) return FDC_ERR_INVALID;
+    if (!rows) return FDC_OK;
+    return rc(fdc::launch_concat(a, ca, b, cb, out, rows, split, (cudaStream_t)stream));
+}
+
+int fdc_mse(const float *pred, int32_t c, const float *target, int64_t rows, void *grad, float *loss, void *stream) {
+    if (!pred || !target || !loss || c < 1 || rows < 1) return FDC_ERR_INVALID;
+    return rc(fdc::launch_mse(pred, c, target, rows, grad, loss, (cudaStream_t)stream));
+}
+
+int fdc_adam(float *p, const float *g, float *m, float *v, void *p_bf16, int64_t n, float lr, float beta1,
+             float beta2, float eps, int32_t step, void *stream) {
+    if (!p || !g || !m || !v || n < 0 || step < 1 || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) ||
+        !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+        return FDC_ERR_INVALID;
+    if (!n) return FDC_OK;
+    const float bc1 = 1.0f - powf(beta1, (float)step), bc2 = 1.0f - powf(beta2, (float)step);
+    return rc(fdc::launch_adam(p, g, m, v, p_bf16, n, lr, beta1, beta2, eps, bc1, bc2, (cudaStream_t)stream));
+}
+
+int fdc_add_bf16(const void *a, const void *b, void *out, int64_t n, void *stream) {
+    if (!a || !b || !out || n < 0) return FDC_ERR_INVALID;
+    if (!n) return FDC_OK;
+    return rc(fdc::launch_add_bf16(a, b, out, n, (cudaStream_t)stream));
+}
+
+int fdc_unet_prepare(const double *dose, const float *density, const double *dose_high, int64_t n,
+                     double dose_scale, float density_scale, void *x, float *dose_in, float *target,
+                     void *stream) {
+    if (!dose || !density || !x || !dose_in || n < 1 || !(dose_scale > 0) || (target && !dose_high))
+        return FDC_ERR_INVALID;
+    return rc(fdc::launch_prepare(dose, density, dose_high, n, 1.0 / dose_scale, density_scale, x, dose_in,
+                                  target, (cudaStream_t)stream));
+}
+
+int fdc_unet_finish(const float *head, const float *dose_in, int64_t n, double dose_scale, double *dose_out,
+                    void *stream) {
+    if (!head || !dose_in || !dose_out || n < 1 || !(dose_scale > 0)) return FDC_ERR_INVALID;
+    return rc(fdc::launch_finish(head, dose_in, n, dose_scale, dose_out, (cudaStream_t)stream));
+}
+
+int fdc_gamma(const double *ref, const double *eval, int32_t d, int32_t h, int32_t w, double sd, double sh, double sw,
+              double dose_frac, double dta, double threshold, float *gamma, uint64_t *scratch, double *pass_rate,
+              void *stream) {
+    if (!ref || !eval || !scratch || d < 1 || h < 1 || w < 1 || !(sd > 0 && sh > 0 && sw > 0) ||
+        !(dose_frac > 0) || !(dta > 0) || !(threshold >= 0))
+        return FDC_ERR_INVALID;
+    const double smin = std::fmin(sd, std::fmin(sh, sw));
+    int radius = (int)std::ceil(1.5 * dta / smin);
+    if (radius > 8) radius = 8;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = fdc::launch_gamma(ref, eval, d, h, w, sd, sh, sw, dose_frac, dta, threshold, radius, gamma,
+                                      (unsigned long long *)scratch, st);
+    if (e != cudaSuccess) return FDC_ERR_CUDA;
+    if (pass_rate) {
+        unsigned long long c[3];
+        if (cudaMemcpyAsync(c, scratch, sizeof c, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return FDC_ERR_CUDA;
+        *pass_rate = c[1] ? (double)c[2] / (double)c[1] : 0.0;
+    }
+    return FDC_OK;
+}
+
+int fdc_f32_to_bf16(const float *x, void *y, int64_t n, void *stream) {
+    if (!x || !y || n < 0) return FDC_ERR_INVALID;
+    if (!n) return FDC_OK;
+    return rc(fdc::launch_f32_to_bf16(x, y, n, (cudaStream_t)stream));
+}
+
+}  // extern "C"

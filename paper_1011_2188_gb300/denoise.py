@@ -1,0 +1,420 @@
+"""Learned denoiser: a 3-D U-Net from a low-history dose (plus density) to a
+high-history dose, trained and run with the library's own kernels
+(include/fdc_unet.h).  Not part of the paper: the track-repeating engine
+generates its training pairs and remains both the fallback and the judge of
+its error.
+
+Network (channels-last BF16 activations, FP32 master weights):
+  level 1 (full grid, 16 ch): 2 x conv3 -> skip s1
+  down (conv 2^3, stride 2) to 32 ch, 2 x conv3 -> s2; to 64 ch -> s3; to 128 ch
+  bottleneck: 2 x conv3 (128)
+  up: nearest x2, conv3 to half the channels, concatenate the skip, 2 x conv3
+  head: conv 1^3 to 16 ch; channel 0 is the correction added to the input dose.
+All convolutions but the head apply ReLU.  Loss: mean squared error of the
+corrected dose against the high-history dose (both divided by the input
+dose's maximum).  Optimiser: Adam.
+
+Torch provides device memory and the stream only; every arithmetic step is a
+library kernel.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import fdc
+
+
+class Conv3d(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("batch", "in_d", "in_h", "in_w", "out_d", "out_h", "out_w", "c_in",
+                                           "c_out", "ksize", "stride", "pad", "relu")]
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _s(stream=None):
+    import torch
+    return C.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+
+
+def _ok(rc, what):
+    if rc:
+        raise fdc.FdcError(rc, what)
+
+
+class ConvLayer:
+    """One convolution with its parameters, gradients and Adam moments."""
+
+    def __init__(self, cin, cout, k, stride, pad, relu, rng, device, cin_real=None, f32_out=False):
+        import torch
+        self.cin, self.cout, self.k, self.stride, self.pad, self.relu = cin, cout, k, stride, pad, relu
+        self.f32_out = f32_out
+        fan_in = k ** 3 * (cin_real or cin)
+        w = rng.normal(0.0, math.sqrt(2.0 / fan_in), size=(cout, k, k, k, cin)).astype(np.float32)
+        if cin_real:
+            w[..., cin_real:] = 0.0
+        if f32_out:
+            w *= 0.1
+        self.dev = device
+        self.w32 = torch.from_numpy(w).to(device)
+        self.b32 = torch.zeros(cout, dtype=torch.float32, device=device)
+        self.w16 = torch.empty(self.w32.shape, dtype=torch.bfloat16, device=device)
+        self.wt16 = torch.empty((cin, k, k, k, cout), dtype=torch.bfloat16, device=device)
+        self.gw = torch.zeros_like(self.w32)
+        self.gb = torch.zeros_like(self.b32)
+        self.mw, self.vw = torch.zeros_like(self.w32), torch.zeros_like(self.w32)
+        self.mb, self.vb = torch.zeros_like(self.b32), torch.zeros_like(self.b32)
+        self.sync_weights()
+
+    def geom(self, shape):
+        B, D, H, W, _ = shape
+        o = [(n + 2 * self.pad - self.k) // self.stride + 1 for n in (D, H, W)]
+        return Conv3d(B, D, H, W, o[0], o[1], o[2], self.cin, self.cout, self.k, self.stride, self.pad,
+                      1 if self.relu else 0), (B, o[0], o[1], o[2], self.cout)
+
+    def sync_weights(self):
+        L = fdc.lib()
+        n = self.w32.numel()
+        _ok(L.fdc_f32_to_bf16(_p(self.w32), _p(self.w16), n, _s()), "f32_to_bf16")
+        g, _ = self.geom((1, 8, 8, 8, self.cin))
+        _ok(L.fdc_conv3d_transpose_weights(C.byref(g), _p(self.w16), _p(self.wt16), _s()), "transpose")
+
+    def forward(self, x, keep=True):
+        import torch
+        g, oshape = self.geom(tuple(x.shape))
+        if self.f32_out:
+            y = torch.empty(oshape, dtype=torch.float32, device=self.dev)
+            _ok(fdc.lib().fdc_conv3d_forward(C.byref(g), _p(x), _p(self.w16), _p(self.b32), None, _p(y), _s()),
+                "conv forward")
+        else:
+            y = torch.empty(oshape, dtype=torch.bfloat16, device=self.dev)
+            _ok(fdc.lib().fdc_conv3d_forward(C.byref(g), _p(x), _p(self.w16), _p(self.b32), _p(y), None, _s()),
+                "conv forward")
+        if keep:
+            self.x, self.y = x, y
+        return y
+
+    def backward(self, dy, need_dx=True):
+        import torch
+        L = fdc.lib()
+        g, _ = self.geom(tuple(self.x.shape))
+        if self.relu:
+            d = torch.empty_like(dy)
+            _ok(L.fdc_relu_backward(_p(self.y), _p(dy), _p(d), dy.numel(), _s()), "relu backward")
+            dy = d
+        _ok(L.fdc_conv3d_backward_weights(C.byref(g), _p(self.x), _p(dy), _p(self.gw), _p(self.gb), _s()),
+            "conv wgrad")
+        dx = None
+        if need_dx:
+            dx = torch.empty(self.x.shape, dtype=torch.bfloat16, device=self.dev)
+            _ok(L.fdc_conv3d_backward_data(C.byref(g), _p(dy), _p(self.wt16), _p(dx), _s()), "conv dgrad")
+        self.x = self.y = None
+        return dx
+
+    def zero_grad(self):
+        self.gw.zero_()
+        self.gb.zero_()
+
+    def step(self, lr, t, b1=0.9, b2=0.999, eps=1e-8):
+        L = fdc.lib()
+        _ok(L.fdc_adam(_p(self.w32), _p(self.gw), _p(self.mw), _p(self.vw), _p(self.w16), self.w32.numel(),
+                       lr, b1, b2, eps, t, _s()), "adam")
+        _ok(L.fdc_adam(_p(self.b32), _p(self.gb), _p(self.mb), _p(self.vb), None, self.b32.numel(),
+                       lr, b1, b2, eps, t, _s()), "adam")
+        g, _ = self.geom((1, 8, 8, 8, self.cin))
+        _ok(L.fdc_conv3d_transpose_weights(C.byref(g), _p(self.w16), _p(self.wt16), _s()), "transpose")
+
+    def state(self):
+        return {"w": self.w32.cpu().numpy(), "b": self.b32.cpu().numpy()}
+
+    def load(self, st):
+        import torch
+        self.w32.copy_(torch.from_numpy(st["w"]))
+        self.b32.copy_(torch.from_numpy(st["b"]))
+        self.sync_weights()
+
+
+def _upsample(x, backward=False):
+    import torch
+    B, D, H, W, Cc = x.shape
+    if backward:
+        y = torch.empty((B, D // 2, H // 2, W // 2, Cc), dtype=x.dtype, device=x.device)
+        _ok(fdc.lib().fdc_upsample2(_p(x), _p(y), B, D // 2, H // 2, W // 2, Cc, 1, _s()), "upsample bwd")
+    else:
+        y = torch.empty((B, 2 * D, 2 * H, 2 * W, Cc), dtype=x.dtype, device=x.device)
+        _ok(fdc.lib().fdc_upsample2(_p(x), _p(y), B, D, H, W, Cc, 0, _s()), "upsample")
+    return y
+
+
+def _concat(a, b):
+    import torch
+    out = torch.empty(a.shape[:-1] + (a.shape[-1] + b.shape[-1],), dtype=a.dtype, device=a.device)
+    rows = a.numel() // a.shape[-1]
+    _ok(fdc.lib().fdc_concat_channels(_p(a), a.shape[-1], _p(b), b.shape[-1], _p(out), rows, 0, _s()), "concat")
+    return out
+
+
+def _split(out, ca, cb):
+    import torch
+    a = torch.empty(out.shape[:-1] + (ca,), dtype=out.dtype, device=out.device)
+    b = torch.empty(out.shape[:-1] + (cb,), dtype=out.dtype, device=out.device)
+    rows = out.numel() // out.shape[-1]
+    _ok(fdc.lib().fdc_concat_channels(_p(a), ca, _p(b), cb, _p(out), rows, 1, _s()), "split")
+    return a, b
+
+
+def _add(a, b):
+    _ok(fdc.lib().fdc_add_bf16(_p(a), _p(b), _p(a), a.numel(), _s()), "add")
+    return a
+
+
+class UNet:
+    def __init__(self, channels=(16, 32, 64, 128), seed=0, device="cuda:0"):
+        rng = np.random.default_rng(seed)
+        c1, c2, c3, c4 = channels
+
+        def L(cin, cout, k=3, s=1, p=1, relu=True, **kw):
+            return ConvLayer(cin, cout, k, s, p, relu, rng, device, **kw)
+
+        self.enc1 = [L(16, c1, cin_real=2), L(c1, c1)]
+        self.down1 = L(c1, c2, 2, 2, 0)
+        self.enc2 = [L(c2, c2), L(c2, c2)]
+        self.down2 = L(c2, c3, 2, 2, 0)
+        self.enc3 = [L(c3, c3), L(c3, c3)]
+        self.down3 = L(c3, c4, 2, 2, 0)
+        self.bott = [L(c4, c4), L(c4, c4)]
+        self.up3 = L(c4, c3)
+        self.dec3 = [L(2 * c3, c3), L(c3, c3)]
+        self.up2 = L(c3, c2)
+        self.dec2 = [L(2 * c2, c2), L(c2, c2)]
+        self.up1 = L(c2, c1)
+        self.dec1 = [L(2 * c1, c1), L(c1, c1)]
+        self.head = L(c1, 16, 1, 1, 0, relu=False, f32_out=True)
+        self.channels = channels
+        self.t = 0
+
+    def layers(self):
+        return (self.enc1 + [self.down1] + self.enc2 + [self.down2] + self.enc3 + [self.down3] + self.bott +
+                [self.up3] + self.dec3 + [self.up2] + self.dec2 + [self.up1] + self.dec1 + [self.head])
+
+    @staticmethod
+    def _seq(layers, x, keep):
+        for l in layers:
+            x = l.forward(x, keep)
+        return x
+
+    def forward(self, x, keep=True):
+        e1 = self._seq(self.enc1, x, keep)
+        e2 = self._seq(self.enc2, self.down1.forward(e1, keep), keep)
+        e3 = self._seq(self.enc3, self.down2.forward(e2, keep), keep)
+        b = self._seq(self.bott, self.down3.forward(e3, keep), keep)
+        f3 = self._seq(self.dec3, _concat(self.up3.forward(_upsample(b), keep), e3), keep)
+        f2 = self._seq(self.dec2, _concat(self.up2.forward(_upsample(f3), keep), e2), keep)
+        f1 = self._seq(self.dec1, _concat(self.up1.forward(_upsample(f2), keep), e1), keep)
+        return self.head.forward(f1, keep)
+
+    @staticmethod
+    def _seq_back(layers, dy, need_last=True):
+        for i, l in enumerate(reversed(layers)):
+            dy = l.backward(dy, need_dx=need_last or i < len(layers) - 1)
+        return dy
+
+    def backward(self, dhead):
+        c1, c2, c3, _ = self.channels
+        d = self.head.backward(dhead)
+        dc, de1 = _split(self._seq_back(self.dec1, d), c1, c1)
+        d = _upsample(self.up1.backward(dc), backward=True)
+        dc, de2 = _split(self._seq_back(self.dec2, d), c2, c2)
+        d = _upsample(self.up2.backward(dc), backward=True)
+        dc, de3 = _split(self._seq_back(self.dec3, d), c3, c3)
+        d = _upsample(self.up3.backward(dc), backward=True)
+        d = self.down3.backward(self._seq_back(self.bott, d))
+        d = self.down2.backward(self._seq_back(self.enc3, _add(d, de3)))
+        d = self.down1.backward(self._seq_back(self.enc2, _add(d, de2)))
+        self._seq_back(self.enc1, _add(d, de1), need_last=False)
+
+    def zero_grad(self):
+        for l in self.layers():
+            l.zero_grad()
+
+    def step(self, lr):
+        self.t += 1
+        for l in self.layers():
+            l.step(lr, self.t)
+
+    def state(self):
+        return [l.state() for l in self.layers()]
+
+    def load(self, states):
+        for l, s in zip(self.layers(), states):
+            l.load(s)
+
+
+class Sample:
+    """One case on the device: network input, its FP32 dose channel, and
+    (for training) the target correction; dose_scale maps back to Gy."""
+
+    def __init__(self, dose_low, density, dose_high=None, density_scale=0.5):
+        import torch
+        self.shape = tuple(dose_low.shape)  # (nz, ny, nx)
+        n = dose_low.numel()
+        dev = dose_low.device
+        self.scale = float(dose_low.max())
+        if self.scale <= 0:
+            self.scale = 1.0
+        self.x = torch.empty((1,) + self.shape + (16,), dtype=torch.bfloat16, device=dev)
+        self.dose_in = torch.empty(self.shape, dtype=torch.float32, device=dev)
+        self.target = torch.empty(self.shape, dtype=torch.float32, device=dev) if dose_high is not None else None
+        _ok(fdc.lib().fdc_unet_prepare(_p(dose_low), _p(density), _p(dose_high), n, self.scale, density_scale,
+                                       _p(self.x), _p(self.dose_in), _p(self.target), _s()), "prepare")
+
+
+def train_step(net, sample, lr):
+    """Forward, loss, backward and Adam step; returns the loss tensor (FP32,
+    device) without synchronising."""
+    import torch
+    head = net.forward(sample.x)
+    n = sample.dose_in.numel()
+    dhead = torch.empty(head.shape, dtype=torch.bfloat16, device=head.device)
+    loss = torch.zeros(1, dtype=torch.float32, device=head.device)
+    _ok(fdc.lib().fdc_mse(_p(head), 16, _p(sample.target), n, _p(dhead), _p(loss), _s()), "mse")
+    net.zero_grad()
+    net.backward(dhead)
+    net.step(lr)
+    return loss
+
+
+def evaluate_loss(net, sample):
+    import torch
+    head = net.forward(sample.x, keep=False)
+    loss = torch.zeros(1, dtype=torch.float32, device=head.device)
+    _ok(fdc.lib().fdc_mse(_p(head), 16, _p(sample.target), sample.dose_in.numel(), None, _p(loss), _s()), "mse")
+    return loss
+
+
+def denoise(net, sample):
+    """Denoised dose (Gy, FP64 on the device) of a prepared sample."""
+    import torch
+    head = net.forward(sample.x, keep=False)
+    out = torch.empty(sample.shape, dtype=torch.float64, device=head.device)
+    _ok(fdc.lib().fdc_unet_finish(_p(head), _p(sample.dose_in), sample.dose_in.numel(), sample.scale, _p(out),
+                                  _s()), "finish")
+    return out
+
+
+def gamma_pass_rate(ref, ev, spacing, dose_frac=0.02, dta=0.2, threshold=0.1, gamma_out=None):
+    """Gamma pass rate (fraction of voxels above threshold * max(ref) with
+    gamma <= 1) of an evaluated dose against a reference (FP64 device grids
+    [nz][ny][nx], spacing (dx, dy, dz) cm)."""
+    import torch
+    nz, ny, nx = ref.shape
+    scratch = torch.zeros(3, dtype=torch.int64, device=ref.device)
+    r = C.c_double()
+    _ok(fdc.lib().fdc_gamma(_p(ref), _p(ev), nz, ny, nx, float(spacing[2]), float(spacing[1]), float(spacing[0]),
+                            dose_frac, dta, threshold, _p(gamma_out), _p(scratch), C.byref(r), _s()), "gamma")
+    return r.value
+
+
+# ----------------------------------------------------------------------------
+# Training pairs from the engine, training and evaluation.
+
+def case_beam(seed, n):
+    """Random rectangular field of case `seed`: 100-180 MeV, 2-6 cm sides,
+    centre within 3 cm of the axis, 1 % energy spread."""
+    from . import synth
+    rng = np.random.Generator(np.random.PCG64(10_000 + seed))
+    E = rng.uniform(100.0, 180.0)
+    w, h = rng.uniform(2.0, 6.0, 2)
+    cx, cy = rng.uniform(-3.0, 3.0, 2)
+    return synth.make_spots([dict(x=cx, y=cy, energy=E, sigma_e=0.01 * E, a=w, b=h,
+                                  profile=synth.PROFILE_RECT, layer=0, n_histories=int(n))])
+
+
+def case_phantom(seed, n=128, voxel_cm=0.2):
+    from . import synth
+    return synth.thorax_phantom(seed=20_000 + seed, shape=(n, n, n), voxel_cm=voxel_cm)
+
+
+class Case:
+    def __init__(self, seed, phantom, density, low, high, beam_low):
+        self.seed, self.phantom, self.density, self.low, self.high = seed, phantom, density, low, high
+        self.beam_low = beam_low
+
+
+def generate_cases(eng, seeds, n_low=100_000, n_high=100_000_000, grid=128, keep_phantom=False):
+    """Per seed: random phantom and field; low- and high-history doses from
+    the engine (device FP64), plus the density (device FP32)."""
+    import torch
+    cases = []
+    for sd in seeds:
+        ph = case_phantom(sd, grid)
+        eng.load_phantom(ph)
+        bl = case_beam(sd, n_low)
+        bh = case_beam(sd, n_high)
+        low = eng.run(bl, 0, 1_000_003 * sd + 1)
+        high = eng.run(bh, 0, 1_000_003 * sd + 2)
+        eng.sync()
+        dens = torch.from_numpy(np.ascontiguousarray(ph.density)).cuda()
+        cases.append(Case(sd, ph if keep_phantom else None, dens, low, high, bl))
+    return cases
+
+
+def train(net, samples, epochs, lr=1e-3, lr_final=1e-4, log=None, seed=0):
+    """Adam over the samples in a seeded random order; cosine learning rate
+    from lr to lr_final.  Returns the per-epoch mean losses."""
+    import torch
+    rng = np.random.default_rng(seed)
+    total = epochs * len(samples)
+    it = 0
+    hist = []
+    for ep in range(epochs):
+        losses = []
+        for i in rng.permutation(len(samples)):
+            f = it / max(1, total - 1)
+            cur = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * f))
+            losses.append(train_step(net, samples[i], cur))
+            it += 1
+        m = float(torch.cat(losses).mean())
+        hist.append(m)
+        if log:
+            log(ep, m)
+    return hist
+
+
+def evaluate(net, eng, cases, n_low, spacing, dose_frac=0.02, dta=0.2, threshold=0.1, target_sigma=0.02):
+    """Per held-out case: gamma pass rate (dose_frac / dta) against the
+    high-history plain dose of the denoised low-history dose and of the raw
+    low-history dose; device time of the denoised path (low-history run +
+    network) and of the plain method run to ``target_sigma`` mean batch
+    uncertainty (eq. (1), voxels above half the maximum)."""
+    import torch
+    from .measure import time_to_sigma
+    rows = []
+    for c in cases:
+        eng.load_phantom(c.phantom)
+        shape = c.phantom.shape[::-1]
+        # denoised path, timed from the start of the low-history run to the dose
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        eng.run(c.beam_low, 0, 7 + c.seed)  # warm
+        e0.record()
+        low = eng.run(c.beam_low, 0, 7 + c.seed)
+        s = Sample(low, c.density)
+        out = denoise(net, s)
+        e1.record()
+        e1.synchronize()
+        t_den = e0.elapsed_time(e1) * 1e-3
+        g_den = gamma_pass_rate(c.high, out, spacing, dose_frac, dta, threshold)
+        g_raw = gamma_pass_rate(c.high, low, spacing, dose_frac, dta, threshold)
+        plain = time_to_sigma(eng, case_beam(c.seed, 100_000_000), shape, 11 + c.seed, target_sigma)
+        rows.append({"seed": c.seed, "gamma_denoised": g_den, "gamma_low": g_raw, "seconds_denoised": t_den,
+                     "seconds_plain_2pct": plain["seconds"], "histories_plain_2pct": plain["histories"],
+                     "plain_reached": plain["reached"]})
+    keys = ["gamma_denoised", "gamma_low", "seconds_denoised", "seconds_plain_2pct", "histories_plain_2pct"]
+    summary = {k: float(np.mean([r[k] for r in rows])) for k in keys}
+    summary["min_gamma_denoised"] = float(min(r["gamma_denoised"] for r in rows))
+    summary["cases_gamma_ge_98"] = int(sum(r["gamma_denoised"] >= 0.98 for r in rows))
+    return rows, summary

@@ -34,11 +34,29 @@ SIGNATURES = {
     "fdc_run_host": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, _p]),
     "fdc_sync": (C.c_int, [_p, _p, _p]),
     "fdc_batch_stats": (C.c_int, [_p, _p, _p, C.c_int32, C.c_double, _p, _p, _p, _p]),
+    "fdc_history_stats": (C.c_int, [_p, _p, _p, C.c_uint64, C.c_double, _p, _p, _p, _p]),
     "fdc_autotune": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, _p]),
     "fdc_set_timing": (C.c_int, [_p, C.c_int32]),
     "fdc_last_kernel_ms": (C.c_int, [_p, _p, _p]),
     "fdc_probe_atomics": (C.c_int, [_p, C.c_uint64, C.c_uint64, _p, _p]),
     "fdc_run_noalloc": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, _p, _p, _p]),
+    # denoiser kernels (include/fdc_unet.h)
+    "fdc_conv3d_forward": (C.c_int, [_p, _p, _p, _p, _p, _p, _p]),
+    "fdc_conv3d_backward_data": (C.c_int, [_p, _p, _p, _p, _p]),
+    "fdc_conv3d_backward_weights": (C.c_int, [_p, _p, _p, _p, _p, _p]),
+    "fdc_conv3d_transpose_weights": (C.c_int, [_p, _p, _p, _p]),
+    "fdc_relu_backward": (C.c_int, [_p, _p, _p, C.c_int64, _p]),
+    "fdc_upsample2": (C.c_int, [_p, _p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _p]),
+    "fdc_concat_channels": (C.c_int, [_p, C.c_int32, _p, C.c_int32, _p, C.c_int64, C.c_int32, _p]),
+    "fdc_mse": (C.c_int, [_p, C.c_int32, _p, C.c_int64, _p, _p, _p]),
+    "fdc_adam": (C.c_int, [_p, _p, _p, _p, _p, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int32,
+                           _p]),
+    "fdc_f32_to_bf16": (C.c_int, [_p, _p, C.c_int64, _p]),
+    "fdc_add_bf16": (C.c_int, [_p, _p, _p, C.c_int64, _p]),
+    "fdc_unet_prepare": (C.c_int, [_p, _p, _p, C.c_int64, C.c_double, C.c_float, _p, _p, _p, _p]),
+    "fdc_unet_finish": (C.c_int, [_p, _p, C.c_int64, C.c_double, _p, _p]),
+    "fdc_gamma": (C.c_int, [_p, _p, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                            C.c_double, C.c_double, C.c_double, _p, _p, _p, _p]),
     "fdc_debug_philox": (C.c_int, [C.c_uint64, C.c_uint64, _p, C.c_uint64, _p, _p]),
     "fdc_debug_sample": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int32, C.c_int32,
                                    _p, _p, _p]),
@@ -79,7 +97,8 @@ class RunOpts(C.Structure):
 
 
 class Outputs(C.Structure):
-    _fields_ = [("dose", _p), ("layer_dose", _p), ("batch_sum", _p), ("batch_sumsq", _p), ("tally", _p)]
+    _fields_ = [("dose", _p), ("layer_dose", _p), ("batch_sum", _p), ("batch_sumsq", _p), ("tally", _p),
+                ("history_sumsq", _p)]
 
 
 class Counters(C.Structure):
@@ -229,13 +248,15 @@ class Engine:
 
     def run_ex(self, spots, n_histories=0, seed=0, history_offset=0, track_group=1, rotate=True,
                scaling_mode=0, fp64_geometry=False, n_batches=0, schedule=None, dose=None,
-               layer_dose=None, batch_sum=None, batch_sumsq=None, tally=None, stream=None, graph=True):
+               layer_dose=None, batch_sum=None, batch_sumsq=None, tally=None, stream=None, graph=True,
+               history_sumsq=None):
         k = _Keep()
         b = beam_struct(spots, k)
         sch = Schedule(*(schedule or (0, 0, 0, 0)))
         o = RunOpts(int(history_offset), int(track_group), 0 if rotate else 1, int(scaling_mode),
                     1 if fp64_geometry else 0, int(n_batches), 0 if graph else 1, sch)
-        out = Outputs(_ptr(dose), _ptr(layer_dose), _ptr(batch_sum), _ptr(batch_sumsq), _ptr(tally))
+        out = Outputs(_ptr(dose), _ptr(layer_dose), _ptr(batch_sum), _ptr(batch_sumsq), _ptr(tally),
+                      _ptr(history_sumsq))
         self._check(self._lib.fdc_run_ex(self.h, C.byref(b), int(n_histories), int(seed), C.byref(o),
                                          C.byref(out), _stream_handle(stream)), "run_ex")
 
@@ -290,6 +311,17 @@ class Engine:
         self._check(self._lib.fdc_batch_stats(self.h, _ptr(batch_sum), _ptr(batch_sumsq), int(n_batches),
                                               float(frac), _ptr(mean), _ptr(sigma), C.byref(r),
                                               _stream_handle(stream)), "batch_stats")
+        return mean, sigma, r.value
+
+    def history_stats(self, dose_sum, history_sumsq, n_histories, frac=0.5, stream=None):
+        """Eq. (2): per-history mean dose, its sigma, and the mean sigma/mean."""
+        import torch
+        mean = torch.empty_like(dose_sum)
+        sigma = torch.empty_like(dose_sum)
+        r = C.c_double()
+        self._check(self._lib.fdc_history_stats(self.h, _ptr(dose_sum), _ptr(history_sumsq), int(n_histories),
+                                                float(frac), _ptr(mean), _ptr(sigma), C.byref(r),
+                                                _stream_handle(stream)), "history_stats")
         return mean, sigma, r.value
 
     def autotune(self, spots, n_histories, seed=0):

@@ -1,0 +1,202 @@
+"""Denoiser kernels through the C ABI against the FP64 references of the
+oracle package (GB300 only)."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import conv3d as ref
+from oracle import gamma as gref
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def bf16(a):
+    """Round to bfloat16 (nearest even) and return (torch bf16 tensor on the
+    GPU, the rounded values as float64)."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16)
+    return t.cuda(), t.to(torch.float64).numpy()
+
+
+def geom(x_shape, cout, k, s, p, relu=0):
+    from paper_1011_2188_gb300.denoise import Conv3d
+    B, D, H, W, Ci = x_shape
+    o = [(n + 2 * p - k) // s + 1 for n in (D, H, W)]
+    return Conv3d(B, D, H, W, o[0], o[1], o[2], Ci, cout, k, s, p, relu), (B, *o, cout)
+
+
+def ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+CASES = [
+    # (shape, cout, k, s, p)
+    ((1, 7, 6, 9, 16), 16, 3, 1, 1),
+    ((2, 5, 6, 7, 32), 64, 3, 1, 1),
+    ((1, 8, 6, 10, 16), 32, 2, 2, 0),
+    ((1, 6, 4, 8, 64), 128, 2, 2, 0),
+    ((1, 9, 5, 6, 32), 16, 1, 1, 0),
+    ((1, 4, 4, 6, 128), 64, 3, 1, 1),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("relu", [0, 1])
+def test_conv_forward(case, relu):
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    shape, cout, k, s, p = case
+    rng = np.random.default_rng(hash((shape, cout, relu)) % 2**32)
+    xt, x = bf16(rng.normal(size=shape))
+    wt, w = bf16(rng.normal(size=(cout, k, k, k, shape[-1])) / np.sqrt(k ** 3 * shape[-1]))
+    b = rng.normal(size=cout).astype(np.float32)
+    g, oshape = geom(shape, cout, k, s, p, relu)
+    y32 = torch.empty(oshape, dtype=torch.float32, device="cuda:0")
+    y16 = torch.empty(oshape, dtype=torch.bfloat16, device="cuda:0")
+    bt = torch.from_numpy(b).cuda()
+    assert fdc.lib().fdc_conv3d_forward(C.byref(g), ptr(xt), ptr(wt), ptr(bt), ptr(y16), ptr(y32), None) == 0
+    torch.cuda.synchronize()
+    r = ref.forward(x, w, b.astype(np.float64), stride=s, pad=p, relu=bool(relu))
+    mx = np.abs(r).max()
+    np.testing.assert_allclose(y32.cpu().numpy(), r, rtol=0, atol=2e-5 * mx)
+    np.testing.assert_allclose(y16.float().cpu().numpy(), r, rtol=0, atol=8e-3 * mx)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_conv_backward_data_and_weights(case):
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    shape, cout, k, s, p = case
+    rng = np.random.default_rng(7 + len(shape) + cout)
+    xt, x = bf16(rng.normal(size=shape))
+    wt, w = bf16(rng.normal(size=(cout, k, k, k, shape[-1])) / np.sqrt(k ** 3 * shape[-1]))
+    g, oshape = geom(shape, cout, k, s, p)
+    dyt, dy = bf16(rng.normal(size=oshape))
+    L = fdc.lib()
+    w_t = torch.empty((shape[-1], k, k, k, cout), dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_conv3d_transpose_weights(C.byref(g), ptr(wt), ptr(w_t), None) == 0
+    dx = torch.empty(shape, dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_conv3d_backward_data(C.byref(g), ptr(dyt), ptr(w_t), ptr(dx), None) == 0
+    dw = torch.zeros(w.shape, dtype=torch.float32, device="cuda:0")
+    db = torch.zeros(cout, dtype=torch.float32, device="cuda:0")
+    assert L.fdc_conv3d_backward_weights(C.byref(g), ptr(xt), ptr(dyt), ptr(dw), ptr(db), None) == 0
+    torch.cuda.synchronize()
+    rdx = ref.backward_data(dy, w, shape, stride=s, pad=p)
+    rdw, rdb = ref.backward_weights(x, dy, k, stride=s, pad=p)
+    np.testing.assert_allclose(dx.float().cpu().numpy(), rdx, rtol=0, atol=8e-3 * np.abs(rdx).max())
+    np.testing.assert_allclose(dw.cpu().numpy(), rdw, rtol=0, atol=2e-5 * np.abs(rdw).max())
+    np.testing.assert_allclose(db.cpu().numpy(), rdb, rtol=0, atol=2e-5 * np.abs(rdb).max())
+
+
+def test_elementwise_kernels():
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    L = fdc.lib()
+    rng = np.random.default_rng(3)
+    xt, x = bf16(rng.normal(size=(1, 3, 2, 4, 16)))
+    up = torch.empty((1, 6, 4, 8, 16), dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_upsample2(ptr(xt), ptr(up), 1, 3, 2, 4, 16, 0, None) == 0
+    dyt, dy = bf16(rng.normal(size=(1, 6, 4, 8, 16)))
+    back = torch.empty((1, 3, 2, 4, 16), dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_upsample2(ptr(dyt), ptr(back), 1, 3, 2, 4, 16, 1, None) == 0
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(up.double().cpu().numpy(), ref.upsample2(x))
+    np.testing.assert_allclose(back.double().cpu().numpy(), ref.upsample2_adjoint(dy), rtol=8e-3, atol=1e-2)
+    # concat / split round trip, add, relu backward
+    at, a = bf16(rng.normal(size=(10, 16)))
+    bt, b = bf16(rng.normal(size=(10, 32)))
+    out = torch.empty((10, 48), dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_concat_channels(ptr(at), 16, ptr(bt), 32, ptr(out), 10, 0, None) == 0
+    a2, b2 = torch.empty_like(at), torch.empty_like(bt)
+    assert L.fdc_concat_channels(ptr(a2), 16, ptr(b2), 32, ptr(out), 10, 1, None) == 0
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.double().cpu().numpy(), np.concatenate([a, b], axis=1))
+    assert torch.equal(a2, at) and torch.equal(b2, bt)
+    s = torch.empty_like(at)
+    assert L.fdc_add_bf16(ptr(at), ptr(a2), ptr(s), at.numel(), None) == 0
+    dx = torch.empty_like(at)
+    assert L.fdc_relu_backward(ptr(at), ptr(a2), ptr(dx), at.numel(), None) == 0
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(s.double().cpu().numpy(), 2 * a, rtol=8e-3)
+    np.testing.assert_array_equal(dx.double().cpu().numpy(), np.where(a > 0, a, 0.0))
+
+
+def test_mse_and_adam():
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    L = fdc.lib()
+    rng = np.random.default_rng(4)
+    pred = rng.normal(size=(1000, 16)).astype(np.float32)
+    tgt = rng.normal(size=1000).astype(np.float32)
+    pt, tt = torch.from_numpy(pred).cuda(), torch.from_numpy(tgt).cuda()
+    grad = torch.empty((1000, 16), dtype=torch.bfloat16, device="cuda:0")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda:0")
+    assert L.fdc_mse(ptr(pt), 16, ptr(tt), 1000, ptr(grad), ptr(loss), None) == 0
+    torch.cuda.synchronize()
+    e = pred[:, 0].astype(np.float64) - tgt
+    assert float(loss) == pytest.approx(np.mean(e ** 2), rel=1e-5)
+    g = grad.double().cpu().numpy()
+    np.testing.assert_allclose(g[:, 0], 2 * e / 1000, rtol=8e-3, atol=1e-9)
+    assert np.all(g[:, 1:] == 0)
+    # Adam, two steps, against the textbook update
+    p = rng.normal(size=100).astype(np.float32)
+    gr = [rng.normal(size=100).astype(np.float32) for _ in range(2)]
+    tp = torch.from_numpy(p.copy()).cuda()
+    m = torch.zeros_like(tp)
+    v = torch.zeros_like(tp)
+    pb = torch.empty(100, dtype=torch.bfloat16, device="cuda:0")
+    pr, mr, vr = p.astype(np.float64), np.zeros(100), np.zeros(100)
+    for t, gg in enumerate(gr, start=1):
+        tg = torch.from_numpy(gg).cuda()
+        assert L.fdc_adam(ptr(tp), ptr(tg), ptr(m), ptr(v), ptr(pb), 100, 1e-3, 0.9, 0.999, 1e-8, t, None) == 0
+        mr = 0.9 * mr + 0.1 * gg
+        vr = 0.999 * vr + 0.001 * gg.astype(np.float64) ** 2
+        pr = pr - 1e-3 * (mr / (1 - 0.9 ** t)) / (np.sqrt(vr / (1 - 0.999 ** t)) + 1e-8)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(tp.cpu().numpy(), pr, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(pb.double().cpu().numpy(), pr, rtol=8e-3, atol=1e-6)
+
+
+def test_gamma_matches_oracle():
+    import torch
+    from paper_1011_2188_gb300 import denoise
+    rng = np.random.default_rng(5)
+    z = np.linspace(0, 1, 20)[:, None, None]
+    r = np.exp(-((z - 0.6) / 0.2) ** 2) * np.ones((20, 18, 16)) + 0.05 * rng.random((20, 18, 16))
+    e = r * (1 + 0.03 * rng.normal(size=r.shape))
+    sp = (0.2, 0.2, 0.2)
+    gout = torch.empty(r.shape, dtype=torch.float32, device="cuda:0")
+    rate = denoise.gamma_pass_rate(torch.from_numpy(r).cuda(), torch.from_numpy(e).cuda(), sp, gamma_out=gout)
+    g_ref, rate_ref = gref.gamma(r, e, sp)
+    np.testing.assert_allclose(gout.cpu().numpy(), g_ref, rtol=1e-5, atol=1e-6)
+    assert rate == pytest.approx(rate_ref, abs=1e-12)
+
+
+def test_unet_forward_backward_and_training_reduces_loss():
+    """A small U-Net on a 32^3 toy problem: the loss decreases under the
+    project's forward, backward and Adam kernels."""
+    import torch
+    from paper_1011_2188_gb300 import denoise
+    rng = np.random.default_rng(6)
+    n = 32
+    zz, yy, xx = np.meshgrid(*[np.linspace(-1, 1, n)] * 3, indexing="ij")
+    clean = np.exp(-(xx ** 2 + yy ** 2) / 0.2) * (1 + zz)
+    noisy = clean + 0.2 * rng.normal(size=clean.shape) * clean.max() / 3
+    dens = np.ones_like(clean, dtype=np.float32)
+    s = denoise.Sample(torch.from_numpy(noisy).cuda(), torch.from_numpy(dens).cuda(),
+                       torch.from_numpy(clean).cuda())
+    net = denoise.UNet(channels=(16, 32, 32, 64), seed=1)
+    l0 = float(denoise.evaluate_loss(net, s))
+    for _ in range(60):
+        denoise.train_step(net, s, 2e-3)
+    l1 = float(denoise.evaluate_loss(net, s))
+    assert np.isfinite(l1) and l1 < 0.5 * l0, (l0, l1)
+    out = denoise.denoise(net, s)
+    assert out.shape == (n, n, n) and bool(torch.isfinite(out).all())
