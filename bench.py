@@ -53,7 +53,12 @@ def parse():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--schedule", default="", help="ctas_per_sm,warps_per_cta,chunk,aggregate")
     ap.add_argument("--quick", action="store_true", help="device timing only (sweeps)")
-    ap.add_argument("--study", default="", choices=["", "precision"],
+    ap.add_argument("--train-cases", type=int, default=200)
+    ap.add_argument("--eval-cases", type=int, default=20)
+    ap.add_argument("--epochs", type=int, default=12)
+    ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--high", type=int, default=100_000_000, help="histories of the target dose")
+    ap.add_argument("--study", default="", choices=["", "precision", "denoiser", "unet_timing"],
                     help="precision: FP32 vs FP64 step geometry on the slab phantom, 10^8 histories "
                          "in 100 batches (prints its own JSON line)")
     return ap.parse_args()
@@ -210,6 +215,105 @@ def history_vs_batch(eng, beam, ph, n, seed, n_batches=10, local=0, track_group=
             "squares_overhead": t_sq / t_plain - 1.0}
 
 
+def denoiser_study(args):
+    """Learned denoiser: random thorax-like phantoms (grid^3 x 2 mm) and
+    random fields; inputs 10^5-history doses (+ density), targets
+    high-history doses, all from the engine.  Trains the U-Net with the
+    library's kernels and evaluates held-out cases by 2 %/2 mm gamma against
+    the high-history plain dose, and by device time against the plain method
+    run to 2 % mean uncertainty."""
+    import numpy as np
+    import torch
+    from paper_1011_2188_gb300 import denoise, fdc, synth
+    t_all = time.perf_counter()
+    eng = fdc.Engine(0)
+    db = synth.water_database(synth.database_energies(24), 20_000, seed=2)
+    eng.load_database(db)
+    n_low = 100_000
+    t = time.perf_counter()
+    train_cases = denoise.generate_cases(eng, range(args.train_cases), n_low, args.high, args.grid)
+    eval_cases = denoise.generate_cases(eng, range(100_000, 100_000 + args.eval_cases), n_low, args.high,
+                                        args.grid, keep_phantom=True)
+    t_gen = time.perf_counter() - t
+    samples = [denoise.Sample(c.low, c.density, c.high) for c in train_cases]
+    for c in train_cases:
+        c.low = c.high = None
+    net = denoise.UNet(seed=0)
+    # iteration time
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    denoise.train_step(net, samples[0], 1e-4)
+    e1.record()
+    e1.synchronize()
+    e0.record()
+    for i in range(3):
+        denoise.train_step(net, samples[i % len(samples)], 1e-4)
+    e1.record()
+    e1.synchronize()
+    it_ms = e0.elapsed_time(e1) / 3
+    e0.record()
+    for i in range(3):
+        denoise.denoise(net, samples[i % len(samples)])
+    e1.record()
+    e1.synchronize()
+    inf_ms = e0.elapsed_time(e1) / 3
+    t = time.perf_counter()
+    hist = denoise.train(net, samples, args.epochs, lr=1e-3, lr_final=5e-5)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t
+    rows, summary = denoise.evaluate(net, eng, eval_cases, n_low, (0.2, 0.2, 0.2))
+    flops = 0.0  # forward FLOPs of one grid^3 sample: 2 * taps * cin * cout * output voxels per conv
+    g = args.grid
+    out_grid = [g, g, g // 2, g // 2, g // 2, g // 4, g // 4, g // 4, g // 8, g // 8, g // 8,
+                g // 4, g // 4, g // 4, g // 2, g // 2, g // 2, g, g, g, g]  # output grid of each layer
+    for l, vox in zip(net.layers(), out_grid):
+        flops += 2.0 * l.k ** 3 * l.cin * l.cout * vox ** 3
+    line = {"study": "denoiser", "grid": g, "train_cases": args.train_cases, "eval_cases": args.eval_cases,
+            "epochs": args.epochs, "histories_low": n_low, "histories_high": args.high,
+            "generate_s": t_gen, "train_s": t_train, "iteration_ms": it_ms, "inference_ms": inf_ms,
+            "forward_gflop": flops / 1e9, "inference_tflops": flops / (inf_ms * 1e-3) / 1e12,
+            "training_tflops": 3 * flops / (it_ms * 1e-3) / 1e12,
+            "loss_history": hist, "summary": summary, "cases": rows,
+            "note": "doses compared at the low-history count (high-history dose scaled by n_low / n_high)",
+            "total_s": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+    np.savez("gpurun_out/unet_weights.npz" if os.path.isdir("gpurun_out") else "/tmp/unet_weights.npz",
+             *[a for st in net.state() for a in (st["w"], st["b"])])
+
+
+def unet_timing(args):
+    """Inference and training-step time of the U-Net on one grid^3 sample
+    (a Gaussian dose on a water grid; the weights do not change the cost)."""
+    import numpy as np
+    import torch
+    from paper_1011_2188_gb300 import denoise
+    g = args.grid
+    z, y, x = np.meshgrid(*[np.linspace(-1, 1, g)] * 3, indexing="ij")
+    dose = torch.from_numpy(np.exp(-(x ** 2 + y ** 2) / 0.1) * (1 + z)).cuda()
+    dens = torch.ones((g, g, g), dtype=torch.float32, device="cuda:0")
+    s = denoise.Sample(dose, dens, dose)
+    net = denoise.UNet(seed=0)
+    for _ in range(args.warmup):
+        denoise.denoise(net, s)
+        denoise.train_step(net, s, 1e-5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        denoise.denoise(net, s)
+    e1.record()
+    e1.synchronize()
+    inf = e0.elapsed_time(e1) / args.steps
+    e0.record()
+    for _ in range(args.steps):
+        denoise.train_step(net, s, 1e-5)
+    e1.record()
+    e1.synchronize()
+    tr = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"study": "unet_timing", "grid": g, "inference_ms": inf, "train_step_ms": tr}), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -259,6 +363,14 @@ def main():
     if args.study == "precision":
         if rank == 0:
             precision_study(args)
+        return
+    if args.study == "denoiser":
+        if rank == 0:
+            denoiser_study(args)
+        return
+    if args.study == "unet_timing":
+        if rank == 0:
+            unet_timing(args)
         return
 
     import numpy as np

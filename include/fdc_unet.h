@@ -12,7 +12,7 @@
  * Conventions: all pointers are device memory owned by the caller; tensors
  * are channels-last [batch][d][h][w][c]; "bf16" arrays hold IEEE bfloat16
  * values (uint16 storage); weights are [c_out][k][k][k][c_in] (bf16) and
- * their transposed copy for the data gradient [c_in][k][k][k][c_out].
+ * their data-gradient copy [c_in][k][k][k][c_out] (fdc_conv3d_transpose_weights).
  * Calls are asynchronous on `stream` (cudaStream_t as void *, NULL = legacy
  * default stream) and return FDC_OK, FDC_ERR_INVALID (bad shapes: channel
  * counts must be multiples of 16, sizes positive and consistent) or
@@ -41,13 +41,16 @@ int fdc_conv3d_forward(const fdc_conv3d *g, const void *x, const void *w, const 
                        float *y_f32, void *stream);
 /* dx[b][i][ci] = sum over (tap, co) with i + pad - tap = stride * o of dy[b][o][co] w[co][tap][ci]
  * (the gradient of the forward map with respect to x, without the ReLU).
- * dy bf16 [batch][out...][c_out]; w_t bf16 [c_in][tap][c_out]; dx bf16. */
+ * dy bf16 [batch][out...][c_out]; w_t the data-gradient weights that
+ * fdc_conv3d_transpose_weights produced for this convolution; dx bf16. */
 int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_t, void *dx, void *stream);
 /* dw[co][tap][ci] += sum_o dy[o][co] x[o * stride - pad + tap][ci] and, if db is not NULL,
  * db[co] += sum_o dy[o][co]; dw, db FP32 (accumulated: zero them first). */
 int fdc_conv3d_backward_weights(const fdc_conv3d *g, const void *x, const void *dy, float *dw, float *db,
                                 void *stream);
-/* w_t[ci][tap][co] = w[co][tap][ci] (bf16). */
+/* Data-gradient weights (bf16, c_in x k^3 x c_out): w_t[ci][tap][co] = w[co][tap][ci], with the
+ * tap reflected (tap -> k^3 - 1 - tap) for 3^3 stride-1 padding-1 convolutions, whose data
+ * gradient is then a forward convolution of dy. */
 int fdc_conv3d_transpose_weights(const fdc_conv3d *g, const void *w, void *w_t, void *stream);
 
 /* dx = dy where y > 0, else 0 (bf16, n elements). */

@@ -195,6 +195,143 @@ __global__ void __launch_bounds__(128) conv_igemm_kernel(const Conv3dArgs g, con
     }
 }
 
+// 3x3x3, stride 1, padding 1: a CTA owns a 2 x 8 x 8 block of output voxels
+// (M = 128) and NT output channels.  Per 16-channel input slice it stages the
+// 4 x 10 x 10 input halo in shared memory once (cp.async, zero fill outside
+// the grid) and runs all 27 taps from it; weight fragments are read from
+// global memory through L1 (the slice's weights are a few KB).  Also serves
+// the data gradient with flipped, transposed weights.
+constexpr int kHD = 4, kHH = 10, kHW = 10, kHalo = kHD * kHH * kHW;
+
+template <int NT>
+__global__ void __launch_bounds__(128) conv3_halo_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
+                                                         const __nv_bfloat16 *wt, const float *bias,
+                                                         __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn,
+                                                         int relu) {
+    __shared__ __align__(16) unsigned char sH[2][kHalo * kRowBytes];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int grp = lane >> 2, tig = lane & 3;
+    const int D = g.in_d, H = g.in_h, W = g.in_w;  // stride 1, pad 1: output grid = input grid
+    const int tiles_w = (W + 7) / 8, tiles_h = (H + 7) / 8, tiles_d = (D + 1) / 2;
+    long long t = blockIdx.x;
+    const int tw = (int)(t % tiles_w); t /= tiles_w;
+    const int th = (int)(t % tiles_h); t /= tiles_h;
+    const int td = (int)(t % tiles_d);
+    const int b = (int)(t / tiles_d);
+    const int d0 = td * 2, h0 = th * 8, w0 = tw * 8;
+    const int n0 = blockIdx.y * NT;
+    const int slices = Cs / 16;
+
+    auto load_halo = [&](int buf, int c0) {
+        for (int i = tid; i < kHalo * 2; i += 128) {
+            const int row = i >> 1, half = i & 1;
+            const int hd = row / (kHH * kHW), hh = (row / kHW) % kHH, hw = row % kHW;
+            const int d = d0 - 1 + hd, h = h0 - 1 + hh, w = w0 - 1 + hw;
+            const bool ok = d >= 0 && d < D && h >= 0 && h < H && w >= 0 && w < W;
+            const __nv_bfloat16 *p = ok ? src + ((((long long)b * D + d) * H + h) * W + w) * Cs + c0 + half * 8 : src;
+            cp_async16(sH[buf] + row * kRowBytes + half * 16, p, ok);
+        }
+    };
+
+    float acc[2][NT / 8][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < NT / 8; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+
+    // output rows of this lane's fragments: r = warp*32 + mt*16 + grp (+8);
+    // within the 2 x 8 x 8 block: od = r / 64, oh = (r / 8) % 8, ow = r % 8
+    int hbase[2][2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+            const int r = warp * 32 + mt * 16 + grp + hf * 8;
+            hbase[mt][hf] = ((r >> 6) * kHH + ((r >> 3) & 7)) * kHW + (r & 7);
+        }
+
+    load_halo(0, 0);
+    cp_async_commit();
+    for (int sl = 0; sl < slices; ++sl) {
+        const int buf = sl & 1;
+        if (sl + 1 < slices) load_halo(buf ^ 1, (sl + 1) * 16);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const unsigned char *Hs = sH[buf];
+        const int c0 = sl * 16;
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+            const int kd = tap / 9, kh = (tap / 3) % 3, kw = tap % 3;
+            const int off = (kd * kHH + kh) * kHW + kw;
+            unsigned bfrag[NT / 8][2];
+#pragma unroll
+            for (int nt = 0; nt < NT / 8; ++nt) {
+                const int n = n0 + nt * 8 + grp;
+                const __nv_bfloat16 *q = wt + ((long long)(n < Nn ? n : 0) * 27 + tap) * Cs + c0 + tig * 2;
+                bfrag[nt][0] = n < Nn ? __ldg((const unsigned *)q) : 0u;
+                bfrag[nt][1] = n < Nn ? __ldg((const unsigned *)(q + 8)) : 0u;
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const unsigned char *r0p = Hs + (hbase[mt][0] + off) * kRowBytes + tig * 4;
+                const unsigned char *r1p = Hs + (hbase[mt][1] + off) * kRowBytes + tig * 4;
+                const unsigned a0 = lds32(r0p), a1 = lds32(r1p), a2 = lds32(r0p + 16), a3 = lds32(r1p + 16);
+#pragma unroll
+                for (int nt = 0; nt < NT / 8; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bfrag[nt][0], bfrag[nt][1]);
+            }
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+            const int r = warp * 32 + mt * 16 + grp + hf * 8;
+            const int d = d0 + (r >> 6), h = h0 + ((r >> 3) & 7), w = w0 + (r & 7);
+            if (d >= D || h >= H || w >= W) continue;
+            const long long v = (((long long)b * D + d) * H + h) * W + w;
+#pragma unroll
+            for (int nt = 0; nt < NT / 8; ++nt) {
+                const int n = n0 + nt * 8 + tig * 2;
+                if (n >= Nn) continue;
+                float v0 = acc[mt][nt][hf * 2], v1 = acc[mt][nt][hf * 2 + 1];
+                if (bias) {
+                    v0 += bias[n];
+                    v1 += bias[n + 1];
+                }
+                if (relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                if (out_f32) {
+                    out_f32[v * Nn + n] = v0;
+                    out_f32[v * Nn + n + 1] = v1;
+                }
+                if (out_bf16) *(__nv_bfloat162 *)(out_bf16 + v * Nn + n) = __floats2bfloat162_rn(v0, v1);
+            }
+        }
+    }
+}
+
+// [ci][tap'][co] <- [co][tap][ci] with tap' the point reflection of tap
+// (the data gradient of a stride-1 convolution is the forward convolution
+// of dy with these weights)
+__global__ void flip_transpose_kernel(const __nv_bfloat16 *w, __nv_bfloat16 *wf, int co_n, int k, int ci_n) {
+    const int taps = k * k * k;
+    const long long n = (long long)co_n * taps * ci_n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)(i % ci_n);
+        const long long q = i / ci_n;
+        const int tap = (int)(q % taps), co = (int)(q / taps);
+        wf[((long long)ci * taps + (taps - 1 - tap)) * co_n + co] = w[i];
+    }
+}
+
 // Weight gradient: dW[co][tap][ci] += sum_v dy[v][co] * x[src(v, tap)][ci]
 // over a chunk of output voxels v, as a GEMM with M = output channels,
 // N = input channels and K = voxels; FP32 partial sums are added atomically.
@@ -511,6 +648,26 @@ int grid_for(long long n, int threads = 256) {
 
 }  // namespace
 
+cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *wt, const float *bias,
+                             void *out_bf16, float *out_f32, int Cs, int Nn, int relu, cudaStream_t st) {
+    const int nt = Nn >= 64 ? 64 : (Nn >= 32 ? 32 : 16);
+    const long long tiles = (long long)g.batch * ((g.in_d + 1) / 2) * ((g.in_h + 7) / 8) * ((g.in_w + 7) / 8);
+    dim3 grid((unsigned)tiles, (unsigned)((Nn + nt - 1) / nt));
+    auto s = (const __nv_bfloat16 *)src;
+    auto w = (const __nv_bfloat16 *)wt;
+    auto ob = (__nv_bfloat16 *)out_bf16;
+    if (nt == 64) conv3_halo_kernel<64><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu);
+    else if (nt == 32) conv3_halo_kernel<32><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu);
+    else conv3_halo_kernel<16><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flip_transpose(const void *w, void *wf, int co, int k, int ci, cudaStream_t st) {
+    const long long n = (long long)co * k * k * k * ci;
+    flip_transpose_kernel<<<grid_for(n), 256, 0, st>>>((const __nv_bfloat16 *)w, (__nv_bfloat16 *)wf, co, k, ci);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const void *wt, const float *bias,
                         void *out_bf16, float *out_f32, cudaStream_t st) {
     const int Nn = mode == 0 ? g.c_out : g.c_in;
@@ -671,9 +828,14 @@ int rc(cudaError_t e) { return e == cudaSuccess ? FDC_OK : FDC_ERR_CUDA; }
 
 extern "C" {
 
+bool is_k3s1p1(const fdc_conv3d *g) { return g->ksize == 3 && g->stride == 1 && g->pad == 1; }
+
 int fdc_conv3d_forward(const fdc_conv3d *g, const void *x, const void *w, const float *bias, void *y_bf16,
                        float *y_f32, void *stream) {
     if (!conv_ok(g) || !x || !w || (!y_bf16 && !y_f32)) return FDC_ERR_INVALID;
+    if (is_k3s1p1(g))
+        return rc(fdc::launch_conv_halo(to_args(g), x, w, bias, y_bf16, y_f32, g->c_in, g->c_out, g->relu ? 1 : 0,
+                                        (cudaStream_t)stream));
     return rc(fdc::launch_conv(to_args(g), 0, x, w, bias, y_bf16, y_f32, (cudaStream_t)stream));
 }
 
@@ -681,6 +843,9 @@ int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_
     if (!conv_ok(g) || !dy || !w_t || !dx) return FDC_ERR_INVALID;
     fdc::Conv3dArgs a = to_args(g);
     a.relu = 0;
+    if (is_k3s1p1(g))  // forward convolution of dy with the reflected, transposed weights
+        return rc(fdc::launch_conv_halo(a, dy, w_t, nullptr, dx, nullptr, g->c_out, g->c_in, 0,
+                                        (cudaStream_t)stream));
     return rc(fdc::launch_conv(a, 1, dy, w_t, nullptr, dx, nullptr, (cudaStream_t)stream));
 }
 
@@ -692,6 +857,8 @@ int fdc_conv3d_backward_weights(const fdc_conv3d *g, const void *x, const void *
 
 int fdc_conv3d_transpose_weights(const fdc_conv3d *g, const void *w, void *w_t, void *stream) {
     if (!conv_ok(g) || !w || !w_t) return FDC_ERR_INVALID;
+    if (is_k3s1p1(g))
+        return rc(fdc::launch_flip_transpose(w, w_t, g->c_out, 3, g->c_in, (cudaStream_t)stream));
     return rc(fdc::launch_transpose_weights(w, w_t, g->c_out, g->ksize * g->ksize * g->ksize, g->c_in,
                                             (cudaStream_t)stream));
 }

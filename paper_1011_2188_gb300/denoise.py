@@ -347,7 +347,9 @@ class Case:
 
 def generate_cases(eng, seeds, n_low=100_000, n_high=100_000_000, grid=128, keep_phantom=False):
     """Per seed: random phantom and field; low- and high-history doses from
-    the engine (device FP64), plus the density (device FP32)."""
+    the engine (device FP64), plus the density (device FP32).  The engine's
+    dose is the total of its histories, so the high-history dose is rescaled
+    to the low-history count (both are then the dose of n_low protons)."""
     import torch
     cases = []
     for sd in seeds:
@@ -357,6 +359,7 @@ def generate_cases(eng, seeds, n_low=100_000, n_high=100_000_000, grid=128, keep
         bh = case_beam(sd, n_high)
         low = eng.run(bl, 0, 1_000_003 * sd + 1)
         high = eng.run(bh, 0, 1_000_003 * sd + 2)
+        high.mul_(n_low / n_high)
         eng.sync()
         dens = torch.from_numpy(np.ascontiguousarray(ph.density)).cuda()
         cases.append(Case(sd, ph if keep_phantom else None, dens, low, high, bl))

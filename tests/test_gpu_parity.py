@@ -344,3 +344,35 @@ def test_history_squares_against_exact_per_history_squares():
     rel_ref = stats.mean_relative_uncertainty(d_ref / 40000, sg_ref)
     assert rel == pytest.approx(rel_ref, rel=0.05), (rel, rel_ref)
     eng.close()
+
+
+def test_parity_straggling_and_local_deposits_ragged_tracks():
+    """Database with Bohr straggling and local deposits: every track has its
+    own step count and energy losses (ragged CSR), off-bin energies start
+    mid-track."""
+    db = synth.water_database(synth.database_energies(8, 90, 160), 150, seed=9, straggling=True, nuclear=True)
+    lens = np.diff(db.step_begin)
+    assert lens.min() < lens.max()
+    ph = synth.thorax_phantom(seed=5, shape=(80, 80, 64))
+    beam = synth.make_spots([dict(x=0.5, y=-0.5, energy=128.0, sigma_e=4.0, a=1.0, profile=0, layer=0,
+                                  n_histories=40000)])
+    eng = engine(db, ph)
+    r = gpu_energy(eng, ph, beam, 77)
+    ref = oracle.run(db, ph, beam, seed=77)
+    assert_conservation(r)
+    assert_parity(r["energy"], ref.edep, "straggling")
+    assert r["counters"]["steps"] == ref.n_steps
+    eng.close()
+
+
+def test_autotune_picks_a_valid_schedule_and_results_do_not_change():
+    db = synth.water_database([150.0], 200, seed=1)
+    ph = synth.slab_phantom()
+    beam = synth.pencil_beam(200000, energy=150.0, sigma_cm=0.3)
+    eng = engine(db, ph)
+    before = gpu_energy(eng, ph, beam, 5)["tally"]
+    ctas, warps, chunk, agg = eng.autotune(beam, 100000, 5)
+    assert 1 <= warps <= 8 and ctas >= 1 and chunk >= 1 and agg in (1, 2)
+    after = gpu_energy(eng, ph, beam, 5)["tally"]  # runs with the tuned default
+    assert np.array_equal(before, after)
+    eng.close()

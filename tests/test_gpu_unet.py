@@ -44,6 +44,8 @@ CASES = [
     ((1, 6, 4, 8, 64), 128, 2, 2, 0),
     ((1, 9, 5, 6, 32), 16, 1, 1, 0),
     ((1, 4, 4, 6, 128), 64, 3, 1, 1),
+    ((1, 16, 16, 16, 16), 16, 3, 1, 1),
+    ((2, 3, 9, 17, 48), 32, 3, 1, 1),
 ]
 
 
@@ -82,6 +84,11 @@ def test_conv_backward_data_and_weights(case):
     L = fdc.lib()
     w_t = torch.empty((shape[-1], k, k, k, cout), dtype=torch.bfloat16, device="cuda:0")
     assert L.fdc_conv3d_transpose_weights(C.byref(g), ptr(wt), ptr(w_t), None) == 0
+    # layout of the data-gradient weights: transposed, taps reflected for 3^3 stride 1 padding 1
+    wr = np.transpose(w, (4, 1, 2, 3, 0))
+    if (k, s, p) == (3, 1, 1):
+        wr = wr[:, ::-1, ::-1, ::-1, :]
+    np.testing.assert_array_equal(w_t.double().cpu().numpy(), wr)
     dx = torch.empty(shape, dtype=torch.bfloat16, device="cuda:0")
     assert L.fdc_conv3d_backward_data(C.byref(g), ptr(dyt), ptr(w_t), ptr(dx), None) == 0
     dw = torch.zeros(w.shape, dtype=torch.float32, device="cuda:0")
