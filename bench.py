@@ -166,14 +166,15 @@ def cpu_baseline(db, ph, beam, seed, target_s=12.0):
             "track_steps_per_s": r.n_steps / dt, "seconds": dt}
 
 
-def time_to_sigma(eng, beam, ph, seed, target=0.02, n_batches=10, n0=200_000, local=0):
+def time_to_sigma(eng, beam, ph, seed, target=0.02, n_batches=10, n0=200_000, local=0, track_group=1):
     """Plain method: device time to reach a mean relative batch uncertainty
     (eq. (1)) of ``target`` over voxels above half the maximum dose (Sec. 2.4)
     and, separately, above 0.9 of it (the Bragg-peak region)."""
     from paper_1011_2188_gb300.measure import time_to_sigma as tts
     shape = ph.shape[::-1]
-    return {"half_max": tts(eng, beam, shape, seed, target, 0.5, n_batches, n0, local),
-            "bragg_peak_0.9max": tts(eng, beam, shape, seed, target, 0.9, n_batches, n0, local)}
+    return {"half_max": tts(eng, beam, shape, seed, target, 0.5, n_batches, n0, local, track_group=track_group),
+            "bragg_peak_0.9max": tts(eng, beam, shape, seed, target, 0.9, n_batches, n0, local,
+                                     track_group=track_group)}
 
 
 def history_vs_batch(eng, beam, ph, n, seed, n_batches=10, local=0, track_group=1):
@@ -480,7 +481,7 @@ def main():
     sub = beam.copy()
     for i in range(max(2, min(args.steps, 5))):
         t = time.perf_counter()
-        eng.run_host(sub, n, seed + 1 + i, host_dose)
+        eng.run_host(sub, n, seed + 1 + i, host_dose, track_group=args.track_group)
         e2e_times.append(time.perf_counter() - t)
     e2e_s = statistics.median(e2e_times[1:])
     h2d = int(fdc.SPOT_DTYPE.itemsize * len(beam) + 8 * (len(beam) + 1))
@@ -526,7 +527,8 @@ def main():
         "load_s": t_load,
     }
     if rank == 0 and args.workload != "spots":  # batches of a spot plan would cover different spots
-        line["time_to_2pct_sigma_plain"] = time_to_sigma(eng, beam, ph, seed + 99, local=local)
+        line["time_to_2pct_sigma_plain"] = time_to_sigma(eng, beam, ph, seed + 99, local=local,
+                                                         track_group=args.track_group)
         line["history_by_history"] = history_vs_batch(eng, beam, ph, n, seed + 7, local=local,
                                                       track_group=args.track_group)
     if rank == 0 and not args.no_cpu_baseline:

@@ -207,10 +207,11 @@ int fdc_run(fdc_ctx *ctx, const fdc_beam *beam, uint64_t n_histories, uint64_t s
 int fdc_run_ex(fdc_ctx *ctx, const fdc_beam *beam, uint64_t n_histories, uint64_t seed,
                const fdc_run_opts *opts, const fdc_outputs *out, void *stream);
 
-/* As fdc_run with a HOST dose buffer: copies the beam in, runs, copies the
- * dose out and waits.  Returns the device status as fdc_sync does. */
+/* As fdc_run_ex with a HOST dose buffer: copies the beam in, runs with
+ * `opts` (may be NULL), copies the dose out and waits.  Returns the device
+ * status as fdc_sync does. */
 int fdc_run_host(fdc_ctx *ctx, const fdc_beam *beam, uint64_t n_histories, uint64_t seed,
-                 double *dose_host);
+                 const fdc_run_opts *opts, double *dose_host);
 
 /* Wait for `stream`, read the device status word of the last run and its
  * counters.  Returns FDC_OK or the first device error (FDC_ERR_STEP_LIMIT,

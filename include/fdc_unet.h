@@ -39,6 +39,14 @@ typedef struct fdc_conv3d {
  * y_bf16 [batch][out...][c_out] and/or y_f32 (either may be NULL). */
 int fdc_conv3d_forward(const fdc_conv3d *g, const void *x, const void *w, const float *bias, void *y_bf16,
                        float *y_f32, void *stream);
+/* The forward map of a 3^3, stride-1, padding-1 convolution (ksize 3, stride 1,
+ * pad 1 required) whose input is the channel concatenation [xa | xb]: xa holds
+ * the first ca channels (multiple of 16), at half resolution and read through
+ * nearest x2 upsampling when upsample_a = 1 (in_d, in_h, in_w even); xb holds
+ * the other c_in - ca channels at full resolution (may be NULL when ca = c_in).
+ * Same result as fdc_conv3d_forward on the materialised input. */
+int fdc_conv3d_forward_fused(const fdc_conv3d *g, const void *xa, int32_t ca, int32_t upsample_a, const void *xb,
+                             const void *w, const float *bias, void *y_bf16, float *y_f32, void *stream);
 /* dx[b][i][ci] = sum over (tap, co) with i + pad - tap = stride * o of dy[b][o][co] w[co][tap][ci]
  * (the gradient of the forward map with respect to x, without the ReLU).
  * dy bf16 [batch][out...][c_out]; w_t the data-gradient weights that

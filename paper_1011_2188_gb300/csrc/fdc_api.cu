@@ -662,7 +662,8 @@ int fdc_sync(fdc_ctx *c, void *stream, fdc_counters *counters) {
     return FDC_OK;
 }
 
-int fdc_run_host(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t seed, double *dose_host) {
+int fdc_run_host(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t seed, const fdc_run_opts *opts,
+                 double *dose_host) {
     if (!c) return FDC_ERR_INVALID;
     if (!dose_host) return fail(c, FDC_ERR_INVALID, "dose_host is null");
     if (!c->ph_loaded) return fail(c, FDC_ERR_NOT_LOADED, "phantom must be loaded");
@@ -672,7 +673,7 @@ int fdc_run_host(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_
     std::memset(&out, 0, sizeof out);
     out.dose = c->scratch_dose.p;
     // the beam is this call's input: always copy it in
-    int rc = run_impl(c, beam, n_histories, seed, nullptr, &out, nullptr, true);
+    int rc = run_impl(c, beam, n_histories, seed, opts, &out, nullptr, true);
     if (rc) return rc;
     FDC_CUDA(c, cudaMemcpyAsync(dose_host, c->scratch_dose.p, sizeof(double) * c->nvox, cudaMemcpyDeviceToHost, nullptr));
     return fdc_sync(c, nullptr, nullptr);

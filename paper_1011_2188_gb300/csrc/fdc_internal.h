@@ -100,7 +100,8 @@ struct Conv3dArgs {
 cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const void *wt, const float *bias,
                         void *out_bf16, float *out_f32, cudaStream_t st);
 cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *wt, const float *bias,
-                             void *out_bf16, float *out_f32, int Cs, int Nn, int relu, cudaStream_t st);
+                             void *out_bf16, float *out_f32, int Cs, int Nn, int relu, cudaStream_t st,
+                             int ca, int up_a, const void *src_b);
 cudaError_t launch_flip_transpose(const void *w, void *wf, int co, int k, int ci, cudaStream_t st);
 cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy, float *dw, float *db,
                               cudaStream_t st);

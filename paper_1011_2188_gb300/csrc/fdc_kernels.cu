@@ -244,11 +244,17 @@ __device__ __forceinline__ void tally_add(unsigned long long *tally, long long i
 // into the same tally word are summed in registers and written with one
 // atomic when the lane moves to another word (or finishes the history).
 // Integer sums, so the tally is the same bit for bit.
-// Energy (MeV) to tally units.  Shares below 2^31 units (8 MeV) take the
-// 32-bit conversion; larger ones the 64-bit one.  Both round to nearest even,
-// so the result equals the 64-bit conversion of the same value.
+// Energy (MeV) to tally units: round to nearest (even) integer.  Below 2^31
+// units (8 MeV) the 32-bit conversion; above, the value is an integer-valued
+// float and is rebuilt exactly from its bits (m * 2^e, e >= 8), so no 64-bit
+// conversion instruction is issued (those run on the narrow FP64 pipe).
 __device__ __forceinline__ long long units_of(float scaled) {
-    return fabsf(scaled) < 2147483520.0f ? (long long)__float2int_rn(scaled) : __float2ll_rn(scaled);
+    const int r = __float2int_rn(scaled);
+    if (fabsf(scaled) < 2147483520.0f) return r;
+    const unsigned b = __float_as_uint(scaled);
+    const int e = (int)((b >> 23) & 0xffu) - 150;
+    const long long v = (long long)((b & 0x7fffffu) | 0x800000u) << e;
+    return (b >> 31) ? -v : v;
 }
 __device__ __forceinline__ long long units_of(double scaled) { return __double2ll_rn(scaled); }
 __device__ __forceinline__ float unit_scale(float) { return kUnitsF; }
@@ -490,10 +496,17 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
             ny_ = sgn * st_ * sp_;
             nz_ = sgn * ct_;
         }
-        const R inorm = rsqrt_(nx_ * nx_ + ny_ * ny_ + nz_ * nz_);
-        dx = nx_ * inorm;
-        dy = ny_ * inorm;
-        dz = nz_ * inorm;
+        // the rotation keeps |d| = 1 up to rounding; renormalising every
+        // eighth step bounds the drift at ~1e-6
+        if ((s & 7) == 0) {
+            const R inorm = rsqrt_(nx_ * nx_ + ny_ * ny_ + nz_ * nz_);
+            nx_ *= inorm;
+            ny_ *= inorm;
+            nz_ *= inorm;
+        }
+        dx = nx_;
+        dy = ny_;
+        dz = nz_;
     }
 }
 

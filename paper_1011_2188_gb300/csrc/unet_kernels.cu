@@ -47,6 +47,15 @@ __device__ __forceinline__ void mma_bf16(float c[4], unsigned a0, unsigned a1, u
 
 __device__ __forceinline__ unsigned lds32(const unsigned char *p) { return *(const unsigned *)p; }
 
+// Four 8 x 8 b16 matrices from shared memory, one row address per lane.
+__device__ __forceinline__ void ldmatrix_x4(const unsigned char *p, unsigned &r0, unsigned &r1, unsigned &r2,
+                                            unsigned &r3) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
 struct RowCoord {
     int b, d, h, w;
     bool valid;
@@ -203,11 +212,15 @@ __global__ void __launch_bounds__(128) conv_igemm_kernel(const Conv3dArgs g, con
 // the data gradient with flipped, transposed weights.
 constexpr int kHD = 4, kHH = 10, kHW = 10, kHalo = kHD * kHH * kHW;
 
+// The input may be the channel concatenation of two tensors, src (ca channels,
+// optionally at half resolution and read through nearest x2 upsampling) and
+// src_b (cs - ca channels, full resolution), so that upsampling and skip
+// concatenation never materialise.
 template <int NT>
 __global__ void __launch_bounds__(128) conv3_halo_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
                                                          const __nv_bfloat16 *wt, const float *bias,
                                                          __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn,
-                                                         int relu) {
+                                                         int relu, int ca, int up_a, const __nv_bfloat16 *src_b) {
     __shared__ __align__(16) unsigned char sH[2][kHalo * kRowBytes];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int grp = lane >> 2, tig = lane & 3;
@@ -222,13 +235,24 @@ __global__ void __launch_bounds__(128) conv3_halo_kernel(const Conv3dArgs g, con
     const int n0 = blockIdx.y * NT;
     const int slices = Cs / 16;
 
+    const int cb = Cs - ca;
+    const int Da = up_a ? D / 2 : D, Ha = up_a ? H / 2 : H, Wa = up_a ? W / 2 : W;
     auto load_halo = [&](int buf, int c0) {
+        const bool from_a = c0 < ca;
         for (int i = tid; i < kHalo * 2; i += 128) {
             const int row = i >> 1, half = i & 1;
             const int hd = row / (kHH * kHW), hh = (row / kHW) % kHH, hw = row % kHW;
             const int d = d0 - 1 + hd, h = h0 - 1 + hh, w = w0 - 1 + hw;
             const bool ok = d >= 0 && d < D && h >= 0 && h < H && w >= 0 && w < W;
-            const __nv_bfloat16 *p = ok ? src + ((((long long)b * D + d) * H + h) * W + w) * Cs + c0 + half * 8 : src;
+            const __nv_bfloat16 *p = src;
+            if (ok) {
+                if (from_a) {
+                    const int da = up_a ? d >> 1 : d, ha = up_a ? h >> 1 : h, wa = up_a ? w >> 1 : w;
+                    p = src + ((((long long)b * Da + da) * Ha + ha) * Wa + wa) * ca + c0 + half * 8;
+                } else {
+                    p = src_b + ((((long long)b * D + d) * H + h) * W + w) * cb + (c0 - ca) + half * 8;
+                }
+            }
             cp_async16(sH[buf] + row * kRowBytes + half * 16, p, ok);
         }
     };
@@ -241,16 +265,16 @@ __global__ void __launch_bounds__(128) conv3_halo_kernel(const Conv3dArgs g, con
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
 
-    // output rows of this lane's fragments: r = warp*32 + mt*16 + grp (+8);
-    // within the 2 x 8 x 8 block: od = r / 64, oh = (r / 8) % 8, ow = r % 8
-    int hbase[2][2];
+    // A fragments by ldmatrix.x4: lane L supplies row (L & 7) + 8 ((L >> 3) & 1)
+    // of the 16-row tile at channel offset 8 (L >> 4).  Output row r of the
+    // 2 x 8 x 8 block: od = r / 64, oh = (r / 8) % 8, ow = r % 8.
+    unsigned lrow[2];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {
-            const int r = warp * 32 + mt * 16 + grp + hf * 8;
-            hbase[mt][hf] = ((r >> 6) * kHH + ((r >> 3) & 7)) * kHW + (r & 7);
-        }
+    for (int mt = 0; mt < 2; ++mt) {
+        const int r = warp * 32 + mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
+        const int hidx = ((r >> 6) * kHH + ((r >> 3) & 7)) * kHW + (r & 7);
+        lrow[mt] = hidx * kRowBytes + (lane >> 4) * 16;
+    }
 
     load_halo(0, 0);
     cp_async_commit();
@@ -276,9 +300,8 @@ __global__ void __launch_bounds__(128) conv3_halo_kernel(const Conv3dArgs g, con
             }
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
-                const unsigned char *r0p = Hs + (hbase[mt][0] + off) * kRowBytes + tig * 4;
-                const unsigned char *r1p = Hs + (hbase[mt][1] + off) * kRowBytes + tig * 4;
-                const unsigned a0 = lds32(r0p), a1 = lds32(r1p), a2 = lds32(r0p + 16), a3 = lds32(r1p + 16);
+                unsigned a0, a1, a2, a3;
+                ldmatrix_x4(Hs + lrow[mt] + off * kRowBytes, a0, a1, a2, a3);
 #pragma unroll
                 for (int nt = 0; nt < NT / 8; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bfrag[nt][0], bfrag[nt][1]);
             }
@@ -315,6 +338,116 @@ __global__ void __launch_bounds__(128) conv3_halo_kernel(const Conv3dArgs g, con
                 if (out_bf16) *(__nv_bfloat162 *)(out_bf16 + v * Nn + n) = __floats2bfloat162_rn(v0, v1);
             }
         }
+    }
+}
+
+// Weight gradient of a 3^3 stride-1 padding-1 convolution for one 16-wide
+// output-channel tile and one 16-wide input-channel slice:
+//   dW[co][tap][ci] += sum over voxels v of dy[v][co] * x[v + tap - 1][ci].
+// A CTA walks 2 x 8 x 8 voxel blocks (grid-stride); per block it stages the
+// dy tile (128 voxels x 16) and the x halo (4 x 10 x 10 x 16) in shared
+// memory, and each warp accumulates the GEMMs of its taps (M = 16 co, N = 16
+// ci, K = the block's 128 voxels) with ldmatrix.trans fragments; the CTA's
+// partial dW is added atomically at the end.
+constexpr int kDyRowBytes = 48;  // 16 BF16 padded
+#ifndef FDC_WGRAD_HALO
+#define FDC_WGRAD_HALO 0
+#endif
+
+__device__ __forceinline__ void ldmatrix_x4_trans(const unsigned char *p, unsigned &r0, unsigned &r1, unsigned &r2,
+                                                  unsigned &r3) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+__global__ void __launch_bounds__(128) conv3_wgrad_halo_kernel(const Conv3dArgs g, const __nv_bfloat16 *x,
+                                                               const __nv_bfloat16 *dy, float *dw) {
+    __shared__ __align__(16) unsigned char sX[kHalo * kRowBytes];
+    __shared__ __align__(16) unsigned char sDy[kRows * kDyRowBytes];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int grp = lane >> 2, tig = lane & 3;
+    const int D = g.in_d, H = g.in_h, W = g.in_w, Ci = g.c_in, Co = g.c_out;
+    const int co0 = blockIdx.y * 16, ci0 = blockIdx.z * 16;
+    const int tiles_w = (W + 7) / 8, tiles_h = (H + 7) / 8, tiles_d = (D + 1) / 2;
+    const long long n_blocks = (long long)g.batch * tiles_d * tiles_h * tiles_w;
+    // taps of this warp: warp, warp + 4, ... (7 or 6 of the 27)
+    float acc[7][2][4];
+#pragma unroll
+    for (int i = 0; i < 7; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+    // ldmatrix row of this lane: voxel (lane & 7) + 8 ((lane >> 3) & 1) of a
+    // 16-voxel k-step, channel offset 8 (lane >> 4)
+    const int lv = (lane & 7) + ((lane >> 3) & 1) * 8, lc = (lane >> 4) * 16;
+    // for B (x): lanes 0-15 channels 0-7 with voxels 0-15, lanes 16-31 channels 8-15
+    for (long long blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
+        long long t = blk;
+        const int tw = (int)(t % tiles_w); t /= tiles_w;
+        const int th = (int)(t % tiles_h); t /= tiles_h;
+        const int td = (int)(t % tiles_d);
+        const int b = (int)(t / tiles_d);
+        const int d0 = td * 2, h0 = th * 8, w0 = tw * 8;
+        for (int i = tid; i < kHalo * 2; i += 128) {
+            const int row = i >> 1, half = i & 1;
+            const int hd = row / (kHH * kHW), hh = (row / kHW) % kHH, hw = row % kHW;
+            const int d = d0 - 1 + hd, h = h0 - 1 + hh, w = w0 - 1 + hw;
+            const bool ok = d >= 0 && d < D && h >= 0 && h < H && w >= 0 && w < W;
+            const __nv_bfloat16 *p = ok ? x + ((((long long)b * D + d) * H + h) * W + w) * Ci + ci0 + half * 8 : x;
+            cp_async16(sX + row * kRowBytes + half * 16, p, ok);
+        }
+        for (int i = tid; i < kRows * 2; i += 128) {
+            const int r = i >> 1, half = i & 1;
+            const int d = d0 + (r >> 6), h = h0 + ((r >> 3) & 7), w = w0 + (r & 7);
+            const bool ok = d < D && h < H && w < W;
+            const __nv_bfloat16 *p = ok ? dy + ((((long long)b * D + d) * H + h) * W + w) * Co + co0 + half * 8 : dy;
+            cp_async16(sDy + r * kDyRowBytes + half * 16, p, ok);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+#pragma unroll 1
+        for (int ks = 0; ks < 8; ++ks) {  // 16 voxels per k-step
+            // A = dy^T: rows co, k = voxels ks*16 .. +15
+            unsigned a0, a1, a2, a3;
+            {
+                const int v = ks * 16 + (lane & 7) + (lane >> 4) * 8;  // matrices: (v 0-7, co 0-7), (v 0-7, co 8-15), (v 8-15, co 0-7), (v 8-15, co 8-15)
+                ldmatrix_x4_trans(sDy + v * kDyRowBytes + ((lane >> 3) & 1) * 16, a0, a1, a2, a3);
+            }
+            const int v = ks * 16 + lv;  // this lane's voxel row for the B matrices
+            const int hidx = ((v >> 6) * kHH + ((v >> 3) & 7)) * kHW + (v & 7);
+#pragma unroll
+            for (int i = 0; i < 7; ++i) {
+                const int tap = warp + 4 * i;
+                if (tap < 27) {
+                    const int kd = tap / 9, kh = (tap / 3) % 3, kw = tap % 3;
+                    const int off = (kd * kHH + kh) * kHW + kw;
+                    unsigned b0, b1, b2, b3;
+                    ldmatrix_x4_trans(sX + (hidx + off) * kRowBytes + lc, b0, b1, b2, b3);
+                    // b0,b1: k = voxels 0-7 / 8-15, n = ci 0-7; b2,b3: ci 8-15
+                    mma_bf16(acc[i][0], a0, a1, a2, a3, b0, b1);
+                    mma_bf16(acc[i][1], a0, a1, a2, a3, b2, b3);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        const int tap = warp + 4 * i;
+        if (tap >= 27) continue;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                const int co = co0 + grp + hf * 8, ci = ci0 + nt * 8 + tig * 2;
+                float *q = dw + ((long long)co * 27 + tap) * Ci + ci;
+                atomicAdd(q, acc[i][nt][hf * 2]);
+                atomicAdd(q + 1, acc[i][nt][hf * 2 + 1]);
+            }
     }
 }
 
@@ -649,16 +782,19 @@ int grid_for(long long n, int threads = 256) {
 }  // namespace
 
 cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *wt, const float *bias,
-                             void *out_bf16, float *out_f32, int Cs, int Nn, int relu, cudaStream_t st) {
+                             void *out_bf16, float *out_f32, int Cs, int Nn, int relu, cudaStream_t st,
+                             int ca, int up_a, const void *src_b) {
+    if (ca <= 0) ca = Cs;
     const int nt = Nn >= 64 ? 64 : (Nn >= 32 ? 32 : 16);
     const long long tiles = (long long)g.batch * ((g.in_d + 1) / 2) * ((g.in_h + 7) / 8) * ((g.in_w + 7) / 8);
     dim3 grid((unsigned)tiles, (unsigned)((Nn + nt - 1) / nt));
     auto s = (const __nv_bfloat16 *)src;
     auto w = (const __nv_bfloat16 *)wt;
     auto ob = (__nv_bfloat16 *)out_bf16;
-    if (nt == 64) conv3_halo_kernel<64><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu);
-    else if (nt == 32) conv3_halo_kernel<32><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu);
-    else conv3_halo_kernel<16><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu);
+    auto sb = (const __nv_bfloat16 *)src_b;
+    if (nt == 64) conv3_halo_kernel<64><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
+    else if (nt == 32) conv3_halo_kernel<32><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
+    else conv3_halo_kernel<16><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
     return cudaGetLastError();
 }
 
@@ -693,6 +829,23 @@ cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const vo
 cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy, float *dw, float *db,
                               cudaStream_t st) {
     const long long rows = (long long)g.batch * g.out_d * g.out_h * g.out_w;
+    if (FDC_WGRAD_HALO && g.ksize == 3 && g.stride == 1 && g.pad == 1) {
+        const long long blocks = (long long)g.batch * ((g.in_d + 1) / 2) * ((g.in_h + 7) / 8) * ((g.in_w + 7) / 8);
+        const int pairs = (g.c_out / 16) * (g.c_in / 16);
+        long long per = (152ll * 8 + pairs - 1) / pairs;  // CTAs per channel-tile pair
+        if (per > blocks) per = blocks;
+        if (per < 1) per = 1;
+        dim3 grid((unsigned)per, (unsigned)(g.c_out / 16), (unsigned)(g.c_in / 16));
+        conv3_wgrad_halo_kernel<<<grid, 128, 0, st>>>(g, (const __nv_bfloat16 *)x, (const __nv_bfloat16 *)dy, dw);
+        if (db) {
+            const int C = g.c_out;
+            const int threads = (256 / C) * C;
+            const int ch = 4096;
+            bias_grad_kernel<<<(unsigned)((rows + ch - 1) / ch), threads, 0, st>>>((const __nv_bfloat16 *)dy, rows,
+                                                                                    C, db, ch);
+        }
+        return cudaGetLastError();
+    }
     const int taps = g.ksize * g.ksize * g.ksize;
     const int tiles = ((g.c_out + 63) / 64) * ((g.c_in + 63) / 64);
     // enough CTAs to fill the GPU, K chunks of whole 16-voxel steps
@@ -835,8 +988,17 @@ int fdc_conv3d_forward(const fdc_conv3d *g, const void *x, const void *w, const 
     if (!conv_ok(g) || !x || !w || (!y_bf16 && !y_f32)) return FDC_ERR_INVALID;
     if (is_k3s1p1(g))
         return rc(fdc::launch_conv_halo(to_args(g), x, w, bias, y_bf16, y_f32, g->c_in, g->c_out, g->relu ? 1 : 0,
-                                        (cudaStream_t)stream));
+                                        (cudaStream_t)stream, g->c_in, 0, nullptr));
     return rc(fdc::launch_conv(to_args(g), 0, x, w, bias, y_bf16, y_f32, (cudaStream_t)stream));
+}
+
+int fdc_conv3d_forward_fused(const fdc_conv3d *g, const void *xa, int32_t ca, int32_t upsample_a, const void *xb,
+                             const void *w, const float *bias, void *y_bf16, float *y_f32, void *stream) {
+    if (!conv_ok(g) || !is_k3s1p1(g) || !xa || !w || (!y_bf16 && !y_f32)) return FDC_ERR_INVALID;
+    if (ca < 16 || ca % 16 || ca > g->c_in || (ca < g->c_in && !xb)) return FDC_ERR_INVALID;
+    if (upsample_a && (g->in_d % 2 || g->in_h % 2 || g->in_w % 2)) return FDC_ERR_INVALID;
+    return rc(fdc::launch_conv_halo(to_args(g), xa, w, bias, y_bf16, y_f32, g->c_in, g->c_out, g->relu ? 1 : 0,
+                                    (cudaStream_t)stream, ca, upsample_a ? 1 : 0, xb));
 }
 
 int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_t, void *dx, void *stream) {
@@ -845,7 +1007,7 @@ int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_
     a.relu = 0;
     if (is_k3s1p1(g))  // forward convolution of dy with the reflected, transposed weights
         return rc(fdc::launch_conv_halo(a, dy, w_t, nullptr, dx, nullptr, g->c_out, g->c_in, 0,
-                                        (cudaStream_t)stream));
+                                        (cudaStream_t)stream, g->c_out, 0, nullptr));
     return rc(fdc::launch_conv(a, 1, dy, w_t, nullptr, dx, nullptr, (cudaStream_t)stream));
 }
 

@@ -31,7 +31,7 @@ SIGNATURES = {
     "fdc_load_phantom": (C.c_int, [_p, _p]),
     "fdc_run": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, _p, _p]),
     "fdc_run_ex": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, _p, _p, _p]),
-    "fdc_run_host": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, _p]),
+    "fdc_run_host": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, _p, _p]),
     "fdc_sync": (C.c_int, [_p, _p, _p]),
     "fdc_batch_stats": (C.c_int, [_p, _p, _p, C.c_int32, C.c_double, _p, _p, _p, _p]),
     "fdc_history_stats": (C.c_int, [_p, _p, _p, C.c_uint64, C.c_double, _p, _p, _p, _p]),
@@ -42,6 +42,7 @@ SIGNATURES = {
     "fdc_run_noalloc": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, _p, _p, _p]),
     # denoiser kernels (include/fdc_unet.h)
     "fdc_conv3d_forward": (C.c_int, [_p, _p, _p, _p, _p, _p, _p]),
+    "fdc_conv3d_forward_fused": (C.c_int, [_p, _p, C.c_int32, C.c_int32, _p, _p, _p, _p, _p, _p]),
     "fdc_conv3d_backward_data": (C.c_int, [_p, _p, _p, _p, _p]),
     "fdc_conv3d_backward_weights": (C.c_int, [_p, _p, _p, _p, _p, _p]),
     "fdc_conv3d_transpose_weights": (C.c_int, [_p, _p, _p, _p]),
@@ -274,13 +275,14 @@ class Engine:
                                               _ptr(counters), _stream_handle(stream)), "run_noalloc")
         return dose
 
-    def run_host(self, spots, n_histories=0, seed=0, dose_host=None):
+    def run_host(self, spots, n_histories=0, seed=0, dose_host=None, track_group=1):
         """End-to-end call with a host (numpy float64) dose buffer."""
         if dose_host is None:
             dose_host = np.empty(self.shape, np.float64)
         k = _Keep()
         b = beam_struct(spots, k)
-        self._check(self._lib.fdc_run_host(self.h, C.byref(b), int(n_histories), int(seed),
+        o = RunOpts(0, int(track_group), 0, 0, 0, 0, 0, Schedule(0, 0, 0, 0))
+        self._check(self._lib.fdc_run_host(self.h, C.byref(b), int(n_histories), int(seed), C.byref(o),
                                            C.c_void_p(dose_host.ctypes.data)), "run_host")
         return dose_host
 

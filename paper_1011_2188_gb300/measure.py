@@ -5,7 +5,7 @@ from __future__ import annotations
 
 
 def time_to_sigma(eng, beam, shape, seed, target=0.02, frac=0.5, n_batches=10, n0=200_000, device=0,
-                  max_rounds=5):
+                  max_rounds=5, track_group=1):
     """Device seconds and histories for the mean eq. (1) uncertainty over
     voxels above frac * max to fall to ``target``.  The history count is
     predicted from sigma ~ N^-1/2 and re-measured until reached (or the beam
@@ -18,10 +18,11 @@ def time_to_sigma(eng, beam, shape, seed, target=0.02, frac=0.5, n_batches=10, n
 
     def measure(n):
         n = min(total, max(n_batches, (n // n_batches) * n_batches))
-        eng.run_ex(beam, n, seed, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2)  # capture / warm
+        kw = dict(n_batches=n_batches, batch_sum=s1, batch_sumsq=s2, track_group=track_group)
+        eng.run_ex(beam, n, seed, **kw)  # capture / warm
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        eng.run_ex(beam, n, seed, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2)
+        eng.run_ex(beam, n, seed, **kw)
         e1.record()
         e1.synchronize()
         _, _, rel = eng.batch_stats(s1, s2, n_batches, frac)
@@ -33,4 +34,4 @@ def time_to_sigma(eng, beam, shape, seed, target=0.02, frac=0.5, n_batches=10, n
             break
         n, sec, rel = measure(int(n * (rel / target) ** 2 * 1.05) + n_batches)
     return {"histories": n, "seconds": sec, "mean_rel_sigma": rel, "target": target, "frac": frac,
-            "n_batches": n_batches, "reached": bool(rel <= target)}
+            "n_batches": n_batches, "track_group": track_group, "reached": bool(rel <= target)}

@@ -207,3 +207,46 @@ def test_unet_forward_backward_and_training_reduces_loss():
     assert np.isfinite(l1) and l1 < 0.5 * l0, (l0, l1)
     out = denoise.denoise(net, s)
     assert out.shape == (n, n, n) and bool(torch.isfinite(out).all())
+
+
+@pytest.mark.parametrize("ca,cb,up", [(32, 0, 1), (16, 16, 0), (64, 64, 0), (32, 32, 1)])
+def test_fused_upsample_concat_forward(ca, cb, up):
+    """fdc_conv3d_forward_fused equals fdc_conv3d_forward on the materialised
+    [upsample(xa) | xb] input."""
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    L = fdc.lib()
+    rng = np.random.default_rng(ca + cb + up)
+    D, H, W = 6, 8, 10
+    sa = (1, D // 2, H // 2, W // 2, ca) if up else (1, D, H, W, ca)
+    xat, xa = bf16(rng.normal(size=sa))
+    xbt, xb = bf16(rng.normal(size=(1, D, H, W, cb))) if cb else (None, None)
+    cin, cout = ca + cb, 32
+    wt, w = bf16(rng.normal(size=(cout, 3, 3, 3, cin)) / np.sqrt(27 * cin))
+    g, oshape = geom((1, D, H, W, cin), cout, 3, 1, 1, 1)
+    y = torch.empty(oshape, dtype=torch.float32, device="cuda:0")
+    assert L.fdc_conv3d_forward_fused(C.byref(g), ptr(xat), ca, up, ptr(xbt), ptr(wt), None, None, ptr(y), None) == 0
+    torch.cuda.synchronize()
+    full = ref.upsample2(xa) if up else xa
+    if cb:
+        full = np.concatenate([full, xb], axis=-1)
+    r = ref.forward(full, w, None, relu=True)
+    np.testing.assert_allclose(y.cpu().numpy(), r, rtol=0, atol=2e-5 * np.abs(r).max())
+
+
+def test_unet_inference_matches_training_forward():
+    """The fused inference path gives the same output as the training path."""
+    import torch
+    from paper_1011_2188_gb300 import denoise
+    rng = np.random.default_rng(9)
+    n = 32
+    dose = torch.from_numpy(rng.random((n, n, n))).cuda()
+    dens = torch.ones((n, n, n), dtype=torch.float32, device="cuda:0")
+    s = denoise.Sample(dose, dens, dose)
+    net = denoise.UNet(seed=2)
+    a = net.forward(s.x, keep=True).clone()
+    for l in net.layers():
+        l.x = l.y = None
+    b = net.forward(s.x, keep=False)
+    torch.cuda.synchronize()
+    assert torch.allclose(a, b, rtol=0, atol=1e-3 * float(a.abs().max()))
