@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(128) conv3_halo_kernel(const Conv3dArgs g, con
 // partial dW is added atomically at the end.
 constexpr int kDyRowBytes = 48;  // 16 BF16 padded
 #ifndef FDC_WGRAD_HALO
-#define FDC_WGRAD_HALO 0
+#define FDC_WGRAD_HALO 1
 #endif
 
 __device__ __forceinline__ void ldmatrix_x4_trans(const unsigned char *p, unsigned &r0, unsigned &r1, unsigned &r2,
