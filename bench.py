@@ -29,10 +29,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "histories/sec and track-steps/sec on 1 GB300; wall time to 2% σ (plain vs denoised)"
-# Algorithmic HBM bytes of the replay kernel: one 16-byte step record per
-# replayed step, plus per history its track/start-step lookups (step_begin 16,
-# ~9 residual-energy probes 36, tail 8) rounded to 64.
-BYTES_PER_STEP = 16
+# Algorithmic HBM bytes of the replay kernel: the 16-byte step record of each
+# replayed step, read once per group of histories sharing the track (16 / G B
+# per step for track group G), plus per history its track and start-step
+# lookups (step_begin 16, ~9 residual-energy probes 36, tail 8) rounded to 64.
+BYTES_PER_RECORD = 16
 BYTES_PER_HISTORY = 64
 L2_FLUSH_BYTES = 512 << 20
 
@@ -56,6 +57,7 @@ def parse():
     ap.add_argument("--train-cases", type=int, default=200)
     ap.add_argument("--eval-cases", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=12)
+    ap.add_argument("--variants", type=int, default=1, help="mirror images per training phantom (1-4)")
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--high", type=int, default=100_000_000, help="histories of the target dose")
     ap.add_argument("--study", default="", choices=["", "precision", "denoiser", "unet_timing"],
@@ -177,6 +179,43 @@ def time_to_sigma(eng, beam, ph, seed, target=0.02, n_batches=10, n0=200_000, lo
                                      track_group=track_group)}
 
 
+def denoised_vs_plain(db, local=0, seed=100_000, n_low=100_000, grid=128, track_group=1):
+    """Metric's second half on one held-out-style case (random thorax-like
+    grid^3 x 2 mm phantom and field, as in the denoiser study): device time of
+    the denoised path (10^5-history run + U-Net inference) against the plain
+    method run to 2 % mean uncertainty.  The network's cost does not depend
+    on its weights; its accuracy is measured by --study denoiser."""
+    import torch
+    from paper_1011_2188_gb300 import denoise, fdc
+    from paper_1011_2188_gb300.measure import time_to_sigma
+    eng = fdc.Engine(local)
+    eng.load_database(db)
+    ph = denoise.case_phantom(seed, grid)
+    eng.load_phantom(ph)
+    net = denoise.UNet(seed=0)
+    dens = torch.from_numpy(ph.density).cuda(local)
+    bl = denoise.case_beam(seed, n_low)
+    opts = dict(track_group=track_group)
+    times = []
+    for i in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dose = torch.empty(ph.shape[::-1], dtype=torch.float64, device=f"cuda:{local}")
+        e0.record()
+        eng.run_ex(bl, 0, 7 + i, dose=dose, **opts)
+        out = denoise.denoise(net, denoise.Sample(dose, dens))
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    plain = time_to_sigma(eng, denoise.case_beam(seed, 100_000_000), ph.shape[::-1], 11, 0.02, 0.5,
+                          device=local, track_group=track_group)
+    eng.close()
+    t_den = min(times[1:])
+    return {"grid": grid, "histories_low": n_low, "seconds_denoised_path": t_den,
+            "seconds_plain_2pct": plain["seconds"], "histories_plain_2pct": plain["histories"],
+            "plain_over_denoised": plain["seconds"] / t_den,
+            "accuracy": "2%/2mm gamma of the trained network: bench.py --study denoiser"}
+
+
 def history_vs_batch(eng, beam, ph, n, seed, n_batches=10, local=0, track_group=1):
     """Sec. 2.4 / Fig. 5 analogue on the bench workload: one run of n
     histories in n_batches batches that also keeps the second (squared) tally;
@@ -232,7 +271,8 @@ def denoiser_study(args):
     eng.load_database(db)
     n_low = 100_000
     t = time.perf_counter()
-    train_cases = denoise.generate_cases(eng, range(args.train_cases), n_low, args.high, args.grid)
+    train_cases = denoise.generate_cases(eng, range(args.train_cases), n_low, args.high, args.grid,
+                                         variants=args.variants)
     eval_cases = denoise.generate_cases(eng, range(100_000, 100_000 + args.eval_cases), n_low, args.high,
                                         args.grid, keep_phantom=True)
     t_gen = time.perf_counter() - t
@@ -270,7 +310,8 @@ def denoiser_study(args):
                 g // 4, g // 4, g // 4, g // 2, g // 2, g // 2, g, g, g, g]  # output grid of each layer
     for l, vox in zip(net.layers(), out_grid):
         flops += 2.0 * l.k ** 3 * l.cin * l.cout * vox ** 3
-    line = {"study": "denoiser", "grid": g, "train_cases": args.train_cases, "eval_cases": args.eval_cases,
+    line = {"study": "denoiser", "grid": g, "train_cases": len(train_cases), "train_phantoms": args.train_cases,
+            "eval_cases": args.eval_cases,
             "epochs": args.epochs, "histories_low": n_low, "histories_high": args.high,
             "generate_s": t_gen, "train_s": t_train, "iteration_ms": it_ms, "inference_ms": inf_ms,
             "forward_gflop": flops / 1e9, "inference_tflops": flops / (inf_ms * 1e-3) / 1e12,
@@ -495,7 +536,7 @@ def main():
     atom_peak = n_ops / (atom_ms * 1e-3)
 
     hbm_peak, peak_kind = load_peaks()
-    alg_bytes = BYTES_PER_STEP * steps_per_run + BYTES_PER_HISTORY * hist_per_run
+    alg_bytes = BYTES_PER_RECORD * steps_per_run / max(1, args.track_group) + BYTES_PER_HISTORY * hist_per_run
     achieved = alg_bytes / (rep_ms * 1e-3) / 1e9
     atom_achieved = segs_per_run / (rep_ms * 1e-3)
 
@@ -514,7 +555,9 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None,
                      "peak_source": f"{peak_kind} hbm_gbs",
-                     "algorithmic_bytes_per_launch": alg_bytes},
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "note": "not the binding resource: the replay kernel is bound by instruction issue "
+                             "(~82 % of issue slots in ncu) and L2 atomics (roofline_l2_atomic)"},
         "roofline_l2_atomic": {"achieved": atom_achieved, "peak": atom_peak, "unit": "atomic/s",
                                "frac": atom_achieved / atom_peak,
                                "note": "one tally update per voxel segment; peak from the hashed int64 "
@@ -531,6 +574,9 @@ def main():
                                                          track_group=args.track_group)
         line["history_by_history"] = history_vs_batch(eng, beam, ph, n, seed + 7, local=local,
                                                       track_group=args.track_group)
+    if rank == 0 and args.workload == "thorax":
+        line["wall_time_to_2pct_plain_vs_denoised"] = denoised_vs_plain(db, local=local,
+                                                                        track_group=args.track_group)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(db, ph, beam, seed)
     if rank == 0:

@@ -365,25 +365,48 @@ class Case:
         self.beam_low = beam_low
 
 
-def generate_cases(eng, seeds, n_low=100_000, n_high=100_000_000, grid=128, keep_phantom=False):
-    """Per seed: random phantom and field; low- and high-history doses from
-    the engine (device FP64), plus the density (device FP32).  The engine's
-    dose is the total of its histories, so the high-history dose is rescaled
-    to the low-history count (both are then the dose of n_low protons)."""
+def _mirrored(ph, variant):
+    """The phantom mirrored in x (variant & 1) and/or y (variant & 2)."""
+    import copy
+    q = copy.copy(ph)
+    m, d = ph.material, ph.density
+    if variant & 1:
+        m, d = m[:, :, ::-1], d[:, :, ::-1]
+    if variant & 2:
+        m, d = m[:, ::-1, :], d[:, ::-1, :]
+    q.material, q.density = np.ascontiguousarray(m), np.ascontiguousarray(d)
+    return q
+
+
+def generate_cases(eng, seeds, n_low=100_000, n_high=100_000_000, grid=128, keep_phantom=False, variants=1):
+    """Per seed: random phantom (and, with variants > 1, its mirror images in
+    x, y and xy), each with its own random field; low- and high-history doses
+    from the engine (device FP64), plus the density (device FP32).  The
+    engine's dose is the total of its histories, so the high-history dose is
+    rescaled to the low-history count (both are then the dose of n_low
+    protons)."""
     import torch
     cases = []
-    for sd in seeds:
-        ph = case_phantom(sd, grid)
-        eng.load_phantom(ph)
-        bl = case_beam(sd, n_low)
-        bh = case_beam(sd, n_high)
-        low = eng.run(bl, 0, 1_000_003 * sd + 1)
-        high = eng.run(bh, 0, 1_000_003 * sd + 2)
-        high.mul_(n_low / n_high)
-        eng.sync()
-        dens = torch.from_numpy(np.ascontiguousarray(ph.density)).cuda()
-        cases.append(Case(sd, ph if keep_phantom else None, dens, low, high, bl))
+    for sd0 in seeds:
+        base = case_phantom(sd0, grid)
+        for var in range(variants):
+            sd = sd0 if variants == 1 else 1_000_000 + sd0 * variants + var
+            ph = base if var == 0 else _mirrored(base, var)
+            cases.extend(_one_case(eng, sd, ph, n_low, n_high, keep_phantom))
     return cases
+
+
+def _one_case(eng, sd, ph, n_low, n_high, keep_phantom):
+    import torch
+    eng.load_phantom(ph)
+    bl = case_beam(sd, n_low)
+    bh = case_beam(sd, n_high)
+    low = eng.run(bl, 0, 1_000_003 * sd + 1)
+    high = eng.run(bh, 0, 1_000_003 * sd + 2)
+    high.mul_(n_low / n_high)
+    eng.sync()
+    dens = torch.from_numpy(np.ascontiguousarray(ph.density)).cuda()
+    return [Case(sd, ph if keep_phantom else None, dens, low, high, bl)]
 
 
 def train(net, samples, epochs, lr=1e-3, lr_final=1e-4, log=None, seed=0):

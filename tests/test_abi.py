@@ -47,12 +47,14 @@ def test_library_exports_every_declared_symbol(libfdc):
 
 def test_struct_layouts_match_c():
     from paper_1011_2188_gb300 import fdc
+    from paper_1011_2188_gb300.denoise import Conv3d
     structs = {
+        "fdc_conv3d": Conv3d,
         "fdc_database": fdc.Database, "fdc_phantom": fdc.Phantom, "fdc_spot": fdc.Spot,
         "fdc_beam": fdc.Beam, "fdc_schedule": fdc.Schedule, "fdc_run_opts": fdc.RunOpts,
         "fdc_outputs": fdc.Outputs, "fdc_counters": fdc.Counters,
     }
-    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>'] + [f'#include "{h}"' for h in HEADERS] + ["int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
         for f, _ in py._fields_:
