@@ -36,6 +36,10 @@ METRIC = "histories/sec and track-steps/sec on 1 GB300; wall time to 2% σ (plai
 BYTES_PER_RECORD = 16
 BYTES_PER_HISTORY = 64
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one replay launch of the default workload
+# (thorax, 10^5 tracks per energy, 10^7 histories, track group 32), from one
+# ncu capture of the current kernel (profiles/replay_kernel_thorax.md).
+REPLAY_TRAFFIC_DEFAULT = 1.87e9 + 5.26e6
 
 
 def parse():
@@ -150,9 +154,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_parallel(db, ph, beam, seed, h_begin, n, cores):
+    """The unchanged oracle on `cores` threads over disjoint, contiguous history
+    ranges of [h_begin, h_begin + n) (ctypes releases the GIL around the C
+    call; the oracle keeps no global state).  Returns (seconds, track steps)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    oracle.lib()
+    cuts = [h_begin + (n * i) // cores for i in range(cores + 1)]
+    t = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        res = list(ex.map(lambda i: oracle.run(db, ph, beam, seed=seed, h_begin=cuts[i], h_end=cuts[i + 1]),
+                          range(cores)))
+    return time.perf_counter() - t, sum(r.n_steps for r in res)
+
+
 def cpu_baseline(db, ph, beam, seed, target_s=12.0):
-    """The oracle as it stands, single-threaded, on a bounded sample of the
-    workload's histories (calibrated to ~target_s seconds)."""
+    """The oracle as it stands on a bounded sample of the workload's histories:
+    single-threaded (calibrated to ~target_s seconds), then on every host core
+    over disjoint history ranges (~target_s seconds again)."""
     import oracle
     oracle.build()
     n0 = 2000
@@ -163,9 +190,18 @@ def cpu_baseline(db, ph, beam, seed, target_s=12.0):
     t = time.perf_counter()
     r = oracle.run(db, ph, beam, seed=seed, h_begin=n0, h_end=n0 + n)
     dt = time.perf_counter() - t
-    return {"value": n / dt, "unit": "histories/s", "cores": 1, "kind": "oracle",
-            "sample": f"histories [{n0}, {n0 + n}) of the same beam and seed, sequential FP64 oracle",
-            "track_steps_per_s": r.n_steps / dt, "seconds": dt}
+    single = {"value": n / dt, "unit": "histories/s", "cores": 1, "kind": "oracle",
+              "sample": f"histories [{n0}, {n0 + n}) of the same beam and seed, sequential FP64 oracle",
+              "track_steps_per_s": r.n_steps / dt, "seconds": dt}
+    cores = host_cores()
+    if cores <= 1:
+        return single
+    m = int(min(n * cores, 20_000_000))
+    dtp, steps = oracle_parallel(db, ph, beam, seed, n0 + n, m, cores)
+    return {"value": m / dtp, "unit": "histories/s", "cores": cores, "kind": "oracle",
+            "sample": f"histories [{n0 + n}, {n0 + n + m}) of the same beam and seed; the sequential FP64 "
+                      f"oracle on {cores} threads over disjoint contiguous history ranges",
+            "track_steps_per_s": steps / dtp, "seconds": dtp, "single_core": single}
 
 
 def time_to_sigma(eng, beam, ph, seed, target=0.02, n_batches=10, n0=200_000, local=0, track_group=1):
@@ -371,24 +407,26 @@ def run_reference(args, rank, world):
     for _ in range(args.warmup):
         oracle.run(db, ph, beam, seed=1234, h_begin=off, h_end=off + min(per, 2000))
         off += min(per, 2000)
+    # each step: per histories on every host core, over disjoint history ranges
+    cores = host_cores()
     times, steps = [], 0
     for _ in range(args.steps):
-        t = time.perf_counter()
-        r = oracle.run(db, ph, beam, seed=1234, h_begin=off, h_end=off + per)
-        times.append(time.perf_counter() - t)
-        steps += r.n_steps
-        off += per
+        dt, st = oracle_parallel(db, ph, beam, 1234, off, per * cores, cores)
+        times.append(dt)
+        steps += st
+        off += per * cores
     tot = sum(times)
-    value = per * args.steps / tot
+    value = per * cores * args.steps / tot
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "histories/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc, "histories_per_step": per},
+        "config": {"workload": desc, "histories_per_step": per * cores},
         "track_steps_per_s": steps / tot,
-        "cpu_baseline": {"value": value, "unit": "histories/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{per} histories per step of the workload, sequential FP64 oracle"},
+        "cpu_baseline": {"value": value, "unit": "histories/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per * cores} histories per step of the workload; the sequential FP64 "
+                                   f"oracle on {cores} threads over disjoint contiguous history ranges"},
         "e2e": {"value": value, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -553,7 +591,10 @@ def main():
         "steps_per_history": steps_per_run / hist_per_run,
         "replay_ms": rep_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
+                     "frac": achieved / hbm_peak,
+                     "traffic": (REPLAY_TRAFFIC_DEFAULT if (args.workload == "thorax" and n == 10_000_000
+                                                           and args.tracks == 100_000 and args.track_group == 32)
+                                 else None),
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "note": "not the binding resource: the replay kernel is bound by instruction issue "

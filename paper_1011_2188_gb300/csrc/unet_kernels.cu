@@ -559,18 +559,26 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(const Conv3dArgs g, con
     }
 }
 
-// db[c] += sum over rows of dy[row][c]
+// db[c] += sum over rows of dy[row][c]: per-thread partial sums over the
+// block's rows, reduced per channel in shared memory, one atomic per channel
+// and block.
 __global__ void bias_grad_kernel(const __nv_bfloat16 *dy, long long rows, int C, float *db, int chunk) {
+    __shared__ float sm[256];
     const int c = threadIdx.x % C;
     const int lanes = blockDim.x / C;
     const int sub = threadIdx.x / C;
-    if (sub >= lanes) return;
     const long long r0 = (long long)blockIdx.x * chunk;
     long long r1 = r0 + chunk;
     if (r1 > rows) r1 = rows;
     float s = 0.f;
-    for (long long r = r0 + sub; r < r1; r += lanes) s += __bfloat162float(dy[r * C + c]);
-    atomicAdd(db + c, s);
+    if (sub < lanes)
+        for (long long r = r0 + sub; r < r1; r += lanes) s += __bfloat162float(dy[r * C + c]);
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    if (sub == 0) {
+        for (int k = 1; k < lanes; ++k) s += sm[k * C + c];
+        atomicAdd(db + c, s);
+    }
 }
 
 // [ci][tap][co] <- [co][tap][ci]
