@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--eval-cases", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=12)
     ap.add_argument("--variants", type=int, default=1, help="mirror images per training phantom (1-4)")
+    ap.add_argument("--no-augment", action="store_true", help="train without the lateral symmetries")
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--high", type=int, default=100_000_000, help="histories of the target dose")
     ap.add_argument("--study", default="", choices=["", "precision", "denoiser", "unet_timing"],
@@ -336,7 +337,10 @@ def denoiser_study(args):
     e1.synchronize()
     inf_ms = e0.elapsed_time(e1) / 3
     t = time.perf_counter()
-    hist = denoise.train(net, samples, args.epochs, lr=1e-3, lr_final=5e-5)
+    held_out = [denoise.Sample(c.low, c.density, c.high) for c in eval_cases]
+    hist, hist_out = denoise.train(net, samples, args.epochs, lr=1e-3, lr_final=5e-5, augment=not args.no_augment,
+                                   held_out=held_out)
+    del held_out
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t
     rows, summary = denoise.evaluate(net, eng, eval_cases, n_low, (0.2, 0.2, 0.2))
@@ -352,7 +356,8 @@ def denoiser_study(args):
             "generate_s": t_gen, "train_s": t_train, "iteration_ms": it_ms, "inference_ms": inf_ms,
             "forward_gflop": flops / 1e9, "inference_tflops": flops / (inf_ms * 1e-3) / 1e12,
             "training_tflops": 3 * flops / (it_ms * 1e-3) / 1e12,
-            "loss_history": hist, "summary": summary, "cases": rows,
+            "augment": not args.no_augment, "loss_history": hist, "held_out_loss_history": hist_out,
+            "summary": summary, "cases": rows,
             "note": "doses compared at the low-history count (high-history dose scaled by n_low / n_high)",
             "total_s": time.perf_counter() - t_all}
     print(json.dumps(line), flush=True)

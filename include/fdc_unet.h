@@ -95,6 +95,21 @@ int fdc_add_bf16(const void *a, const void *b, void *out, int64_t n, void *strea
 int fdc_unet_prepare(const double *dose, const float *density, const double *dose_high, int64_t n,
                      double dose_scale, float density_scale, void *x, float *dose_in, float *target,
                      void *stream);
+/* Training augmentation by a lateral symmetry of a field along +z (the
+ * physics is unchanged by mirroring x or y or exchanging them, so a transformed
+ * pair is another valid low/high-history pair): for every voxel of the d x h x w
+ * grid (x fastest), x_out[z][y][x] = x[z][y'][x'] (16 bf16 channels) and, if
+ * target is not NULL, target_out likewise (FP32), where (y', x') is (y, x)
+ * after exchanging them (code bit 2; needs h == w), then mirroring x (bit 0)
+ * and y (bit 1).  Outputs must not alias inputs.  FDC_ERR_INVALID on bad
+ * sizes, a code outside 0..7 or aliasing. */
+int fdc_unet_dihedral(const void *x, const float *target, int32_t d, int32_t h, int32_t w, int32_t code,
+                      void *x_out, float *target_out, void *stream);
+/* Device status of the tensor-core convolutions: FDC_OK, or FDC_ERR_TIMEOUT
+ * once a convolution CTA gave up waiting for its accumulator (that CTA wrote
+ * no output); clear != 0 resets it.  Synchronises with the device; not for
+ * use inside stream capture. */
+int fdc_unet_status(int32_t clear);
 /* Denoised dose: dose_out [n] (FP64, Gy) = max(0, (head[n][16] channel 0 + dose_in) * dose_scale). */
 int fdc_unet_finish(const float *head, const float *dose_in, int64_t n, double dose_scale, double *dose_out,
                     void *stream);

@@ -163,16 +163,19 @@ __device__ Start sample_start(const ReplayArgs &P, unsigned long long h) {
 #ifndef FDC_RECORD_EVICT_FIRST
 #define FDC_RECORD_EVICT_FIRST 0
 #endif
-// A lane reads its track's records in order, eight to a 128-byte line; when
-// it enters a line, the next line is prefetched into L2 (some eight steps of
-// lead over its use).
+// A lane reads its track's records in order, eight to a 128-byte line; with
+// FDC_RECORD_PREFETCH, entering a line prefetches the next one into L2 (some
+// eight steps of lead).  Measured slower on GB300 (1.4 % with shared tracks,
+// 4.9 % with independent ones), so off.
 #ifndef FDC_RECORD_PREFETCH
-#define FDC_RECORD_PREFETCH 1
+#define FDC_RECORD_PREFETCH 0
 #endif
 
+#if FDC_RECORD_PREFETCH
 __device__ __forceinline__ void prefetch_l2(const void *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
+#endif
 
 __device__ __forceinline__ unsigned long long evict_first_policy() {
     unsigned long long pol = 0;
@@ -197,7 +200,13 @@ __device__ __forceinline__ uint4 load_record(const uint4 *p, unsigned long long 
 
 __device__ __forceinline__ void sincos_(float a, float *s, float *c) { sincosf(a, s, c); }
 __device__ __forceinline__ void sincos_(double a, double *s, double *c) { sincos(a, s, c); }
-__device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
+// FP32 square root of the angle-scaling factor: the hardware approximation
+// (relative error ~2^-22, far below the half-precision database angles).
+__device__ __forceinline__ float sqrt_(float a) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
 __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
 __device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
 // Reciprocal: hardware approximation in FP32 (relative error ~1e-7, used for

@@ -13,7 +13,9 @@
 //            (r + pad - tap) / stride when that divides exactly.
 // Tiles: 128 rows x NT columns per CTA of four warps, K in steps of 16 channels
 // of one tap, operands staged through shared memory with cp.async (zero fill
-// for padding), mma.sync m16n8k16 BF16 -> FP32.
+// for padding), mma.sync m16n8k16 BF16 -> FP32.  It serves the 2^3 stride-2
+// and 1^3 layers; the 3^3 stride-1 layers (nearly all of the network's FLOPs)
+// run on the tcgen05 tensor cores with TMEM accumulators (conv3_tc_kernel).
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -46,15 +48,6 @@ __device__ __forceinline__ void mma_bf16(float c[4], unsigned a0, unsigned a1, u
 }
 
 __device__ __forceinline__ unsigned lds32(const unsigned char *p) { return *(const unsigned *)p; }
-
-// Four 8 x 8 b16 matrices from shared memory, one row address per lane.
-__device__ __forceinline__ void ldmatrix_x4(const unsigned char *p, unsigned &r0, unsigned &r1, unsigned &r2,
-                                            unsigned &r3) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(a));
-}
 
 struct RowCoord {
     int b, d, h, w;
@@ -204,140 +197,223 @@ __global__ void __launch_bounds__(128) conv_igemm_kernel(const Conv3dArgs g, con
     }
 }
 
-// 3x3x3, stride 1, padding 1: a CTA owns a 2 x 8 x 8 block of output voxels
-// (M = 128) and NT output channels.  Per 16-channel input slice it stages the
-// 4 x 10 x 10 input halo in shared memory once (cp.async, zero fill outside
-// the grid) and runs all 27 taps from it; weight fragments are read from
-// global memory through L1 (the slice's weights are a few KB).  Also serves
-// the data gradient with flipped, transposed weights.
+// Halo of a 2 x 8 x 8 voxel block for a 3^3 stencil (weight gradient).
 constexpr int kHD = 4, kHH = 10, kHW = 10, kHalo = kHD * kHH * kHW;
 
+// ---------------------------------------------------------------- tcgen05
+// 3x3x3 stride-1 padding-1 convolution on the fifth-generation tensor cores:
+// a CTA of four warps owns a 1 x 16 x 8 block of output voxels (M = 128 rows,
+// row m = 8 * (h - h0) + (w - w0)) and NT output channels.  Per 16-channel
+// input slice it stages the 3 x 18 x 10 input halo and the slice's weights in
+// shared memory in the canonical K-major layout without swizzle (8 rows of
+// 16 bytes per core matrix), and one thread issues the 27 tap GEMMs
+// (128 x NT x 16 each) as tcgen05.mma with the FP32 accumulator in tensor
+// memory.  The halo is stored [d][h][k-chunk][w][8 channels], so the eight
+// rows of a core matrix (eight consecutive w) are contiguous for any tap
+// offset kw: the A operand of tap (kd, kh, kw) is the halo itself, seen
+// through a descriptor at byte offset ((kd * 18 + kh) * 2) * 160 + kw * 16
+// with 160 bytes between k-chunks and 320 bytes between rows of w.
 // The input may be the channel concatenation of two tensors, src (ca channels,
 // optionally at half resolution and read through nearest x2 upsampling) and
-// src_b (cs - ca channels, full resolution), so that upsampling and skip
-// concatenation never materialise.
+// src_b (cs - ca channels, full resolution), so that the decoder's upsampling
+// and skip concatenation never materialise.  Every wait on the accumulator is
+// bounded; on timeout the CTA records FDC_ERR_TIMEOUT in g_tc_status, skips
+// its epilogue, frees its tensor memory and returns.
+constexpr int kTcHD = 3, kTcHH = 18, kTcHW = 10;
+constexpr int kTcHaloRows = kTcHD * kTcHH * kTcHW;             // 540 voxels
+constexpr int kTcChunkBytes = kTcHW * 16;                      // one k-chunk of one (d, h) row: 160 B
+constexpr int kTcHaloBytes = kTcHD * kTcHH * 2 * kTcChunkBytes;  // 17280 B
+constexpr long long kTcWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
+
+__device__ int g_tc_status;  // FDC_ERR_TIMEOUT once an accumulator wait has timed out
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor (no swizzle, K-major): start address,
+// leading byte offset (between core matrices along K), stride byte offset
+// (between groups of eight rows), all in 16-byte units; descriptor version 1.
+__device__ __forceinline__ unsigned long long umma_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((saddr >> 4) & 0x3fffu) | ((unsigned long long)((lbo >> 4) & 0x3fffu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 and M >> 4.
+__host__ __device__ constexpr unsigned umma_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(unsigned tmem_d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                          int accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned mbar, unsigned parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > kTcWaitCycles) return false;
+    }
+}
+
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float v[16]) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 template <int NT>
-__global__ void __launch_bounds__(128) conv3_halo_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
-                                                         const __nv_bfloat16 *wt, const float *bias,
-                                                         __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn,
-                                                         int relu, int ca, int up_a, const __nv_bfloat16 *src_b) {
-    __shared__ __align__(16) unsigned char sH[2][kHalo * kRowBytes];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int grp = lane >> 2, tig = lane & 3;
-    const int D = g.in_d, H = g.in_h, W = g.in_w;  // stride 1, pad 1: output grid = input grid
-    const int tiles_w = (W + 7) / 8, tiles_h = (H + 7) / 8, tiles_d = (D + 1) / 2;
+__global__ void __launch_bounds__(128) conv3_tc_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
+                                                       const __nv_bfloat16 *wt, const float *bias,
+                                                       __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn,
+                                                       int relu, int ca, int up_a, const __nv_bfloat16 *src_b) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *sH = smem;
+    unsigned char *sW = smem + kTcHaloBytes;
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ unsigned tmem_slot;
+    constexpr unsigned kCols = NT < 32 ? 32 : NT;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int D = g.in_d, H = g.in_h, W = g.in_w;
+    const int tiles_w = (W + 7) / 8, tiles_h = (H + 15) / 16;
     long long t = blockIdx.x;
     const int tw = (int)(t % tiles_w); t /= tiles_w;
     const int th = (int)(t % tiles_h); t /= tiles_h;
-    const int td = (int)(t % tiles_d);
-    const int b = (int)(t / tiles_d);
-    const int d0 = td * 2, h0 = th * 8, w0 = tw * 8;
+    const int d0 = (int)(t % D);
+    const int b = (int)(t / D);
+    const int h0 = th * 16, w0 = tw * 8;
     const int n0 = blockIdx.y * NT;
     const int slices = Cs / 16;
-
     const int cb = Cs - ca;
     const int Da = up_a ? D / 2 : D, Ha = up_a ? H / 2 : H, Wa = up_a ? W / 2 : W;
-    auto load_halo = [&](int buf, int c0) {
+    const unsigned mb = smem_u32(&mbar);
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = tmem_slot;
+
+    bool ok = true;
+    unsigned phase = 0;
+    for (int sl = 0; sl < slices && ok; ++sl) {
+        const int c0 = sl * 16;
         const bool from_a = c0 < ca;
-        for (int i = tid; i < kHalo * 2; i += 128) {
-            const int row = i >> 1, half = i & 1;
-            const int hd = row / (kHH * kHW), hh = (row / kHW) % kHH, hw = row % kHW;
+        for (int i = tid; i < kTcHaloRows * 2; i += 128) {
+            const int row = i >> 1, kc = i & 1;
+            const int hd = row / (kTcHH * kTcHW), hh = (row / kTcHW) % kTcHH, hw = row % kTcHW;
             const int d = d0 - 1 + hd, h = h0 - 1 + hh, w = w0 - 1 + hw;
-            const bool ok = d >= 0 && d < D && h >= 0 && h < H && w >= 0 && w < W;
+            const bool in = d >= 0 && d < D && h >= 0 && h < H && w >= 0 && w < W;
             const __nv_bfloat16 *p = src;
-            if (ok) {
+            if (in) {
                 if (from_a) {
                     const int da = up_a ? d >> 1 : d, ha = up_a ? h >> 1 : h, wa = up_a ? w >> 1 : w;
-                    p = src + ((((long long)b * Da + da) * Ha + ha) * Wa + wa) * ca + c0 + half * 8;
+                    p = src + ((((long long)b * Da + da) * Ha + ha) * Wa + wa) * ca + c0 + kc * 8;
                 } else {
-                    p = src_b + ((((long long)b * D + d) * H + h) * W + w) * cb + (c0 - ca) + half * 8;
+                    p = src_b + ((((long long)b * D + d) * H + h) * W + w) * cb + (c0 - ca) + kc * 8;
                 }
             }
-            cp_async16(sH[buf] + row * kRowBytes + half * 16, p, ok);
+            cp_async16(sH + ((hd * kTcHH + hh) * 2 + kc) * kTcChunkBytes + hw * 16, p, in);
         }
-    };
-
-    float acc[2][NT / 8][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < NT / 8; ++j)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
-
-    // A fragments by ldmatrix.x4: lane L supplies row (L & 7) + 8 ((L >> 3) & 1)
-    // of the 16-row tile at channel offset 8 (L >> 4).  Output row r of the
-    // 2 x 8 x 8 block: od = r / 64, oh = (r / 8) % 8, ow = r % 8.
-    unsigned lrow[2];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        const int r = warp * 32 + mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
-        const int hidx = ((r >> 6) * kHH + ((r >> 3) & 7)) * kHW + (r & 7);
-        lrow[mt] = hidx * kRowBytes + (lane >> 4) * 16;
-    }
-
-    load_halo(0, 0);
-    cp_async_commit();
-    for (int sl = 0; sl < slices; ++sl) {
-        const int buf = sl & 1;
-        if (sl + 1 < slices) load_halo(buf ^ 1, (sl + 1) * 16);
+        for (int i = tid; i < 27 * 2 * NT; i += 128) {
+            const int n = i % NT, q = i / NT, kc = q & 1, tap = q >> 1;
+            const int co = n0 + n;
+            const bool in = co < Nn;
+            const __nv_bfloat16 *p = in ? wt + ((long long)co * 27 + tap) * Cs + c0 + kc * 8 : wt;
+            cp_async16(sW + ((tap * 2 + kc) * NT + n) * 16, p, in);
+        }
         cp_async_commit();
-        cp_async_wait<1>();
+        cp_async_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
-        const unsigned char *Hs = sH[buf];
-        const int c0 = sl * 16;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned ha = smem_u32(sH), wa = smem_u32(sW);
+            constexpr unsigned idesc = umma_idesc(128, NT);
 #pragma unroll 1
-        for (int tap = 0; tap < 27; ++tap) {
-            const int kd = tap / 9, kh = (tap / 3) % 3, kw = tap % 3;
-            const int off = (kd * kHH + kh) * kHW + kw;
-            unsigned bfrag[NT / 8][2];
-#pragma unroll
-            for (int nt = 0; nt < NT / 8; ++nt) {
-                const int n = n0 + nt * 8 + grp;
-                const __nv_bfloat16 *q = wt + ((long long)(n < Nn ? n : 0) * 27 + tap) * Cs + c0 + tig * 2;
-                bfrag[nt][0] = n < Nn ? __ldg((const unsigned *)q) : 0u;
-                bfrag[nt][1] = n < Nn ? __ldg((const unsigned *)(q + 8)) : 0u;
+            for (int tap = 0; tap < 27; ++tap) {
+                const int kd = tap / 9, kh = (tap / 3) % 3, kw = tap % 3;
+                const unsigned long long ad =
+                    umma_desc(ha + ((kd * kTcHH + kh) * 2) * kTcChunkBytes + kw * 16, kTcChunkBytes, 2 * kTcChunkBytes);
+                const unsigned long long bd = umma_desc(wa + tap * 2 * NT * 16, NT * 16, 128);
+                umma_bf16(tmem, ad, bd, idesc, (sl | tap) != 0);
             }
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                unsigned a0, a1, a2, a3;
-                ldmatrix_x4(Hs + lrow[mt] + off * kRowBytes, a0, a1, a2, a3);
-#pragma unroll
-                for (int nt = 0; nt < NT / 8; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bfrag[nt][0], bfrag[nt][1]);
-            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
+                         : "memory");
         }
-        __syncthreads();
+        ok = mbar_wait_bounded(mb, phase);
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        ok = __syncthreads_and(ok);
     }
-    cp_async_wait<0>();
 
+    if (ok) {
+        const int m = warp * 32 + lane;
+        const int h = h0 + (m >> 3), w = w0 + (m & 7);
+        const bool in = h < H && w < W;
+        const long long v = (((long long)b * D + d0) * H + h) * W + w;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
+        for (int c = 0; c < NT; c += 16) {
+            float acc[16];
+            tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c, acc);
+            const int n = n0 + c;
+            if (!in || n >= Nn) continue;
 #pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {
-            const int r = warp * 32 + mt * 16 + grp + hf * 8;
-            const int d = d0 + (r >> 6), h = h0 + ((r >> 3) & 7), w = w0 + (r & 7);
-            if (d >= D || h >= H || w >= W) continue;
-            const long long v = (((long long)b * D + d) * H + h) * W + w;
+            for (int j = 0; j < 16; ++j) {
+                float x = acc[j];
+                if (bias) x += bias[n + j];
+                if (relu) x = fmaxf(x, 0.f);
+                acc[j] = x;
+            }
+            if (out_f32) {
 #pragma unroll
-            for (int nt = 0; nt < NT / 8; ++nt) {
-                const int n = n0 + nt * 8 + tig * 2;
-                if (n >= Nn) continue;
-                float v0 = acc[mt][nt][hf * 2], v1 = acc[mt][nt][hf * 2 + 1];
-                if (bias) {
-                    v0 += bias[n];
-                    v1 += bias[n + 1];
+                for (int j = 0; j < 16; ++j) out_f32[v * Nn + n + j] = acc[j];
+            }
+            if (out_bf16) {
+                uint4 q[2];
+                unsigned *qq = (unsigned *)q;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    __nv_bfloat162 p2 = __floats2bfloat162_rn(acc[2 * j], acc[2 * j + 1]);
+                    qq[j] = *(unsigned *)&p2;
                 }
-                if (relu) {
-                    v0 = fmaxf(v0, 0.f);
-                    v1 = fmaxf(v1, 0.f);
-                }
-                if (out_f32) {
-                    out_f32[v * Nn + n] = v0;
-                    out_f32[v * Nn + n + 1] = v1;
-                }
-                if (out_bf16) *(__nv_bfloat162 *)(out_bf16 + v * Nn + n) = __floats2bfloat162_rn(v0, v1);
+                uint4 *dst = (uint4 *)(out_bf16 + v * Nn + n);
+                dst[0] = q[0];
+                dst[1] = q[1];
             }
         }
+    } else if (tid == 0) {
+        atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
     }
 }
 
@@ -714,6 +790,27 @@ __global__ void prepare_kernel(const double *dose, const float *density, const d
     }
 }
 
+// Lateral symmetry of a field along +z: out[d][h][w] = in[d][h'][w'] with
+// (h', w') the image of (h, w) under code (bit 0: mirror w, bit 1: mirror h,
+// bit 2: exchange h and w; h == w when bit 2 is set).  One 32-byte row of 16
+// bf16 channels per voxel of x, one FP32 value per voxel of t.
+__global__ void dihedral_kernel(const uint4 *x, const float *t, int D, int H, int W, int code, uint4 *xo,
+                                float *to) {
+    const long long n = (long long)D * H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(i % W);
+        const int h = (int)((i / W) % H);
+        const long long d = i / ((long long)W * H);
+        int hs = (code & 4) ? w : h, ws = (code & 4) ? h : w;
+        if (code & 1) ws = W - 1 - ws;
+        if (code & 2) hs = H - 1 - hs;
+        const long long j = (d * H + hs) * W + ws;
+        xo[2 * i] = x[2 * j];
+        xo[2 * i + 1] = x[2 * j + 1];
+        if (t) to[i] = t[j];
+    }
+}
+
 __global__ void finish_kernel(const float *head, const float *dose_in, long long n, double scale, double *dose_out) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double v = ((double)head[i * 16] + (double)dose_in[i]) * scale;
@@ -793,17 +890,35 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
                              void *out_bf16, float *out_f32, int Cs, int Nn, int relu, cudaStream_t st,
                              int ca, int up_a, const void *src_b) {
     if (ca <= 0) ca = Cs;
-    const int nt = Nn >= 64 ? 64 : (Nn >= 32 ? 32 : 16);
-    const long long tiles = (long long)g.batch * ((g.in_d + 1) / 2) * ((g.in_h + 7) / 8) * ((g.in_w + 7) / 8);
-    dim3 grid((unsigned)tiles, (unsigned)((Nn + nt - 1) / nt));
+    const long long tiles = (long long)g.batch * g.in_d * ((g.in_h + 15) / 16) * ((g.in_w + 7) / 8);
+    const int nt = Nn % 64 == 0 ? 64 : (Nn % 32 == 0 ? 32 : 16);  // Nn is a multiple of 16
+    dim3 grid((unsigned)tiles, (unsigned)(Nn / nt));
+    const int smem = kTcHaloBytes + 27 * 2 * nt * 16;
     auto s = (const __nv_bfloat16 *)src;
     auto w = (const __nv_bfloat16 *)wt;
     auto ob = (__nv_bfloat16 *)out_bf16;
     auto sb = (const __nv_bfloat16 *)src_b;
-    if (nt == 64) conv3_halo_kernel<64><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
-    else if (nt == 32) conv3_halo_kernel<32><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
-    else conv3_halo_kernel<16><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
+    if (nt == 64) {  // 71 KB of shared memory: above the default 48 KB limit
+        const cudaError_t e =
+            cudaFuncSetAttribute(conv3_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        conv3_tc_kernel<64><<<grid, 128, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
+    } else if (nt == 32) {
+        conv3_tc_kernel<32><<<grid, 128, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
+    } else {
+        conv3_tc_kernel<16><<<grid, 128, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
+    }
     return cudaGetLastError();
+}
+
+int tc_status(bool clear) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int)) != cudaSuccess) return (int)FDC_ERR_CUDA;
+    if (clear && v) {
+        const int z = 0;
+        if (cudaMemcpyToSymbol(g_tc_status, &z, sizeof(int)) != cudaSuccess) return (int)FDC_ERR_CUDA;
+    }
+    return v;
 }
 
 cudaError_t launch_flip_transpose(const void *w, void *wf, int co, int k, int ci, cudaStream_t st) {
@@ -927,6 +1042,13 @@ cudaError_t launch_prepare(const double *dose, const float *density, const doubl
                            cudaStream_t st) {
     prepare_kernel<<<grid_for(n), 256, 0, st>>>(dose, density, dose_high, n, inv_scale, density_scale,
                                                 (__nv_bfloat16 *)x, dose_in, target);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dihedral(const void *x, const float *t, int D, int H, int W, int code, void *xo, float *to,
+                            cudaStream_t st) {
+    const long long n = (long long)D * H * W;
+    dihedral_kernel<<<grid_for(n), 256, 0, st>>>((const uint4 *)x, t, D, H, W, code, (uint4 *)xo, to);
     return cudaGetLastError();
 }
 
@@ -1081,6 +1203,16 @@ int fdc_unet_prepare(const double *dose, const float *density, const double *dos
     return rc(fdc::launch_prepare(dose, density, dose_high, n, 1.0 / dose_scale, density_scale, x, dose_in,
                                   target, (cudaStream_t)stream));
 }
+
+int fdc_unet_dihedral(const void *x, const float *target, int32_t d, int32_t h, int32_t w, int32_t code,
+                      void *x_out, float *target_out, void *stream) {
+    if (!x || !x_out || x == (const void *)x_out || d < 1 || h < 1 || w < 1 || code < 0 || code > 7 ||
+        ((code & 4) && h != w) || (target && (!target_out || target == target_out)))
+        return FDC_ERR_INVALID;
+    return rc(fdc::launch_dihedral(x, target, d, h, w, code, x_out, target_out, (cudaStream_t)stream));
+}
+
+int fdc_unet_status(int32_t clear) { return fdc::tc_status(clear != 0); }
 
 int fdc_unet_finish(const float *head, const float *dose_in, int64_t n, double dose_scale, double *dose_out,
                     void *stream) {

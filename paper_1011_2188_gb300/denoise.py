@@ -293,6 +293,23 @@ class Sample:
                                        _p(self.x), _p(self.dose_in), _p(self.target), _s()), "prepare")
 
 
+class _Transformed:
+    """Scratch pair holding a sample after a lateral symmetry (input and target)."""
+
+    def __init__(self, like):
+        import torch
+        self.shape = like.shape
+        self.x = torch.empty_like(like.x)
+        self.target = torch.empty_like(like.target)
+        self.dose_in = like.dose_in
+
+    def load(self, sample, code):
+        d, h, w = sample.shape
+        _ok(fdc.lib().fdc_unet_dihedral(_p(sample.x), _p(sample.target), d, h, w, code, _p(self.x),
+                                        _p(self.target), _s()), "dihedral")
+        return self
+
+
 def train_step(net, sample, lr):
     """Forward, loss, backward and Adam step; returns the loss tensor (FP32,
     device) without synchronising."""
@@ -409,26 +426,38 @@ def _one_case(eng, sd, ph, n_low, n_high, keep_phantom):
     return [Case(sd, ph if keep_phantom else None, dens, low, high, bl)]
 
 
-def train(net, samples, epochs, lr=1e-3, lr_final=1e-4, log=None, seed=0):
+def train(net, samples, epochs, lr=1e-3, lr_final=1e-4, log=None, seed=0, augment=False, held_out=None):
     """Adam over the samples in a seeded random order; cosine learning rate
-    from lr to lr_final.  Returns the per-epoch mean losses."""
+    from lr to lr_final.  With augment, every visit of a sample sees it under
+    a random lateral symmetry (mirror x / y, exchange x and y: exact symmetries
+    of a field along +z).  Returns the per-epoch mean training losses and, with
+    held_out samples, their mean loss after every epoch."""
     import torch
     rng = np.random.default_rng(seed)
     total = epochs * len(samples)
     it = 0
-    hist = []
+    hist, hist_out = [], []
+    scratch = _Transformed(samples[0]) if augment and samples else None
     for ep in range(epochs):
         losses = []
         for i in rng.permutation(len(samples)):
             f = it / max(1, total - 1)
             cur = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * f))
-            losses.append(train_step(net, samples[i], cur))
+            s = samples[i]
+            if scratch is not None:
+                d, h, w = s.shape
+                code = int(rng.integers(0, 8 if h == w else 4))
+                if code:
+                    s = scratch.load(s, code)
+            losses.append(train_step(net, s, cur))
             it += 1
         m = float(torch.cat(losses).mean())
         hist.append(m)
+        if held_out:
+            hist_out.append(float(torch.cat([evaluate_loss(net, s) for s in held_out]).mean()))
         if log:
             log(ep, m)
-    return hist
+    return (hist, hist_out) if held_out else hist
 
 
 def evaluate(net, eng, cases, n_low, spacing, dose_frac=0.02, dta=0.2, threshold=0.1, target_sigma=0.02):

@@ -56,6 +56,8 @@ SIGNATURES = {
     "fdc_add_bf16": (C.c_int, [_p, _p, _p, C.c_int64, _p]),
     "fdc_unet_prepare": (C.c_int, [_p, _p, _p, C.c_int64, C.c_double, C.c_float, _p, _p, _p, _p]),
     "fdc_unet_finish": (C.c_int, [_p, _p, C.c_int64, C.c_double, _p, _p]),
+    "fdc_unet_status": (C.c_int, [C.c_int32]),
+    "fdc_unet_dihedral": (C.c_int, [_p, _p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _p, _p, _p]),
     "fdc_gamma": (C.c_int, [_p, _p, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
                             C.c_double, C.c_double, C.c_double, _p, _p, _p, _p]),
     "fdc_debug_philox": (C.c_int, [C.c_uint64, C.c_uint64, _p, C.c_uint64, _p, _p]),

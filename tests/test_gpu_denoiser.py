@@ -23,7 +23,7 @@ def test_denoiser_beats_the_raw_low_history_dose():
     held = denoise.generate_cases(eng, range(5000, 5004), n_low, n_high, grid, keep_phantom=True)
     samples = [denoise.Sample(c.low, c.density, c.high) for c in train]
     net = denoise.UNet(seed=3)
-    hist = denoise.train(net, samples, epochs=10, lr=1e-3, lr_final=1e-4)
+    hist = denoise.train(net, samples, epochs=10, lr=1e-3, lr_final=1e-4, augment=True)
     assert hist[-1] < 0.7 * hist[0], hist
     gains = []
     for c in held:

@@ -46,6 +46,7 @@ CASES = [
     ((1, 4, 4, 6, 128), 64, 3, 1, 1),
     ((1, 16, 16, 16, 16), 16, 3, 1, 1),
     ((2, 3, 9, 17, 48), 32, 3, 1, 1),
+    ((1, 3, 37, 12, 16), 32, 3, 1, 1),  # three 16-row tiles in h, the last ragged
 ]
 
 
@@ -133,6 +134,45 @@ def test_elementwise_kernels():
     torch.cuda.synchronize()
     np.testing.assert_allclose(s.double().cpu().numpy(), 2 * a, rtol=8e-3)
     np.testing.assert_array_equal(dx.double().cpu().numpy(), np.where(a > 0, a, 0.0))
+
+
+def test_tensor_core_status_clean():
+    """No tensor-core convolution gave up waiting for its accumulator in the
+    convolutions above (the status is sticky until cleared)."""
+    from paper_1011_2188_gb300 import fdc
+    assert fdc.lib().fdc_unet_status(1) == 0
+
+
+@pytest.mark.parametrize("code", range(8))
+def test_dihedral_augmentation(code):
+    """Mirror x (bit 0), mirror y (bit 1), exchange x and y first (bit 2),
+    against numpy's own array operations; byte-exact."""
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    L = fdc.lib()
+    rng = np.random.default_rng(10 + code)
+    D, H, W = 3, 6, 6
+    xt, x = bf16(rng.normal(size=(1, D, H, W, 16)))
+    t = rng.normal(size=(D, H, W)).astype(np.float32)
+    tt = torch.from_numpy(t).cuda()
+    xo, to = torch.empty_like(xt), torch.empty_like(tt)
+    assert L.fdc_unet_dihedral(ptr(xt), ptr(tt), D, H, W, code, ptr(xo), ptr(to), None) == 0
+    torch.cuda.synchronize()
+    # out[z][y][x] = in[z][y'][x']: (y', x') = (x, y) when exchanged, then
+    # x' -> W-1-x' (bit 0) and y' -> H-1-y' (bit 1)
+    yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    ys, xs = (xx, yy) if code & 4 else (yy, xx)
+    if code & 1:
+        xs = W - 1 - xs
+    if code & 2:
+        ys = H - 1 - ys
+    ex, et = x[0][:, ys, xs], t[:, ys, xs]
+    np.testing.assert_array_equal(xo.double().cpu().numpy()[0], ex)
+    np.testing.assert_array_equal(to.cpu().numpy(), et)
+    # refused: exchange on a non-square slice, aliasing, bad code
+    assert L.fdc_unet_dihedral(ptr(xt), ptr(tt), D, H, W + 1, 4, ptr(xo), ptr(to), None) != 0
+    assert L.fdc_unet_dihedral(ptr(xt), ptr(tt), D, H, W, 1, ptr(xt), ptr(to), None) != 0
+    assert L.fdc_unet_dihedral(ptr(xt), ptr(tt), D, H, W, 8, ptr(xo), ptr(to), None) != 0
 
 
 def test_mse_and_adam():
