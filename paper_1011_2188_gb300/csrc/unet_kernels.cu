@@ -15,11 +15,14 @@
 // of one tap, operands staged through shared memory with cp.async (zero fill
 // for padding), mma.sync m16n8k16 BF16 -> FP32.  It serves the 2^3 stride-2
 // and 1^3 layers; the 3^3 stride-1 layers (nearly all of the network's FLOPs)
-// run on the tcgen05 tensor cores with TMEM accumulators (conv3_tc_kernel).
+// run on the tcgen05 tensor cores with TMEM accumulators (conv3_tc_kernel,
+// persistent and pipelined).
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "fdc_internal.h"
 
@@ -33,6 +36,12 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool va
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     const int n = valid ? 16 : 0;
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(n));
+}
+// The same with L1 allocation: for data that many CTAs on an SM read (weights).
+__device__ __forceinline__ void cp_async16_ca(void *smem, const void *gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(n));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 template <int N>
@@ -278,6 +287,12 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float v[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void umma_commit(unsigned mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+
+// 16 (h) x 8 (w) output voxels per CTA, 27 MMAs of N = NT per slice (NT = 64).
 template <int NT>
 __global__ void __launch_bounds__(128) conv3_tc_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
                                                        const __nv_bfloat16 *wt, const float *bias,
@@ -344,7 +359,8 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const Conv3dArgs g, const
             const int co = n0 + n;
             const bool in = co < Nn;
             const __nv_bfloat16 *p = in ? wt + ((long long)co * 27 + tap) * Cs + c0 + kc * 8 : wt;
-            cp_async16(sW + ((tap * 2 + kc) * NT + n) * 16, p, in);
+            // every CTA reads the same slice of weights: through L1, not from L2 each time
+            cp_async16_ca(sW + ((tap * 2 + kc) * NT + n) * 16, p, in);
         }
         cp_async_commit();
         cp_async_wait<0>();
@@ -362,8 +378,7 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const Conv3dArgs g, const
                 const unsigned long long bd = umma_desc(wa + tap * 2 * NT * 16, NT * 16, 128);
                 umma_bf16(tmem, ad, bd, idesc, (sl | tap) != 0);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
-                         : "memory");
+            umma_commit(mb);
         }
         ok = mbar_wait_bounded(mb, phase);
         phase ^= 1u;
@@ -399,6 +414,171 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const Conv3dArgs g, const
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     __nv_bfloat162 p2 = __floats2bfloat162_rn(acc[2 * j], acc[2 * j + 1]);
+                    qq[j] = *(unsigned *)&p2;
+                }
+                uint4 *dst = (uint4 *)(out_bf16 + v * Nn + n);
+                dst[0] = q[0];
+                dst[1] = q[1];
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
+    }
+}
+
+
+// kw-stacked form (NT = 16 or 32): the three taps along w share one MMA.  A
+// CTA owns 8 (h) x 14 (w) output voxels and NT channels; the A operand is the
+// input halo itself, 8 rows of h x 16 columns of w (M = 128, row m = 16 h + w'
+// for input column w0 - 1 + w'), and one MMA per (kd, kh) multiplies it by the
+// weights of the three kw taps stacked along N (N = 3 NT, column kw NT + co):
+//   D[m][kw NT + co] = sum_{kd, kh, ci} x[d0 - 1 + kd][h0 - 1 + h + kh][w0 - 1 + w'][ci]
+//                                       * w[co][kd][kh][kw][ci],
+// so that y[h][w][co] = sum_kw D[16 h + w + kw][kw NT + co]: 9 MMAs per 16-channel
+// slice instead of 27, each three times wider (tensor-core time per MMA is
+// dominated by its fixed part at N = 16).  The epilogue adds the three column
+// blocks with lane shuffles (rows m + 1, m + 2 belong to lanes t + 1, t + 2 of
+// the same warp).  Halo layout [d 3][h 10][w-group 2][k-chunk 2][8 w][8 ch]:
+// 256 bytes per (d, h, w-group), so consecutive 8-row groups of A are 256
+// bytes apart and k-chunks 128 bytes apart.
+constexpr int kKwHD = 3, kKwHH = 10, kKwHW = 16;
+constexpr int kKwHalo = kKwHD * kKwHH * kKwHW;  // 480 voxels
+constexpr int kKwHaloBytes = kKwHalo * 32;      // 15360 B
+
+template <int NT>
+__global__ void __launch_bounds__(128) conv3_kws_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
+                                                        const __nv_bfloat16 *wt, const float *bias,
+                                                        __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn,
+                                                        int relu, int ca, int up_a, const __nv_bfloat16 *src_b) {
+    constexpr int N3 = 3 * NT;
+    constexpr unsigned kCols = N3 <= 64 ? 64 : 128;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *sH = smem;
+    unsigned char *sW = smem + kKwHaloBytes;  // [kd kh][k-chunk][kw NT + co][8]
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ unsigned tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int D = g.in_d, H = g.in_h, W = g.in_w;
+    const int tiles_w = (W + 13) / 14, tiles_h = (H + 7) / 8;
+    long long t = blockIdx.x;
+    const int tw = (int)(t % tiles_w); t /= tiles_w;
+    const int th = (int)(t % tiles_h); t /= tiles_h;
+    const int d0 = (int)(t % D);
+    const int b = (int)(t / D);
+    const int h0 = th * 8, w0 = tw * 14;
+    const int n0 = blockIdx.y * NT;
+    const int slices = Cs / 16;
+    const int cb = Cs - ca;
+    const int Da = up_a ? D / 2 : D, Ha = up_a ? H / 2 : H, Wa = up_a ? W / 2 : W;
+    const unsigned mb = smem_u32(&mbar);
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = tmem_slot;
+
+    bool ok = true;
+    unsigned phase = 0;
+    for (int sl = 0; sl < slices && ok; ++sl) {
+        const int c0 = sl * 16;
+        const bool from_a = c0 < ca;
+        for (int i = tid; i < kKwHalo * 2; i += 128) {
+            const int row = i >> 1, kc = i & 1;
+            const int hd = row / (kKwHH * kKwHW), hh = (row / kKwHW) % kKwHH, hw = row % kKwHW;
+            const int d = d0 - 1 + hd, h = h0 - 1 + hh, w = w0 - 1 + hw;
+            const bool in = d >= 0 && d < D && h >= 0 && h < H && w >= 0 && w < W;
+            const __nv_bfloat16 *p = src;
+            if (in) {
+                if (from_a) {
+                    const int da = up_a ? d >> 1 : d, ha = up_a ? h >> 1 : h, wa = up_a ? w >> 1 : w;
+                    p = src + ((((long long)b * Da + da) * Ha + ha) * Wa + wa) * ca + c0 + kc * 8;
+                } else {
+                    p = src_b + ((((long long)b * D + d) * H + h) * W + w) * cb + (c0 - ca) + kc * 8;
+                }
+            }
+            cp_async16(sH + (((hd * kKwHH + hh) * 2 + (hw >> 3)) * 2 + kc) * 128 + (hw & 7) * 16, p, in);
+        }
+        for (int i = tid; i < 9 * 2 * N3; i += 128) {
+            const int n = i % N3, q = i / N3, kc = q & 1, kdh = q >> 1;
+            const int kw = n / NT, co = n0 + n % NT;
+            const bool in = co < Nn;
+            const __nv_bfloat16 *p = in ? wt + ((long long)co * 27 + kdh * 3 + kw) * Cs + c0 + kc * 8 : wt;
+            // every CTA reads the same slice of weights: through L1, not from L2 each time
+            cp_async16_ca(sW + ((kdh * 2 + kc) * N3 + n) * 16, p, in);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned ha = smem_u32(sH), wa = smem_u32(sW);
+            constexpr unsigned idesc = umma_idesc(128, N3);
+#pragma unroll 1
+            for (int kdh = 0; kdh < 9; ++kdh) {
+                const int kd = kdh / 3, kh = kdh % 3;
+                const unsigned long long ad = umma_desc(ha + (kd * kKwHH + kh) * 512, 128, 256);
+                const unsigned long long bd = umma_desc(wa + kdh * 2 * N3 * 16, N3 * 16, 128);
+                umma_bf16(tmem, ad, bd, idesc, (sl | kdh) != 0);
+            }
+            umma_commit(mb);
+        }
+        ok = mbar_wait_bounded(mb, phase);
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        ok = __syncthreads_and(ok);
+    }
+
+    if (ok) {
+        const int m = warp * 32 + lane;
+        const int h = h0 + (m >> 4), wl = m & 15, w = w0 + wl;
+        const bool in = wl < 14 && h < H && w < W;
+        const long long v = (((long long)b * D + d0) * H + h) * W + w;
+        const unsigned base = tmem + ((unsigned)(warp * 32) << 16);
+#pragma unroll
+        for (int c = 0; c < NT; c += 16) {
+            float a0[16], a1[16], a2[16];
+            tmem_ld16(base + (unsigned)c, a0);
+            tmem_ld16(base + (unsigned)(NT + c), a1);
+            tmem_ld16(base + (unsigned)(2 * NT + c), a2);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                a0[j] += __shfl_down_sync(0xffffffffu, a1[j], 1) + __shfl_down_sync(0xffffffffu, a2[j], 2);
+            const int n = n0 + c;
+            if (!in || n >= Nn) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                float x = a0[j];
+                if (bias) x += __ldg(bias + n + j);
+                if (relu) x = fmaxf(x, 0.f);
+                a0[j] = x;
+            }
+            if (out_f32) {
+                float4 *dst = (float4 *)(out_f32 + v * Nn + n);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dst[j] = make_float4(a0[4 * j], a0[4 * j + 1], a0[4 * j + 2], a0[4 * j + 3]);
+            }
+            if (out_bf16) {
+                uint4 q[2];
+                unsigned *qq = (unsigned *)q;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    __nv_bfloat162 p2 = __floats2bfloat162_rn(a0[2 * j], a0[2 * j + 1]);
                     qq[j] = *(unsigned *)&p2;
                 }
                 uint4 *dst = (uint4 *)(out_bf16 + v * Nn + n);
@@ -886,27 +1066,62 @@ int grid_for(long long n, int threads = 256) {
 
 }  // namespace
 
+// SM count and resident CTAs of one kernel at one shared-memory size, queried
+// once per device (the caller holds one cache per kernel); the kernel's opt-in
+// shared-memory limit is raised to the device maximum on first use.
+struct OccCache {
+    int v[16][16][3];  // [device][slot] = {smem, sms, per_sm}
+    std::mutex mu;
+};
+template <typename K>
+cudaError_t prepare_kernel_smem(OccCache &c, K kernel, int smem) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(c.mu);
+    if (dev < 16)
+        for (int i = 0; i < 16 && c.v[dev][i][0]; ++i)
+            if (c.v[dev][i][0] == smem) return cudaSuccess;
+    int maxopt = 0;
+    e = cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxopt - 1024);
+    if (e != cudaSuccess) return e;
+    if (dev < 16)
+        for (int i = 0; i < 16; ++i)
+            if (!c.v[dev][i][0]) {
+                c.v[dev][i][0] = smem;
+                break;
+            }
+    return cudaSuccess;
+}
+
 cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *wt, const float *bias,
                              void *out_bf16, float *out_f32, int Cs, int Nn, int relu, cudaStream_t st,
                              int ca, int up_a, const void *src_b) {
     if (ca <= 0) ca = Cs;
-    const long long tiles = (long long)g.batch * g.in_d * ((g.in_h + 15) / 16) * ((g.in_w + 7) / 8);
-    const int nt = Nn % 64 == 0 ? 64 : (Nn % 32 == 0 ? 32 : 16);  // Nn is a multiple of 16
-    dim3 grid((unsigned)tiles, (unsigned)(Nn / nt));
-    const int smem = kTcHaloBytes + 27 * 2 * nt * 16;
     auto s = (const __nv_bfloat16 *)src;
     auto w = (const __nv_bfloat16 *)wt;
     auto ob = (__nv_bfloat16 *)out_bf16;
     auto sb = (const __nv_bfloat16 *)src_b;
-    if (nt == 64) {  // 71 KB of shared memory: above the default 48 KB limit
-        const cudaError_t e =
-            cudaFuncSetAttribute(conv3_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (Nn % 64 == 0) {
+        static OccCache cache;
+        const int smem = kTcHaloBytes + 27 * 2 * 64 * 16;
+        const cudaError_t e = prepare_kernel_smem(cache, conv3_tc_kernel<64>, smem);
         if (e != cudaSuccess) return e;
-        conv3_tc_kernel<64><<<grid, 128, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
-    } else if (nt == 32) {
-        conv3_tc_kernel<32><<<grid, 128, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
+        const long long tiles = (long long)g.batch * g.in_d * ((g.in_h + 15) / 16) * ((g.in_w + 7) / 8);
+        conv3_tc_kernel<64><<<dim3((unsigned)tiles, (unsigned)(Nn / 64)), 128, smem, st>>>(
+            g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
+        return cudaGetLastError();
+    }
+    const long long tiles = (long long)g.batch * g.in_d * ((g.in_h + 7) / 8) * ((g.in_w + 13) / 14);
+    if (Nn % 32 == 0) {
+        constexpr int smem = kKwHaloBytes + 9 * 2 * 96 * 16;  // 42.5 KB
+        conv3_kws_kernel<32><<<dim3((unsigned)tiles, (unsigned)(Nn / 32)), 128, smem, st>>>(
+            g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
     } else {
-        conv3_tc_kernel<16><<<grid, 128, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
+        constexpr int smem = kKwHaloBytes + 9 * 2 * 48 * 16;  // 28.5 KB
+        conv3_kws_kernel<16><<<dim3((unsigned)tiles, (unsigned)(Nn / 16)), 128, smem, st>>>(
+            g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
     }
     return cudaGetLastError();
 }
