@@ -397,6 +397,79 @@ def unet_timing(args):
     print(json.dumps({"study": "unet_timing", "grid": g, "inference_ms": inf, "train_step_ms": tr}), flush=True)
 
 
+def precision_study(args):
+    """Slab phantom (64^3 x 2 mm, bone slab), 150 MeV pencil (and 121 MeV):
+    10^8 histories in 100 batches with FP32 and with FP64 step geometry;
+    dose differences FP32 vs FP64 on the device, both against the FP64 oracle
+    on a history subset, per-voxel batch uncertainty from the FP64 batch sums,
+    and the device time to 2 % mean uncertainty in the Bragg-peak region."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1011_2188_gb300 import fdc, synth
+    oracle.build()
+    n_total = args.histories or 100_000_000
+    n_batches = 100
+    res = {"study": "precision", "histories": n_total, "n_batches": n_batches}
+    for E in (150.0, 121.0):
+        db = synth.water_database([E], 10_000, seed=1)
+        ph = synth.slab_phantom()
+        beam = synth.pencil_beam(n_total, energy=E, sigma_cm=0.3)
+        eng = fdc.Engine(0)
+        eng.load_database(db)
+        eng.load_phantom(ph)
+        shape = ph.shape[::-1]
+        out = {}
+        doses = {}
+        for fp64 in (False, True):
+            s1 = torch.zeros(shape, dtype=torch.float64, device="cuda:0")
+            s2 = torch.zeros_like(s1)
+            dose = torch.zeros_like(s1)
+            eng.run_ex(beam, n_total, 5, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2, dose=dose,
+                       fp64_geometry=fp64)
+            eng.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            eng.run_ex(beam, n_total, 5, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2, dose=dose,
+                       fp64_geometry=fp64)
+            e1.record()
+            e1.synchronize()
+            cnt = eng.sync()
+            mean, sigma, rel_half = eng.batch_stats(s1, s2, n_batches, 0.5)
+            _, _, rel_peak = eng.batch_stats(s1, s2, n_batches, 0.9)
+            key = "fp64" if fp64 else "fp32"
+            sec = e0.elapsed_time(e1) * 1e-3
+            # histories to reach 2 % in the Bragg-peak region, from sigma ~ N^-1/2
+            n2 = n_total * (rel_peak / 0.02) ** 2
+            out[key] = {"seconds": sec, "histories_per_s": n_total / sec,
+                        "track_steps_per_s": cnt["steps"] / sec,
+                        "mean_rel_sigma_half_max": rel_half, "mean_rel_sigma_peak": rel_peak,
+                        "histories_for_2pct_peak": n2, "seconds_for_2pct_peak": sec * n2 / n_total}
+            doses[key] = dose.cpu().numpy()
+        d32, d64 = doses["fp32"], doses["fp64"]
+        mx = d64.max()
+        out["fp32_vs_fp64_device"] = {"max_abs_over_max": float(np.abs(d32 - d64).max() / mx),
+                                      "mean_abs_over_max": float(np.abs(d32 - d64).mean() / mx)}
+        # against the FP64 oracle on the first n_sub histories
+        n_sub = 300_000
+        ref = oracle.run(db, ph, beam, seed=5, h_begin=0, h_end=n_sub)
+        d_ref = oracle.dose(ph, ref.edep)
+        sub = {}
+        for fp64 in (False, True):
+            d = torch.zeros(shape, dtype=torch.float64, device="cuda:0")
+            eng.run_ex(beam, n_sub, 5, dose=d, fp64_geometry=fp64)
+            eng.sync()
+            dd = d.cpu().numpy()
+            sub["fp64" if fp64 else "fp32"] = {
+                "max_abs_over_max": float(np.abs(dd - d_ref).max() / d_ref.max()),
+                "mean_abs_over_max": float(np.abs(dd - d_ref).mean() / d_ref.max()),
+                "total_energy_rel": float(abs(dd.sum() - d_ref.sum()) / d_ref.sum())}
+        out["vs_oracle_first_%d" % n_sub] = sub
+        res[f"{E:g}MeV"] = out
+        eng.close()
+    print(json.dumps(res), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return

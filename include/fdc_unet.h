@@ -15,7 +15,7 @@
  * their data-gradient copy [c_in][k][k][k][c_out] (fdc_conv3d_transpose_weights).
  * Calls are asynchronous on `stream` (cudaStream_t as void *, NULL = legacy
  * default stream) and return FDC_OK, FDC_ERR_INVALID (bad shapes: channel
- * counts must be multiples of 16, sizes positive and consistent) or
+ * counts must be multiples of 16 and at most 2048, sizes positive and consistent) or
  * FDC_ERR_CUDA (launch failure).
  */
 #ifndef FDC_UNET_H

@@ -815,29 +815,43 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(const Conv3dArgs g, con
     }
 }
 
-// db[c] += sum over rows of dy[row][c]: per-thread partial sums over the
-// block's rows, reduced per channel in shared memory, one atomic per channel
-// and block.
-__global__ void bias_grad_kernel(const __nv_bfloat16 *dy, long long rows, int C, float *db, int chunk) {
-    __shared__ float sm[256];
-    const int c = threadIdx.x % C;
-    const int lanes = blockDim.x / C;
-    const int sub = threadIdx.x / C;
+// db[c] += sum over rows of dy[row][c]: a thread reads 16-byte groups of 8
+// channels (G = C / 8 groups per row, 256 / G rows in flight per block), sums
+// its rows' groups in FP32, the block reduces per channel in shared memory,
+// one atomic per channel and block.
+__global__ void __launch_bounds__(256) bias_grad_kernel(const __nv_bfloat16 *dy, long long rows, int C, float *db,
+                                                         int chunk) {
+    __shared__ float sm[256 * 8];
+    const int G = C / 8, lanes = 256 / G;
+    const int gi = threadIdx.x % G, sub = threadIdx.x / G;
     const long long r0 = (long long)blockIdx.x * chunk;
     long long r1 = r0 + chunk;
     if (r1 > rows) r1 = rows;
-    float s = 0.f;
-    if (sub < lanes)
-        for (long long r = r0 + sub; r < r1; r += lanes) s += __bfloat162float(dy[r * C + c]);
-    sm[threadIdx.x] = s;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (sub < lanes) {
+#pragma unroll 4
+        for (long long r = r0 + sub; r < r1; r += lanes) {
+            const uint4 q = __ldg((const uint4 *)(dy + r * C) + gi);
+            const __nv_bfloat162 *h2 = (const __nv_bfloat162 *)&q;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 f = __bfloat1622float2(h2[j]);
+                acc[2 * j] += f.x;
+                acc[2 * j + 1] += f.y;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sm[threadIdx.x * 8 + j] = acc[j];
     __syncthreads();
-    if (sub == 0) {
-        for (int k = 1; k < lanes; ++k) s += sm[k * C + c];
-        atomicAdd(db + c, s);
+    for (int c = threadIdx.x; c < C; c += 256) {  // C <= 2048: G <= 256, at least one row in flight
+        const int g = c / 8, j = c % 8;
+        float t = 0.f;
+        for (int k = 0; k < lanes; ++k) t += sm[(k * G + g) * 8 + j];
+        atomicAdd(db + c, t);
     }
 }
 
-// [ci][tap][co] <- [co][tap][ci]
 __global__ void transpose_weights_kernel(const __nv_bfloat16 *w, __nv_bfloat16 *wt, int co_n, int taps, int ci_n) {
     const long long n = (long long)co_n * taps * ci_n;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -1176,11 +1190,9 @@ cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy
         dim3 grid((unsigned)per, (unsigned)(g.c_out / 16), (unsigned)(g.c_in / 16));
         conv3_wgrad_halo_kernel<<<grid, 128, 0, st>>>(g, (const __nv_bfloat16 *)x, (const __nv_bfloat16 *)dy, dw);
         if (db) {
-            const int C = g.c_out;
-            const int threads = (256 / C) * C;
             const int ch = 4096;
-            bias_grad_kernel<<<(unsigned)((rows + ch - 1) / ch), threads, 0, st>>>((const __nv_bfloat16 *)dy, rows,
-                                                                                    C, db, ch);
+            bias_grad_kernel<<<(unsigned)((rows + ch - 1) / ch), 256, 0, st>>>((const __nv_bfloat16 *)dy, rows,
+                                                                                g.c_out, db, ch);
         }
         return cudaGetLastError();
     }
@@ -1196,11 +1208,9 @@ cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy
     dim3 grid((unsigned)tiles, (unsigned)taps, (unsigned)chunks);
     conv_wgrad_kernel<<<grid, 128, 0, st>>>(g, (const __nv_bfloat16 *)x, (const __nv_bfloat16 *)dy, dw, (int)chunk);
     if (db) {
-        const int C = g.c_out;
-        const int threads = (256 / C) * C;
         const int ch = 4096;
-        bias_grad_kernel<<<(unsigned)((rows + ch - 1) / ch), threads, 0, st>>>((const __nv_bfloat16 *)dy, rows, C, db,
-                                                                                ch);
+        bias_grad_kernel<<<(unsigned)((rows + ch - 1) / ch), 256, 0, st>>>((const __nv_bfloat16 *)dy, rows, g.c_out,
+                                                                            db, ch);
     }
     return cudaGetLastError();
 }
@@ -1301,6 +1311,7 @@ namespace {
 
 bool conv_ok(const fdc_conv3d *g) {
     if (!g || g->batch < 1 || g->c_in < 16 || g->c_out < 16 || g->c_in % 16 || g->c_out % 16) return false;
+    if (g->c_in > 2048 || g->c_out > 2048) return false;
     if (g->ksize < 1 || g->ksize > 3 || g->stride < 1 || g->pad < 0) return false;
     const int in[3] = {g->in_d, g->in_h, g->in_w}, out[3] = {g->out_d, g->out_h, g->out_w};
     for (int a = 0; a < 3; ++a) {
