@@ -451,27 +451,30 @@ constexpr int kKwHD = 3, kKwHH = 10, kKwHW = 16;
 constexpr int kKwHalo = kKwHD * kKwHH * kKwHW;  // 480 voxels
 constexpr int kKwHaloBytes = kKwHalo * 32;      // 15360 B
 
+// A CTA walks `tpc` consecutive output blocks of its NT-channel column; when
+// the weights of all input slices fit (resw), they are staged once per CTA.
+// Staging addresses are updated incrementally: in the halo loader every
+// thread keeps one w column and one k-chunk and steps through (d, h) rows.
 template <int NT>
 __global__ void __launch_bounds__(128) conv3_kws_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
                                                         const __nv_bfloat16 *wt, const float *bias,
                                                         __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn,
-                                                        int relu, int ca, int up_a, const __nv_bfloat16 *src_b) {
+                                                        int relu, int ca, int up_a, const __nv_bfloat16 *src_b,
+                                                        int tpc, int resw) {
     constexpr int N3 = 3 * NT;
     constexpr unsigned kCols = N3 <= 64 ? 64 : 128;
+    constexpr int kWChunks = 9 * 2 * N3;       // 16-byte chunks of one slice of weights
+    constexpr int kWBytes = kWChunks * 16;
+    constexpr int kQa = 128 / N3, kNa = 128 % N3;  // loader stride 128 in (q, n) digits
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *sH = smem;
-    unsigned char *sW = smem + kKwHaloBytes;  // [kd kh][k-chunk][kw NT + co][8]
+    unsigned char *sW = smem + kKwHaloBytes;  // [slice][kd kh][k-chunk][kw NT + co][8]
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ unsigned tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = g.in_d, H = g.in_h, W = g.in_w;
     const int tiles_w = (W + 13) / 14, tiles_h = (H + 7) / 8;
-    long long t = blockIdx.x;
-    const int tw = (int)(t % tiles_w); t /= tiles_w;
-    const int th = (int)(t % tiles_h); t /= tiles_h;
-    const int d0 = (int)(t % D);
-    const int b = (int)(t / D);
-    const int h0 = th * 8, w0 = tw * 14;
+    const long long n_tiles = (long long)g.batch * D * tiles_h * tiles_w;
     const int n0 = blockIdx.y * NT;
     const int slices = Cs / 16;
     const int cb = Cs - ca;
@@ -492,63 +495,92 @@ __global__ void __launch_bounds__(128) conv3_kws_kernel(const Conv3dArgs g, cons
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const unsigned tmem = tmem_slot;
 
+    // weights of slice sl into sW + slot * kWBytes (through L1: every CTA reads the same)
+    auto load_weights = [&](int sl, int slot) {
+        int n = tid % N3, q = tid / N3;
+        unsigned char *dst = sW + slot * kWBytes;
+        for (int i = tid; i < kWChunks; i += 128) {
+            const int kc = q & 1, kdh = q >> 1;
+            const int co = n0 + (n % NT), kw = n / NT;
+            const bool in = co < Nn;
+            const __nv_bfloat16 *p = in ? wt + (size_t)((co * 27 + kdh * 3 + kw) * Cs + sl * 16 + kc * 8) : wt;
+            cp_async16_ca(dst + i * 16, p, in);
+            n += kNa;
+            q += kQa;
+            if (n >= N3) {
+                n -= N3;
+                ++q;
+            }
+        }
+    };
+    // this thread's halo column and k-chunk; rows r = d * 10 + h of the halo
+    const int kc = tid & 1, hw = (tid >> 1) & 15, r0 = tid >> 5;
+    const unsigned hdst = (unsigned)((((hw >> 3) * 2 + kc) * 128) + (hw & 7) * 16);
+
+    if (resw)
+        for (int sl = 0; sl < slices; ++sl) load_weights(sl, sl);
+
     bool ok = true;
     unsigned phase = 0;
-    for (int sl = 0; sl < slices && ok; ++sl) {
-        const int c0 = sl * 16;
-        const bool from_a = c0 < ca;
-        for (int i = tid; i < kKwHalo * 2; i += 128) {
-            const int row = i >> 1, kc = i & 1;
-            const int hd = row / (kKwHH * kKwHW), hh = (row / kKwHW) % kKwHH, hw = row % kKwHW;
-            const int d = d0 - 1 + hd, h = h0 - 1 + hh, w = w0 - 1 + hw;
-            const bool in = d >= 0 && d < D && h >= 0 && h < H && w >= 0 && w < W;
-            const __nv_bfloat16 *p = src;
-            if (in) {
-                if (from_a) {
-                    const int da = up_a ? d >> 1 : d, ha = up_a ? h >> 1 : h, wa = up_a ? w >> 1 : w;
-                    p = src + ((((long long)b * Da + da) * Ha + ha) * Wa + wa) * ca + c0 + kc * 8;
-                } else {
-                    p = src_b + ((((long long)b * D + d) * H + h) * W + w) * cb + (c0 - ca) + kc * 8;
+    for (int it = 0; it < tpc && ok; ++it) {
+        const long long tile = (long long)blockIdx.x * tpc + it;
+        if (tile >= n_tiles) break;
+        long long t = tile;
+        const int w0 = (int)(t % tiles_w) * 14; t /= tiles_w;
+        const int h0 = (int)(t % tiles_h) * 8; t /= tiles_h;
+        const int d0 = (int)(t % D);
+        const int b = (int)(t / D);
+        const int w = w0 - 1 + hw;
+        const bool w_in = w >= 0 && w < W;
+        for (int sl = 0; sl < slices && ok; ++sl) {
+            const int c0 = sl * 16;
+            if (!resw) load_weights(sl, 0);
+            const bool from_a = c0 < ca;
+#pragma unroll 2
+            for (int r = r0; r < kKwHD * kKwHH; r += 4) {
+                const int hd = (r >= 10) + (r >= 20), hh = r - 10 * hd;
+                const int d = d0 - 1 + hd, h = h0 - 1 + hh;
+                const bool in = w_in && d >= 0 && d < D && h >= 0 && h < H;
+                const __nv_bfloat16 *p = src;
+                if (in) {
+                    if (!from_a)
+                        p = src_b + ((((long long)b * D + d) * H + h) * W + w) * cb + (c0 - ca) + kc * 8;
+                    else if (up_a)
+                        p = src + ((((long long)b * Da + (d >> 1)) * Ha + (h >> 1)) * Wa + (w >> 1)) * ca + c0 + kc * 8;
+                    else
+                        p = src + ((((long long)b * D + d) * H + h) * W + w) * ca + c0 + kc * 8;
                 }
+                cp_async16(sH + r * 512 + hdst, p, in);
             }
-            cp_async16(sH + (((hd * kKwHH + hh) * 2 + (hw >> 3)) * 2 + kc) * 128 + (hw & 7) * 16, p, in);
-        }
-        for (int i = tid; i < 9 * 2 * N3; i += 128) {
-            const int n = i % N3, q = i / N3, kc = q & 1, kdh = q >> 1;
-            const int kw = n / NT, co = n0 + n % NT;
-            const bool in = co < Nn;
-            const __nv_bfloat16 *p = in ? wt + ((long long)co * 27 + kdh * 3 + kw) * Cs + c0 + kc * 8 : wt;
-            // every CTA reads the same slice of weights: through L1, not from L2 each time
-            cp_async16_ca(sW + ((kdh * 2 + kc) * N3 + n) * 16, p, in);
-        }
-        cp_async_commit();
-        cp_async_wait<0>();
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const unsigned ha = smem_u32(sH), wa = smem_u32(sW);
-            constexpr unsigned idesc = umma_idesc(128, N3);
+            cp_async_commit();
+            cp_async_wait<0>();
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const unsigned ha = smem_u32(sH), wa = smem_u32(sW + (resw ? sl : 0) * kWBytes);
+                constexpr unsigned idesc = umma_idesc(128, N3);
 #pragma unroll 1
-            for (int kdh = 0; kdh < 9; ++kdh) {
-                const int kd = kdh / 3, kh = kdh % 3;
-                const unsigned long long ad = umma_desc(ha + (kd * kKwHH + kh) * 512, 128, 256);
-                const unsigned long long bd = umma_desc(wa + kdh * 2 * N3 * 16, N3 * 16, 128);
-                umma_bf16(tmem, ad, bd, idesc, (sl | kdh) != 0);
+                for (int kdh = 0; kdh < 9; ++kdh) {
+                    const int kd = kdh / 3, kh = kdh % 3;
+                    const unsigned long long ad = umma_desc(ha + (kd * kKwHH + kh) * 512, 128, 256);
+                    const unsigned long long bd = umma_desc(wa + kdh * 2 * N3 * 16, N3 * 16, 128);
+                    umma_bf16(tmem, ad, bd, idesc, (sl | kdh) != 0);
+                }
+                umma_commit(mb);
             }
-            umma_commit(mb);
+            // the MMAs read the halo (and a reloaded weight slice): wait before restaging
+            ok = mbar_wait_bounded(mb, phase);
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            ok = __syncthreads_and(ok);
         }
-        ok = mbar_wait_bounded(mb, phase);
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        ok = __syncthreads_and(ok);
-    }
+        if (!ok) break;
 
-    if (ok) {
         const int m = warp * 32 + lane;
-        const int h = h0 + (m >> 4), wl = m & 15, w = w0 + wl;
-        const bool in = wl < 14 && h < H && w < W;
-        const long long v = (((long long)b * D + d0) * H + h) * W + w;
+        const int ho = h0 + (m >> 4), wl = m & 15, wo = w0 + wl;
+        const bool out_in = wl < 14 && ho < H && wo < W;
+        const long long v = (((long long)b * D + d0) * H + ho) * W + wo;
         const unsigned base = tmem + ((unsigned)(warp * 32) << 16);
 #pragma unroll
         for (int c = 0; c < NT; c += 16) {
@@ -560,7 +592,7 @@ __global__ void __launch_bounds__(128) conv3_kws_kernel(const Conv3dArgs g, cons
             for (int j = 0; j < 16; ++j)
                 a0[j] += __shfl_down_sync(0xffffffffu, a1[j], 1) + __shfl_down_sync(0xffffffffu, a2[j], 2);
             const int n = n0 + c;
-            if (!in || n >= Nn) continue;
+            if (!out_in || n >= Nn) continue;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 float x = a0[j];
@@ -586,9 +618,13 @@ __global__ void __launch_bounds__(128) conv3_kws_kernel(const Conv3dArgs g, cons
                 dst[1] = q[1];
             }
         }
-    } else if (tid == 0) {
-        atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
+        // every warp has read the accumulator before the next block's MMAs overwrite it
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     }
+    if (!ok && tid == 0) atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
+    cp_async_wait<0>();
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -1128,14 +1164,27 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
         return cudaGetLastError();
     }
     const long long tiles = (long long)g.batch * g.in_d * ((g.in_h + 7) / 8) * ((g.in_w + 13) / 14);
+    // blocks per CTA: enough CTAs for a few waves, weights staged once per CTA
+    const int tpc = tiles >= 8 * 152 * 4 ? 4 : (tiles >= 4 * 152 * 2 ? 2 : 1);
+    const unsigned grid_x = (unsigned)((tiles + tpc - 1) / tpc);
     if (Nn % 32 == 0) {
-        constexpr int smem = kKwHaloBytes + 9 * 2 * 96 * 16;  // 42.5 KB
-        conv3_kws_kernel<32><<<dim3((unsigned)tiles, (unsigned)(Nn / 32)), 128, smem, st>>>(
-            g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
+        constexpr int kW = 9 * 2 * 96 * 16;
+        const int resw = (Cs / 16) * kW <= 56 * 1024;
+        const int smem = kKwHaloBytes + (resw ? Cs / 16 : 1) * kW;
+        static OccCache cache;
+        const cudaError_t e = prepare_kernel_smem(cache, conv3_kws_kernel<32>, smem);
+        if (e != cudaSuccess) return e;
+        conv3_kws_kernel<32><<<dim3(grid_x, (unsigned)(Nn / 32)), 128, smem, st>>>(
+            g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb, tpc, resw);
     } else {
-        constexpr int smem = kKwHaloBytes + 9 * 2 * 48 * 16;  // 28.5 KB
-        conv3_kws_kernel<16><<<dim3((unsigned)tiles, (unsigned)(Nn / 16)), 128, smem, st>>>(
-            g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb);
+        constexpr int kW = 9 * 2 * 48 * 16;
+        const int resw = (Cs / 16) * kW <= 56 * 1024;
+        const int smem = kKwHaloBytes + (resw ? Cs / 16 : 1) * kW;
+        static OccCache cache;
+        const cudaError_t e = prepare_kernel_smem(cache, conv3_kws_kernel<16>, smem);
+        if (e != cudaSuccess) return e;
+        conv3_kws_kernel<16><<<dim3(grid_x, (unsigned)(Nn / 16)), 128, smem, st>>>(
+            g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb, tpc, resw);
     }
     return cudaGetLastError();
 }
