@@ -1153,7 +1153,11 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
     auto w = (const __nv_bfloat16 *)wt;
     auto ob = (__nv_bfloat16 *)out_bf16;
     auto sb = (const __nv_bfloat16 *)src_b;
-    if (Nn % 64 == 0) {
+    // 64-channel tiles (27 MMAs of N = 64) when they give at least one CTA per SM
+    // (measured: 32^3 x 64 channels 46 vs 55 us); otherwise the kw-stacked kernel
+    // with 32-channel tiles spreads small grids wider (16^3 x 128: 43 vs 64 us)
+    const long long tiles64 = (long long)g.batch * g.in_d * ((g.in_h + 15) / 16) * ((g.in_w + 7) / 8);
+    if (Nn % 64 == 0 && tiles64 * (Nn / 64) >= 152) {
         static OccCache cache;
         const int smem = kTcHaloBytes + 27 * 2 * 64 * 16;
         const cudaError_t e = prepare_kernel_smem(cache, conv3_tc_kernel<64>, smem);

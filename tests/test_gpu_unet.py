@@ -47,6 +47,7 @@ CASES = [
     ((1, 16, 16, 16, 16), 16, 3, 1, 1),
     ((2, 3, 9, 17, 48), 32, 3, 1, 1),
     ((1, 3, 37, 12, 16), 32, 3, 1, 1),  # three 16-row tiles in h, the last ragged
+    ((1, 10, 31, 64, 16), 64, 3, 1, 1),  # enough blocks for the 64-channel tile kernel, ragged h
 ]
 
 
