@@ -184,12 +184,16 @@ def cpu_baseline(db, ph, beam, seed, target_s=8.0):
     import oracle
     oracle.build()
     oracle.run(db, ph, beam, seed=seed, h_begin=0, h_end=200)  # first touch of the inputs, untimed
-    n0 = 2000
+    # per-history cost from two sizes (a call also has a fixed set-up cost)
     t = time.perf_counter()
-    oracle.run(db, ph, beam, seed=seed, h_begin=200, h_end=200 + n0)
-    dt = time.perf_counter() - t
-    n0 += 200
-    n = int(min(max(n0, n0 * target_s / max(dt, 1e-3)), 2_000_000))
+    oracle.run(db, ph, beam, seed=seed, h_begin=200, h_end=2200)
+    t1 = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.run(db, ph, beam, seed=seed, h_begin=2200, h_end=22200)
+    t2 = time.perf_counter() - t
+    per_h = max((t2 - t1) / 18000, t2 / 20000 * 0.1, 1e-7)
+    n0 = 22200
+    n = int(min(max(2000, target_s / per_h), 5_000_000))
     t = time.perf_counter()
     r = oracle.run(db, ph, beam, seed=seed, h_begin=n0, h_end=n0 + n)
     dt = time.perf_counter() - t
