@@ -181,6 +181,7 @@ def cpu_baseline(db, ph, beam, seed, target_s=8.0):
     """The oracle as it stands on a bounded sample of the workload's histories:
     single-threaded (calibrated to ~target_s seconds), then on every host core
     over disjoint history ranges (~target_s seconds again)."""
+    import numpy as np
     import oracle
     oracle.build()
     oracle.run(db, ph, beam, seed=seed, h_begin=0, h_end=200)  # first touch of the inputs, untimed
@@ -193,7 +194,8 @@ def cpu_baseline(db, ph, beam, seed, target_s=8.0):
     t2 = time.perf_counter() - t
     per_h = max((t2 - t1) / 18000, t2 / 20000 * 0.1, 1e-7)
     n0 = 22200
-    n = int(min(max(2000, target_s / per_h), 5_000_000))
+    total = int(np.sum(np.asarray(beam["n_histories"], dtype=np.uint64)))  # the sample stays inside the beam
+    n = int(min(max(2000, target_s / per_h), 5_000_000, (total - n0) // 4))
     t = time.perf_counter()
     r = oracle.run(db, ph, beam, seed=seed, h_begin=n0, h_end=n0 + n)
     dt = time.perf_counter() - t
@@ -203,7 +205,7 @@ def cpu_baseline(db, ph, beam, seed, target_s=8.0):
     cores = host_cores()
     if cores <= 1:
         return single
-    m = int(min(n * cores, 20_000_000))
+    m = int(min(n * cores, 20_000_000, total - n0 - n))
     dtp, steps = oracle_parallel(db, ph, beam, seed, n0 + n, m, cores)
     return {"value": m / dtp, "unit": "histories/s", "cores": cores, "kind": "oracle",
             "sample": f"histories [{n0 + n}, {n0 + n + m}) of the same beam and seed; the sequential FP64 "
@@ -483,22 +485,35 @@ def run_reference(args, rank, world):
     import oracle
     oracle.build()
     oracle.run(db, ph, beam, seed=1234, h_begin=0, h_end=200)  # first touch of the inputs, untimed
+    # per-history cost from two sizes (a call also has a fixed set-up cost)
     t = time.perf_counter()
     oracle.run(db, ph, beam, seed=1234, h_begin=200, h_end=1200)
-    dt = time.perf_counter() - t
-    per = int(max(1000, min(200_000, 1000 * 8.0 / max(dt, 1e-3))))  # ~8 s per thread and step
-    off = 1200
+    t1 = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.run(db, ph, beam, seed=1234, h_begin=1200, h_end=11200)
+    t2 = time.perf_counter() - t
+    per_h = max((t2 - t1) / 9000, t2 / 10000 * 0.1, 1e-7)
+    cores = host_cores()
+    total = int(sum(int(x) for x in beam["n_histories"]))
+    per = int(max(1000, min(8.0 / per_h, (total - 11200) // (2 * cores))))  # ~8 s per thread and step
+    off = 11200
+
+    def next_range():  # consecutive history ranges of the beam, wrapping inside it
+        nonlocal off
+        if off + per * cores > total:
+            off = 11200
+        h0 = off
+        off += per * cores
+        return h0
+
     for _ in range(args.warmup):
         oracle.run(db, ph, beam, seed=1234, h_begin=off, h_end=off + min(per, 2000))
-        off += min(per, 2000)
     # each step: per histories on every host core, over disjoint history ranges
-    cores = host_cores()
     times, steps = [], 0
     for _ in range(args.steps):
-        dt, st = oracle_parallel(db, ph, beam, 1234, off, per * cores, cores)
+        dt, st = oracle_parallel(db, ph, beam, 1234, next_range(), per * cores, cores)
         times.append(dt)
         steps += st
-        off += per * cores
     tot = sum(times)
     value = per * cores * args.steps / tot
     line = {
