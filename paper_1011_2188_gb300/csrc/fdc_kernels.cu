@@ -224,7 +224,7 @@ template <> __device__ __forceinline__ double inf_<double>() { return __longlong
 // limbs of the two's-complement value with redux.sync inside each group, one
 // atomic per group); otherwise one atomic per lane.
 template <bool AGG>
-__device__ __forceinline__ void tally_add(unsigned long long *tally, long long idx, long long units) {
+__device__ __forceinline__ void tally_add(unsigned long long *tally, int idx, long long units) {
     unsigned long long *const addr = tally + idx;
     if (!AGG) {
         atomicAdd(addr, (unsigned long long)units);
@@ -271,31 +271,35 @@ __device__ __forceinline__ double unit_scale(double) { return 268435456.0; }
 
 template <bool AGG, bool SQ>
 struct PendingTally {
-    long long idx = -1;  // tally word (layer offset included)
+    unsigned long long *tally;  // this history's tally (layer offset included)
+    unsigned long long *sumsq;  // SQ: the squares tally, same offset
+    int idx = -1;               // voxel of the pending deposit
     long long units = 0;
-    __device__ __forceinline__ void add(const ReplayArgs &P, long long i, long long u) {
+    __device__ __forceinline__ PendingTally(const ReplayArgs &P, long long tbase)
+        : tally(P.tally + tbase), sumsq(SQ ? P.sumsq + tbase : nullptr) {}
+    __device__ __forceinline__ void add(int v, long long u) {
         if (!SQ && !FDC_LANE_COALESCE) {
-            if (u) tally_add<AGG>(P.tally, i, u);
+            if (u) tally_add<AGG>(tally, v, u);
             return;
         }
-        if (i == idx) {
+        if (v == idx) {
             units += u;
             return;
         }
-        flush(P);
-        idx = i;
+        flush();
+        idx = v;
         units = u;
     }
     // With SQ the pending sum is one whole visit of the history to the voxel;
     // its square goes to the second tally (2^-28 MeV^2 units):
     // (u * 2^-14)^2 = u^2 * 2^-28.
-    __device__ __forceinline__ void flush(const ReplayArgs &P) {
+    __device__ __forceinline__ void flush() {
         if (idx >= 0 && units) {
-            tally_add<AGG>(P.tally, idx, units);
+            tally_add<AGG>(tally, idx, units);
             if (SQ) {
                 const float e = (float)units * 6.103515625e-05f;
                 const long long q = units_of(e * e);
-                if (q) atomicAdd(P.sumsq + idx, (unsigned long long)q);
+                if (q) atomicAdd(sumsq + idx, (unsigned long long)q);
             }
         }
         idx = -1;
@@ -343,7 +347,10 @@ __device__ __forceinline__ void sincos_phi(unsigned code, double *s, double *c) 
 // faces at integers), which keeps FP32 rounding relative to the voxel rather
 // than to the whole grid; distances along the ray are in cm.  Per-lane
 // counters are updated in place.
-template <typename R, bool AGG, bool SQ>
+// FIXED: the voxel where a step starts scales the whole step (ablation of
+// Sec. 2.2's step scaling); a template parameter, so the default path carries
+// no per-segment test.
+template <typename R, bool AGG, bool SQ, bool FIXED>
 __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start &st,
                                                unsigned long long h, unsigned long long &steps,
                                                unsigned long long &segs, long long &replayed,
@@ -382,7 +389,7 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
     const R US = unit_scale((R)0);
     // material of the current voxel, carried from one step to the next
     float2 sk = __ldg(P.vox + v);
-    PendingTally<AGG, SQ> pend;
+    PendingTally<AGG, SQ> pend(P, tbase);
 
     for (long long s = s_first;;) {
         const float dE_f = __uint_as_float(rec.y);
@@ -414,7 +421,7 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
 
         R rem = len, t = (R)0, acc = (R)0;
         long long dep = 0;
-        const bool fixed = P.scaling_mode == 1;
+        constexpr bool fixed = FIXED;
         const R S_fix = (R)sk.x, k2_fix = (R)sk.y;
         int nseg = 0;
         bool gone = false;
@@ -431,14 +438,14 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
             ++segs;
             if (wexit >= rem) {  // the step ends in this voxel
                 const long long units = Qk - dep;
-                pend.add(P, tbase + v, units);
+                pend.add(v, units);
                 acc += rem * k2;
                 t += rem * rcp_(S);
                 break;
             }
             const long long units = units_of(wexit * dEu);
             dep += units;
-            pend.add(P, tbase + v, units);
+            pend.add(v, units);
             acc += wexit * k2;
             rem -= wexit;
             t = tm;
@@ -459,16 +466,16 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
             sk = __ldg(P.vox + v);
         }
         if (gone) {
-            pend.flush(P);
+            pend.flush();
             return;
         }
         // fractional position in the end voxel
         fx = ((R)(ix0 - ix) + fx) + t * rx;
         fy = ((R)(iy0 - iy) + fy) + t * ry;
         fz = ((R)(iz0 - iz) + fz) + t * rz;
-        if (Qs) pend.add(P, tbase + v, Qs);
+        if (Qs) pend.add(v, Qs);
         if (++s >= s_end) {
-            pend.flush(P);
+            pend.flush();
             return;
         }
         const unsigned ang = rec.w;
@@ -538,7 +545,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? FDC_REPLAY_MIN_CTAS : 2)
             if (li < P.n) {
                 const unsigned long long h = P.h_begin + li;
                 const Start st = sample_start(P, h);
-                replay_history<R, AGG, SQ>(P, st, h, steps, segs, replayed, escaped);
+                if (P.scaling_mode == 1)
+                    replay_history<R, AGG, SQ, true>(P, st, h, steps, segs, replayed, escaped);
+                else
+                    replay_history<R, AGG, SQ, false>(P, st, h, steps, segs, replayed, escaped);
                 ++hist;
             }
         }
