@@ -142,7 +142,9 @@ struct Pinned {
     }
 };
 
-int resolve_schedule(fdc_ctx *c, const fdc_schedule *req, int fp64, fdc_schedule *out) {
+// track_group and squares select the kernel variant whose occupancy bounds ctas_per_sm
+int resolve_schedule(fdc_ctx *c, const fdc_schedule *req, int fp64, int track_group, bool squares,
+                     fdc_schedule *out) {
     fdc_schedule s = {0, 0, 0, 0};
     if (req) s = *req;
     if (!s.warps_per_cta) s.warps_per_cta = c->tuned.warps_per_cta ? c->tuned.warps_per_cta : 8;
@@ -154,7 +156,7 @@ int resolve_schedule(fdc_ctx *c, const fdc_schedule *req, int fp64, fdc_schedule
     if (s.warps_per_cta < 1 || s.warps_per_cta > 8 || s.chunk < 1 || s.chunk > 1024 || s.aggregate < 1 ||
         s.aggregate > 2 || s.ctas_per_sm < 0)
         return fail(c, FDC_ERR_INVALID, "invalid schedule");
-    const int maxc = fdc::replay_max_ctas_per_sm(s.warps_per_cta, fp64, s.aggregate);
+    const int maxc = fdc::replay_max_ctas_per_sm(s.warps_per_cta, fp64, s.aggregate, squares ? 1 : track_group);
     if (!s.ctas_per_sm) s.ctas_per_sm = c->tuned.ctas_per_sm ? std::min(c->tuned.ctas_per_sm, maxc) : maxc;
     if (s.ctas_per_sm > maxc) s.ctas_per_sm = maxc;
     *out = s;
@@ -491,7 +493,8 @@ int run_impl(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t se
         (double)per_launch * (double)c->max_track_units > 9.0e18)
         return fail(c, FDC_ERR_OVERFLOW, "too many histories per launch for the int64 tally");
     fdc_schedule sched;
-    rc = resolve_schedule(c, &opts.schedule, opts.fp64_geometry, &sched);
+    rc = resolve_schedule(c, &opts.schedule, opts.fp64_geometry, opts.track_group > 1 ? opts.track_group : 1,
+                          out.history_sumsq != nullptr, &sched);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     FDC_CUDA(c, cudaSetDevice(c->device));
@@ -734,7 +737,7 @@ int fdc_autotune(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_
     float best_ms = std::numeric_limits<float>::max();
     int rc = FDC_OK;
     for (int w : warps_opts) {
-        const int maxc = fdc::replay_max_ctas_per_sm(w, 0, 1);
+        const int maxc = fdc::replay_max_ctas_per_sm(w, 0, 1, 1);
         const int cta_opts[] = {maxc, std::max(1, maxc / 2)};
         for (int ci = 0; ci < 2 && !rc; ++ci) {
             if (ci == 1 && cta_opts[1] == cta_opts[0]) continue;
@@ -850,7 +853,7 @@ int fdc_run_noalloc(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint
     if (c->max_track_units > 0 && (double)n * (double)c->max_track_units > 9.0e18)
         return fail(c, FDC_ERR_OVERFLOW, "too many histories per launch for the int64 tally");
     fdc_schedule sched;
-    rc = resolve_schedule(c, nullptr, 0, &sched);
+    rc = resolve_schedule(c, nullptr, 0, 1, false, &sched);
     if (rc) return rc;
     FDC_CUDA(c, cudaSetDevice(c->device));
     fdc::NoallocScratch sc;

@@ -92,7 +92,7 @@ cudaError_t launch_debug_philox(unsigned long long k0, unsigned long long k1,
                                 unsigned long long *out, cudaStream_t st);
 cudaError_t launch_debug_sample(const ReplayArgs &a, float *xyEpsi, long long *btk,
                                 cudaStream_t st);
-int replay_max_ctas_per_sm(int warps_per_cta, int fp64, int aggregate);
+int replay_max_ctas_per_sm(int warps_per_cta, int fp64, int aggregate, int track_group);
 // Denoiser convolutions (layout in fdc_unet.h).
 struct Conv3dArgs {
     int batch, in_d, in_h, in_w, out_d, out_h, out_w, c_in, c_out, ksize, stride, pad, relu;

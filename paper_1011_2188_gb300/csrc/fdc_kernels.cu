@@ -523,13 +523,20 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
 }
 
 // Minimum resident CTAs of 256 threads per SM requested from the register
-// allocator (4 caps the kernel at 64 registers).
+// allocator: 4 caps the kernel at 64 registers (no spills).  With 32 or more
+// histories per track (a warp shares one track) the kernel is bound by
+// instruction issue and 5 CTAs (48 registers, a few spills, 40 warps per SM)
+// was measured 3 % faster; with independent tracks it is bound by the latency
+// of scattered record loads and 5 was 12 % slower.
 #ifndef FDC_REPLAY_MIN_CTAS
 #define FDC_REPLAY_MIN_CTAS 4
 #endif
+#ifndef FDC_REPLAY_MIN_CTAS_SHARED
+#define FDC_REPLAY_MIN_CTAS_SHARED 5
+#endif
 
-template <typename R, bool AGG, bool SQ>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? FDC_REPLAY_MIN_CTAS : 2)
+template <typename R, bool AGG, bool SQ, int MINB = FDC_REPLAY_MIN_CTAS>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? MINB : 2)
     replay_kernel(const ReplayArgs P) {
     const unsigned lane = threadIdx.x & 31u;
     unsigned long long steps = 0, segs = 0, hist = 0;
@@ -725,18 +732,24 @@ __global__ void probe_atomics_kernel(unsigned long long *slots, unsigned long lo
     }
 }
 
-template <typename R, bool AGG, bool SQ>
+template <typename R, bool AGG, bool SQ, int MINB = FDC_REPLAY_MIN_CTAS>
 cudaError_t launch_replay_t(const ReplayArgs &a, int ctas, int threads, cudaStream_t st) {
-    replay_kernel<R, AGG, SQ><<<ctas, threads, 0, st>>>(a);
+    replay_kernel<R, AGG, SQ, MINB><<<ctas, threads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename R, bool AGG, bool SQ>
+template <typename R, bool AGG, bool SQ, int MINB = FDC_REPLAY_MIN_CTAS>
 int max_ctas_t(int threads) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, replay_kernel<R, AGG, SQ>, threads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, replay_kernel<R, AGG, SQ, MINB>, threads, 0) !=
+        cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
+}
+
+// the FP32 plain-atomic kernel with the register budget of shared tracks
+bool shared_track_variant(int track_group, int fp64, int aggregate, bool squares) {
+    return track_group >= 32 && !fp64 && aggregate != 1 && !squares;
 }
 
 }  // namespace
@@ -806,14 +819,18 @@ cudaError_t launch_replay(const ReplayArgs &a, const fdc_schedule &s, int fp64, 
     const bool agg = s.aggregate == 1;
     if (fp64) return agg ? launch_replay_t<double, true, false>(a, ctas, threads, st)
                          : launch_replay_t<double, false, false>(a, ctas, threads, st);
+    if (shared_track_variant(a.track_group, fp64, s.aggregate, false))
+        return launch_replay_t<float, false, false, FDC_REPLAY_MIN_CTAS_SHARED>(a, ctas, threads, st);
     return agg ? launch_replay_t<float, true, false>(a, ctas, threads, st)
                : launch_replay_t<float, false, false>(a, ctas, threads, st);
 }
 
-int replay_max_ctas_per_sm(int warps_per_cta, int fp64, int aggregate) {
+int replay_max_ctas_per_sm(int warps_per_cta, int fp64, int aggregate, int track_group) {
     const int threads = 32 * warps_per_cta;
     const bool agg = aggregate == 1;
     if (fp64) return agg ? max_ctas_t<double, true, false>(threads) : max_ctas_t<double, false, false>(threads);
+    if (shared_track_variant(track_group, fp64, aggregate, false))
+        return max_ctas_t<float, false, false, FDC_REPLAY_MIN_CTAS_SHARED>(threads);
     return agg ? max_ctas_t<float, true, false>(threads) : max_ctas_t<float, false, false>(threads);
 }
 
