@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one replay launch of the default workload
 # (thorax, 10^5 tracks per energy, 10^7 histories, track group 32), from one
 # ncu capture of the current kernel (profiles/replay_kernel_thorax.md).
-REPLAY_TRAFFIC_DEFAULT = 1.87e9 + 4.27e6
+REPLAY_TRAFFIC_DEFAULT = 1.91e9 + 38.4e6
 
 
 def parse():
