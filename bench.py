@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--epochs", type=int, default=12)
     ap.add_argument("--variants", type=int, default=1, help="mirror images per training phantom (1-4)")
     ap.add_argument("--no-augment", action="store_true", help="train without the lateral symmetries")
+    ap.add_argument("--weights-out", default="", help="save the trained U-Net weights (.npz) to this path")
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--high", type=int, default=100_000_000, help="histories of the target dose")
     ap.add_argument("--study", default="", choices=["", "precision", "denoiser", "unet_timing"],
@@ -369,8 +370,8 @@ def denoiser_study(args):
             "note": "doses compared at the low-history count (high-history dose scaled by n_low / n_high)",
             "total_s": time.perf_counter() - t_all}
     print(json.dumps(line), flush=True)
-    np.savez("gpurun_out/unet_weights.npz" if os.path.isdir("gpurun_out") else "/tmp/unet_weights.npz",
-             *[a for st in net.state() for a in (st["w"], st["b"])])
+    if args.weights_out:
+        np.savez(args.weights_out, *[a for st in net.state() for a in (st["w"], st["b"])])
 
 
 def unet_timing(args):

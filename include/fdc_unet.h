@@ -4,7 +4,7 @@
  * The denoiser is not part of the paper: it is a small 3-D U-Net that maps a
  * dose computed from few histories (plus the phantom density) to the dose of
  * many histories; the track-repeating engine of fdc.h generates its training
- * pairs and stays the fallback and the judge of its error.  These calls are
+ * pairs and stays the fallback and the reference its error is measured against.  These calls are
  * the building blocks the network is trained and run with: BF16 tensor-core
  * convolutions with FP32 accumulation and their gradients, plus the
  * element-wise pieces.

@@ -1,8 +1,8 @@
 """Learned denoiser: a 3-D U-Net from a low-history dose (plus density) to a
 high-history dose, trained and run with the library's own kernels
 (include/fdc_unet.h).  Not part of the paper: the track-repeating engine
-generates its training pairs and remains both the fallback and the judge of
-its error.
+generates its training pairs and remains both the fallback and the reference
+its error is measured against.
 
 Network (channels-last BF16 activations, FP32 master weights):
   level 1 (full grid, 16 ch): 2 x conv3 -> skip s1
