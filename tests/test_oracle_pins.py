@@ -363,3 +363,25 @@ def test_history_squares_exact():
         one = oracle.run(db, ph, beam, seed=8, h_begin=hh, h_end=hh + 1)
         sq += one.edep ** 2
     np.testing.assert_allclose(r.hh_sumsq, sq, rtol=1e-12, atol=1e-12)
+
+
+def test_per_layer_tallies_partition_the_run():
+    """Per-layer tallies (a history scores into its spot's layer): the layers
+    add up to the plain run, and each layer equals a run over exactly the
+    histories of its spots (histories are numbered over the spots in order)."""
+    db = synth.water_database([120.0, 150.0], 60, seed=3)
+    ph = synth.slab_phantom()
+    beam = synth.make_spots([
+        dict(x=-0.5, y=0.0, energy=120.0, sigma_e=0.0, a=0.3, profile=synth.PROFILE_GAUSS, layer=0, n_histories=300),
+        dict(x=0.5, y=0.2, energy=118.0, sigma_e=0.0, a=0.3, profile=synth.PROFILE_GAUSS, layer=0, n_histories=200),
+        dict(x=0.0, y=-0.4, energy=150.0, sigma_e=0.0, a=0.2, profile=synth.PROFILE_GAUSS, layer=1, n_histories=400),
+    ])
+    per = oracle.run(db, ph, beam, seed=21, per_layer=True)
+    whole = oracle.run(db, ph, beam, seed=21)
+    assert per.edep.shape[0] == 2
+    np.testing.assert_allclose(per.edep.sum(axis=0), whole.edep, rtol=1e-12, atol=1e-9)
+    first = oracle.run(db, ph, beam, seed=21, h_begin=0, h_end=500)
+    second = oracle.run(db, ph, beam, seed=21, h_begin=500, h_end=900)
+    np.testing.assert_allclose(per.edep[0], first.edep, rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(per.edep[1], second.edep, rtol=1e-12, atol=1e-9)
+    assert per.edep[1][:, :, :].sum() > 0 and per.edep[0].sum() > 0
