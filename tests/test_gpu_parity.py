@@ -376,3 +376,34 @@ def test_autotune_picks_a_valid_schedule_and_results_do_not_change():
     after = gpu_energy(eng, ph, beam, 5)["tally"]  # runs with the tuned default
     assert np.array_equal(before, after)
     eng.close()
+
+
+def test_full_size_thorax_workload():
+    """The benchmark's workload at full size (24 x 10^5-track database,
+    4.5 x 10^8 step records, 10^7 histories, 32 histories per track, the
+    launch configuration bench.py times): exact integer bookkeeping and a
+    bitwise-repeatable tally over the whole run; and a sample of 2 x 10^5
+    histories from the middle of the run against the oracle on the same
+    history numbers -- voxel by voxel with FP64 geometry, and with the FP32
+    path per depth slab (single voxels need more histories per column in FP32,
+    see test_parity_thorax) and in total."""
+    db = synth.water_database(synth.database_energies(24), 100_000, seed=2)
+    ph = synth.thorax_phantom(seed=7)
+    beam = synth.field_beam(10_000_000, energy=150.0, width=10.0, height=10.0, sigma_e_rel=0.01)
+    eng = engine(db, ph)
+    r1 = gpu_energy(eng, ph, beam, 1234, track_group=32)
+    assert_conservation(r1)
+    assert r1["counters"]["histories"] == 10_000_000
+    r2 = gpu_energy(eng, ph, beam, 1234, track_group=32)
+    assert np.array_equal(r1["tally"], r2["tally"])
+    h0, n = 4_000_000, 200_000
+    ref = oracle.run(db, ph, beam, seed=1234, h_begin=h0, h_end=h0 + n, track_group=32)
+    r64 = gpu_energy(eng, ph, beam, 1234, n=n, history_offset=h0, track_group=32, fp64_geometry=True)
+    assert_conservation(r64)
+    assert_parity(r64["energy"], ref.edep, "full-size thorax sample, FP64 geometry")
+    r32 = gpu_energy(eng, ph, beam, 1234, n=n, history_offset=h0, track_group=32)
+    assert_conservation(r32)
+    slab_gpu, slab_ref = r32["energy"].sum(axis=(1, 2)), ref.edep.sum(axis=(1, 2))
+    assert np.abs(slab_gpu - slab_ref).max() <= 1e-3 * slab_ref.max()
+    assert abs(r32["energy"].sum() - ref.edep.sum()) <= 1e-6 * ref.edep.sum()
+    eng.close()
