@@ -110,6 +110,11 @@ int fdc_unet_dihedral(const void *x, const float *target, int32_t d, int32_t h, 
  * no output); clear != 0 resets it.  Synchronises with the device; not for
  * use inside stream capture. */
 int fdc_unet_status(int32_t clear);
+/* Test hook of that status (no counterpart in the paper): launches one thread
+ * that waits on a barrier nothing completes, gives up after `cycles` SM clock
+ * cycles (1 .. 4e9) and records FDC_ERR_TIMEOUT as a timed-out convolution
+ * would.  Asynchronous on `stream`; FDC_ERR_INVALID for cycles out of range. */
+int fdc_debug_wait_timeout(int64_t cycles, void *stream);
 /* Denoised dose: dose_out [n] (FP64, Gy) = max(0, (head[n][16] channel 0 + dose_in) * dose_scale). */
 int fdc_unet_finish(const float *head, const float *dose_in, int64_t n, double dose_scale, double *dose_out,
                     void *stream);

@@ -100,6 +100,7 @@ struct Conv3dArgs {
 cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const void *wt, const float *bias,
                         void *out_bf16, float *out_f32, cudaStream_t st);
 int tc_status(bool clear);
+cudaError_t launch_wait_timeout(long long cycles, cudaStream_t st);
 cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *wt, const float *bias,
                              void *out_bf16, float *out_f32, int Cs, int Nn, int relu, cudaStream_t st,
                              int ca, int up_a, const void *src_b);

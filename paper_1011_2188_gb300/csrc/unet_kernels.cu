@@ -260,7 +260,7 @@ __device__ __forceinline__ void umma_bf16(unsigned tmem_d, unsigned long long a,
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned mbar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned mbar, unsigned parity, long long limit = kTcWaitCycles) {
     const long long t0 = clock64();
     for (;;) {
         unsigned ok;
@@ -270,8 +270,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned mbar, unsigned parity
             : "r"(mbar), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > kTcWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
+}
+
+// Test hook of the timeout path: one thread waits on an mbarrier that nothing
+// completes, gives up after `cycles` and records FDC_ERR_TIMEOUT exactly as a
+// convolution CTA would.
+__global__ void wait_timeout_kernel(long long cycles) {
+    __shared__ __align__(8) unsigned long long mbar;
+    if (threadIdx.x != 0) return;
+    const unsigned mb = smem_u32(&mbar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    if (!mbar_wait_bounded(mb, 0, cycles)) atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
 }
 
 __device__ __forceinline__ void tmem_ld16(unsigned taddr, float v[16]) {
@@ -1193,6 +1205,11 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
     return cudaGetLastError();
 }
 
+cudaError_t launch_wait_timeout(long long cycles, cudaStream_t st) {
+    wait_timeout_kernel<<<1, 32, 0, st>>>(cycles);
+    return cudaGetLastError();
+}
+
 int tc_status(bool clear) {
     int v = 0;
     if (cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int)) != cudaSuccess) return (int)FDC_ERR_CUDA;
@@ -1492,6 +1509,11 @@ int fdc_unet_dihedral(const void *x, const float *target, int32_t d, int32_t h, 
 }
 
 int fdc_unet_status(int32_t clear) { return fdc::tc_status(clear != 0); }
+
+int fdc_debug_wait_timeout(int64_t cycles, void *stream) {
+    if (cycles < 1 || cycles > 4000000000ll) return FDC_ERR_INVALID;
+    return rc(fdc::launch_wait_timeout(cycles, (cudaStream_t)stream));
+}
 
 int fdc_unet_finish(const float *head, const float *dose_in, int64_t n, double dose_scale, double *dose_out,
                     void *stream) {

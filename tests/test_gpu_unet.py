@@ -144,6 +144,28 @@ def test_tensor_core_status_clean():
     assert fdc.lib().fdc_unet_status(1) == 0
 
 
+def test_tensor_core_wait_timeout_is_reported():
+    """The bounded-wait path: a barrier that nothing completes times out, the
+    status reads FDC_ERR_TIMEOUT, clearing resets it, and the context stays
+    usable (a convolution afterwards still succeeds)."""
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    L = fdc.lib()
+    L.fdc_unet_status(1)
+    assert L.fdc_debug_wait_timeout(0, None) != 0
+    assert L.fdc_debug_wait_timeout(2_000_000, None) == 0
+    torch.cuda.synchronize()
+    assert L.fdc_unet_status(1) == 7
+    assert L.fdc_unet_status(0) == 0
+    xt, _ = bf16(np.ones((1, 4, 8, 14, 16)))
+    wt, _ = bf16(np.zeros((16, 3, 3, 3, 16)))
+    g, oshape = geom((1, 4, 8, 14, 16), 16, 3, 1, 1)
+    y = torch.empty(oshape, dtype=torch.float32, device="cuda:0")
+    assert L.fdc_conv3d_forward(C.byref(g), ptr(xt), ptr(wt), None, None, ptr(y), None) == 0
+    torch.cuda.synchronize()
+    assert float(y.abs().max()) == 0.0 and L.fdc_unet_status(1) == 0
+
+
 @pytest.mark.parametrize("code", range(8))
 def test_dihedral_augmentation(code):
     """Mirror x (bit 0), mirror y (bit 1), exchange x and y first (bit 2),
