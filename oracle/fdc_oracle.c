@@ -47,6 +47,14 @@
  * Random numbers: Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11,
  * "Parallel random numbers: as easy as 1, 2, 3"), key = (seed, 0),
  * counter = (history or group index, purpose, 0, 0).
+ *
+ * Pins (tests/test_oracle_pins.py): Philox against an independent
+ * implementation; sampling moments; hand-computed tiny phantoms; the water
+ * identity (depth dose equals the database's chords); 3-D brute force of
+ * single histories; energy conservation; Bragg-Kleeman ranges in slabs;
+ * sharding, per-layer partition and thread reentrancy.  The dose of a full
+ * heterogeneous phantom has no pin beyond these special cases: parity
+ * unpinned there (the paper prints no voxel values).
  */
 #include <math.h>
 #include <stdint.h>
