@@ -36,10 +36,8 @@ METRIC = "histories/sec and track-steps/sec on 1 GB300; wall time to 2% σ (plai
 BYTES_PER_RECORD = 16
 BYTES_PER_HISTORY = 64
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one replay launch of the default workload
-# (thorax, 10^5 tracks per energy, 10^7 histories, track group 32), from one
-# ncu capture of the current kernel (profiles/replay_kernel_thorax.md).
-REPLAY_TRAFFIC_DEFAULT = 1.91e9 + 38.4e6
+# trained U-Net weights (written by --study denoiser --weights-out)
+WEIGHTS = os.path.join(ROOT, "paper_1011_2188_gb300", "data", "unet_thorax128.npz")
 
 
 def parse():
@@ -58,6 +56,8 @@ def parse():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--schedule", default="", help="ctas_per_sm,warps_per_cta,chunk,aggregate")
     ap.add_argument("--quick", action="store_true", help="device timing only (sweeps)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the spot-plan, precision and denoiser measurements of the default line")
     ap.add_argument("--train-cases", type=int, default=200)
     ap.add_argument("--eval-cases", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=12)
@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--weights-out", default="", help="save the trained U-Net weights (.npz) to this path")
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--high", type=int, default=100_000_000, help="histories of the target dose")
-    ap.add_argument("--study", default="", choices=["", "precision", "denoiser", "unet_timing"],
+    ap.add_argument("--study", default="", choices=["", "precision", "denoiser", "unet_timing", "profile_case"],
                     help="precision: FP32 vs FP64 step geometry on the slab phantom, 10^8 histories "
                          "in 100 batches (prints its own JSON line)")
     return ap.parse_args()
@@ -225,41 +225,72 @@ def time_to_sigma(eng, beam, ph, seed, target=0.02, n_batches=10, n0=200_000, lo
                                      track_group=track_group)}
 
 
-def denoised_vs_plain(db, local=0, seed=100_000, n_low=100_000, grid=128, track_group=1):
-    """Metric's second half on one held-out-style case (random thorax-like
-    grid^3 x 2 mm phantom and field, as in the denoiser study): device time of
-    the denoised path (10^5-history run + U-Net inference) against the plain
-    method run to 2 % mean uncertainty.  The network's cost does not depend
-    on its weights; its accuracy is measured by --study denoiser."""
-    import torch
-    from paper_1011_2188_gb300 import denoise, fdc
-    from paper_1011_2188_gb300.measure import time_to_sigma
+def denoiser_eval(weights, local=0, n_cases=20, grid=128, n_low=100_000, n_high=100_000_000):
+    """The metric's second half (learned denoiser, 128^3 x 2 mm cases): the
+    committed U-Net weights on the 20 held-out cases of the denoiser study
+    (random thorax-like phantoms and fields, seeds 100000...), each against
+    the plain 10^8-history dose by 2 %/2 mm gamma; device time and host wall
+    time (beam in host memory to dose in host memory, copies included) of the
+    denoised path (10^5-history run + U-Net) and of the plain method run to
+    2 % mean uncertainty (eq. (1), D > D_max / 2)."""
+    import numpy as np
+    from paper_1011_2188_gb300 import denoise, fdc, synth
+    if not os.path.exists(weights):
+        return {"unavailable": f"no trained weights at {os.path.relpath(weights, ROOT)}"}
+    t0 = time.perf_counter()
     eng = fdc.Engine(local)
+    db = synth.water_database(synth.database_energies(24), 20_000, seed=2)  # the study's database
     eng.load_database(db)
-    ph = denoise.case_phantom(seed, grid)
-    eng.load_phantom(ph)
-    net = denoise.UNet(seed=0)
-    dens = torch.from_numpy(ph.density).cuda(local)
-    bl = denoise.case_beam(seed, n_low)
-    opts = dict(track_group=track_group)
-    times = []
-    for i in range(4):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        dose = torch.empty(ph.shape[::-1], dtype=torch.float64, device=f"cuda:{local}")
-        e0.record()
-        eng.run_ex(bl, 0, 7 + i, dose=dose, **opts)
-        out = denoise.denoise(net, denoise.Sample(dose, dens))
-        e1.record()
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1) * 1e-3)
-    plain = time_to_sigma(eng, denoise.case_beam(seed, 100_000_000), ph.shape[::-1], 11, 0.02, 0.5,
-                          device=local, track_group=track_group)
+    net = denoise.UNet(seed=0, device=f"cuda:{local}")
+    net.load_npz(weights)
+    cases = denoise.generate_cases(eng, range(100_000, 100_000 + n_cases), n_low, n_high, grid, keep_phantom=True)
+    rows, summary = denoise.evaluate(net, eng, cases, n_low, (0.2, 0.2, 0.2), host_timing=True)
     eng.close()
-    t_den = min(times[1:])
-    return {"grid": grid, "histories_low": n_low, "seconds_denoised_path": t_den,
-            "seconds_plain_2pct": plain["seconds"], "histories_plain_2pct": plain["histories"],
-            "plain_over_denoised": plain["seconds"] / t_den,
-            "accuracy": "2%/2mm gamma of the trained network: bench.py --study denoiser"}
+    summary["plain_over_denoised_device"] = summary["seconds_plain_2pct"] / summary["seconds_denoised"]
+    summary["plain_over_denoised_wall"] = summary["wall_seconds_plain_2pct"] / summary["wall_seconds_denoised"]
+    return {"weights": os.path.relpath(weights, ROOT), "grid": grid, "eval_cases": n_cases,
+            "histories_low": n_low, "histories_reference": n_high,
+            "gamma": "2%/2mm global, threshold 10% of max, against the plain 10^8-history dose",
+            "summary": summary,
+            "gamma_denoised_per_case": [round(r["gamma_denoised"], 5) for r in rows],
+            "seconds": time.perf_counter() - t0}
+
+
+def spot_plan_bench(eng, local=0, steps=5, seed=21):
+    """2000 scanning spots in 40 layers (70-230 MeV, log-normal counts,
+    2 x 10^7 histories) on the slab phantom, total plus per-layer dose: one
+    persistent launch per run with the autotuned schedule, replayed as a CUDA
+    graph (timed with events on the caller's stream around the graph
+    launch)."""
+    import torch
+    from paper_1011_2188_gb300 import synth
+    ph = synth.slab_phantom()
+    beam = synth.spot_plan(seed=11, total=20_000_000)
+    n = int(beam["n_histories"].sum())
+    eng.load_phantom(ph)
+    eng.set_timing(False)
+    sched = eng.autotune(beam, n, seed)
+    dev = f"cuda:{local}"
+    n_layers = int(beam["layer"].max()) + 1
+    dose = torch.empty(ph.shape[::-1], dtype=torch.float64, device=dev)
+    ld = torch.empty((n_layers,) + tuple(ph.shape[::-1]), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):  # capture, then relaunches
+        eng.run_ex(beam, 0, seed, dose=dose, layer_dose=ld, stream=stream)
+    cnt = eng.sync(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        e0.record(stream)
+        eng.run_ex(beam, 0, seed, dose=dose, layer_dose=ld, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    eng.sync(stream)
+    t = statistics.median(ms)
+    return {"spots": len(beam), "layers": n_layers, "histories": n, "schedule": list(sched),
+            "timed": "CUDA graph (memsets, replay, per-layer finalize) relaunched; events around the launch",
+            "ms_per_run": t, "histories_per_s": n / (t * 1e-3), "track_steps_per_s": cnt["steps"] / (t * 1e-3)}
 
 
 def history_vs_batch(eng, beam, ph, n, seed, n_batches=10, local=0, track_group=1):
@@ -371,7 +402,7 @@ def denoiser_study(args):
             "total_s": time.perf_counter() - t_all}
     print(json.dumps(line), flush=True)
     if args.weights_out:
-        np.savez(args.weights_out, *[a for st in net.state() for a in (st["w"], st["b"])])
+        net.save_npz(args.weights_out)
 
 
 def unet_timing(args):
@@ -406,77 +437,110 @@ def unet_timing(args):
     print(json.dumps({"study": "unet_timing", "grid": g, "inference_ms": inf, "train_step_ms": tr}), flush=True)
 
 
-def precision_study(args):
-    """Slab phantom (64^3 x 2 mm, bone slab), 150 MeV pencil (and 121 MeV):
-    10^8 histories in 100 batches with FP32 and with FP64 step geometry;
-    dose differences FP32 vs FP64 on the device, both against the FP64 oracle
-    on a history subset, per-voxel batch uncertainty from the FP64 batch sums,
-    and the device time to 2 % mean uncertainty in the Bragg-peak region."""
+def precision_case(E, n_total, n_batches=100, n_sub=300_000, local=0):
+    """Slab phantom (64^3 x 2 mm, bone slab), pencil beam of energy E:
+    n_total histories in n_batches batches with FP32 and with FP64 step
+    geometry; FP32 vs FP64 dose on the device, both against the FP64 oracle on
+    the first n_sub histories (threaded over disjoint history ranges),
+    per-voxel batch uncertainty from the FP64 batch sums (eq. (1)), and the
+    device time to 2 % mean uncertainty in the Bragg-peak region."""
     import numpy as np
     import torch
     import oracle
     from paper_1011_2188_gb300 import fdc, synth
     oracle.build()
+    db = synth.water_database([E], 10_000, seed=1)
+    ph = synth.slab_phantom()
+    beam = synth.pencil_beam(n_total, energy=E, sigma_cm=0.3)
+    eng = fdc.Engine(local)
+    eng.load_database(db)
+    eng.load_phantom(ph)
+    shape = ph.shape[::-1]
+    dev = f"cuda:{local}"
+    out = {"energy_mev": E, "histories": n_total, "n_batches": n_batches}
+    doses = {}
+    for fp64 in (False, True):
+        s1 = torch.zeros(shape, dtype=torch.float64, device=dev)
+        s2 = torch.zeros_like(s1)
+        dose = torch.zeros_like(s1)
+        eng.run_ex(beam, n_total, 5, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2, dose=dose,
+                   fp64_geometry=fp64)
+        eng.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        eng.run_ex(beam, n_total, 5, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2, dose=dose,
+                   fp64_geometry=fp64)
+        e1.record()
+        e1.synchronize()
+        cnt = eng.sync()
+        mean, sigma, rel_half = eng.batch_stats(s1, s2, n_batches, 0.5)
+        _, _, rel_peak = eng.batch_stats(s1, s2, n_batches, 0.9)
+        key = "fp64" if fp64 else "fp32"
+        sec = e0.elapsed_time(e1) * 1e-3
+        # histories to reach 2 % in the Bragg-peak region, from sigma ~ N^-1/2
+        n2 = n_total * (rel_peak / 0.02) ** 2
+        out[key] = {"seconds": sec, "histories_per_s": n_total / sec,
+                    "track_steps_per_s": cnt["steps"] / sec,
+                    "mean_rel_sigma_half_max": rel_half, "mean_rel_sigma_peak_0.9max": rel_peak,
+                    "histories_for_2pct_peak": n2, "seconds_for_2pct_peak": sec * n2 / n_total}
+        doses[key] = dose.cpu().numpy()
+    d32, d64 = doses["fp32"], doses["fp64"]
+    mx = d64.max()
+    out["fp32_vs_fp64_device"] = {"max_abs_over_max": float(np.abs(d32 - d64).max() / mx),
+                                  "mean_abs_over_max": float(np.abs(d32 - d64).mean() / mx)}
+    ref = oracle.run_parallel(db, ph, beam, seed=5, h_begin=0, h_end=n_sub)
+    d_ref = oracle.dose(ph, ref.edep)
+    sub = {"histories": n_sub}
+    for fp64 in (False, True):
+        d = torch.zeros(shape, dtype=torch.float64, device=dev)
+        eng.run_ex(beam, n_sub, 5, dose=d, fp64_geometry=fp64)
+        eng.sync()
+        dd = d.cpu().numpy()
+        sub["fp64" if fp64 else "fp32"] = {
+            "max_abs_over_max": float(np.abs(dd - d_ref).max() / d_ref.max()),
+            "mean_abs_over_max": float(np.abs(dd - d_ref).mean() / d_ref.max()),
+            "total_energy_rel": float(abs(dd.sum() - d_ref.sum()) / d_ref.sum())}
+    out["vs_oracle"] = sub
+    eng.close()
+    return out
+
+
+def precision_study(args):
+    """Precision study (10^8 histories in 100 batches, FP32 vs FP64 step
+    geometry vs the FP64 oracle) at 150 MeV and at the paper's 121 MeV."""
     n_total = args.histories or 100_000_000
-    n_batches = 100
-    res = {"study": "precision", "histories": n_total, "n_batches": n_batches}
+    res = {"study": "precision", "histories": n_total, "n_batches": 100}
     for E in (150.0, 121.0):
-        db = synth.water_database([E], 10_000, seed=1)
-        ph = synth.slab_phantom()
-        beam = synth.pencil_beam(n_total, energy=E, sigma_cm=0.3)
-        eng = fdc.Engine(0)
-        eng.load_database(db)
-        eng.load_phantom(ph)
-        shape = ph.shape[::-1]
-        out = {}
-        doses = {}
-        for fp64 in (False, True):
-            s1 = torch.zeros(shape, dtype=torch.float64, device="cuda:0")
-            s2 = torch.zeros_like(s1)
-            dose = torch.zeros_like(s1)
-            eng.run_ex(beam, n_total, 5, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2, dose=dose,
-                       fp64_geometry=fp64)
-            eng.sync()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            eng.run_ex(beam, n_total, 5, n_batches=n_batches, batch_sum=s1, batch_sumsq=s2, dose=dose,
-                       fp64_geometry=fp64)
-            e1.record()
-            e1.synchronize()
-            cnt = eng.sync()
-            mean, sigma, rel_half = eng.batch_stats(s1, s2, n_batches, 0.5)
-            _, _, rel_peak = eng.batch_stats(s1, s2, n_batches, 0.9)
-            key = "fp64" if fp64 else "fp32"
-            sec = e0.elapsed_time(e1) * 1e-3
-            # histories to reach 2 % in the Bragg-peak region, from sigma ~ N^-1/2
-            n2 = n_total * (rel_peak / 0.02) ** 2
-            out[key] = {"seconds": sec, "histories_per_s": n_total / sec,
-                        "track_steps_per_s": cnt["steps"] / sec,
-                        "mean_rel_sigma_half_max": rel_half, "mean_rel_sigma_peak": rel_peak,
-                        "histories_for_2pct_peak": n2, "seconds_for_2pct_peak": sec * n2 / n_total}
-            doses[key] = dose.cpu().numpy()
-        d32, d64 = doses["fp32"], doses["fp64"]
-        mx = d64.max()
-        out["fp32_vs_fp64_device"] = {"max_abs_over_max": float(np.abs(d32 - d64).max() / mx),
-                                      "mean_abs_over_max": float(np.abs(d32 - d64).mean() / mx)}
-        # against the FP64 oracle on the first n_sub histories
-        n_sub = 300_000
-        ref = oracle.run(db, ph, beam, seed=5, h_begin=0, h_end=n_sub)
-        d_ref = oracle.dose(ph, ref.edep)
-        sub = {}
-        for fp64 in (False, True):
-            d = torch.zeros(shape, dtype=torch.float64, device="cuda:0")
-            eng.run_ex(beam, n_sub, 5, dose=d, fp64_geometry=fp64)
-            eng.sync()
-            dd = d.cpu().numpy()
-            sub["fp64" if fp64 else "fp32"] = {
-                "max_abs_over_max": float(np.abs(dd - d_ref).max() / d_ref.max()),
-                "mean_abs_over_max": float(np.abs(dd - d_ref).mean() / d_ref.max()),
-                "total_energy_rel": float(abs(dd.sum() - d_ref.sum()) / d_ref.sum())}
-        out["vs_oracle_first_%d" % n_sub] = sub
-        res[f"{E:g}MeV"] = out
-        eng.close()
+        res[f"{E:g}MeV"] = precision_case(E, n_total)
     print(json.dumps(res), flush=True)
+
+
+def profile_case(args):
+    """Small cases for ncu captures (the full-size workload holds ~13 GB on
+    the device): the thorax phantom with a 24 x 10^4-track database
+    (4.6 x 10^7 step records, 1.3 GB), 10^6 histories over the 10 x 10 cm
+    field with 32 histories per track, replayed twice (capture the second
+    launch); then one launch of the atomic probe (2^28 updates over 64 MB).
+    Prints the replay's counters so per-step figures can be formed."""
+    import torch
+    from paper_1011_2188_gb300 import fdc, synth
+    n = args.histories or 1_000_000
+    db = synth.water_database(synth.database_energies(24), 10_000, seed=2)
+    ph = synth.thorax_phantom(seed=7)
+    beam = synth.field_beam(n, energy=150.0, width=10.0, height=10.0, sigma_e_rel=0.01)
+    eng = fdc.Engine(0)
+    eng.load_database(db)
+    eng.load_phantom(ph)
+    dose = torch.empty(ph.shape[::-1], dtype=torch.float64, device="cuda:0")
+    for _ in range(2):
+        eng.run_ex(beam, n, 1234, dose=dose, track_group=args.track_group, graph=False)
+        cnt = eng.sync()
+    slots = torch.zeros(1 << 23, dtype=torch.int64, device="cuda:0")
+    ms = fdc.probe_atomics(slots, 1 << 28)
+    eng.close()
+    print(json.dumps({"study": "profile_case", "histories": n, "track_group": args.track_group,
+                      "steps": cnt["steps"], "segments": cnt["segments"], "probe_ops": 1 << 28,
+                      "probe_ms": ms, "kernel_source_sha16": kernel_source_hash()}), flush=True)
 
 
 def run_reference(args, rank, world):
@@ -532,6 +596,35 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def kernel_source_hash():
+    """Hash of the replay kernel's sources: a DRAM-traffic figure measured on
+    one version of the kernel is reported only for that version."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("fdc_kernels.cu", "fdc_internal.h"):
+        with open(os.path.join(ROOT, "paper_1011_2188_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic_per_step():
+    """DRAM bytes (read + write) per replayed track step of the replay kernel
+    from the committed ncu summary, if it was taken on the current kernel
+    source; else None."""
+    path = os.path.join(ROOT, "profiles", "replay_kernel_dram_per_step.txt")
+    if not os.path.exists(path):
+        return None, "no capture summary"
+    kv = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha16") != kernel_source_hash():
+        return None, "kernel changed since the capture"
+    return float(kv["dram_bytes_per_step"]), kv.get("workload", "")
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -552,6 +645,10 @@ def main():
         if rank == 0:
             unet_timing(args)
         return
+    if args.study == "profile_case":
+        if rank == 0:
+            profile_case(args)
+        return
 
     import numpy as np
     import torch
@@ -562,8 +659,11 @@ def main():
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
+        # one rank per GPU; the ranks' int64 tallies are summed over NCCL
+        os.environ.setdefault("NCCL_DEBUG", "INFO")
+        os.environ.setdefault("NCCL_DEBUG_SUBSYS", "INIT")
         import torch.distributed as dist
-        dist.init_process_group("gloo")
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
 
     db, ph, beam, n, desc = workload(args, world)
     eng = fdc.Engine(local)
@@ -578,20 +678,30 @@ def main():
     if args.schedule:
         sched = tuple(int(x) for x in args.schedule.split(","))
     if args.autotune:
-        sched = eng.autotune(beam, min(n, 1_000_000), seed)
-    dose = torch.empty(ph.shape[::-1], dtype=torch.float64, device=f"cuda:{local}")
+        sched = eng.autotune(beam, min(n, 1_000_000), seed, history_offset=offset, track_group=args.track_group)
+    dev = f"cuda:{local}"
+    dose = torch.empty(ph.shape[::-1], dtype=torch.float64, device=dev)
+    tally = torch.empty(ph.shape[::-1], dtype=torch.int64, device=dev) if world > 1 else None
     layer_dose = None
     if args.workload == "spots":  # total dose plus the dose of every energy layer
         n_layers = int(beam["layer"].max()) + 1
-        layer_dose = torch.empty((n_layers,) + tuple(ph.shape[::-1]), dtype=torch.float64,
-                                 device=f"cuda:{local}")
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=f"cuda:{local}")
+        layer_dose = torch.empty((n_layers,) + tuple(ph.shape[::-1]), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
     eng.set_timing(True)
 
     def one_step():
-        eng.run_ex(beam, n, seed, history_offset=offset, dose=dose, layer_dose=layer_dose, stream=stream,
-                   schedule=sched, track_group=args.track_group)
+        if world == 1:
+            eng.run_ex(beam, n, seed, history_offset=offset, dose=dose, layer_dose=layer_dose, stream=stream,
+                       schedule=sched, track_group=args.track_group)
+        else:
+            # this rank's histories into its int64 tally, the exact sum over
+            # the ranks (Sec. 2.3: the two GPUs' doses summed at the end),
+            # then the dose of the whole job
+            eng.run_ex(beam, n, seed, history_offset=offset, tally=tally, stream=stream,
+                       schedule=sched, track_group=args.track_group)
+            dist.all_reduce(tally)
+            eng.dose_from_tally(tally, dose, stream=stream)
 
     for _ in range(max(args.warmup, 0)):
         one_step()
@@ -625,7 +735,7 @@ def main():
     cnt = eng.sync(stream)
     ms = sum(step_ms) / len(step_ms)
     if dist:
-        t = torch.tensor([ms], dtype=torch.float64)
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t[0])
     value = n * world / (ms * 1e-3)
@@ -636,11 +746,13 @@ def main():
                               "tracks": args.tracks, "track_group": args.track_group,
                               "track_steps_per_s": steps_per_run * world / (ms * 1e-3), "clocks": clk,
                               "flags": os.environ.get("FDC_NVCC_FLAGS", "")}), flush=True)
+        if dist:
+            dist.destroy_process_group()
         return
 
     # ---- ablation: a separate track per history (Sec. 4: +50 % time on the GTX 295)
     indep = None
-    if args.track_group != 1 and not args.quick:
+    if args.track_group != 1 and world == 1:
         t_ind = []
         for i in range(3 + 3):
             ev0.record(stream)
@@ -667,16 +779,24 @@ def main():
     d2h = int(host_dose.nbytes)
 
     # ---- L2 atomic probe (denominator of the tally-update roofline)
-    slots = torch.zeros(1 << 23, dtype=torch.int64, device=f"cuda:{local}")  # 64 MB, like the tally
-    n_ops = 1 << 30
+    slots = torch.zeros(1 << 23, dtype=torch.int64, device=dev)  # 64 MB, like the tally
+    n_ops = 1 << 31
     fdc.probe_atomics(slots, n_ops // 8)  # warm-up
     atom_ms = min(fdc.probe_atomics(slots, n_ops) for _ in range(3))
     atom_peak = n_ops / (atom_ms * 1e-3)
 
     hbm_peak, peak_kind = load_peaks()
-    alg_bytes = BYTES_PER_RECORD * steps_per_run / max(1, args.track_group) + BYTES_PER_HISTORY * hist_per_run
+    # algorithmic HBM bytes of one replay launch: the step records (16 B per
+    # replayed step, shared by the G histories of a track group), and, as a
+    # second count, the same plus every history's track and start-step lookups
+    rec_bytes = BYTES_PER_RECORD * steps_per_run / max(1, args.track_group)
+    alg_bytes = rec_bytes
+    alg_bytes_lookups = rec_bytes + BYTES_PER_HISTORY * hist_per_run
     achieved = alg_bytes / (rep_ms * 1e-3) / 1e9
+    achieved_lookups = alg_bytes_lookups / (rep_ms * 1e-3) / 1e9
     atom_achieved = segs_per_run / (rep_ms * 1e-3)
+    per_step, traffic_src = measured_traffic_per_step()
+    traffic = per_step * steps_per_run if per_step is not None and args.workload == "thorax" else None
 
     line = {
         "metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world,
@@ -684,28 +804,32 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "histories_per_step": n, "tally": "int64 fixed point 2^-28 MeV",
                    "l2": "flushed between timed steps (512 MB write); track working set > L2",
-                   "schedule": list(sched) if sched else "default", "parallelism": f"replicas x{world}",
-                   "track_group": args.track_group},
+                   "schedule": list(sched) if sched else "default",
+                   "parallelism": "history ranges per rank, int64 tally all-reduce (NCCL)" if world > 1
+                   else "one GPU", "track_group": args.track_group},
         "track_steps_per_s": steps_per_run * world / (ms * 1e-3),
         "segments_per_s": segs_per_run * world / (ms * 1e-3),
         "steps_per_history": steps_per_run / hist_per_run,
         "replay_ms": rep_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak,
-                     "traffic": (REPLAY_TRAFFIC_DEFAULT if (args.workload == "thorax" and n == 10_000_000
-                                                           and args.tracks == 100_000 and args.track_group == 32)
-                                 else None),
+                     "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": alg_bytes,
+                     "algorithmic_count": f"{BYTES_PER_RECORD} B per replayed step / track group "
+                                          f"({args.track_group})",
+                     "with_history_lookups": {"bytes_per_launch": alg_bytes_lookups, "achieved": achieved_lookups,
+                                              "frac": achieved_lookups / hbm_peak,
+                                              "count": f"+ {BYTES_PER_HISTORY} B per history"},
+                     "traffic_source": traffic_src,
                      "note": "not the binding resource: the replay kernel is bound by instruction issue "
-                             "(~82 % of issue slots in ncu) and L2 atomics (roofline_l2_atomic)"},
+                             "(ncu issue-slot utilisation) and L2 atomics (roofline_l2_atomic)"},
         "roofline_l2_atomic": {"achieved": atom_achieved, "peak": atom_peak, "unit": "atomic/s",
                                "frac": atom_achieved / atom_peak,
                                "note": "one tally update per voxel segment; peak from the hashed int64 "
-                                       "atomic probe on this GPU"},
+                                       "atomic probe on this GPU (random 8-byte slots of a 64 MB array)"},
         "e2e": {"value": n / e2e_s, "unit": "histories/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (2 if world == 1 else 3) * args.steps,
         "ablation_independent_tracks": indep,
         "clocks": clk,
         "load_s": t_load,
@@ -715,14 +839,19 @@ def main():
                                                          track_group=args.track_group)
         line["history_by_history"] = history_vs_batch(eng, beam, ph, n, seed + 7, local=local,
                                                       track_group=args.track_group)
-    if rank == 0 and args.workload == "thorax":
-        line["wall_time_to_2pct_plain_vs_denoised"] = denoised_vs_plain(db, local=local,
-                                                                        track_group=args.track_group)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(db, ph, beam, seed)
+    if rank == 0 and args.workload == "thorax" and world == 1 and not args.no_extras:
+        # the other configurations, each timed on its own (not part of `value`)
+        line["spot_plan_2000"] = spot_plan_bench(eng, local=local)
+        eng.close()
+        eng = None
+        line["precision_fp32_fp64"] = precision_case(150.0, 100_000_000, local=local)
+        line["denoiser"] = denoiser_eval(WEIGHTS, local=local)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    eng.close()
+    if eng is not None:
+        eng.close()
     if dist:
         dist.destroy_process_group()
 

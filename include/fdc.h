@@ -73,9 +73,11 @@ typedef struct fdc_ctx fdc_ctx;
  *     theta[k] polar deflection applied at the end of the step (rad, [0, pi]);
  *     phi[k]   its azimuth (rad);
  *     esec[k]  energy deposited locally at the end of the step (MeV, >= 0).
- * Storage: theta is kept as IEEE half precision and phi as a multiple of
- * 2 pi / 65536 (one 16-byte record per step); values already on those grids
- * are stored exactly. */
+ * Storage: one 16-byte record per step holds len, dE and the deflection as
+ * the vector theta * (cos phi, sin phi), formed in FP64 and rounded once to
+ * FP32 (so theta and phi keep FP32 precision; phi needs no range reduction
+ * by the caller); esec goes to a side array that is read only for tracks
+ * with a nonzero entry. */
 typedef struct fdc_database {
     int32_t n_energies;
     const float *energy;
@@ -213,6 +215,17 @@ int fdc_run_ex(fdc_ctx *ctx, const fdc_beam *beam, uint64_t n_histories, uint64_
 int fdc_run_host(fdc_ctx *ctx, const fdc_beam *beam, uint64_t n_histories, uint64_t seed,
                  const fdc_run_opts *opts, double *dose_host);
 
+/* Sec. 2.3 (end of run: energy divided by the voxel mass) for a tally the
+ * caller holds: converts tally[nvox] (device, int64 energy in units of
+ * 2^-FDC_TALLY_SHIFT MeV, read only) to dose_out[nvox] (device, Gy) with the
+ * loaded phantom's densities and voxel volume.  This is the last step after
+ * runs over disjoint history ranges -- on one device or on several (the
+ * paper's two GPUs each replayed part of the histories and the doses were
+ * summed at the end, Sec. 2.3) -- whose `tally` outputs were added: integer
+ * sums are exact, so the dose equals that of one run over all the
+ * histories, bit for bit.  Asynchronous on `stream`. */
+int fdc_dose_from_tally(fdc_ctx *ctx, const int64_t *tally, double *dose_out, void *stream);
+
 /* Wait for `stream`, read the device status word of the last run and its
  * counters.  Returns FDC_OK or the first device error (FDC_ERR_STEP_LIMIT,
  * ...); `counters` (host, may be NULL) receives the counters. */
@@ -235,12 +248,21 @@ int fdc_history_stats(fdc_ctx *ctx, const double *dose_sum, const double *histor
                       uint64_t n_histories, double frac, double *mean, double *sigma,
                       double *mean_rel, void *stream);
 
-/* Pick the replay schedule for this beam by timing candidates on the device
- * (runs the beam's first n_histories histories several times; results are
- * discarded).  The choice becomes the context's default; *best (host, may be
- * NULL) receives it.  Synchronous. */
+/* Pick the replay schedule for this beam and these run options by timing
+ * candidates on the device (Sec. 3 tuned the paper's N_B and N_T by hand):
+ * the built-in default and warps per CTA x CTAs per SM x chunk x tally
+ * aggregation, each CTA count bounded by the occupancy of the kernel
+ * instantiation the options select (track group, FP64 geometry, and whether
+ * the database has local deposits).  Runs histories [h, h + n_histories) of
+ * the beam, h = opts->history_offset, several times and keeps the candidate
+ * with the shortest replay-kernel time (CUDA events); results are discarded.
+ * opts (host, may be NULL) is read for history_offset, track_group,
+ * no_rotation, scaling_mode and fp64_geometry; its schedule and n_batches
+ * are ignored.  The choice becomes the context's default schedule for runs
+ * that select the same kernel instantiation; *best (host, may be NULL)
+ * receives it.  Synchronous. */
 int fdc_autotune(fdc_ctx *ctx, const fdc_beam *beam, uint64_t n_histories, uint64_t seed,
-                 fdc_schedule *best);
+                 const fdc_run_opts *opts, fdc_schedule *best);
 
 /* Measurement.  fdc_set_timing(ctx, 1) makes later runs record CUDA events
  * on their stream around the replay kernel(s) and the finalize kernel (timed
@@ -250,10 +272,12 @@ int fdc_autotune(fdc_ctx *ctx, const fdc_beam *beam, uint64_t n_histories, uint6
 int fdc_set_timing(fdc_ctx *ctx, int32_t enable);
 int fdc_last_kernel_ms(fdc_ctx *ctx, double *replay_ms, double *finalize_ms);
 
-/* L2 atomic throughput probe (roofline denominator of the tally updates):
- * n_ops 64-bit atomic adds of 1 spread by a hash over the n_slots counters of
- * device array slots[n_slots] (zeroed by the call), issued by a full grid;
- * *ms (host) receives the kernel time.  Synchronous on `stream`. */
+/* L2 atomic throughput probe (roofline denominator of the tally updates; no
+ * counterpart in the paper): n_ops 64-bit atomic adds of 1 spread by a hash
+ * over the first P counters of device array slots[n_slots] (zeroed by the
+ * call), P the largest power of two <= n_slots, issued by a full-occupancy
+ * grid with four independent updates in flight per thread; *ms (host)
+ * receives the kernel time.  Synchronous on `stream`. */
 int fdc_probe_atomics(uint64_t *slots, uint64_t n_slots, uint64_t n_ops, double *ms, void *stream);
 
 /* Run without allocating device memory.
@@ -264,7 +288,11 @@ int fdc_probe_atomics(uint64_t *slots, uint64_t n_slots, uint64_t n_ops, double 
  * for the whole device) or an out-of-memory failure in the middle of a plan
  * is not acceptable.  The paper has no counterpart to this call.
  *
- * Same computation and result as fdc_run.  The database and phantom must
+ * Same computation and result as fdc_run with default options -- histories
+ * [0, n_histories), one track per history (track group 1), rotated reuse,
+ * per-voxel step scaling, FP32 geometry, the context's default schedule --
+ * and bit for bit the same dose; there are no run options, so runs with a
+ * track group, batches or per-layer dose need fdc_run_ex.  The database and phantom must
  * already be loaded into ctx (those loads allocate, once, beforehand); the
  * caller passes the beam (host) and dose_out[nvox] (device).  All scratch --
  * the int64 tally, the counters, the work counter and the device copy of the
@@ -281,7 +309,11 @@ int fdc_probe_atomics(uint64_t *slots, uint64_t n_slots, uint64_t n_ops, double 
  * and corrupt each other's results.
  * counters_dev (device, may be NULL) receives the run's counters and device
  * status (as fdc_sync reports them for other runs) once the work on `stream`
- * completes.  Asynchronous on `stream`. */
+ * completes.  Asynchronous on `stream`, except for the copy of the spot
+ * table from the caller's host memory: from pageable memory that copy is
+ * synchronous (the host waits for it) and cannot be recorded in a stream
+ * capture; from pinned memory it is asynchronous.  The call allocates no
+ * staging buffer for it. */
 #define FDC_NOALLOC_MAX_VOXELS (1 << 21)
 #define FDC_NOALLOC_MAX_SPOTS 4096
 #define FDC_NOALLOC_SCRATCH_BYTES                                                  \

@@ -108,12 +108,21 @@ int fdc_unet_dihedral(const void *x, const float *target, int32_t d, int32_t h, 
 /* Device status of the tensor-core convolutions: FDC_OK, or FDC_ERR_TIMEOUT
  * once a convolution CTA gave up waiting for its accumulator (that CTA wrote
  * no output); clear != 0 resets it.  Synchronises with the device; not for
- * use inside stream capture. */
+ * use inside stream capture.
+ * After FDC_ERR_TIMEOUT nothing computed on the device from that launch on
+ * can be trusted: the CTA that gave up frees its tensor memory and returns
+ * while the matrix operations it issued may still be reading its shared
+ * memory and writing the columns it freed, which later CTAs may hold.  Treat
+ * the timeout as fatal to the process's GPU state: discard the outputs of
+ * that and every later launch and rebuild the CUDA context. */
 int fdc_unet_status(int32_t clear);
 /* Test hook of that status (no counterpart in the paper): launches one thread
  * that waits on a barrier nothing completes, gives up after `cycles` SM clock
  * cycles (1 .. 4e9) and records FDC_ERR_TIMEOUT as a timed-out convolution
- * would.  Asynchronous on `stream`; FDC_ERR_INVALID for cycles out of range. */
+ * would.  It issues no matrix operation, so it exercises the bounded wait and
+ * the status word only, not a convolution CTA abandoning operations in
+ * flight.  Asynchronous on `stream`; FDC_ERR_INVALID for cycles out of
+ * range. */
 int fdc_debug_wait_timeout(int64_t cycles, void *stream);
 /* Denoised dose: dose_out [n] (FP64, Gy) = max(0, (head[n][16] channel 0 + dose_in) * dose_scale). */
 int fdc_unet_finish(const float *head, const float *dose_in, int64_t n, double dose_scale, double *dose_out,

@@ -189,6 +189,41 @@ def run(db, ph, beam, seed, h_begin=0, h_end=None, track_group=1, scaling_mode=0
     return Result(edep if per_layer else edep[0], sq, out)
 
 
+def run_parallel(db, ph, beam, seed, h_begin=0, h_end=None, threads=None, **kw):
+    """``run`` over [h_begin, h_end) split into contiguous history ranges, one
+    per thread (the C oracle keeps no global state and ctypes releases the GIL
+    during the call); the per-thread FP64 grids and counters are summed.
+    Histories are independent (Sec. 2.3), so this is the same replay as one
+    sequential call up to the order of the FP64 additions."""
+    from concurrent.futures import ThreadPoolExecutor
+    lib()
+    total = int(np.sum(np.asarray(beam["n_histories"], dtype=np.uint64)))
+    if h_end is None:
+        h_end = total
+    if threads is None:
+        try:
+            threads = len(os.sched_getaffinity(0))
+        except AttributeError:
+            threads = os.cpu_count() or 1
+    n = h_end - h_begin
+    threads = max(1, min(int(threads), n))
+    cuts = [h_begin + n * i // threads for i in range(threads + 1)]
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(lambda i: run(db, ph, beam, seed, h_begin=cuts[i], h_end=cuts[i + 1], **kw),
+                            range(threads)))
+    res = parts[0]
+    for r in parts[1:]:
+        res.edep += r.edep
+        if res.hh_sumsq is not None:
+            res.hh_sumsq += r.hh_sumsq
+        res.replayed += r.replayed
+        res.escaped += r.escaped
+        res.n_histories += r.n_histories
+        res.n_steps += r.n_steps
+        res.n_segments += r.n_segments
+    return res
+
+
 def dose(ph, edep):
     """Energy (MeV per voxel) to dose (Gy), Sec. 2.3."""
     keep = _Keep()

@@ -2,7 +2,6 @@
 // the track database into 16-byte step records, device buffers, and the run
 // sequence (zero tally -> replay -> finalize) on the caller's stream.
 
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -67,6 +66,9 @@ struct fdc_ctx {
     long long n_tracks = 0, n_steps = 0;
     long long max_track_units = 0;
     DevBuf<uint4> rec;
+    bool has_esec = false;
+    DevBuf<float> esec;
+    DevBuf<unsigned char> trk_esec;
     DevBuf<float> eres;
     DevBuf<long long> tail;
     DevBuf<long long> step_begin;
@@ -100,8 +102,10 @@ struct fdc_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     GraphKey graph_key;
-    // schedule
+    // schedule picked by fdc_autotune and the instantiation it was tuned on
     fdc_schedule tuned = {0, 0, 0, 0};
+    bool tuned_valid = false;
+    fdc::ReplayVariant tuned_variant = {0, 0, 0, 1, 0};
     int last_fp64 = 0;
 };
 
@@ -142,25 +146,48 @@ struct Pinned {
     }
 };
 
-// track_group and squares select the kernel variant whose occupancy bounds ctas_per_sm
-int resolve_schedule(fdc_ctx *c, const fdc_schedule *req, int fp64, int track_group, bool squares,
-                     fdc_schedule *out) {
+// The tuned schedule applies to runs of the kernel instantiation it was
+// tuned on (aggregate aside, which the schedule itself picks).
+bool same_tuning_class(const fdc::ReplayVariant &a, const fdc::ReplayVariant &b) {
+    return a.fp64 == b.fp64 && a.squares == b.squares && a.esec == b.esec &&
+           (a.track_group >= 32) == (b.track_group >= 32);
+}
+
+// Fill the zero fields of a requested schedule from the tuned schedule (when
+// it was tuned on this run's kernel instantiation) or the built-in defaults;
+// ctas_per_sm is bounded by the occupancy of the instantiation that will run.
+int resolve_schedule(fdc_ctx *c, const fdc_schedule *req, fdc::ReplayVariant v, fdc_schedule *out) {
     fdc_schedule s = {0, 0, 0, 0};
     if (req) s = *req;
-    if (!s.warps_per_cta) s.warps_per_cta = c->tuned.warps_per_cta ? c->tuned.warps_per_cta : 8;
-    if (!s.chunk) s.chunk = c->tuned.chunk ? c->tuned.chunk : 1;
+    const fdc_schedule t = (c->tuned_valid && same_tuning_class(c->tuned_variant, v)) ? c->tuned
+                                                                                     : fdc_schedule{0, 0, 0, 0};
+    if (!s.warps_per_cta) s.warps_per_cta = t.warps_per_cta ? t.warps_per_cta : 8;
+    if (!s.chunk) s.chunk = t.chunk ? t.chunk : 1;
     // plain atomics by default: on GB300 the L2 absorbs the tally updates
     // faster than a match/redux combine across the warp
-    if (!s.aggregate) s.aggregate = c->tuned.aggregate ? c->tuned.aggregate : 2;
+    if (!s.aggregate) s.aggregate = t.aggregate ? t.aggregate : 2;
     // the replay kernel is compiled for at most 256 threads per CTA
     if (s.warps_per_cta < 1 || s.warps_per_cta > 8 || s.chunk < 1 || s.chunk > 1024 || s.aggregate < 1 ||
         s.aggregate > 2 || s.ctas_per_sm < 0)
         return fail(c, FDC_ERR_INVALID, "invalid schedule");
-    const int maxc = fdc::replay_max_ctas_per_sm(s.warps_per_cta, fp64, s.aggregate, squares ? 1 : track_group);
-    if (!s.ctas_per_sm) s.ctas_per_sm = c->tuned.ctas_per_sm ? std::min(c->tuned.ctas_per_sm, maxc) : maxc;
+    v.aggregate = s.aggregate;
+    const int maxc = fdc::replay_max_ctas_per_sm(s.warps_per_cta, v);
+    if (!s.ctas_per_sm) s.ctas_per_sm = t.ctas_per_sm ? std::min(t.ctas_per_sm, maxc) : maxc;
     if (s.ctas_per_sm > maxc) s.ctas_per_sm = maxc;
     *out = s;
     return FDC_OK;
+}
+
+// The kernel instantiation a run with these options selects (aggregate is
+// filled in by resolve_schedule).
+fdc::ReplayVariant run_variant(const fdc_ctx *c, const fdc_run_opts &o, bool squares) {
+    fdc::ReplayVariant v;
+    v.fp64 = o.fp64_geometry ? 1 : 0;
+    v.aggregate = 0;
+    v.squares = squares ? 1 : 0;
+    v.track_group = o.track_group > 1 ? o.track_group : 1;
+    v.esec = c->has_esec ? 1 : 0;
+    return v;
 }
 
 struct BeamInfo {
@@ -225,6 +252,8 @@ fdc::ReplayArgs base_args(fdc_ctx *c) {
     fdc::ReplayArgs a;
     std::memset(&a, 0, sizeof a);
     a.rec = c->rec.p;
+    a.esec = c->has_esec ? c->esec.p : nullptr;
+    a.trk_esec = c->trk_esec.p;
     a.eres = c->eres.p;
     a.tail = c->tail.p;
     a.step_begin = c->step_begin.p;
@@ -285,6 +314,8 @@ void fdc_destroy(fdc_ctx *c) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     c->rec.release();
+    c->esec.release();
+    c->trk_esec.release();
     c->eres.release();
     c->tail.release();
     c->step_begin.release();
@@ -339,18 +370,38 @@ int fdc_load_database(fdc_ctx *c, const fdc_database *db) {
             return fail(c, FDC_ERR_INVALID, "database: bad step record %lld", k);
         if (e > 1.0e6f || s > 1.0e6f) return fail(c, FDC_ERR_OVERFLOW, "database: step energy %lld beyond the fixed-point range", k);
     }
+    // tracks with local deposits (the kernel reads the esec side array only for those)
+    std::vector<unsigned char> trk_esec((size_t)std::max<long long>(nt, 1), 0);
+    bool any_esec = false;
+    for (long long t = 0; t < nt; ++t)
+        for (long long k = db->step_begin[t]; k < db->step_begin[t + 1]; ++k)
+            if (db->esec[k] != 0.0f) {
+                trk_esec[t] = 1;
+                any_esec = true;
+                break;
+            }
     // ---- device buffers
     c->db_loaded = false;
     FDC_CUDA(c, c->rec.ensure(ns));
     FDC_CUDA(c, c->eres.ensure(ns));
     FDC_CUDA(c, c->tail.ensure(ns));
     FDC_CUDA(c, c->step_begin.ensure(nt + 1));
+    FDC_CUDA(c, c->trk_esec.ensure(nt));
     FDC_CUDA(c, c->bin_energy.ensure(nb));
     FDC_CUDA(c, c->bin_track_begin.ensure(nb + 1));
     FDC_CUDA(c, cudaMemcpy(c->step_begin.p, db->step_begin, sizeof(long long) * (nt + 1), cudaMemcpyHostToDevice));
+    FDC_CUDA(c, cudaMemcpy(c->trk_esec.p, trk_esec.data(), (size_t)nt, cudaMemcpyHostToDevice));
     FDC_CUDA(c, cudaMemcpy(c->bin_energy.p, db->energy, sizeof(float) * nb, cudaMemcpyHostToDevice));
     FDC_CUDA(c, cudaMemcpy(c->bin_track_begin.p, db->track_begin, sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice));
-    // ---- pack in chunks of whole tracks through pinned staging
+    if (any_esec) {
+        FDC_CUDA(c, c->esec.ensure(ns));
+        FDC_CUDA(c, cudaMemcpy(c->esec.p, db->esec, sizeof(float) * ns, cudaMemcpyHostToDevice));
+    } else {
+        c->esec.release();
+    }
+    c->has_esec = any_esec;
+    // ---- pack in chunks of whole tracks through pinned staging; the
+    // deflection vector of each record is formed on the device after the copy
     const long long CH = std::max<long long>(1 << 22, kMaxTrack);
     Pinned prec, peres, ptail;
     FDC_CUDA(c, cudaMallocHost(&prec.p, sizeof(uint4) * CH));
@@ -363,13 +414,15 @@ int fdc_load_database(fdc_ctx *c, const fdc_database *db) {
     auto flush = [&]() -> int {
         if (!fill) return FDC_OK;
         FDC_CUDA(c, cudaMemcpy(c->rec.p + chunk_first, hr, sizeof(uint4) * fill, cudaMemcpyHostToDevice));
+        FDC_CUDA(c, fdc::launch_pack_deflections(c->rec.p + chunk_first, fill, nullptr));
         FDC_CUDA(c, cudaMemcpy(c->eres.p + chunk_first, he, sizeof(float) * fill, cudaMemcpyHostToDevice));
         FDC_CUDA(c, cudaMemcpy(c->tail.p + chunk_first, ht, sizeof(long long) * fill, cudaMemcpyHostToDevice));
+        // the pinned record staging is refilled next: wait for the packing kernel
+        FDC_CUDA(c, cudaDeviceSynchronize());
         chunk_first += fill;
         fill = 0;
         return FDC_OK;
     };
-    const double two_pi = 6.283185307179586476925286766559;
     for (int b = 0; b < nb; ++b) {
         const double Eb = (double)db->energy[b];
         for (long long t = db->track_begin[b]; t < db->track_begin[b + 1]; ++t) {
@@ -385,17 +438,11 @@ int fdc_load_database(fdc_ctx *c, const fdc_database *db) {
                 he[fill + k] = (float)(Eb - used);
                 used += (double)db->dE[g] + (double)db->esec[g];
                 uint4 r;
-                float l = db->len[g], e = db->dE[g], s = db->esec[g];
+                const float l = db->len[g], e = db->dE[g], th = db->theta[g], ph = db->phi[g];
                 std::memcpy(&r.x, &l, 4);
                 std::memcpy(&r.y, &e, 4);
-                std::memcpy(&r.z, &s, 4);
-                const __half th = __float2half_rn(db->theta[g]);
-                unsigned short thb;
-                std::memcpy(&thb, &th, 2);
-                double q = std::fmod((double)db->phi[g], two_pi);
-                if (q < 0) q += two_pi;
-                const unsigned code = (unsigned)llrint(q * (65536.0 / two_pi)) & 0xffffu;
-                r.w = (unsigned)thb | (code << 16);
+                std::memcpy(&r.z, &th, 4);  // (theta, phi) until packed on the device
+                std::memcpy(&r.w, &ph, 4);
                 hr[fill + k] = r;
             }
             long long acc = 0;
@@ -493,8 +540,7 @@ int run_impl(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t se
         (double)per_launch * (double)c->max_track_units > 9.0e18)
         return fail(c, FDC_ERR_OVERFLOW, "too many histories per launch for the int64 tally");
     fdc_schedule sched;
-    rc = resolve_schedule(c, &opts.schedule, opts.fp64_geometry, opts.track_group > 1 ? opts.track_group : 1,
-                          out.history_sumsq != nullptr, &sched);
+    rc = resolve_schedule(c, &opts.schedule, run_variant(c, opts, out.history_sumsq != nullptr), &sched);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     FDC_CUDA(c, cudaSetDevice(c->device));
@@ -654,6 +700,23 @@ int fdc_run(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t see
     return fdc_run_ex(c, beam, n_histories, seed, nullptr, &out, stream);
 }
 
+int fdc_dose_from_tally(fdc_ctx *c, const int64_t *tally, double *dose_out, void *stream) {
+    if (!c) return FDC_ERR_INVALID;
+    if (!c->ph_loaded) return fail(c, FDC_ERR_NOT_LOADED, "phantom must be loaded");
+    if (!tally || !dose_out) return fail(c, FDC_ERR_INVALID, "dose_from_tally: null pointer");
+    FDC_CUDA(c, cudaSetDevice(c->device));
+    fdc::FinalizeArgs f;
+    std::memset(&f, 0, sizeof f);
+    f.tally = (long long *)tally;  // read only: zero_after stays 0
+    f.n_tallies = 1;
+    f.nvox = c->nvox;
+    f.density = c->density.p;
+    f.scale = fdc::kMeVToJ / (fdc::kTallyUnitsPerMeV * c->dx * c->dy * c->dz * 1e-3);
+    f.dose = dose_out;
+    FDC_CUDA(c, fdc::launch_finalize(f, c->sm_count, (cudaStream_t)stream));
+    return FDC_OK;
+}
+
 int fdc_sync(fdc_ctx *c, void *stream, fdc_counters *counters) {
     if (!c) return FDC_ERR_INVALID;
     FDC_CUDA(c, cudaSetDevice(c->device));
@@ -720,67 +783,80 @@ int fdc_history_stats(fdc_ctx *c, const double *dose_sum, const double *history_
     return FDC_OK;
 }
 
-int fdc_autotune(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t seed, fdc_schedule *best) {
+int fdc_autotune(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t seed,
+                 const fdc_run_opts *opts_in, fdc_schedule *best) {
     if (!c) return FDC_ERR_INVALID;
     if (!c->db_loaded || !c->ph_loaded) return fail(c, FDC_ERR_NOT_LOADED, "database and phantom must be loaded");
     FDC_CUDA(c, cudaSetDevice(c->device));
     FDC_CUDA(c, c->scratch_dose.ensure(c->nvox));
-    cudaStream_t st;
-    FDC_CUDA(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    const int warps_opts[] = {2, 4, 8};
-    const int chunk_opts[] = {1, 4};
-    const int agg_opts[] = {1, 2};
-    fdc_schedule best_s = {0, 0, 0, 0};
-    float best_ms = std::numeric_limits<float>::max();
-    int rc = FDC_OK;
-    for (int w : warps_opts) {
-        const int maxc = fdc::replay_max_ctas_per_sm(w, 0, 1, 1);
-        const int cta_opts[] = {maxc, std::max(1, maxc / 2)};
-        for (int ci = 0; ci < 2 && !rc; ++ci) {
-            if (ci == 1 && cta_opts[1] == cta_opts[0]) continue;
-            for (int ch : chunk_opts) {
-                for (int ag : agg_opts) {
-                    fdc_run_opts o;
-                    std::memset(&o, 0, sizeof o);
-                    o.schedule.ctas_per_sm = cta_opts[ci];
-                    o.schedule.warps_per_cta = w;
-                    o.schedule.chunk = ch;
-                    o.schedule.aggregate = ag;
-                    fdc_outputs out;
-                    std::memset(&out, 0, sizeof out);
-                    out.dose = c->scratch_dose.p;
-                    float ms_min = std::numeric_limits<float>::max();
-                    for (int rep = 0; rep < 3 && !rc; ++rep) {
-                        cudaEventRecord(e0, st);
-                        rc = fdc_run_ex(c, beam, n_histories, seed, &o, &out, st);
-                        cudaEventRecord(e1, st);
-                        if (rc) break;
-                        if (cudaEventSynchronize(e1) != cudaSuccess) {
-                            rc = fail(c, FDC_ERR_CUDA, "autotune: event sync failed");
-                            break;
-                        }
-                        float ms = 0;
-                        cudaEventElapsedTime(&ms, e0, e1);
-                        if (rep > 0) ms_min = std::min(ms_min, ms);
-                    }
-                    if (rc) break;
-                    if (ms_min < best_ms) {
-                        best_ms = ms_min;
-                        best_s = o.schedule;
-                    }
-                }
-            }
+    fdc_run_opts base;
+    std::memset(&base, 0, sizeof base);
+    if (opts_in) base = *opts_in;
+    base.n_batches = 0;
+    std::memset(&base.schedule, 0, sizeof base.schedule);
+    const fdc::ReplayVariant var = run_variant(c, base, false);
+    // candidates: the built-in default first, then warps x CTAs x chunk x
+    // aggregate, each CTA count bounded by the occupancy of the instantiation
+    // that candidate launches
+    std::vector<fdc_schedule> cand;
+    {
+        const bool was_valid = c->tuned_valid;
+        c->tuned_valid = false;
+        fdc_schedule d;
+        int rc0 = resolve_schedule(c, nullptr, var, &d);
+        c->tuned_valid = was_valid;
+        if (rc0) return rc0;
+        cand.push_back(d);
+    }
+    for (int w : {4, 8}) {
+        for (int ag : {2, 1}) {
+            fdc::ReplayVariant v = var;
+            v.aggregate = ag;
+            const int maxc = fdc::replay_max_ctas_per_sm(w, v);
+            std::vector<int> ctas = {maxc};
+            if (maxc > 1) ctas.push_back(maxc - 1);
+            if (maxc > 3) ctas.push_back(maxc / 2);
+            for (int ct : ctas)
+                for (int ch : {1, 2, 8}) cand.push_back(fdc_schedule{ct, w, ch, ag});
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaStreamSynchronize(st);
-    cudaStreamDestroy(st);
+    fdc_outputs out;
+    std::memset(&out, 0, sizeof out);
+    out.dose = c->scratch_dose.p;
+    const bool timing_before = c->timing;
+    int rc = fdc_set_timing(c, 1);
+    if (rc) return rc;
+    fdc_schedule best_s = cand[0];
+    double best_ms = std::numeric_limits<double>::max();
+    // one warm-up launch of the first candidate, then per candidate the best
+    // of three replay-kernel times (CUDA events around the launch)
+    for (size_t i = 0; i < cand.size() && !rc; ++i) {
+        fdc_run_opts o = base;
+        o.no_graph = 1;
+        o.schedule = cand[i];
+        double ms_min = std::numeric_limits<double>::max();
+        for (int rep = 0; rep < (i == 0 ? 4 : 3) && !rc; ++rep) {
+            rc = fdc_run_ex(c, beam, n_histories, seed, &o, &out, nullptr);
+            if (rc) break;
+            double rms = 0, fms = 0;
+            rc = fdc_last_kernel_ms(c, &rms, &fms);
+            if (rc) break;
+            if (i == 0 && rep == 0) continue;
+            ms_min = std::min(ms_min, rms);
+        }
+        if (!rc && ms_min < best_ms) {
+            best_ms = ms_min;
+            best_s = cand[i];
+        }
+    }
+    c->timing = timing_before;
+    c->timed = false;
+    if (rc) return rc;
+    rc = fdc_sync(c, nullptr, nullptr);
     if (rc) return rc;
     c->tuned = best_s;
+    c->tuned_variant = var;
+    c->tuned_valid = true;
     if (best) *best = best_s;
     return FDC_OK;
 }
@@ -852,8 +928,10 @@ int fdc_run_noalloc(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint
     if (n > bi.total) return fail(c, FDC_ERR_INVALID, "more histories than the beam holds");
     if (c->max_track_units > 0 && (double)n * (double)c->max_track_units > 9.0e18)
         return fail(c, FDC_ERR_OVERFLOW, "too many histories per launch for the int64 tally");
+    fdc_run_opts o0;
+    std::memset(&o0, 0, sizeof o0);
     fdc_schedule sched;
-    rc = resolve_schedule(c, nullptr, 0, 1, false, &sched);
+    rc = resolve_schedule(c, nullptr, run_variant(c, o0, false), &sched);
     if (rc) return rc;
     FDC_CUDA(c, cudaSetDevice(c->device));
     fdc::NoallocScratch sc;

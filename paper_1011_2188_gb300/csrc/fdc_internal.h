@@ -11,11 +11,14 @@ namespace fdc {
 
 // One step of a track, 16 bytes, loaded with a single 128-bit load:
 //   x: len (float bits, cm of water)   y: dE (float bits, MeV)
-//   z: esec (float bits, MeV)          w: theta as IEEE half (low 16 bits) |
-//                                         phi code in units of 2 pi / 65536 (high 16)
+//   z, w: the deflection at the end of the step as the vector
+//         theta * (cos phi, sin phi) (float bits; computed in FP64 from the
+//         database's theta and phi and rounded once to FP32)
 // Per-step side arrays: eres (float residual energy at step start, used by
-// the start-step search) and tail (int64: tally units of all later steps of
-// the track, used to book escaped energy exactly).
+// the start-step search), tail (int64: tally units of all later steps of the
+// track, used to book escaped energy exactly) and, only when the database
+// has local deposits, esec (float MeV) with a per-track flag that says
+// whether the track has any.
 static_assert(sizeof(uint4) == 16, "step record must be 16 bytes");
 
 constexpr double kTallyUnitsPerMeV = 268435456.0;  // 2^FDC_TALLY_SHIFT
@@ -33,6 +36,8 @@ static_assert(sizeof(DeviceCounters) == sizeof(fdc_counters), "counter layout");
 struct ReplayArgs {
     // database (device)
     const uint4 *rec;
+    const float *esec;             // null when no step has a local deposit
+    const unsigned char *trk_esec; // per track: 1 if any of its steps has esec > 0
     const float *eres;
     const long long *tail;
     const long long *step_begin;
@@ -92,7 +97,16 @@ cudaError_t launch_debug_philox(unsigned long long k0, unsigned long long k1,
                                 unsigned long long *out, cudaStream_t st);
 cudaError_t launch_debug_sample(const ReplayArgs &a, float *xyEpsi, long long *btk,
                                 cudaStream_t st);
-int replay_max_ctas_per_sm(int warps_per_cta, int fp64, int aggregate, int track_group);
+// What selects the replay kernel's instantiation (and so its register budget
+// and occupancy).
+struct ReplayVariant {
+    int fp64, aggregate, squares, track_group, esec;
+};
+ReplayVariant replay_variant(const ReplayArgs &a, const fdc_schedule &s, int fp64);
+int replay_max_ctas_per_sm(int warps_per_cta, const ReplayVariant &v);
+// Record packing at load: (len, dE, theta, phi) -> (len, dE, theta cos phi,
+// theta sin phi), in place, FP64 arithmetic rounded to FP32.
+cudaError_t launch_pack_deflections(uint4 *rec, long long n, cudaStream_t st);
 // Denoiser convolutions (layout in fdc_unet.h).
 struct Conv3dArgs {
     int batch, in_d, in_h, in_w, out_d, out_h, out_w, c_in, c_out, ksize, stride, pad, relu;

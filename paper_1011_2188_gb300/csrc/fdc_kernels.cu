@@ -17,7 +17,6 @@
 // blocking tally update (Sec. 2.3) becomes a single L2 reduction, optionally
 // combined across the lanes of a warp that hit the same voxel.
 
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,8 +37,6 @@ constexpr unsigned kFull = 0xffffffffu;
 #endif
 constexpr float kUnitsF = 268435456.0f;  // 2^28
 constexpr double kTwoPi = 6.283185307179586476925286766559;
-constexpr float kPhiQuantumF = 9.58737992428525e-05f;  // 2 pi / 65536
-constexpr double kPhiQuantumD = 9.587379924285257e-05;
 
 // ---------------------------------------------------------------- Philox
 // Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
@@ -200,8 +197,8 @@ __device__ __forceinline__ uint4 load_record(const uint4 *p, unsigned long long 
 
 __device__ __forceinline__ void sincos_(float a, float *s, float *c) { sincosf(a, s, c); }
 __device__ __forceinline__ void sincos_(double a, double *s, double *c) { sincos(a, s, c); }
-// FP32 square root of the angle-scaling factor: the hardware approximation
-// (relative error ~2^-22, far below the half-precision database angles).
+// FP32 square roots of the deflection arithmetic: the hardware approximation
+// (relative error ~2^-22, the order of FP32 rounding itself).
 __device__ __forceinline__ float sqrt_(float a) {
     float r;
     asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(a));
@@ -318,28 +315,29 @@ __device__ void raise_status(DeviceCounters *c, int code, unsigned long long h) 
 }
 
 // ---------------------------------------------------------------- task 2
-// sin and cos of a polar deflection.  Below 0.25 rad (almost every step) the
-// Taylor series to theta^9 / theta^10 (truncation < 1e-11); above, sincos.
+// Deflection factors of a step: with the record's vector q = theta_w (cos
+// phi, sin phi) and the angle-scaling factor f^2 = sum_i w_i k_theta_i^2, the
+// scaled polar angle is theta_m = f |q| and the new direction is
+//   sin(theta_m) (cos phi e1 + sin phi e2) + cos(theta_m) d
+//     = sfac * (q_x e1 + q_y e2) + cos(theta_m) d,  sfac = sin(theta_m) / |q|.
+// Below theta_m = 0.25 rad (almost every step) sfac = f sinc(theta_m) and
+// cos(theta_m) come from their Taylor series in theta_m^2 (to theta^8 /
+// theta^10, truncation < 1e-11), so neither |q| nor a trig call is needed;
+// above, sincos of theta_m.
 template <typename R>
-__device__ __forceinline__ void sincos_theta(R th, R *s, R *c) {
-    if (th < (R)0.25) {
-        const R t2 = th * th;
-        *s = th * ((R)1 - t2 * ((R)(1.0 / 6) - t2 * ((R)(1.0 / 120) - t2 * ((R)(1.0 / 5040) - t2 * (R)(1.0 / 362880)))));
+__device__ __forceinline__ void deflection_factors(R qx, R qy, R f2, R *sfac, R *c) {
+    const R q2 = qx * qx + qy * qy;
+    const R t2 = q2 * f2;  // theta_m^2
+    if (t2 < (R)0.0625) {
+        const R sinc = (R)1 - t2 * ((R)(1.0 / 6) - t2 * ((R)(1.0 / 120) - t2 * ((R)(1.0 / 5040) - t2 * (R)(1.0 / 362880))));
+        *sfac = sqrt_(f2) * sinc;
         *c = (R)1 - t2 * ((R)0.5 - t2 * ((R)(1.0 / 24) - t2 * ((R)(1.0 / 720) - t2 * (R)(1.0 / 40320))));
     } else {
-        sincos_(th, s, c);
+        const R q = sqrt_(q2);
+        R s;
+        sincos_(q * sqrt_(f2), &s, c);
+        *sfac = s / q;
     }
-}
-
-// sin and cos of an azimuth given as a 16-bit code of 2 pi / 65536: the code
-// is read as a signed value so the angle lies in [-pi, pi), where the
-// hardware approximation has an absolute error below 1e-6 (FP32 path).
-__device__ __forceinline__ void sincos_phi(unsigned code, float *s, float *c) {
-    const float a = (float)(short)(unsigned short)code * kPhiQuantumF;
-    __sincosf(a, s, c);
-}
-__device__ __forceinline__ void sincos_phi(unsigned code, double *s, double *c) {
-    sincos((double)(short)(unsigned short)code * kPhiQuantumD, s, c);
 }
 
 // Re-trace one history.  Positions are kept as the voxel index plus the
@@ -350,7 +348,9 @@ __device__ __forceinline__ void sincos_phi(unsigned code, double *s, double *c) 
 // FIXED: the voxel where a step starts scales the whole step (ablation of
 // Sec. 2.2's step scaling); a template parameter, so the default path carries
 // no per-segment test.
-template <typename R, bool AGG, bool SQ, bool FIXED>
+// ESEC: the database has local deposits (read per step from the esec side
+// array); a template parameter so that runs without any carry no extra state.
+template <typename R, bool AGG, bool SQ, bool FIXED, bool ESEC>
 __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start &st,
                                                unsigned long long h, unsigned long long &steps,
                                                unsigned long long &segs, long long &replayed,
@@ -362,9 +362,11 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
 #if FDC_RECORD_PREFETCH
     if (s_first + 8 < s_end) prefetch_l2(P.rec + ((s_first + 8) & ~7ll));
 #endif
+    // local deposit of the current step (side array, tracks that have any)
+    float esec = ESEC ? __ldg(P.esec + s_first) : 0.0f;
     // energy of the replayed steps, in tally units
-    const long long rep = units_of(__uint_as_float(rec.y) * kUnitsF) +
-                          units_of(__uint_as_float(rec.z) * kUnitsF) + __ldg(P.tail + s_first);
+    const long long rep = units_of(__uint_as_float(rec.y) * kUnitsF) + units_of(esec * kUnitsF) +
+                          __ldg(P.tail + s_first);
     replayed += rep;
     // entry on the upstream face; inside test and voxel in FP64 (the
     // per-proton state is FP32, the comparison is exact in FP64)
@@ -395,7 +397,7 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
         const float dE_f = __uint_as_float(rec.y);
         const R len = (R)__uint_as_float(rec.x), dE = (R)dE_f;
         const long long Qk = units_of(dE_f * kUnitsF);
-        const long long Qs = units_of(__uint_as_float(rec.z) * kUnitsF);
+        const long long Qs = ESEC ? units_of(esec * kUnitsF) : 0ll;
         const R inv_len = rcp_(len);
         const R dEu = dE * inv_len * US;  // tally units per cm of water-equivalent length
         ++steps;
@@ -473,43 +475,40 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
         fx = ((R)(ix0 - ix) + fx) + t * rx;
         fy = ((R)(iy0 - iy) + fy) + t * ry;
         fz = ((R)(iz0 - iz) + fz) + t * rz;
-        if (Qs) pend.add(v, Qs);
+        if (ESEC && Qs) pend.add(v, Qs);
         if (++s >= s_end) {
             pend.flush();
             return;
         }
-        const unsigned ang = rec.w;
+        const R qx = (R)__uint_as_float(rec.z), qy = (R)__uint_as_float(rec.w);
         rec = load_record(P.rec + s, pol);  // next record: issued before the deflection arithmetic
+        if (ESEC) esec = __ldg(P.esec + s);
 #if FDC_RECORD_PREFETCH
         if ((s & 7) == 0 && s + 8 < s_end) prefetch_l2(P.rec + s + 8);
 #endif
 
         // deflection at the end of the step, scaled by the crossed materials
-        const R theta = (R)__half2float(__ushort_as_half((unsigned short)(ang & 0xffffu))) *
-                        sqrt_(acc * inv_len);
-        R st_, ct_;
-        sincos_theta(theta, &st_, &ct_);
+        R sfac, ct_;
+        deflection_factors(qx, qy, acc * inv_len, &sfac, &ct_);
+        const R a = sfac * qx, b = sfac * qy;  // sin(theta_m) cos(phi), sin(theta_m) sin(phi)
         const R p2 = dx * dx + dy * dy;
         R nx_, ny_, nz_;
         if (p2 > (R)0) {
-            R sp_, cp_;
-            sincos_phi(ang >> 16, &sp_, &cp_);
             const R ip = rsqrt_(p2), p = p2 * ip;
-            const R a = st_ * cp_, b = st_ * sp_;
             // e1 = (dx dz, dy dz, -p^2)/p, e2 = (-dy, dx, 0)/p
             const R az = a * dz * ip;
             nx_ = az * dx - b * (dy * ip) + ct_ * dx;
             ny_ = az * dy + b * (dx * ip) + ct_ * dy;
             nz_ = -a * p + ct_ * dz;
         } else {
-            // along the beam axis: the frame is (x, y) turned by psi, which
-            // makes the replay a rigid rotation of the track
+            // along the beam axis: the frame is (x, sgn y) turned by sgn psi,
+            // which makes the replay a rigid rotation of the track:
+            // azimuth phi + sgn psi, expanded with the record's cos/sin phi
             const R sgn = dz > (R)0 ? (R)1 : (R)-1;
-            const R phi = (R)(ang >> 16) * (sizeof(R) == 4 ? (R)kPhiQuantumF : (R)kPhiQuantumD);
-            R sp_, cp_;
-            sincos_(phi + sgn * psi, &sp_, &cp_);
-            nx_ = st_ * cp_;
-            ny_ = sgn * st_ * sp_;
+            R sps, cps;
+            sincos_(psi, &sps, &cps);
+            nx_ = a * cps - sgn * b * sps;
+            ny_ = sgn * b * cps + a * sps;
             nz_ = sgn * ct_;
         }
         // the rotation keeps |d| = 1 up to rounding: in FP32 the norm random-walks
@@ -535,7 +534,7 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
 #define FDC_REPLAY_MIN_CTAS_SHARED 5
 #endif
 
-template <typename R, bool AGG, bool SQ, int MINB = FDC_REPLAY_MIN_CTAS>
+template <typename R, bool AGG, bool SQ, bool ESEC, int MINB = FDC_REPLAY_MIN_CTAS>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MINB : 2)
     replay_kernel(const ReplayArgs P) {
     const unsigned lane = threadIdx.x & 31u;
@@ -553,9 +552,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MINB : 2)
                 const unsigned long long h = P.h_begin + li;
                 const Start st = sample_start(P, h);
                 if (P.scaling_mode == 1)
-                    replay_history<R, AGG, SQ, true>(P, st, h, steps, segs, replayed, escaped);
+                    replay_history<R, AGG, SQ, true, ESEC>(P, st, h, steps, segs, replayed, escaped);
                 else
-                    replay_history<R, AGG, SQ, false>(P, st, h, steps, segs, replayed, escaped);
+                    replay_history<R, AGG, SQ, false, ESEC>(P, st, h, steps, segs, replayed, escaped);
                 ++hist;
             }
         }
@@ -707,6 +706,21 @@ __global__ void debug_sample_kernel(const ReplayArgs P, float *xyEpsi, long long
     }
 }
 
+// Database load: each record's (theta, phi) becomes the deflection vector
+// theta (cos phi, sin phi), computed in FP64 and rounded once to FP32.
+__global__ void pack_deflections_kernel(uint4 *rec, long long n) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint4 r = rec[i];
+        const double th = (double)__uint_as_float(r.z), ph = (double)__uint_as_float(r.w);
+        double sp, cp;
+        sincos(ph, &sp, &cp);
+        r.z = __float_as_uint((float)(th * cp));
+        r.w = __float_as_uint((float)(th * sp));
+        rec[i] = r;
+    }
+}
+
 // One thread: prefix sum of the spots' history counts (cum[0] = 0).
 __global__ void spot_prefix_kernel(const fdc_spot *spots, int n_spots, unsigned long long *cum) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -719,37 +733,46 @@ __global__ void spot_prefix_kernel(const fdc_spot *spots, int n_spots, unsigned 
     }
 }
 
-// 64-bit atomic adds to hashed addresses (every thread its own stream of
-// slots), the access pattern of the dose tally without the transport.
-__global__ void probe_atomics_kernel(unsigned long long *slots, unsigned long long n_slots,
+// 64-bit atomic adds of 1 to pseudo-random 8-byte slots (the access pattern
+// of the dose tally without the transport): update i goes to slot
+// mix(i) & mask, mask = n_slots - 1 with n_slots a power of two, so the
+// address costs a multiply, a shift and two logic operations; each thread
+// issues four independent updates per iteration (fire-and-forget reductions,
+// several in flight).
+__global__ void probe_atomics_kernel(unsigned long long *slots, unsigned long long mask,
                                      unsigned long long n_ops) {
     const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
     const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i = tid; i < n_ops; i += nth) {
-        unsigned long long x = i * 0x9E3779B97F4A7C15ull;
-        x ^= x >> 29;
-        atomicAdd(slots + (x % n_slots), 1ull);
+    for (unsigned long long i = 4 * tid; i < n_ops; i += 4 * nth) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (i + u < n_ops) {
+                unsigned long long x = (i + u) * 0x9E3779B97F4A7C15ull;
+                x ^= x >> 29;
+                atomicAdd(slots + (x & mask), 1ull);
+            }
+        }
     }
 }
 
-template <typename R, bool AGG, bool SQ, int MINB = FDC_REPLAY_MIN_CTAS>
-cudaError_t launch_replay_t(const ReplayArgs &a, int ctas, int threads, cudaStream_t st) {
-    replay_kernel<R, AGG, SQ, MINB><<<ctas, threads, 0, st>>>(a);
-    return cudaGetLastError();
-}
+using ReplayFn = void (*)(ReplayArgs);
 
 template <typename R, bool AGG, bool SQ, int MINB = FDC_REPLAY_MIN_CTAS>
-int max_ctas_t(int threads) {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, replay_kernel<R, AGG, SQ, MINB>, threads, 0) !=
-        cudaSuccess)
-        return 1;
-    return n > 0 ? n : 1;
+ReplayFn replay_fn_t(bool esec) {
+    return esec ? replay_kernel<R, AGG, SQ, true, MINB> : replay_kernel<R, AGG, SQ, false, MINB>;
 }
 
-// the FP32 plain-atomic kernel with the register budget of shared tracks
-bool shared_track_variant(int track_group, int fp64, int aggregate, bool squares) {
-    return track_group >= 32 && !fp64 && aggregate != 1 && !squares;
+// The one place that maps a run to its kernel instantiation; the launch and
+// the occupancy query (schedule limits, autotuner) both go through it.
+//   squares: per-visit sums and plain atomics;  aggregate == 1: warp-combined
+//   atomics;  FP32 with plain atomics and 32 or more histories per track: the
+//   48-register variant;  esec: the database has local deposits.
+ReplayFn replay_fn(const ReplayVariant &v) {
+    if (v.squares) return v.fp64 ? replay_fn_t<double, false, true>(v.esec) : replay_fn_t<float, false, true>(v.esec);
+    const bool agg = v.aggregate == 1;
+    if (v.fp64) return agg ? replay_fn_t<double, true, false>(v.esec) : replay_fn_t<double, false, false>(v.esec);
+    if (!agg && v.track_group >= 32) return replay_fn_t<float, false, false, FDC_REPLAY_MIN_CTAS_SHARED>(v.esec);
+    return agg ? replay_fn_t<float, true, false>(v.esec) : replay_fn_t<float, false, false>(v.esec);
 }
 
 }  // namespace
@@ -803,40 +826,52 @@ cudaError_t noalloc_scratch(int device, NoallocScratch *out) {
     return cudaSuccess;
 }
 
+cudaError_t launch_pack_deflections(uint4 *rec, long long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    pack_deflections_kernel<<<(int)blocks, 256, 0, st>>>(rec, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_spot_prefix(const fdc_spot *spots, int n_spots, unsigned long long *cum,
                                cudaStream_t st) {
     spot_prefix_kernel<<<1, 32, 0, st>>>(spots, n_spots, cum);
     return cudaGetLastError();
 }
 
-cudaError_t launch_replay(const ReplayArgs &a, const fdc_schedule &s, int fp64, int sm_count,
-                          cudaStream_t st) {
-    const int threads = 32 * s.warps_per_cta;
-    const int ctas = sm_count * s.ctas_per_sm;
-    if (a.sumsq)  // history-by-history squares: per-visit sums, plain atomics
-        return fp64 ? launch_replay_t<double, false, true>(a, ctas, threads, st)
-                    : launch_replay_t<float, false, true>(a, ctas, threads, st);
-    const bool agg = s.aggregate == 1;
-    if (fp64) return agg ? launch_replay_t<double, true, false>(a, ctas, threads, st)
-                         : launch_replay_t<double, false, false>(a, ctas, threads, st);
-    if (shared_track_variant(a.track_group, fp64, s.aggregate, false))
-        return launch_replay_t<float, false, false, FDC_REPLAY_MIN_CTAS_SHARED>(a, ctas, threads, st);
-    return agg ? launch_replay_t<float, true, false>(a, ctas, threads, st)
-               : launch_replay_t<float, false, false>(a, ctas, threads, st);
+ReplayVariant replay_variant(const ReplayArgs &a, const fdc_schedule &s, int fp64) {
+    ReplayVariant v;
+    v.fp64 = fp64 ? 1 : 0;
+    v.aggregate = s.aggregate;
+    v.squares = a.sumsq ? 1 : 0;
+    v.track_group = a.track_group;
+    v.esec = a.esec ? 1 : 0;
+    return v;
 }
 
-int replay_max_ctas_per_sm(int warps_per_cta, int fp64, int aggregate, int track_group) {
-    const int threads = 32 * warps_per_cta;
-    const bool agg = aggregate == 1;
-    if (fp64) return agg ? max_ctas_t<double, true, false>(threads) : max_ctas_t<double, false, false>(threads);
-    if (shared_track_variant(track_group, fp64, aggregate, false))
-        return max_ctas_t<float, false, false, FDC_REPLAY_MIN_CTAS_SHARED>(threads);
-    return agg ? max_ctas_t<float, true, false>(threads) : max_ctas_t<float, false, false>(threads);
+cudaError_t launch_replay(const ReplayArgs &a, const fdc_schedule &s, int fp64, int sm_count,
+                          cudaStream_t st) {
+    const ReplayFn fn = replay_fn(replay_variant(a, s, fp64));
+    ReplayArgs args = a;
+    void *params[] = {&args};
+    return cudaLaunchKernel((const void *)fn, dim3((unsigned)(sm_count * s.ctas_per_sm)),
+                            dim3((unsigned)(32 * s.warps_per_cta)), params, 0, st);
+}
+
+int replay_max_ctas_per_sm(int warps_per_cta, const ReplayVariant &v) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void *)replay_fn(v), 32 * warps_per_cta, 0) !=
+        cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
 }
 
 cudaError_t launch_probe_atomics(unsigned long long *slots, unsigned long long n_slots,
                                  unsigned long long n_ops, int sm_count, cudaStream_t st) {
-    probe_atomics_kernel<<<sm_count * 8, 256, 0, st>>>(slots, n_slots, n_ops);
+    unsigned long long p2 = 1;  // largest power of two <= n_slots
+    while (p2 <= n_slots / 2) p2 <<= 1;
+    probe_atomics_kernel<<<sm_count * 8, 256, 0, st>>>(slots, p2 - 1, n_ops);
     return cudaGetLastError();
 }
 

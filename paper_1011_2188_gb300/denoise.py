@@ -273,6 +273,22 @@ class UNet:
         for l, s in zip(self.layers(), states):
             l.load(s)
 
+    def save_npz(self, path):
+        """FP32 master weights and biases, layer by layer (w0, b0, w1, b1, ...)."""
+        arrs = {}
+        for i, st in enumerate(self.state()):
+            arrs[f"w{i}"] = st["w"]
+            arrs[f"b{i}"] = st["b"]
+        np.savez(path, **arrs)
+
+    def load_npz(self, path):
+        with np.load(path) as z:
+            states = [{"w": z[f"w{i}"], "b": z[f"b{i}"]} for i in range(len(self.layers()))]
+        for l, st in zip(self.layers(), states):
+            if st["w"].shape != tuple(l.w32.shape) or st["b"].shape != tuple(l.b32.shape):
+                raise ValueError(f"{path}: weight shapes do not match the network")
+        self.load(states)
+
 
 class Sample:
     """One case on the device: network input, its FP32 dose channel, and
@@ -460,12 +476,18 @@ def train(net, samples, epochs, lr=1e-3, lr_final=1e-4, log=None, seed=0, augmen
     return (hist, hist_out) if held_out else hist
 
 
-def evaluate(net, eng, cases, n_low, spacing, dose_frac=0.02, dta=0.2, threshold=0.1, target_sigma=0.02):
+def evaluate(net, eng, cases, n_low, spacing, dose_frac=0.02, dta=0.2, threshold=0.1, target_sigma=0.02,
+             host_timing=False):
     """Per held-out case: gamma pass rate (dose_frac / dta) against the
     high-history plain dose of the denoised low-history dose and of the raw
     low-history dose; device time of the denoised path (low-history run +
     network) and of the plain method run to ``target_sigma`` mean batch
-    uncertainty (eq. (1), voxels above half the maximum)."""
+    uncertainty (eq. (1), voxels above half the maximum).  With host_timing,
+    also the host wall time of both from the beam in host memory to the dose
+    in (pinned) host memory, copies included: the denoised path as a run,
+    the network and one dose download; the plain method as one
+    fdc_run_host call of the history count it needs for target_sigma."""
+    import time
     import torch
     from .measure import time_to_sigma
     rows = []
@@ -490,11 +512,34 @@ def evaluate(net, eng, cases, n_low, spacing, dose_frac=0.02, dta=0.2, threshold
         d2 = eng.run(case_beam(c.seed, n2), 0, 13 + c.seed)
         d2.mul_(n_low / n2)
         g_plain = gamma_pass_rate(c.high, d2, spacing, dose_frac, dta, threshold)
-        rows.append({"seed": c.seed, "gamma_denoised": g_den, "gamma_low": g_raw, "gamma_plain_2pct": g_plain,
-                     "seconds_denoised": t_den, "seconds_plain_2pct": plain["seconds"],
-                     "histories_plain_2pct": n2, "plain_reached": plain["reached"]})
+        row = {"seed": c.seed, "gamma_denoised": g_den, "gamma_low": g_raw, "gamma_plain_2pct": g_plain,
+               "seconds_denoised": t_den, "seconds_plain_2pct": plain["seconds"],
+               "histories_plain_2pct": n2, "plain_reached": plain["reached"]}
+        if host_timing:
+            host = torch.empty(shape, dtype=torch.float64).pin_memory()
+            host_np = np.empty(shape, np.float64)
+            walls = []
+            for rep in range(3):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                low = eng.run(c.beam_low, 0, 17 + c.seed + rep)
+                out = denoise(net, Sample(low, c.density))
+                host.copy_(out)
+                torch.cuda.synchronize()
+                walls.append(time.perf_counter() - t)
+            row["wall_seconds_denoised"] = min(walls[1:])
+            bp = case_beam(c.seed, n2)
+            walls = []
+            for rep in range(3):
+                t = time.perf_counter()
+                eng.run_host(bp, n2, 19 + c.seed + rep, host_np)
+                walls.append(time.perf_counter() - t)
+            row["wall_seconds_plain_2pct"] = min(walls[1:])
+        rows.append(row)
     keys = ["gamma_denoised", "gamma_low", "gamma_plain_2pct", "seconds_denoised", "seconds_plain_2pct",
             "histories_plain_2pct"]
+    if host_timing:
+        keys += ["wall_seconds_denoised", "wall_seconds_plain_2pct"]
     summary = {k: float(np.mean([r[k] for r in rows])) for k in keys}
     summary["min_gamma_denoised"] = float(min(r["gamma_denoised"] for r in rows))
     summary["cases_gamma_ge_98"] = int(sum(r["gamma_denoised"] >= 0.98 for r in rows))

@@ -33,9 +33,10 @@ SIGNATURES = {
     "fdc_run_ex": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, _p, _p, _p]),
     "fdc_run_host": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, _p, _p]),
     "fdc_sync": (C.c_int, [_p, _p, _p]),
+    "fdc_dose_from_tally": (C.c_int, [_p, _p, _p, _p]),
     "fdc_batch_stats": (C.c_int, [_p, _p, _p, C.c_int32, C.c_double, _p, _p, _p, _p]),
     "fdc_history_stats": (C.c_int, [_p, _p, _p, C.c_uint64, C.c_double, _p, _p, _p, _p]),
-    "fdc_autotune": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, _p]),
+    "fdc_autotune": (C.c_int, [_p, _p, C.c_uint64, C.c_uint64, _p, _p]),
     "fdc_set_timing": (C.c_int, [_p, C.c_int32]),
     "fdc_last_kernel_ms": (C.c_int, [_p, _p, _p]),
     "fdc_probe_atomics": (C.c_int, [_p, C.c_uint64, C.c_uint64, _p, _p]),
@@ -289,6 +290,16 @@ class Engine:
                                            C.c_void_p(dose_host.ctypes.data)), "run_host")
         return dose_host
 
+    def dose_from_tally(self, tally, dose=None, stream=None):
+        """Dose (Gy) of an int64 energy tally (CUDA tensor, e.g. the sum of the
+        tallies of several history ranges) into a float64 CUDA tensor."""
+        import torch
+        if dose is None:
+            dose = torch.empty(tally.shape, dtype=torch.float64, device=tally.device)
+        self._check(self._lib.fdc_dose_from_tally(self.h, _ptr(tally), _ptr(dose), _stream_handle(stream)),
+                    "dose_from_tally")
+        return dose
+
     def sync(self, stream=None):
         c = Counters()
         self._check(self._lib.fdc_sync(self.h, _stream_handle(stream), C.byref(c)), "sync")
@@ -329,12 +340,17 @@ class Engine:
                                                 _stream_handle(stream)), "history_stats")
         return mean, sigma, r.value
 
-    def autotune(self, spots, n_histories, seed=0):
+    def autotune(self, spots, n_histories, seed=0, history_offset=0, track_group=1, rotate=True,
+                 scaling_mode=0, fp64_geometry=False):
+        """fdc_autotune for runs with these options; returns the chosen
+        (ctas_per_sm, warps_per_cta, chunk, aggregate)."""
         k = _Keep()
         b = beam_struct(spots, k)
+        o = RunOpts(int(history_offset), int(track_group), 0 if rotate else 1, int(scaling_mode),
+                    1 if fp64_geometry else 0, 0, 0, Schedule(0, 0, 0, 0))
         s = Schedule()
-        self._check(self._lib.fdc_autotune(self.h, C.byref(b), int(n_histories), int(seed), C.byref(s)),
-                    "autotune")
+        self._check(self._lib.fdc_autotune(self.h, C.byref(b), int(n_histories), int(seed), C.byref(o),
+                                           C.byref(s)), "autotune")
         return (s.ctas_per_sm, s.warps_per_cta, s.chunk, s.aggregate)
 
     def debug_sample(self, spots, seed, h_begin, n, track_group=1, rotate=True, stream=None):

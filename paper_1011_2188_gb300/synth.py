@@ -23,10 +23,10 @@ thorax CT are not available, Sec. 2.1, 2.2, 2.5):
   ellipsoids (body outline, lungs, spine, ribs), 256x256x128 voxels of 2 mm.
 * ``pencil_beam`` / ``field_beam`` / ``spot_plan``: beam descriptions.
 
-Database storage convention (shared by every consumer of these arrays):
-polar angles are rounded to the nearest IEEE half-precision value and
-azimuths to a multiple of 2*pi/65536, so that the values are exactly
-representable in the engine's packed 16-byte step record.
+The deflection angles are emitted as the generator computes them (FP32
+theta in [0, pi], phi = atan2 in [-pi, pi]), on no storage grid: whatever
+packing a consumer uses is its own business, and the oracle reads the values
+as given.
 """
 from __future__ import annotations
 
@@ -42,10 +42,6 @@ BK_P = 1.77
 M_P = 938.272
 X_WATER = 36.08
 STEP_CM = 0.1
-
-PHI_CODES = 65536
-PHI_QUANTUM = 2.0 * math.pi / PHI_CODES
-_PHI_TABLE = (np.arange(PHI_CODES, dtype=np.float64) * PHI_QUANTUM).astype(np.float32)
 
 # Synthetic material table: (name, mass stopping-power ratio to water,
 # radiation-length ratio X_water/X_material (mass units)).  These are this
@@ -86,16 +82,6 @@ def highland_theta0(E, step):
     x = step / X_WATER
     corr = np.maximum(1.0 + 0.038 * np.log(np.maximum(x, 1e-300)), 0.0)
     return 13.6 / np.maximum(beta_cp, 1e-12) * np.sqrt(x) * corr
-
-
-def quantize_theta(theta):
-    t = np.clip(theta, 0.0, math.pi)
-    return t.astype(np.float16).astype(np.float32)
-
-
-def quantize_phi(phi):
-    code = np.rint(np.mod(phi, 2.0 * math.pi) / PHI_QUANTUM).astype(np.int64) % PHI_CODES
-    return (code.astype(np.float64) * PHI_QUANTUM).astype(np.float32)
 
 
 @dataclass
@@ -209,8 +195,8 @@ def water_database(energies, n_tracks, seed, step_cm=STEP_CM, scatter=True,
             pos = starts[idx] + fill[idx]
             arrays["dE"][pos] = de
             arrays["len"][pos] = ln
-            arrays["theta"][pos] = quantize_theta(theta)
-            arrays["phi"][pos] = quantize_phi(phi)
+            arrays["theta"][pos] = np.minimum(theta, math.pi)
+            arrays["phi"][pos] = phi
             arrays["esec"][pos] = esec
             fill[idx] += 1
         t0 += n_tracks
@@ -262,10 +248,8 @@ def _water_database_csda(energies, n_tracks, rng, step_cm, scatter, chunk=20000)
                 th0f = th0.astype(np.float32)[None, :]
                 tx = rng.standard_normal((c1 - c0, n), dtype=np.float32) * th0f
                 ty = rng.standard_normal((c1 - c0, n), dtype=np.float32) * th0f
-                th = np.minimum(np.hypot(tx, ty), np.float32(math.pi))
-                arrays["theta"][sub] = th.astype(np.float16).astype(np.float32).reshape(-1)
-                code = np.rint(np.arctan2(ty, tx) * np.float32(1.0 / PHI_QUANTUM)).astype(np.int32) & (PHI_CODES - 1)
-                arrays["phi"][sub] = _PHI_TABLE[code].reshape(-1)
+                arrays["theta"][sub] = np.minimum(np.hypot(tx, ty), np.float32(math.pi)).reshape(-1)
+                arrays["phi"][sub] = np.arctan2(ty, tx).reshape(-1)
             else:
                 arrays["theta"][sub] = 0.0
                 arrays["phi"][sub] = 0.0

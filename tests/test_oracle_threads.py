@@ -23,3 +23,16 @@ def test_parallel_ranges_add_up_to_one_run():
     assert sum(p.n_segments for p in parts) == whole.n_segments
     np.testing.assert_allclose(sum(p.edep for p in parts), whole.edep, rtol=1e-12, atol=1e-9)
     assert abs(sum(p.escaped for p in parts) - whole.escaped) <= 1e-9 * max(1.0, whole.escaped)
+
+
+def test_run_parallel_equals_one_run():
+    db = synth.water_database([150.0], 200, seed=1, nuclear=True)
+    ph = synth.slab_phantom()
+    beam = synth.pencil_beam(3001, energy=150.0, sigma_cm=0.3)
+    whole = oracle.run(db, ph, beam, seed=5, h_begin=7, h_end=3001, track_group=32)
+    par = oracle.run_parallel(db, ph, beam, seed=5, h_begin=7, h_end=3001, threads=5, track_group=32)
+    assert par.n_histories == whole.n_histories == 2994
+    assert par.n_steps == whole.n_steps and par.n_segments == whole.n_segments
+    np.testing.assert_allclose(par.edep, whole.edep, rtol=1e-12, atol=1e-9)
+    assert abs(par.replayed - whole.replayed) <= 1e-9 * whole.replayed
+    assert abs(par.escaped - whole.escaped) <= 1e-9 * max(1.0, whole.escaped)

@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from paper_1011_2188_gb300 import synth
 
@@ -36,16 +37,22 @@ def test_highland_width():
     th0 = 13.6 / bcp * math.sqrt(x) * (1 + 0.038 * math.log(x))
     assert abs(np.mean(first ** 2) / (2 * th0 ** 2) - 1) < 0.01
     phi = db.phi[db.step_begin[:-1]]
-    assert phi.min() >= 0 and phi.max() < 2 * math.pi
+    assert phi.min() >= -math.pi and phi.max() <= math.pi
     assert abs(np.mean(np.cos(phi))) < 0.01
 
 
-def test_storage_quantisation_is_exact_in_the_record():
-    db = synth.water_database([100.0], 50, seed=2)
-    assert np.array_equal(db.theta.astype(np.float16).astype(np.float32), db.theta)
-    code = np.rint(db.phi.astype(np.float64) / synth.PHI_QUANTUM)
-    assert np.all(np.abs(db.phi.astype(np.float64) - code * synth.PHI_QUANTUM) < 1e-6)
-    assert code.max() < 65536
+@pytest.mark.parametrize("kw", [{}, {"straggling": True, "nuclear": True}])
+def test_angles_are_not_rounded_to_a_storage_grid(kw):
+    """The generator emits FP32 angles as computed: almost none sits on the
+    IEEE-half grid or on a multiple of 2 pi / 65536 (a record format that
+    stored them on such grids would have to round them)."""
+    db = synth.water_database([100.0, 150.0], 200, seed=2, **kw)
+    th = db.theta[db.theta > 0]
+    on_half = th.astype(np.float16).astype(np.float32) == th
+    assert on_half.mean() < 0.01
+    code = db.phi.astype(np.float64) / (2 * math.pi / 65536)
+    assert np.mean(np.abs(code - np.rint(code)) < 1e-3) < 0.01
+    assert db.theta.dtype == np.float32 and db.phi.dtype == np.float32
 
 
 def test_phantoms_and_plan():
