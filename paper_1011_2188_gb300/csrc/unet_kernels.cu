@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "fdc_internal.h"
@@ -645,6 +646,234 @@ __global__ void __launch_bounds__(128) conv3_kws_kernel(const Conv3dArgs g, cons
     }
 }
 
+// d-walking form of the kw-stacked convolution (input channels Cs <= 32,
+// NT = 16 or 32 output channels per CTA): a CTA owns a contiguous range of
+// output planes of one 8 (h) x 14 (w) column of tiles -- the flattened
+// (tile, d) index space is split evenly over the CTAs, a range restarting at
+// most once or twice at a tile boundary -- and walks it along d, so that each
+// input plane of the column is staged once instead of three times.  Input
+// planes (10 h x 16 w x Cs, layout [slice][h][w-group 2][k-chunk 2][8 w][8 ch],
+// 5120 bytes per slice) live in a ring of R = PF + 4 slots and are fetched
+// PF + 2 planes ahead of the output plane with cp.async (zero fill outside the
+// grid); the weights of all input slices stay resident.  Output plane i of a
+// range is computed by 9 * Cs / 16 MMAs (M = 128, N = 3 NT, K = 16) into one of
+// two TMEM accumulators, and its epilogue (as in conv3_kws_kernel) runs while
+// the MMAs of plane i + 1 execute.  Ring reuse: plane j overwrites plane
+// j - R, last read by the MMAs of output plane j - R, whose completion was
+// awaited two iterations before.  Every accumulator wait is bounded (on
+// timeout: FDC_ERR_TIMEOUT, no further output, TMEM freed).
+constexpr int kDwPlaneSliceBytes = 10 * 512;  // [h 10][w-group 2][k-chunk 2][8 w][8 ch]
+#ifndef FDC_CONV_DWALK
+#define FDC_CONV_DWALK 1
+#endif
+
+template <int NT>
+__global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
+                                                          const __nv_bfloat16 *wt, const float *bias,
+                                                          __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn,
+                                                          int relu, int ca, int up_a, const __nv_bfloat16 *src_b,
+                                                          int pf) {
+    constexpr int N3 = 3 * NT;
+    constexpr unsigned kAccCols = N3 <= 64 ? 64 : 128;  // columns per accumulator buffer
+    constexpr unsigned kCols = 2 * kAccCols;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ unsigned tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int D = g.in_d, H = g.in_h, W = g.in_w;
+    const int S = Cs / 16;
+    const int R = pf + 4;
+    const int plane_bytes = S * kDwPlaneSliceBytes;
+    const int wbytes = S * 9 * 2 * N3 * 16;
+    unsigned char *sW = smem;                // [slice][kd kh][k-chunk][kw NT + co][8]
+    unsigned char *sP = smem + wbytes;       // R plane slots
+    const int tiles_w = (W + 13) / 14, tiles_h = (H + 7) / 8;
+    const long long n_cols = (long long)g.batch * tiles_h * tiles_w;
+    const long long total = n_cols * D;      // (tile column, d) output planes
+    const long long q_begin = total * blockIdx.x / gridDim.x, q_end = total * (blockIdx.x + 1) / gridDim.x;
+    const int n0 = blockIdx.y * NT;
+    const int cb = Cs - ca;
+    const int Da = up_a ? D / 2 : D, Ha = up_a ? H / 2 : H, Wa = up_a ? W / 2 : W;
+    const unsigned mb0 = smem_u32(&mbar[0]), mb1 = smem_u32(&mbar[1]);
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb1));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    // resident weights of every input slice (through L1: all CTAs read the same)
+    {
+        constexpr int kChunks = 9 * 2 * N3;  // per slice
+        for (int i = tid; i < S * kChunks; i += 128) {
+            const int sl = i / kChunks, r = i % kChunks;
+            const int n = r % N3, q = r / N3, kc = q & 1, kdh = q >> 1;
+            const int co = n0 + (n % NT), kw = n / NT;
+            const bool in = co < Nn;
+            const __nv_bfloat16 *p = in ? wt + (size_t)((co * 27 + kdh * 3 + kw) * Cs + sl * 16 + kc * 8) : wt;
+            cp_async16_ca(sW + i * 16, p, in);
+        }
+        cp_async_commit();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = tmem_slot;
+
+    // this thread's halo column and k-chunk; it walks rows r = slice * 10 + h
+    const int kc = tid & 1, hw = (tid >> 1) & 15, r0 = tid >> 5;
+    const unsigned hdst = (unsigned)((((hw >> 3) * 2 + kc) * 128) + (hw & 7) * 16);
+    bool ok = true;
+    unsigned it_all = 0;  // iterations over all ranges: accumulator buffer and barrier phase
+    for (long long q = q_begin; q < q_end && ok;) {
+        const long long col = q / D;
+        const int d_begin = (int)(q % D);
+        const int nd = (int)(q_end - q < (long long)(D - d_begin) ? q_end - q : (long long)(D - d_begin));
+        q += nd;
+        long long t = col;
+        const int w0 = (int)(t % tiles_w) * 14; t /= tiles_w;
+        const int h0 = (int)(t % tiles_h) * 8;
+        const int b = (int)(t / tiles_h);
+        const int w = w0 - 1 + hw;
+        const bool w_in = w >= 0 && w < W;
+        // stage input plane j (= d_begin - 1 + j) into slot j % R, one commit group
+        auto load_plane = [&](int j) {
+            if (j <= nd + 1) {
+                const int d = d_begin - 1 + j;
+                unsigned char *dst = sP + (j % R) * plane_bytes + hdst;
+                const bool d_in = w_in && d >= 0 && d < D;
+                for (int r = r0; r < S * 10; r += 4) {
+                    const int sl = r / 10, hh = r - 10 * sl;
+                    const int h = h0 - 1 + hh, c0 = sl * 16;
+                    const bool in = d_in && h >= 0 && h < H;
+                    const __nv_bfloat16 *p = src;
+                    if (in) {
+                        if (c0 >= ca)
+                            p = src_b + ((((long long)b * D + d) * H + h) * W + w) * cb + (c0 - ca) + kc * 8;
+                        else if (up_a)
+                            p = src + ((((long long)b * Da + (d >> 1)) * Ha + (h >> 1)) * Wa + (w >> 1)) * ca + c0 +
+                                kc * 8;
+                        else
+                            p = src + ((((long long)b * D + d) * H + h) * W + w) * ca + c0 + kc * 8;
+                    }
+                    cp_async16(dst + r * 512, p, in);
+                }
+            }
+            cp_async_commit();
+        };
+        for (int j = 0; j < pf + 2; ++j) load_plane(j);
+        // epilogue of output plane i of this range (accumulator buffer ab, barrier phase ph)
+        auto epilogue = [&](int i, unsigned ab, unsigned ph) -> bool {
+            // warp-uniform outcome (the shuffles below need every lane)
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(ab ? mb1 : mb0, ph))) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const int m = warp * 32 + lane;
+            const int ho = h0 + (m >> 4), wl = m & 15, wo = w0 + wl;
+            const bool out_in = wl < 14 && ho < H && wo < W;
+            const long long v = (((long long)b * D + d_begin + i) * H + ho) * W + wo;
+            const unsigned base = tmem + ((unsigned)(warp * 32) << 16) + ab * kAccCols;
+#pragma unroll
+            for (int c = 0; c < NT; c += 16) {
+                float a0[16], a1[16], a2[16];
+                tmem_ld16(base + (unsigned)c, a0);
+                tmem_ld16(base + (unsigned)(NT + c), a1);
+                tmem_ld16(base + (unsigned)(2 * NT + c), a2);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    a0[j] += __shfl_down_sync(0xffffffffu, a1[j], 1) + __shfl_down_sync(0xffffffffu, a2[j], 2);
+                const int n = n0 + c;
+                if (!out_in || n >= Nn) continue;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float x = a0[j];
+                    if (bias) x += __ldg(bias + n + j);
+                    if (relu) x = fmaxf(x, 0.f);
+                    a0[j] = x;
+                }
+                if (out_f32) {
+                    float4 *dst = (float4 *)(out_f32 + v * Nn + n);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        dst[j] = make_float4(a0[4 * j], a0[4 * j + 1], a0[4 * j + 2], a0[4 * j + 3]);
+                }
+                if (out_bf16) {
+                    uint4 qv[2];
+                    unsigned *qq = (unsigned *)qv;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        __nv_bfloat162 p2 = __floats2bfloat162_rn(a0[2 * j], a0[2 * j + 1]);
+                        qq[j] = *(unsigned *)&p2;
+                    }
+                    uint4 *dst = (uint4 *)(out_bf16 + v * Nn + n);
+                    dst[0] = qv[0];
+                    dst[1] = qv[1];
+                }
+            }
+            // every warp has read this accumulator before MMAs overwrite it
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            return true;
+        };
+        for (int i = 0; i < nd; ++i) {
+            load_plane(i + pf + 2);
+            // planes i, i + 1, i + 2 of the range are in shared memory (the
+            // pf most recent groups may still be in flight)
+            switch (pf) {  // all but the pf most recent plane groups have landed
+                case 1: cp_async_wait<1>(); break;
+                case 2: cp_async_wait<2>(); break;
+                case 3: cp_async_wait<3>(); break;
+                case 4: cp_async_wait<4>(); break;
+                case 5: cp_async_wait<5>(); break;
+                case 6: cp_async_wait<6>(); break;
+                default: cp_async_wait<0>(); break;
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            // also agrees on the outcome of the previous epilogue's bounded wait
+            if (!__syncthreads_and(ok)) {
+                ok = false;
+                break;
+            }
+            const unsigned ab = it_all & 1u;
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const unsigned wa = smem_u32(sW);
+                constexpr unsigned idesc = umma_idesc(128, N3);
+#pragma unroll 1
+                for (int sl = 0; sl < S; ++sl) {
+#pragma unroll 1
+                    for (int kdh = 0; kdh < 9; ++kdh) {
+                        const int kd = kdh / 3, kh = kdh % 3;
+                        const unsigned pa = smem_u32(sP + ((i + kd) % R) * plane_bytes) + sl * kDwPlaneSliceBytes + kh * 512;
+                        const unsigned long long ad = umma_desc(pa, 128, 256);
+                        const unsigned long long bd = umma_desc(wa + (sl * 9 + kdh) * 2 * N3 * 16, N3 * 16, 128);
+                        umma_bf16(tmem + ab * kAccCols, ad, bd, idesc, (sl | kdh) != 0);
+                    }
+                }
+                umma_commit(ab ? mb1 : mb0);
+            }
+            if (i > 0) ok = epilogue(i - 1, ab ^ 1u, ((it_all - 1) >> 1) & 1u);
+            ++it_all;
+        }
+        // the range's last plane
+        if (__syncthreads_and(ok)) ok = epilogue(nd - 1, (it_all - 1) & 1u, ((it_all - 1) >> 1) & 1u);
+        else ok = false;
+        ok = __syncthreads_and(ok);
+        cp_async_wait<0>();
+        __syncthreads();
+    }
+    if (!ok && tid == 0) atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
+    cp_async_wait<0>();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
+    }
+}
+
 // Weight gradient of a 3^3 stride-1 padding-1 convolution for one 16-wide
 // output-channel tile and one 16-wide input-channel slice:
 //   dW[co][tap][ci] += sum over voxels v of dy[v][co] * x[v + tap - 1][ci].
@@ -1147,6 +1376,9 @@ cudaError_t prepare_kernel_smem(OccCache &c, K kernel, int smem) {
     int maxopt = 0;
     e = cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxopt - 1024);
+    // as much of the unified L1 / shared memory as shared memory as residency needs
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     if (dev < 16)
         for (int i = 0; i < 16; ++i)
@@ -1165,6 +1397,53 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
     auto w = (const __nv_bfloat16 *)wt;
     auto ob = (__nv_bfloat16 *)out_bf16;
     auto sb = (const __nv_bfloat16 *)src_b;
+    // input channels <= 32 (the 128^3 and 64^3 levels of the network): the
+    // d-walking kernel, CTAs spread over the flattened (tile, d) planes
+    if (FDC_CONV_DWALK && Cs <= 32 && Nn % 16 == 0) {
+        int dev = 0, sms = 0, smem_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e != cudaSuccess) return e;
+        const int S = Cs / 16;
+        const int NT = Nn % 32 == 0 ? 32 : 16;
+        const int wbytes = S * 9 * 2 * (3 * NT) * 16;
+        const int plane = S * kDwPlaneSliceBytes;
+        // CTAs per SM are bounded by TMEM (two accumulators of 64 or 128 of the
+        // 512 columns): 4 with 16-channel tiles, 2 with 32.  The plane ring
+        // takes what shared memory leaves at that residency: 5 to 10 slots
+        // (prefetch 1 to 6 planes ahead).
+        const int per_sm_tmem = NT == 32 ? 2 : 4;
+        const int budget = smem_sm / per_sm_tmem - 2048;
+        const int R = std::max(5, std::min(10, (budget - wbytes) / plane));
+        const int pf = R - 4;
+        const int smem = wbytes + R * plane;
+        cudaFuncAttributes fa;
+        int per_sm = 0;
+        if (NT == 32) {
+            static OccCache cache;
+            e = prepare_kernel_smem(cache, conv3_dwalk_kernel<32>, smem);
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv3_dwalk_kernel<32>);
+        } else {
+            static OccCache cache;
+            e = prepare_kernel_smem(cache, conv3_dwalk_kernel<16>, smem);
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv3_dwalk_kernel<16>);
+        }
+        if (e != cudaSuccess) return e;
+        const int by_smem = smem_sm / (smem + (int)fa.sharedSizeBytes + 1024);
+        const int by_regs = 65536 / (128 * std::max(fa.numRegs, 1));
+        per_sm = std::max(1, std::min(per_sm_tmem, std::min(by_smem, by_regs)));
+        const int ntiles = (Nn + NT - 1) / NT;
+        const long long planes = (long long)g.batch * ((g.in_h + 7) / 8) * ((g.in_w + 13) / 14) * g.in_d;
+        long long gx = std::max(1ll, (long long)sms * per_sm / ntiles);
+        if (gx > planes) gx = planes;
+        const dim3 grid((unsigned)gx, (unsigned)ntiles);
+        if (NT == 32)
+            conv3_dwalk_kernel<32><<<grid, 128, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb, pf);
+        else
+            conv3_dwalk_kernel<16><<<grid, 128, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb, pf);
+        return cudaGetLastError();
+    }
     // 64-channel tiles (27 MMAs of N = 64) when they give at least one CTA per SM
     // (measured: 32^3 x 64 channels 46 vs 55 us); otherwise the kw-stacked kernel
     // with 32-channel tiles spreads small grids wider (16^3 x 128: 43 vs 64 us)

@@ -48,6 +48,11 @@ CASES = [
     ((2, 3, 9, 17, 48), 32, 3, 1, 1),
     ((1, 3, 37, 12, 16), 32, 3, 1, 1),  # three 16-row tiles in h, the last ragged
     ((1, 10, 31, 64, 16), 64, 3, 1, 1),  # enough blocks for the 64-channel tile kernel, ragged h
+    # d-walking kernel (input channels <= 32): batch 2 with ragged h and w,
+    # two input slices with 32-channel output tiles, a single plane
+    ((2, 9, 17, 29, 32), 16, 3, 1, 1),
+    ((1, 12, 9, 30, 32), 32, 3, 1, 1),
+    ((1, 1, 8, 14, 16), 16, 3, 1, 1),
 ]
 
 
