@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--schedule", default="", help="ctas_per_sm,warps_per_cta,chunk,aggregate")
     ap.add_argument("--quick", action="store_true", help="device timing only (sweeps)")
+    ap.add_argument("--profile-tracks", type=int, default=10_000,
+                    help="database tracks per energy of --study profile_case")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the spot-plan, precision and denoiser measurements of the default line")
     ap.add_argument("--train-cases", type=int, default=200)
@@ -517,15 +519,16 @@ def precision_study(args):
 
 def profile_case(args):
     """Small cases for ncu captures (the full-size workload holds ~13 GB on
-    the device): the thorax phantom with a 24 x 10^4-track database
-    (4.6 x 10^7 step records, 1.3 GB), 10^6 histories over the 10 x 10 cm
-    field with 32 histories per track, replayed twice (capture the second
-    launch); then one launch of the atomic probe (2^28 updates over 64 MB).
-    Prints the replay's counters so per-step figures can be formed."""
+    the device): the thorax phantom with a 24 x --profile-tracks database
+    (default 10^4: 4.6 x 10^7 step records, 1.3 GB), --histories (default
+    10^6) over the 10 x 10 cm field with 32 histories per track, replayed
+    twice (capture the second launch); then one launch of the atomic probe
+    (2^28 updates over 64 MB).  Prints the replay's counters so per-step
+    figures can be formed."""
     import torch
     from paper_1011_2188_gb300 import fdc, synth
     n = args.histories or 1_000_000
-    db = synth.water_database(synth.database_energies(24), 10_000, seed=2)
+    db = synth.water_database(synth.database_energies(24), args.profile_tracks, seed=2)
     ph = synth.thorax_phantom(seed=7)
     beam = synth.field_beam(n, energy=150.0, width=10.0, height=10.0, sigma_e_rel=0.01)
     eng = fdc.Engine(0)
@@ -538,7 +541,8 @@ def profile_case(args):
     slots = torch.zeros(1 << 23, dtype=torch.int64, device="cuda:0")
     ms = fdc.probe_atomics(slots, 1 << 28)
     eng.close()
-    print(json.dumps({"study": "profile_case", "histories": n, "track_group": args.track_group,
+    print(json.dumps({"study": "profile_case", "histories": n, "tracks_per_energy": args.profile_tracks,
+                      "track_group": args.track_group,
                       "steps": cnt["steps"], "segments": cnt["segments"], "probe_ops": 1 << 28,
                       "probe_ms": ms, "kernel_source_sha16": kernel_source_hash()}), flush=True)
 

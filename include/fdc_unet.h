@@ -48,10 +48,15 @@ int fdc_conv3d_forward(const fdc_conv3d *g, const void *x, const void *w, const 
 int fdc_conv3d_forward_fused(const fdc_conv3d *g, const void *xa, int32_t ca, int32_t upsample_a, const void *xb,
                              const void *w, const float *bias, void *y_bf16, float *y_f32, void *stream);
 /* dx[b][i][ci] = sum over (tap, co) with i + pad - tap = stride * o of dy[b][o][co] w[co][tap][ci]
- * (the gradient of the forward map with respect to x, without the ReLU).
+ * (the gradient of the forward map with respect to x, without this layer's ReLU).
  * dy bf16 [batch][out...][c_out]; w_t the data-gradient weights that
- * fdc_conv3d_transpose_weights produced for this convolution; dx bf16. */
-int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_t, void *dx, void *stream);
+ * fdc_conv3d_transpose_weights produced for this convolution; dx bf16.
+ * relu_mask (may be NULL): this convolution's forward input x (bf16, the
+ * layout of dx); where it is not positive dx is written as zero -- the
+ * derivative of the ReLU that produced x, applied in the same pass (dx is
+ * then the gradient with respect to the previous layer's pre-activation). */
+int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_t, const void *relu_mask, void *dx,
+                             void *stream);
 /* dw[co][tap][ci] += sum_o dy[o][co] x[o * stride - pad + tap][ci] and, if db is not NULL,
  * db[co] += sum_o dy[o][co]; dw, db FP32 (accumulated: zero them first). */
 int fdc_conv3d_backward_weights(const fdc_conv3d *g, const void *x, const void *dy, float *dw, float *db,

@@ -110,6 +110,10 @@ cudaError_t launch_pack_deflections(uint4 *rec, long long n, cudaStream_t st);
 // Denoiser convolutions (layout in fdc_unet.h).
 struct Conv3dArgs {
     int batch, in_d, in_h, in_w, out_d, out_h, out_w, c_in, c_out, ksize, stride, pad, relu;
+    // data gradient only: null, or the layer's forward input (same layout as
+    // the output, BF16); output values where it is not positive become zero
+    // (the ReLU derivative of the layer that produced that input)
+    const void *mask;
 };
 cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const void *wt, const float *bias,
                         void *out_bf16, float *out_f32, cudaStream_t st);

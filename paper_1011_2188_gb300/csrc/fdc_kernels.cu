@@ -29,6 +29,24 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Measurement toggles of the step loop (compile-time):
+//   FDC_OPT_ZFIRST  the face-crossing update tests the z axis first;
+//   FDC_OPT_U32     a step's energy bookkeeping in 32-bit units (needs every
+//                   step below 2^32 tally units, i.e. 16 MeV);
+//   FDC_OPT_C32     per-history 32-bit step and segment counters;
+//   FDC_OPT_RECPTR  the step loop walks a record pointer with a 32-bit count.
+#ifndef FDC_OPT_ZFIRST
+#define FDC_OPT_ZFIRST 0
+#endif
+#ifndef FDC_OPT_U32
+#define FDC_OPT_U32 0
+#endif
+#ifndef FDC_OPT_C32
+#define FDC_OPT_C32 0
+#endif
+#ifndef FDC_OPT_RECPTR
+#define FDC_OPT_RECPTR 0
+#endif
 // 1: a lane sums consecutive deposits into one voxel before its atomic
 // (fewer atomics, more registers; measured slower on GB300 under the
 // 64-register cap, so off by default).
@@ -350,12 +368,31 @@ __device__ __forceinline__ void deflection_factors(R qx, R qy, R f2, R *sfac, R 
 // no per-segment test.
 // ESEC: the database has local deposits (read per step from the esec side
 // array); a template parameter so that runs without any carry no extra state.
+__device__ __forceinline__ unsigned seg_units_u32(float x) { return __float2uint_rn(x); }
+__device__ __forceinline__ unsigned seg_units_u32(double x) { return __double2uint_rn(x); }
+
+struct Counts32 {  // per-history counters added to the lane's totals on exit
+    unsigned long long &steps, &segs;
+    unsigned st = 0, sg = 0;
+    __device__ __forceinline__ Counts32(unsigned long long &a, unsigned long long &b) : steps(a), segs(b) {}
+    __device__ __forceinline__ ~Counts32() {
+        steps += st;
+        segs += sg;
+    }
+};
+
 template <typename R, bool AGG, bool SQ, bool FIXED, bool ESEC>
 __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start &st,
-                                               unsigned long long h, unsigned long long &steps,
-                                               unsigned long long &segs, long long &replayed,
+                                               unsigned long long h, unsigned long long &steps_tot,
+                                               unsigned long long &segs_tot, long long &replayed,
                                                long long &escaped) {
     if (st.k0 >= st.n) return;
+#if FDC_OPT_C32
+    Counts32 cnt(steps_tot, segs_tot);
+    unsigned &steps = cnt.st, &segs = cnt.sg;
+#else
+    unsigned long long &steps = steps_tot, &segs = segs_tot;
+#endif
     const long long s_first = st.s0 + st.k0, s_end = st.s0 + st.n;
     const unsigned long long pol = evict_first_policy();
     uint4 rec = load_record(P.rec + s_first, pol);
@@ -393,7 +430,18 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
     float2 sk = __ldg(P.vox + v);
     PendingTally<AGG, SQ> pend(P, tbase);
 
+#if FDC_OPT_RECPTR
+    const uint4 *rp = P.rec + s_first;
+    int left = (int)(s_end - s_first);
+#define FDC_S_NOW (rp - P.rec)
+#else
+#define FDC_S_NOW s
+#endif
+#if FDC_OPT_RECPTR
+    for (;;) {
+#else
     for (long long s = s_first;;) {
+#endif
         const float dE_f = __uint_as_float(rec.y);
         const R len = (R)__uint_as_float(rec.x), dE = (R)dE_f;
         const long long Qk = units_of(dE_f * kUnitsF);
@@ -422,7 +470,12 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
         tmz = tmz > (R)0 ? tmz : (R)0;
 
         R rem = len, t = (R)0, acc = (R)0;
+#if FDC_OPT_U32
+        unsigned dep = 0;
+        const unsigned Qk32 = (unsigned)Qk;
+#else
         long long dep = 0;
+#endif
         constexpr bool fixed = FIXED;
         const R S_fix = (R)sk.x, k2_fix = (R)sk.y;
         int nseg = 0;
@@ -439,24 +492,44 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
             const R wexit = seg * S;
             ++segs;
             if (wexit >= rem) {  // the step ends in this voxel
+#if FDC_OPT_U32
+                const long long units = (long long)(Qk32 - dep);
+#else
                 const long long units = Qk - dep;
+#endif
                 pend.add(v, units);
                 acc += rem * k2;
                 t += rem * rcp_(S);
                 break;
             }
+#if FDC_OPT_U32
+            const unsigned u32 = seg_units_u32(wexit * dEu);
+            dep += u32;
+            pend.add(v, (long long)u32);
+#else
             const long long units = units_of(wexit * dEu);
             dep += units;
             pend.add(v, units);
+#endif
             acc += wexit * k2;
             rem -= wexit;
             t = tm;
             bool out;
+#if FDC_OPT_ZFIRST
+            if (a == 2) { iz += stz; v += stz * sz; out = (unsigned)iz >= (unsigned)P.nz; tmz += tdz; }
+            else if (a == 0) { ix += stx; v += stx; out = (unsigned)ix >= (unsigned)P.nx; tmx += tdx; }
+            else { iy += sty; v += sty * sy; out = (unsigned)iy >= (unsigned)P.ny; tmy += tdy; }
+#else
             if (a == 0) { ix += stx; v += stx; out = (unsigned)ix >= (unsigned)P.nx; tmx += tdx; }
             else if (a == 1) { iy += sty; v += sty * sy; out = (unsigned)iy >= (unsigned)P.ny; tmy += tdy; }
             else { iz += stz; v += stz * sz; out = (unsigned)iz >= (unsigned)P.nz; tmz += tdz; }
+#endif
             if (out) {  // left the grid: the rest of the history escapes
-                escaped += (Qk - dep) + Qs + __ldg(P.tail + s);
+#if FDC_OPT_U32
+                escaped += (long long)(Qk32 - dep) + Qs + __ldg(P.tail + FDC_S_NOW);
+#else
+                escaped += (Qk - dep) + Qs + __ldg(P.tail + FDC_S_NOW);
+#endif
                 gone = true;
                 break;
             }
@@ -476,15 +549,27 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
         fy = ((R)(iy0 - iy) + fy) + t * ry;
         fz = ((R)(iz0 - iz) + fz) + t * rz;
         if (ESEC && Qs) pend.add(v, Qs);
+#if FDC_OPT_RECPTR
+        if (--left == 0) {
+            pend.flush();
+            return;
+        }
+        ++rp;
+#else
         if (++s >= s_end) {
             pend.flush();
             return;
         }
+#endif
         const R qx = (R)__uint_as_float(rec.z), qy = (R)__uint_as_float(rec.w);
+#if FDC_OPT_RECPTR
+        rec = load_record(rp, pol);  // next record: issued before the deflection arithmetic
+#else
         rec = load_record(P.rec + s, pol);  // next record: issued before the deflection arithmetic
-        if (ESEC) esec = __ldg(P.esec + s);
+#endif
+        if (ESEC) esec = __ldg(P.esec + FDC_S_NOW);
 #if FDC_RECORD_PREFETCH
-        if ((s & 7) == 0 && s + 8 < s_end) prefetch_l2(P.rec + s + 8);
+        if ((FDC_S_NOW & 7) == 0 && FDC_S_NOW + 8 < s_end) prefetch_l2(P.rec + FDC_S_NOW + 8);
 #endif
 
         // deflection at the end of the step, scaled by the crossed materials
@@ -520,6 +605,8 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
         dz = nz_;
     }
 }
+
+#undef FDC_S_NOW
 
 // Minimum resident CTAs of 256 threads per SM requested from the register
 // allocator: 4 caps the kernel at 64 registers (no spills).  With 32 or more

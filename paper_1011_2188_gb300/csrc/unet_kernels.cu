@@ -191,6 +191,11 @@ __global__ void __launch_bounds__(128) conv_igemm_kernel(const Conv3dArgs g, con
                     v0 = fmaxf(v0, 0.f);
                     v1 = fmaxf(v1, 0.f);
                 }
+                if (g.mask) {  // ReLU derivative of the layer whose output is this gradient's tensor
+                    const unsigned short *m = (const unsigned short *)g.mask + r * Nn + n;
+                    if ((short)m[0] <= 0) v0 = 0.f;
+                    if (n + 1 < Nn && (short)m[1] <= 0) v1 = 0.f;
+                }
                 if (out_f32) {
                     out_f32[r * Nn + n] = v0;
                     if (n + 1 < Nn) out_f32[r * Nn + n + 1] = v1;
@@ -298,6 +303,18 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float v[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ReLU derivative of the previous layer, applied to a data-gradient output
+// row: channels [n, n + 16) of voxel v become zero where that layer's output
+// (the convolution's input, `mask`, Nn channels per voxel) is not positive.
+__device__ __forceinline__ void apply_relu_mask16(const void *mask, long long v, int Nn, int n, float a[16]) {
+    const uint4 *m = (const uint4 *)((const __nv_bfloat16 *)mask + v * Nn + n);
+    const uint4 q[2] = {__ldg(m), __ldg(m + 1)};
+    const unsigned short *h = (const unsigned short *)q;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        if ((short)h[j] <= 0) a[j] = 0.f;  // sign bit set, or +0: not positive
 }
 
 __device__ __forceinline__ void umma_commit(unsigned mbar) {
@@ -417,6 +434,7 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const Conv3dArgs g, const
                 if (relu) x = fmaxf(x, 0.f);
                 acc[j] = x;
             }
+            if (g.mask) apply_relu_mask16(g.mask, v, Nn, n, acc);
             if (out_f32) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) out_f32[v * Nn + n + j] = acc[j];
@@ -613,6 +631,7 @@ __global__ void __launch_bounds__(128) conv3_kws_kernel(const Conv3dArgs g, cons
                 if (relu) x = fmaxf(x, 0.f);
                 a0[j] = x;
             }
+            if (g.mask) apply_relu_mask16(g.mask, v, Nn, n, a0);
             if (out_f32) {
                 float4 *dst = (float4 *)(out_f32 + v * Nn + n);
 #pragma unroll
@@ -794,6 +813,7 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
                     if (relu) x = fmaxf(x, 0.f);
                     a0[j] = x;
                 }
+                if (g.mask) apply_relu_mask16(g.mask, v, Nn, n, a0);
                 if (out_f32) {
                     float4 *dst = (float4 *)(out_f32 + v * Nn + n);
 #pragma unroll
@@ -895,8 +915,11 @@ __device__ __forceinline__ void ldmatrix_x4_trans(const unsigned char *p, unsign
                  : "r"(a));
 }
 
+// With db, the CTAs of the first input-channel tile also add the bias
+// gradient of their 16 output channels, db[co] += sum over their voxels of
+// dy[v][co], from the dy tiles they stage anyway.
 __global__ void __launch_bounds__(128) conv3_wgrad_halo_kernel(const Conv3dArgs g, const __nv_bfloat16 *x,
-                                                               const __nv_bfloat16 *dy, float *dw) {
+                                                               const __nv_bfloat16 *dy, float *dw, float *db) {
     __shared__ __align__(16) unsigned char sX[kHalo * kRowBytes];
     __shared__ __align__(16) unsigned char sDy[kRows * kDyRowBytes];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -916,6 +939,10 @@ __global__ void __launch_bounds__(128) conv3_wgrad_halo_kernel(const Conv3dArgs 
     // ldmatrix row of this lane: voxel (lane & 7) + 8 ((lane >> 3) & 1) of a
     // 16-voxel k-step, channel offset 8 (lane >> 4)
     const int lv = (lane & 7) + ((lane >> 3) & 1) * 8, lc = (lane >> 4) * 16;
+    const bool do_bias = db != nullptr && blockIdx.z == 0;
+    float bsum[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) bsum[j] = 0.f;
     // for B (x): lanes 0-15 channels 0-7 with voxels 0-15, lanes 16-31 channels 8-15
     for (long long blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
         long long t = blk;
@@ -942,6 +969,17 @@ __global__ void __launch_bounds__(128) conv3_wgrad_halo_kernel(const Conv3dArgs 
         cp_async_commit();
         cp_async_wait<0>();
         __syncthreads();
+        if (do_bias) {  // row tid of the dy tile (zero outside the grid)
+            const uint4 *row = (const uint4 *)(sDy + tid * kDyRowBytes);
+            const uint4 q[2] = {row[0], row[1]};
+            const __nv_bfloat162 *h2 = (const __nv_bfloat162 *)q;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float2 f = __bfloat1622float2(h2[j]);
+                bsum[2 * j] += f.x;
+                bsum[2 * j + 1] += f.y;
+            }
+        }
 #pragma unroll 1
         for (int ks = 0; ks < 8; ++ks) {  // 16 voxels per k-step
             // A = dy^T: rows co, k = voxels ks*16 .. +15
@@ -982,6 +1020,18 @@ __global__ void __launch_bounds__(128) conv3_wgrad_halo_kernel(const Conv3dArgs 
                 atomicAdd(q + 1, acc[i][nt][hf * 2 + 1]);
             }
     }
+    if (do_bias) {  // block reduction of the 128 per-thread row sums (sX is free after the last tile)
+        __syncthreads();
+        float *red = (float *)sX;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) red[j * 128 + tid] = bsum[j];
+        __syncthreads();
+        if (tid < 16) {
+            float t = 0.f;
+            for (int k = 0; k < 128; ++k) t += red[tid * 128 + k];
+            atomicAdd(db + co0 + tid, t);
+        }
+    }
 }
 
 // [ci][tap'][co] <- [co][tap][ci] with tap' the point reflection of tap
@@ -1004,8 +1054,10 @@ __global__ void flip_transpose_kernel(const __nv_bfloat16 *w, __nv_bfloat16 *wf,
 constexpr int kWgVox = 16;        // voxels per K step
 constexpr int kWgRowBytes = 144;  // 64 BF16 (128 B) padded to 144 B
 
+// With db, the CTAs of tap 0 and the first input-channel tile also add the
+// bias gradient of their output channels from the dy rows they stage.
 __global__ void __launch_bounds__(128) conv_wgrad_kernel(const Conv3dArgs g, const __nv_bfloat16 *x,
-                                                         const __nv_bfloat16 *dy, float *dw, int chunk) {
+                                                         const __nv_bfloat16 *dy, float *dw, float *db, int chunk) {
     __shared__ __align__(16) unsigned char sDy[2][kWgVox * kWgRowBytes];
     __shared__ __align__(16) unsigned char sX[2][kWgVox * kWgRowBytes];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1049,6 +1101,8 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(const Conv3dArgs g, con
     for (int j = 0; j < 8; ++j)
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[j][k] = 0.f;
+    const bool do_bias = db != nullptr && tap == 0 && ci0 == 0;
+    float bsum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // voxel row tid >> 3, channels (tid & 7) * 8 ..
     if (ksteps > 0) {
         load_stage(0, 0);
         cp_async_commit();
@@ -1061,6 +1115,16 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(const Conv3dArgs g, con
         __syncthreads();
         const unsigned char *Dy = sDy[buf];
         const unsigned char *X = sX[buf];
+        if (do_bias) {  // this thread's staged 16-byte piece of dy (zero outside the chunk)
+            const uint4 q = *(const uint4 *)(Dy + (tid >> 3) * kWgRowBytes + (tid & 7) * 16);
+            const __nv_bfloat162 *h2 = (const __nv_bfloat162 *)&q;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 f = __bfloat1622float2(h2[j]);
+                bsum[2 * j] += f.x;
+                bsum[2 * j + 1] += f.y;
+            }
+        }
         // A[m = co][k = v]: warp rows co = warp * 16 + grp (+8); k = 2 tig (+1), (+8)
         const int m = warp * 16 + grp;
         const int k = tig * 2;
@@ -1090,42 +1154,18 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(const Conv3dArgs g, con
             if (ci + 1 < g.c_in && acc[nt][half * 2 + 1] != 0.f) atomicAdd(p + 1, acc[nt][half * 2 + 1]);
         }
     }
-}
-
-// db[c] += sum over rows of dy[row][c]: a thread reads 16-byte groups of 8
-// channels (G = C / 8 groups per row, 256 / G rows in flight per block), sums
-// its rows' groups in FP32, the block reduces per channel in shared memory,
-// one atomic per channel and block.
-__global__ void __launch_bounds__(256) bias_grad_kernel(const __nv_bfloat16 *dy, long long rows, int C, float *db,
-                                                         int chunk) {
-    __shared__ float sm[256 * 8];
-    const int G = C / 8, lanes = 256 / G;
-    const int gi = threadIdx.x % G, sub = threadIdx.x / G;
-    const long long r0 = (long long)blockIdx.x * chunk;
-    long long r1 = r0 + chunk;
-    if (r1 > rows) r1 = rows;
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (sub < lanes) {
-#pragma unroll 4
-        for (long long r = r0 + sub; r < r1; r += lanes) {
-            const uint4 q = __ldg((const uint4 *)(dy + r * C) + gi);
-            const __nv_bfloat162 *h2 = (const __nv_bfloat162 *)&q;
+    if (do_bias) {  // the 16 voxel rows of each 8-channel part, reduced over the CTA
+        __syncthreads();
+        float *red = (float *)sX[0];  // 128 x 8 floats fit in the two x stages
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float2 f = __bfloat1622float2(h2[j]);
-                acc[2 * j] += f.x;
-                acc[2 * j + 1] += f.y;
-            }
+        for (int j = 0; j < 8; ++j) red[tid * 8 + j] = bsum[j];
+        __syncthreads();
+        if (tid < 64) {
+            const int part = tid >> 3, j = tid & 7, co = co0 + part * 8 + j;
+            float t = 0.f;
+            for (int vi = 0; vi < 16; ++vi) t += red[(vi * 8 + part) * 8 + j];
+            if (co < g.c_out) atomicAdd(db + co, t);
         }
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) sm[threadIdx.x * 8 + j] = acc[j];
-    __syncthreads();
-    for (int c = threadIdx.x; c < C; c += 256) {  // C <= 2048: G <= 256, at least one row in flight
-        const int g = c / 8, j = c % 8;
-        float t = 0.f;
-        for (int k = 0; k < lanes; ++k) t += sm[(k * G + g) * 8 + j];
-        atomicAdd(db + c, t);
     }
 }
 
@@ -1537,12 +1577,8 @@ cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy
         if (per > blocks) per = blocks;
         if (per < 1) per = 1;
         dim3 grid((unsigned)per, (unsigned)(g.c_out / 16), (unsigned)(g.c_in / 16));
-        conv3_wgrad_halo_kernel<<<grid, 128, 0, st>>>(g, (const __nv_bfloat16 *)x, (const __nv_bfloat16 *)dy, dw);
-        if (db) {
-            const int ch = 4096;
-            bias_grad_kernel<<<(unsigned)((rows + ch - 1) / ch), 256, 0, st>>>((const __nv_bfloat16 *)dy, rows,
-                                                                                g.c_out, db, ch);
-        }
+        conv3_wgrad_halo_kernel<<<grid, 128, 0, st>>>(g, (const __nv_bfloat16 *)x, (const __nv_bfloat16 *)dy, dw,
+                                                      db);
         return cudaGetLastError();
     }
     const int taps = g.ksize * g.ksize * g.ksize;
@@ -1555,12 +1591,8 @@ cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy
     if (chunk < 256) chunk = 256;
     chunks = (rows + chunk - 1) / chunk;
     dim3 grid((unsigned)tiles, (unsigned)taps, (unsigned)chunks);
-    conv_wgrad_kernel<<<grid, 128, 0, st>>>(g, (const __nv_bfloat16 *)x, (const __nv_bfloat16 *)dy, dw, (int)chunk);
-    if (db) {
-        const int ch = 4096;
-        bias_grad_kernel<<<(unsigned)((rows + ch - 1) / ch), 256, 0, st>>>((const __nv_bfloat16 *)dy, rows, g.c_out,
-                                                                            db, ch);
-    }
+    conv_wgrad_kernel<<<grid, 128, 0, st>>>(g, (const __nv_bfloat16 *)x, (const __nv_bfloat16 *)dy, dw, db,
+                                            (int)chunk);
     return cudaGetLastError();
 }
 
@@ -1677,6 +1709,7 @@ fdc::Conv3dArgs to_args(const fdc_conv3d *g) {
     a.out_d = g->out_d; a.out_h = g->out_h; a.out_w = g->out_w;
     a.c_in = g->c_in; a.c_out = g->c_out;
     a.ksize = g->ksize; a.stride = g->stride; a.pad = g->pad; a.relu = g->relu ? 1 : 0;
+    a.mask = nullptr;
     return a;
 }
 
@@ -1706,10 +1739,12 @@ int fdc_conv3d_forward_fused(const fdc_conv3d *g, const void *xa, int32_t ca, in
                                     (cudaStream_t)stream, ca, upsample_a ? 1 : 0, xb));
 }
 
-int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_t, void *dx, void *stream) {
+int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_t, const void *relu_mask, void *dx,
+                             void *stream) {
     if (!conv_ok(g) || !dy || !w_t || !dx) return FDC_ERR_INVALID;
     fdc::Conv3dArgs a = to_args(g);
     a.relu = 0;
+    a.mask = relu_mask;
     if (is_k3s1p1(g))  // forward convolution of dy with the reflected, transposed weights
         return rc(fdc::launch_conv_halo(a, dy, w_t, nullptr, dx, nullptr, g->c_out, g->c_in, 0,
                                         (cudaStream_t)stream, g->c_out, 0, nullptr));

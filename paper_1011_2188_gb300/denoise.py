@@ -112,19 +112,21 @@ class ConvLayer:
         return y
 
     def backward(self, dy, need_dx=True):
+        """dy: gradient with respect to this layer's pre-activation (its own
+        ReLU derivative already applied: every layer's input is the output of
+        a ReLU layer, and the data gradient below masks dx by x > 0 in its
+        epilogue, which is that derivative for the layer before).  Returns
+        the gradient with respect to the previous layer's pre-activation."""
         import torch
         L = fdc.lib()
         g, _ = self.geom(tuple(self.x.shape))
-        if self.relu:
-            d = torch.empty_like(dy)
-            _ok(L.fdc_relu_backward(_p(self.y), _p(dy), _p(d), dy.numel(), _s()), "relu backward")
-            dy = d
         _ok(L.fdc_conv3d_backward_weights(C.byref(g), _p(self.x), _p(dy), _p(self.gw), _p(self.gb), _s()),
             "conv wgrad")
         dx = None
         if need_dx:
             dx = torch.empty(self.x.shape, dtype=torch.bfloat16, device=self.dev)
-            _ok(L.fdc_conv3d_backward_data(C.byref(g), _p(dy), _p(self.wt16), _p(dx), _s()), "conv dgrad")
+            _ok(L.fdc_conv3d_backward_data(C.byref(g), _p(dy), _p(self.wt16), _p(self.x), _p(dx), _s()),
+                "conv dgrad")
         self.x = self.y = None
         return dx
 

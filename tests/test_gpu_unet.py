@@ -97,7 +97,10 @@ def test_conv_backward_data_and_weights(case):
         wr = wr[:, ::-1, ::-1, ::-1, :]
     np.testing.assert_array_equal(w_t.double().cpu().numpy(), wr)
     dx = torch.empty(shape, dtype=torch.bfloat16, device="cuda:0")
-    assert L.fdc_conv3d_backward_data(C.byref(g), ptr(dyt), ptr(w_t), ptr(dx), None) == 0
+    assert L.fdc_conv3d_backward_data(C.byref(g), ptr(dyt), ptr(w_t), None, ptr(dx), None) == 0
+    # the same with the ReLU derivative of the input applied in the epilogue
+    dxm = torch.empty(shape, dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_conv3d_backward_data(C.byref(g), ptr(dyt), ptr(w_t), ptr(xt), ptr(dxm), None) == 0
     dw = torch.zeros(w.shape, dtype=torch.float32, device="cuda:0")
     db = torch.zeros(cout, dtype=torch.float32, device="cuda:0")
     assert L.fdc_conv3d_backward_weights(C.byref(g), ptr(xt), ptr(dyt), ptr(dw), ptr(db), None) == 0
@@ -105,6 +108,7 @@ def test_conv_backward_data_and_weights(case):
     rdx = ref.backward_data(dy, w, shape, stride=s, pad=p)
     rdw, rdb = ref.backward_weights(x, dy, k, stride=s, pad=p)
     np.testing.assert_allclose(dx.float().cpu().numpy(), rdx, rtol=0, atol=8e-3 * np.abs(rdx).max())
+    assert torch.equal(dxm, torch.where(xt > 0, dx, torch.zeros_like(dx)))
     np.testing.assert_allclose(dw.cpu().numpy(), rdw, rtol=0, atol=2e-5 * np.abs(rdw).max())
     np.testing.assert_allclose(db.cpu().numpy(), rdb, rtol=0, atol=2e-5 * np.abs(rdb).max())
 
