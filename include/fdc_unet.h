@@ -61,6 +61,21 @@ int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_
  * db[co] += sum_o dy[o][co]; dw, db FP32 (accumulated: zero them first). */
 int fdc_conv3d_backward_weights(const fdc_conv3d *g, const void *x, const void *dy, float *dw, float *db,
                                 void *stream);
+/* The gradients of fdc_conv3d_forward_fused (3^3, stride 1, padding 1), whose
+ * input x = [upsample?(xa) | xb] is never materialised (xa: ca channels, at
+ * half resolution when upsample_a; xb: c_in - ca channels, NULL when
+ * ca = c_in):
+ *   backward_weights_fused: as fdc_conv3d_backward_weights on that x;
+ *   backward_data_fused: as fdc_conv3d_backward_data with relu_mask = x,
+ *     the result split by channel: dxa[voxel][ca] (full resolution: the
+ *     gradient with respect to upsample(xa) when upsample_a) and
+ *     dxb[voxel][c_in - ca]; needs c_out <= 32 (the d-walking kernels).
+ * FDC_ERR_INVALID for other geometries, ca not a multiple of 16, a missing
+ * xb / dxb, or odd sizes with upsample_a. */
+int fdc_conv3d_backward_weights_fused(const fdc_conv3d *g, const void *xa, int32_t ca, int32_t upsample_a,
+                                      const void *xb, const void *dy, float *dw, float *db, void *stream);
+int fdc_conv3d_backward_data_fused(const fdc_conv3d *g, const void *dy, const void *w_t, const void *xa, int32_t ca,
+                                   int32_t upsample_a, const void *xb, void *dxa, void *dxb, void *stream);
 /* Data-gradient weights (bf16, c_in x k^3 x c_out): w_t[ci][tap][co] = w[co][tap][ci], with the
  * tap reflected (tap -> k^3 - 1 - tap) for 3^3 stride-1 padding-1 convolutions, whose data
  * gradient is then a forward convolution of dy. */

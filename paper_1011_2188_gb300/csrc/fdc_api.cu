@@ -65,6 +65,7 @@ struct fdc_ctx {
     int n_bins = 0;
     long long n_tracks = 0, n_steps = 0;
     long long max_track_units = 0;
+    long long max_step_units = 0;  // largest energy loss of one step, tally units
     DevBuf<uint4> rec;
     bool has_esec = false;
     DevBuf<float> esec;
@@ -105,7 +106,7 @@ struct fdc_ctx {
     // schedule picked by fdc_autotune and the instantiation it was tuned on
     fdc_schedule tuned = {0, 0, 0, 0};
     bool tuned_valid = false;
-    fdc::ReplayVariant tuned_variant = {0, 0, 0, 1, 0};
+    fdc::ReplayVariant tuned_variant = {0, 0, 0, 1, 0, 0};
     int last_fp64 = 0;
 };
 
@@ -145,6 +146,12 @@ struct Pinned {
         if (p) cudaFreeHost(p);
     }
 };
+
+// Every step of the loaded database loses fewer than 2^32 tally units: the
+// replay may keep a step's running deposit in 32 bits.  The rounded shares of
+// a step's segments can add up to slightly more than the step (FP32 products,
+// relative error ~2^-24 each), so the bound keeps a margin of 2^12 units.
+bool step_units_fit_32(const fdc_ctx *c) { return c->max_step_units < (1ll << 32) - (1ll << 12); }
 
 // The tuned schedule applies to runs of the kernel instantiation it was
 // tuned on (aggregate aside, which the schedule itself picks).
@@ -187,6 +194,7 @@ fdc::ReplayVariant run_variant(const fdc_ctx *c, const fdc_run_opts &o, bool squ
     v.squares = squares ? 1 : 0;
     v.track_group = o.track_group > 1 ? o.track_group : 1;
     v.esec = c->has_esec ? 1 : 0;
+    v.u32 = step_units_fit_32(c) ? 1 : 0;
     return v;
 }
 
@@ -280,6 +288,7 @@ fdc::ReplayArgs base_args(fdc_ctx *c) {
     a.spots = c->spots.p;
     a.spot_cum = c->spot_cum.p;
     a.nvox = c->nvox;
+    a.u32 = step_units_fit_32(c) ? 1 : 0;
     a.work = c->work.p;
     a.counters = c->counters.p;
     return a;
@@ -410,7 +419,7 @@ int fdc_load_database(fdc_ctx *c, const fdc_database *db) {
     uint4 *hr = (uint4 *)prec.p;
     float *he = (float *)peres.p;
     long long *ht = (long long *)ptail.p;
-    long long chunk_first = 0, fill = 0, max_units = 0;
+    long long chunk_first = 0, fill = 0, max_units = 0, max_step = 0;
     auto flush = [&]() -> int {
         if (!fill) return FDC_OK;
         FDC_CUDA(c, cudaMemcpy(c->rec.p + chunk_first, hr, sizeof(uint4) * fill, cudaMemcpyHostToDevice));
@@ -448,7 +457,9 @@ int fdc_load_database(fdc_ctx *c, const fdc_database *db) {
             long long acc = 0;
             for (long long k = n - 1; k >= 0; --k) {
                 ht[fill + k] = acc;
-                acc += to_units_host(db->dE[s0 + k]) + to_units_host(db->esec[s0 + k]);
+                const long long ue = to_units_host(db->dE[s0 + k]);
+                max_step = std::max(max_step, ue);
+                acc += ue + to_units_host(db->esec[s0 + k]);
             }
             max_units = std::max(max_units, acc);
             fill += n;
@@ -460,6 +471,7 @@ int fdc_load_database(fdc_ctx *c, const fdc_database *db) {
     c->n_tracks = nt;
     c->n_steps = ns;
     c->max_track_units = max_units;
+    c->max_step_units = max_step;
     c->db_loaded = true;
     return FDC_OK;
 }

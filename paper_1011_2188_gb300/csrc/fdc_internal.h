@@ -63,6 +63,7 @@ struct ReplayArgs {
     unsigned long long h_begin, n;  // histories [h_begin, h_begin + n)
     unsigned long long seed;
     int track_group, rotate, scaling_mode;
+    int u32;                      // 1: every step of the database is below 2^32 tally units
     int chunk;
     unsigned long long *work;     // work counter (zeroed before launch)
     DeviceCounters *counters;
@@ -100,7 +101,7 @@ cudaError_t launch_debug_sample(const ReplayArgs &a, float *xyEpsi, long long *b
 // What selects the replay kernel's instantiation (and so its register budget
 // and occupancy).
 struct ReplayVariant {
-    int fp64, aggregate, squares, track_group, esec;
+    int fp64, aggregate, squares, track_group, esec, u32;
 };
 ReplayVariant replay_variant(const ReplayArgs &a, const fdc_schedule &s, int fp64);
 int replay_max_ctas_per_sm(int warps_per_cta, const ReplayVariant &v);
@@ -114,6 +115,15 @@ struct Conv3dArgs {
     // the output, BF16); output values where it is not positive become zero
     // (the ReLU derivative of the layer that produced that input)
     const void *mask;
+    // data gradient of a layer whose forward input was [upsample?(a) | b]
+    // (fdc_conv3d_forward_fused), read without materialising it: with
+    // mask_ca > 0 the mask of channels < mask_ca is `mask` (mask_ca channels,
+    // at half resolution when mask_up) and of the others `mask_b` (Nn -
+    // mask_ca channels); with out_b, output channels >= mask_ca go to out_b
+    // ([voxel][Nn - mask_ca]) and the others to the main output ([voxel][mask_ca]).
+    const void *mask_b;
+    int mask_ca, mask_up;
+    void *out_b;
 };
 cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const void *wt, const float *bias,
                         void *out_bf16, float *out_f32, cudaStream_t st);
@@ -124,7 +134,8 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
                              int ca, int up_a, const void *src_b);
 cudaError_t launch_flip_transpose(const void *w, void *wf, int co, int k, int ci, cudaStream_t st);
 cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy, float *dw, float *db,
-                              cudaStream_t st);
+                              cudaStream_t st, int ca, int up_a, const void *xb);
+bool conv_dwalk_enabled();
 cudaError_t launch_transpose_weights(const void *w, void *wt, int co, int taps, int ci, cudaStream_t st);
 cudaError_t launch_relu_bwd(const void *y, const void *dy, void *dx, long long n, cudaStream_t st);
 cudaError_t launch_upsample2(const void *x, void *y, int B, int D, int H, int W, int C, int backward,

@@ -29,24 +29,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Measurement toggles of the step loop (compile-time):
-//   FDC_OPT_ZFIRST  the face-crossing update tests the z axis first;
-//   FDC_OPT_U32     a step's energy bookkeeping in 32-bit units (needs every
-//                   step below 2^32 tally units, i.e. 16 MeV);
-//   FDC_OPT_C32     per-history 32-bit step and segment counters;
-//   FDC_OPT_RECPTR  the step loop walks a record pointer with a 32-bit count.
-#ifndef FDC_OPT_ZFIRST
-#define FDC_OPT_ZFIRST 0
-#endif
-#ifndef FDC_OPT_U32
-#define FDC_OPT_U32 0
-#endif
-#ifndef FDC_OPT_C32
-#define FDC_OPT_C32 0
-#endif
-#ifndef FDC_OPT_RECPTR
-#define FDC_OPT_RECPTR 0
-#endif
 // 1: a lane sums consecutive deposits into one voxel before its atomic
 // (fewer atomics, more registers; measured slower on GB300 under the
 // 64-register cap, so off by default).
@@ -358,18 +340,20 @@ __device__ __forceinline__ void deflection_factors(R qx, R qy, R f2, R *sfac, R 
     }
 }
 
-// Re-trace one history.  Positions are kept as the voxel index plus the
-// fractional position inside the voxel, f in [0, 1] per axis (grid units:
-// faces at integers), which keeps FP32 rounding relative to the voxel rather
-// than to the whole grid; distances along the ray are in cm.  Per-lane
-// counters are updated in place.
-// FIXED: the voxel where a step starts scales the whole step (ablation of
-// Sec. 2.2's step scaling); a template parameter, so the default path carries
-// no per-segment test.
-// ESEC: the database has local deposits (read per step from the esec side
-// array); a template parameter so that runs without any carry no extra state.
-__device__ __forceinline__ unsigned seg_units_u32(float x) { return __float2uint_rn(x); }
-__device__ __forceinline__ unsigned seg_units_u32(double x) { return __double2uint_rn(x); }
+// Integer type of a step's running deposit: 32-bit when every step of the
+// database is below 2^32 tally units, else 64-bit; seg() converts a segment's
+// share (non-negative, rounded to nearest).
+template <bool U32> struct Dep;
+template <> struct Dep<true> {
+    using type = unsigned;
+    __device__ static __forceinline__ unsigned seg(float x) { return __float2uint_rn(x); }
+    __device__ static __forceinline__ unsigned seg(double x) { return __double2uint_rn(x); }
+};
+template <> struct Dep<false> {
+    using type = long long;
+    __device__ static __forceinline__ long long seg(float x) { return units_of(x); }
+    __device__ static __forceinline__ long long seg(double x) { return units_of(x); }
+};
 
 struct Counts32 {  // per-history counters added to the lane's totals on exit
     unsigned long long &steps, &segs;
@@ -381,18 +365,30 @@ struct Counts32 {  // per-history counters added to the lane's totals on exit
     }
 };
 
-template <typename R, bool AGG, bool SQ, bool FIXED, bool ESEC>
+// Re-trace one history.  Positions are kept as the voxel index plus the
+// fractional position inside the voxel, f in [0, 1] per axis (grid units:
+// faces at integers), which keeps FP32 rounding relative to the voxel rather
+// than to the whole grid; distances along the ray are in cm.  Per-lane
+// counters are updated in place.
+// FIXED: the voxel where a step starts scales the whole step (ablation of
+// Sec. 2.2's step scaling); a template parameter, so the default path carries
+// no per-segment test.
+// ESEC: the database has local deposits (read per step from the esec side
+// array); a template parameter so that runs without any carry no extra state.
+// U32: every step of the database loses less than 2^32 tally units (16 MeV),
+// so a step's running deposit and the units of its segments are 32-bit
+// integers (the per-voxel tally and the escape bookkeeping stay 64-bit); the
+// host picks it per database.
+template <typename R, bool AGG, bool SQ, bool FIXED, bool ESEC, bool U32>
 __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start &st,
                                                unsigned long long h, unsigned long long &steps_tot,
                                                unsigned long long &segs_tot, long long &replayed,
                                                long long &escaped) {
     if (st.k0 >= st.n) return;
-#if FDC_OPT_C32
+    // per-history 32-bit step and segment counts, added to the lane's 64-bit
+    // totals when the history ends (a history has fewer than 2^32 of either)
     Counts32 cnt(steps_tot, segs_tot);
     unsigned &steps = cnt.st, &segs = cnt.sg;
-#else
-    unsigned long long &steps = steps_tot, &segs = segs_tot;
-#endif
     const long long s_first = st.s0 + st.k0, s_end = st.s0 + st.n;
     const unsigned long long pol = evict_first_policy();
     uint4 rec = load_record(P.rec + s_first, pol);
@@ -430,18 +426,11 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
     float2 sk = __ldg(P.vox + v);
     PendingTally<AGG, SQ> pend(P, tbase);
 
-#if FDC_OPT_RECPTR
+    // the step loop walks the track's records with a pointer and a 32-bit
+    // count of the steps left (a track has at most 2^22 steps)
     const uint4 *rp = P.rec + s_first;
     int left = (int)(s_end - s_first);
-#define FDC_S_NOW (rp - P.rec)
-#else
-#define FDC_S_NOW s
-#endif
-#if FDC_OPT_RECPTR
     for (;;) {
-#else
-    for (long long s = s_first;;) {
-#endif
         const float dE_f = __uint_as_float(rec.y);
         const R len = (R)__uint_as_float(rec.x), dE = (R)dE_f;
         const long long Qk = units_of(dE_f * kUnitsF);
@@ -470,12 +459,10 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
         tmz = tmz > (R)0 ? tmz : (R)0;
 
         R rem = len, t = (R)0, acc = (R)0;
-#if FDC_OPT_U32
-        unsigned dep = 0;
-        const unsigned Qk32 = (unsigned)Qk;
-#else
-        long long dep = 0;
-#endif
+        // the step's units and the units deposited so far in it (32 bits when
+        // every step fits; only these stay live across the segment loop)
+        const typename Dep<U32>::type Qkd = (typename Dep<U32>::type)Qk;
+        typename Dep<U32>::type dep = 0;
         constexpr bool fixed = FIXED;
         const R S_fix = (R)sk.x, k2_fix = (R)sk.y;
         int nseg = 0;
@@ -492,44 +479,26 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
             const R wexit = seg * S;
             ++segs;
             if (wexit >= rem) {  // the step ends in this voxel
-#if FDC_OPT_U32
-                const long long units = (long long)(Qk32 - dep);
-#else
-                const long long units = Qk - dep;
-#endif
+                // the remainder may be a few units negative (rounded shares of the
+                // earlier segments): formed in 64 bits; dep itself stays below 2^32
+                const long long units = (long long)Qkd - (long long)dep;
                 pend.add(v, units);
                 acc += rem * k2;
                 t += rem * rcp_(S);
                 break;
             }
-#if FDC_OPT_U32
-            const unsigned u32 = seg_units_u32(wexit * dEu);
-            dep += u32;
-            pend.add(v, (long long)u32);
-#else
-            const long long units = units_of(wexit * dEu);
+            const typename Dep<U32>::type units = Dep<U32>::seg(wexit * dEu);
             dep += units;
-            pend.add(v, units);
-#endif
+            pend.add(v, (long long)units);
             acc += wexit * k2;
             rem -= wexit;
             t = tm;
             bool out;
-#if FDC_OPT_ZFIRST
-            if (a == 2) { iz += stz; v += stz * sz; out = (unsigned)iz >= (unsigned)P.nz; tmz += tdz; }
-            else if (a == 0) { ix += stx; v += stx; out = (unsigned)ix >= (unsigned)P.nx; tmx += tdx; }
-            else { iy += sty; v += sty * sy; out = (unsigned)iy >= (unsigned)P.ny; tmy += tdy; }
-#else
             if (a == 0) { ix += stx; v += stx; out = (unsigned)ix >= (unsigned)P.nx; tmx += tdx; }
             else if (a == 1) { iy += sty; v += sty * sy; out = (unsigned)iy >= (unsigned)P.ny; tmy += tdy; }
             else { iz += stz; v += stz * sz; out = (unsigned)iz >= (unsigned)P.nz; tmz += tdz; }
-#endif
             if (out) {  // left the grid: the rest of the history escapes
-#if FDC_OPT_U32
-                escaped += (long long)(Qk32 - dep) + Qs + __ldg(P.tail + FDC_S_NOW);
-#else
-                escaped += (Qk - dep) + Qs + __ldg(P.tail + FDC_S_NOW);
-#endif
+                escaped += ((long long)Qkd - (long long)dep) + Qs + __ldg(P.tail + (rp - P.rec));
                 gone = true;
                 break;
             }
@@ -549,27 +518,16 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
         fy = ((R)(iy0 - iy) + fy) + t * ry;
         fz = ((R)(iz0 - iz) + fz) + t * rz;
         if (ESEC && Qs) pend.add(v, Qs);
-#if FDC_OPT_RECPTR
         if (--left == 0) {
             pend.flush();
             return;
         }
         ++rp;
-#else
-        if (++s >= s_end) {
-            pend.flush();
-            return;
-        }
-#endif
         const R qx = (R)__uint_as_float(rec.z), qy = (R)__uint_as_float(rec.w);
-#if FDC_OPT_RECPTR
         rec = load_record(rp, pol);  // next record: issued before the deflection arithmetic
-#else
-        rec = load_record(P.rec + s, pol);  // next record: issued before the deflection arithmetic
-#endif
-        if (ESEC) esec = __ldg(P.esec + FDC_S_NOW);
+        if (ESEC) esec = __ldg(P.esec + (rp - P.rec));
 #if FDC_RECORD_PREFETCH
-        if ((FDC_S_NOW & 7) == 0 && FDC_S_NOW + 8 < s_end) prefetch_l2(P.rec + FDC_S_NOW + 8);
+        if (((rp - P.rec) & 7) == 0 && left > 8) prefetch_l2(rp + 8);
 #endif
 
         // deflection at the end of the step, scaled by the crossed materials
@@ -606,8 +564,6 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
     }
 }
 
-#undef FDC_S_NOW
-
 // Minimum resident CTAs of 256 threads per SM requested from the register
 // allocator: 4 caps the kernel at 64 registers (no spills).  With 32 or more
 // histories per track (a warp shares one track) the kernel is bound by
@@ -621,7 +577,7 @@ __device__ __forceinline__ void replay_history(const ReplayArgs &P, const Start 
 #define FDC_REPLAY_MIN_CTAS_SHARED 5
 #endif
 
-template <typename R, bool AGG, bool SQ, bool ESEC, int MINB = FDC_REPLAY_MIN_CTAS>
+template <typename R, bool AGG, bool SQ, bool ESEC, bool U32, int MINB = FDC_REPLAY_MIN_CTAS>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MINB : 2)
     replay_kernel(const ReplayArgs P) {
     const unsigned lane = threadIdx.x & 31u;
@@ -639,9 +595,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MINB : 2)
                 const unsigned long long h = P.h_begin + li;
                 const Start st = sample_start(P, h);
                 if (P.scaling_mode == 1)
-                    replay_history<R, AGG, SQ, true, ESEC>(P, st, h, steps, segs, replayed, escaped);
+                    replay_history<R, AGG, SQ, true, ESEC, U32>(P, st, h, steps, segs, replayed, escaped);
                 else
-                    replay_history<R, AGG, SQ, false, ESEC>(P, st, h, steps, segs, replayed, escaped);
+                    replay_history<R, AGG, SQ, false, ESEC, U32>(P, st, h, steps, segs, replayed, escaped);
                 ++hist;
             }
         }
@@ -845,8 +801,9 @@ __global__ void probe_atomics_kernel(unsigned long long *slots, unsigned long lo
 using ReplayFn = void (*)(ReplayArgs);
 
 template <typename R, bool AGG, bool SQ, int MINB = FDC_REPLAY_MIN_CTAS>
-ReplayFn replay_fn_t(bool esec) {
-    return esec ? replay_kernel<R, AGG, SQ, true, MINB> : replay_kernel<R, AGG, SQ, false, MINB>;
+ReplayFn replay_fn_t(bool esec, bool u32) {
+    if (u32) return esec ? replay_kernel<R, AGG, SQ, true, true, MINB> : replay_kernel<R, AGG, SQ, false, true, MINB>;
+    return esec ? replay_kernel<R, AGG, SQ, true, false, MINB> : replay_kernel<R, AGG, SQ, false, false, MINB>;
 }
 
 // The one place that maps a run to its kernel instantiation; the launch and
@@ -855,11 +812,12 @@ ReplayFn replay_fn_t(bool esec) {
 //   atomics;  FP32 with plain atomics and 32 or more histories per track: the
 //   48-register variant;  esec: the database has local deposits.
 ReplayFn replay_fn(const ReplayVariant &v) {
-    if (v.squares) return v.fp64 ? replay_fn_t<double, false, true>(v.esec) : replay_fn_t<float, false, true>(v.esec);
+    const bool u = v.u32 != 0;
+    if (v.squares) return v.fp64 ? replay_fn_t<double, false, true>(v.esec, u) : replay_fn_t<float, false, true>(v.esec, u);
     const bool agg = v.aggregate == 1;
-    if (v.fp64) return agg ? replay_fn_t<double, true, false>(v.esec) : replay_fn_t<double, false, false>(v.esec);
-    if (!agg && v.track_group >= 32) return replay_fn_t<float, false, false, FDC_REPLAY_MIN_CTAS_SHARED>(v.esec);
-    return agg ? replay_fn_t<float, true, false>(v.esec) : replay_fn_t<float, false, false>(v.esec);
+    if (v.fp64) return agg ? replay_fn_t<double, true, false>(v.esec, u) : replay_fn_t<double, false, false>(v.esec, u);
+    if (!agg && v.track_group >= 32) return replay_fn_t<float, false, false, FDC_REPLAY_MIN_CTAS_SHARED>(v.esec, u);
+    return agg ? replay_fn_t<float, true, false>(v.esec, u) : replay_fn_t<float, false, false>(v.esec, u);
 }
 
 }  // namespace
@@ -934,6 +892,7 @@ ReplayVariant replay_variant(const ReplayArgs &a, const fdc_schedule &s, int fp6
     v.squares = a.sumsq ? 1 : 0;
     v.track_group = a.track_group;
     v.esec = a.esec ? 1 : 0;
+    v.u32 = a.u32;
     return v;
 }
 

@@ -317,6 +317,26 @@ __device__ __forceinline__ void apply_relu_mask16(const void *mask, long long v,
         if ((short)h[j] <= 0) a[j] = 0.f;  // sign bit set, or +0: not positive
 }
 
+// Mask of output channels [n, n + 16) at voxel (b, d, h, w) of a D x H x W
+// grid when the layer's forward input was [upsample?(a) | b] (g.mask_ca > 0).
+__device__ __forceinline__ void apply_relu_mask16_fused(const Conv3dArgs &g, int Nn, int bb, int d, int h, int w,
+                                                        int D, int H, int W, int n, float a[16]) {
+    const __nv_bfloat16 *m;
+    if (n < g.mask_ca) {
+        const long long vv = g.mask_up ? (((long long)bb * (D / 2) + (d >> 1)) * (H / 2) + (h >> 1)) * (W / 2) + (w >> 1)
+                                       : (((long long)bb * D + d) * H + h) * W + w;
+        m = (const __nv_bfloat16 *)g.mask + vv * g.mask_ca + n;
+    } else {
+        const long long vv = (((long long)bb * D + d) * H + h) * W + w;
+        m = (const __nv_bfloat16 *)g.mask_b + vv * (Nn - g.mask_ca) + (n - g.mask_ca);
+    }
+    const uint4 q[2] = {__ldg((const uint4 *)m), __ldg((const uint4 *)m + 1)};
+    const unsigned short *hh = (const unsigned short *)q;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        if ((short)hh[j] <= 0) a[j] = 0.f;
+}
+
 __device__ __forceinline__ void umma_commit(unsigned mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
                  : "memory");
@@ -685,6 +705,9 @@ constexpr int kDwPlaneSliceBytes = 10 * 512;  // [h 10][w-group 2][k-chunk 2][8 
 #ifndef FDC_CONV_DWALK
 #define FDC_CONV_DWALK 1
 #endif
+#ifndef FDC_CONV_WS
+#define FDC_CONV_WS 1
+#endif
 
 template <int NT>
 __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
@@ -698,6 +721,7 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ unsigned tmem_slot;
+    __shared__ float sBias[NT];  // the CTA's output channels are fixed: bias staged once
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = g.in_d, H = g.in_h, W = g.in_w;
     const int S = Cs / 16;
@@ -725,6 +749,7 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
                      "r"(kCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
+    if (tid < NT) sBias[tid] = (bias && n0 + tid < Nn) ? bias[n0 + tid] : 0.f;
     // resident weights of every input slice (through L1: all CTAs read the same)
     {
         constexpr int kChunks = 9 * 2 * N3;  // per slice
@@ -785,6 +810,7 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
             cp_async_commit();
         };
         for (int j = 0; j < pf + 2; ++j) load_plane(j);
+        int slot_i = 0;  // ring slot of input plane i (= i % R), advanced per output plane
         // epilogue of output plane i of this range (accumulator buffer ab, barrier phase ph)
         auto epilogue = [&](int i, unsigned ab, unsigned ph) -> bool {
             // warp-uniform outcome (the shuffles below need every lane)
@@ -809,11 +835,16 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     float x = a0[j];
-                    if (bias) x += __ldg(bias + n + j);
+                    if (bias) x += sBias[c + j];
                     if (relu) x = fmaxf(x, 0.f);
                     a0[j] = x;
                 }
-                if (g.mask) apply_relu_mask16(g.mask, v, Nn, n, a0);
+                if (g.mask) {
+                    if (g.mask_ca > 0)
+                        apply_relu_mask16_fused(g, Nn, b, d_begin + i, ho, wo, D, H, W, n, a0);
+                    else
+                        apply_relu_mask16(g.mask, v, Nn, n, a0);
+                }
                 if (out_f32) {
                     float4 *dst = (float4 *)(out_f32 + v * Nn + n);
 #pragma unroll
@@ -828,7 +859,12 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
                         __nv_bfloat162 p2 = __floats2bfloat162_rn(a0[2 * j], a0[2 * j + 1]);
                         qq[j] = *(unsigned *)&p2;
                     }
-                    uint4 *dst = (uint4 *)(out_bf16 + v * Nn + n);
+                    // split output: channels >= mask_ca into out_b
+                    uint4 *dst = g.out_b == nullptr
+                                     ? (uint4 *)(out_bf16 + v * Nn + n)
+                                     : (n < g.mask_ca ? (uint4 *)(out_bf16 + v * g.mask_ca + n)
+                                                      : (uint4 *)((__nv_bfloat16 *)g.out_b + v * (Nn - g.mask_ca) +
+                                                                  (n - g.mask_ca)));
                     dst[0] = qv[0];
                     dst[1] = qv[1];
                 }
@@ -859,16 +895,25 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
             const unsigned ab = it_all & 1u;
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const unsigned wa = smem_u32(sW);
                 constexpr unsigned idesc = umma_idesc(128, N3);
+                // descriptors of the three input planes and of the weights; the
+                // per-MMA offsets are added to the 16-byte address field (shared
+                // addresses stay below 2^18, so the 14-bit field cannot carry)
+                unsigned long long ad_kd[3];
+#pragma unroll
+                for (int kd = 0; kd < 3; ++kd) {
+                    int sk = slot_i + kd;
+                    if (sk >= R) sk -= R;
+                    ad_kd[kd] = umma_desc(smem_u32(sP) + sk * plane_bytes, 128, 256);
+                }
+                const unsigned long long bd0 = umma_desc(smem_u32(sW), N3 * 16, 128);
 #pragma unroll 1
                 for (int sl = 0; sl < S; ++sl) {
-#pragma unroll 1
+#pragma unroll
                     for (int kdh = 0; kdh < 9; ++kdh) {
-                        const int kd = kdh / 3, kh = kdh % 3;
-                        const unsigned pa = smem_u32(sP + ((i + kd) % R) * plane_bytes) + sl * kDwPlaneSliceBytes + kh * 512;
-                        const unsigned long long ad = umma_desc(pa, 128, 256);
-                        const unsigned long long bd = umma_desc(wa + (sl * 9 + kdh) * 2 * N3 * 16, N3 * 16, 128);
+                        const unsigned long long ad =
+                            ad_kd[kdh / 3] + (unsigned long long)((sl * kDwPlaneSliceBytes + (kdh % 3) * 512) >> 4);
+                        const unsigned long long bd = bd0 + (unsigned long long)(((sl * 9 + kdh) * 2 * N3 * 16) >> 4);
                         umma_bf16(tmem + ab * kAccCols, ad, bd, idesc, (sl | kdh) != 0);
                     }
                 }
@@ -876,6 +921,7 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
             }
             if (i > 0) ok = epilogue(i - 1, ab ^ 1u, ((it_all - 1) >> 1) & 1u);
             ++it_all;
+            if (++slot_i == R) slot_i = 0;
         }
         // the range's last plane
         if (__syncthreads_and(ok)) ok = epilogue(nd - 1, (it_all - 1) & 1u, ((it_all - 1) >> 1) & 1u);
@@ -886,6 +932,331 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
     }
     if (!ok && tid == 0) atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
     cp_async_wait<0>();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
+    }
+}
+
+// Warp-specialised form of the d-walking convolution (same tiles, plane ring
+// and accumulators as conv3_dwalk_kernel; input channels Cs <= 32, NT = 16 or
+// 32), 256 threads in three roles joined by mbarriers instead of CTA-wide
+// barriers:
+//   producers (warps 0, 1, 3): stage the planes of the CTA's ranges into the
+//     ring with cp.async, keeping kWsInflight planes in flight per thread; a
+//     plane is published (fence.proxy.async, then an arrive on full[slot])
+//     once the thread's copies of it have landed, and a slot is reused only
+//     after empty[slot] says the MMAs that read its previous plane finished;
+//   MMA issuer (warp 2, one thread): per output plane waits for its newest
+//     input plane and a free accumulator, issues the 9 * Cs / 16 MMAs,
+//     commits to acc_full[b] and to empty[] of the plane no later output
+//     reads (the last two planes of a range at its end);
+//   epilogue (warps 4-7, TMEM lane quarters 0-3): waits for acc_full[b],
+//     loads the accumulator, releases it (acc_empty[b]) and then combines the
+//     kw columns, adds bias, applies ReLU or the ReLU mask and stores.
+// Every wait is bounded; a timeout raises a shared abort flag that every
+// other wait also watches, records FDC_ERR_TIMEOUT and the CTA winds down.
+constexpr int kWsInflight = 3;  // planes in flight per producer thread (<= ring slots - 3)
+
+__device__ __forceinline__ bool mbar_wait_abort(unsigned mbar, unsigned parity, volatile int *abort) {
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > kTcWaitCycles) {
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+
+template <int NT>
+__global__ void __launch_bounds__(256) conv3_ws_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
+                                                       const __nv_bfloat16 *wt, const float *bias,
+                                                       __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn,
+                                                       int relu, int ca, int up_a, const __nv_bfloat16 *src_b,
+                                                       int R) {
+    constexpr int N3 = 3 * NT;
+    constexpr unsigned kAccCols = N3 <= 64 ? 64 : 128;
+    constexpr unsigned kCols = 2 * kAccCols;
+    constexpr int kMaxR = 10;
+    constexpr int kProducers = 96;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long bar_full[kMaxR], bar_empty[kMaxR], bar_acc_full[2],
+        bar_acc_empty[2];
+    __shared__ unsigned tmem_slot;
+    __shared__ volatile int abort_flag;
+    __shared__ float sBias[NT];  // the CTA's output channels are fixed: bias staged once
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int D = g.in_d, H = g.in_h, W = g.in_w;
+    const int S = Cs / 16;
+    const int plane_bytes = S * kDwPlaneSliceBytes;
+    const int wbytes = S * 9 * 2 * N3 * 16;
+    unsigned char *sW = smem;
+    unsigned char *sP = smem + wbytes;
+    const int tiles_w = (W + 13) / 14, tiles_h = (H + 7) / 8;
+    const long long n_cols = (long long)g.batch * tiles_h * tiles_w;
+    const long long total = n_cols * D;
+    const long long q_begin = total * blockIdx.x / gridDim.x, q_end = total * (blockIdx.x + 1) / gridDim.x;
+    const int n0 = blockIdx.y * NT;
+    const int cb = Cs - ca;
+    const int Da = up_a ? D / 2 : D, Ha = up_a ? H / 2 : H, Wa = up_a ? W / 2 : W;
+
+    if (tid == 0) {
+        for (int i = 0; i < R; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&bar_full[i])), "r"(kProducers));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar_empty[i])));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar_acc_full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;\n" ::"r"(smem_u32(&bar_acc_empty[i])));
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid < NT) sBias[tid] = (bias && n0 + tid < Nn) ? bias[n0 + tid] : 0.f;
+    // resident weights (every thread helps; they land before the first plane is published)
+    {
+        constexpr int kChunks = 9 * 2 * N3;
+        for (int i = tid; i < S * kChunks; i += 256) {
+            const int sl = i / kChunks, r = i % kChunks;
+            const int n = r % N3, q = r / N3, kc = q & 1, kdh = q >> 1;
+            const int co = n0 + (n % NT), kw = n / NT;
+            const bool in = co < Nn;
+            const __nv_bfloat16 *p = in ? wt + (size_t)((co * 27 + kdh * 3 + kw) * Cs + sl * 16 + kc * 8) : wt;
+            cp_async16_ca(sW + i * 16, p, in);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = tmem_slot;
+
+    // the CTA's ranges: (column, first plane, number of planes), decoded identically by every role
+    struct Range {
+        int w0, h0, b, d_begin, nd;
+    };
+    auto range_at = [&](long long q, Range &r) {
+        const long long col = q / D;
+        r.d_begin = (int)(q % D);
+        r.nd = (int)(q_end - q < (long long)(D - r.d_begin) ? q_end - q : (long long)(D - r.d_begin));
+        long long t = col;
+        r.w0 = (int)(t % tiles_w) * 14; t /= tiles_w;
+        r.h0 = (int)(t % tiles_h) * 8;
+        r.b = (int)(t / tiles_h);
+    };
+
+    if (warp == 0 || warp == 1 || warp == 3) {
+        // ---------------- producers
+        const int pt = warp == 3 ? 64 + lane : tid;  // 0 .. 95
+        const int kc = pt & 1, hw = (pt >> 1) & 15, r0 = pt >> 5;
+        const unsigned hdst = (unsigned)((((hw >> 3) * 2 + kc) * 128) + (hw & 7) * 16);
+        long long P = 0;  // planes issued
+        bool live = true;
+        for (long long q = q_begin; q < q_end && live;) {
+            Range rg;
+            range_at(q, rg);
+            q += rg.nd;
+            const int w = rg.w0 - 1 + hw;
+            const bool w_in = w >= 0 && w < W;
+            for (int j = 0; j <= rg.nd + 1 && live; ++j, ++P) {
+                const int slot = (int)(P % R);
+                if (P >= R && !mbar_wait_abort(smem_u32(&bar_empty[slot]), (unsigned)((P / R - 1) & 1), &abort_flag)) {
+                    live = false;
+                    break;
+                }
+                const int d = rg.d_begin - 1 + j;
+                const bool d_in = w_in && d >= 0 && d < D;
+                unsigned char *dst = sP + slot * plane_bytes + hdst;
+                for (int r = r0; r < S * 10; r += 3) {
+                    const int sl = r / 10, hh = r - 10 * sl;
+                    const int h = rg.h0 - 1 + hh, c0 = sl * 16;
+                    const bool in = d_in && h >= 0 && h < H;
+                    const __nv_bfloat16 *p = src;
+                    if (in) {
+                        if (c0 >= ca)
+                            p = src_b + ((((long long)rg.b * D + d) * H + h) * W + w) * cb + (c0 - ca) + kc * 8;
+                        else if (up_a)
+                            p = src + ((((long long)rg.b * Da + (d >> 1)) * Ha + (h >> 1)) * Wa + (w >> 1)) * ca + c0 +
+                                kc * 8;
+                        else
+                            p = src + ((((long long)rg.b * D + d) * H + h) * W + w) * ca + c0 + kc * 8;
+                    }
+                    cp_async16(dst + r * 512, p, in);
+                }
+                cp_async_commit();
+                if (P >= kWsInflight) {  // plane P - kWsInflight has landed: publish it
+                    cp_async_wait<kWsInflight>();
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    mbar_arrive(smem_u32(&bar_full[(int)((P - kWsInflight) % R)]));
+                }
+            }
+        }
+        cp_async_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if (live)  // publish the last planes still in flight
+            for (long long k = P - kWsInflight < 0 ? 0 : P - kWsInflight; k < P; ++k)
+                mbar_arrive(smem_u32(&bar_full[(int)(k % R)]));
+    } else if (warp == 2) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            long long P = 0, O = 0;  // planes consumed, outputs issued
+            const unsigned wa = smem_u32(sW);
+            constexpr unsigned idesc = umma_idesc(128, N3);
+            bool live = true;
+            for (long long q = q_begin; q < q_end && live;) {
+                Range rg;
+                range_at(q, rg);
+                q += rg.nd;
+                const long long base = P;
+                // the first two planes of the range
+                for (int j = 0; j < 2 && live; ++j)
+                    live = mbar_wait_abort(smem_u32(&bar_full[(int)((base + j) % R)]),
+                                           (unsigned)(((base + j) / R) & 1), &abort_flag);
+                for (int i = 0; i < rg.nd && live; ++i, ++O) {
+                    const long long pn = base + i + 2;
+                    const unsigned b = (unsigned)(O & 1);
+                    if (!mbar_wait_abort(smem_u32(&bar_full[(int)(pn % R)]), (unsigned)((pn / R) & 1), &abort_flag) ||
+                        (O >= 2 && !mbar_wait_abort(smem_u32(&bar_acc_empty[b]), (unsigned)(((O >> 1) - 1) & 1),
+                                                    &abort_flag))) {
+                        live = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    unsigned long long ad_kd[3];
+                    const int s0 = (int)((base + i) % R);
+#pragma unroll
+                    for (int kd = 0; kd < 3; ++kd) {
+                        int sk = s0 + kd;
+                        if (sk >= R) sk -= R;
+                        ad_kd[kd] = umma_desc(smem_u32(sP) + sk * plane_bytes, 128, 256);
+                    }
+                    const unsigned long long bd0 = umma_desc(wa, N3 * 16, 128);
+#pragma unroll 1
+                    for (int sl = 0; sl < S; ++sl) {
+#pragma unroll
+                        for (int kdh = 0; kdh < 9; ++kdh) {
+                            const unsigned long long ad = ad_kd[kdh / 3] +
+                                (unsigned long long)((sl * kDwPlaneSliceBytes + (kdh % 3) * 512) >> 4);
+                            const unsigned long long bd =
+                                bd0 + (unsigned long long)(((sl * 9 + kdh) * 2 * N3 * 16) >> 4);
+                            umma_bf16(tmem + b * kAccCols, ad, bd, idesc, (sl | kdh) != 0);
+                        }
+                    }
+                    umma_commit(smem_u32(&bar_acc_full[b]));
+                    umma_commit(smem_u32(&bar_empty[(int)((base + i) % R)]));  // no later output reads plane base + i
+                }
+                if (live) {
+                    umma_commit(smem_u32(&bar_empty[(int)((base + rg.nd) % R)]));
+                    umma_commit(smem_u32(&bar_empty[(int)((base + rg.nd + 1) % R)]));
+                }
+                P = base + rg.nd + 2;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 4-7: TMEM lanes 32 (warp - 4) ...)
+        const int qw = warp - 4;
+        const int m = qw * 32 + lane;
+        long long O = 0;
+        bool live = true;
+        for (long long q = q_begin; q < q_end && live;) {
+            Range rg;
+            range_at(q, rg);
+            q += rg.nd;
+            const int ho = rg.h0 + (m >> 4), wl = m & 15, wo = rg.w0 + wl;
+            const bool out_in = wl < 14 && ho < H && wo < W;
+            for (int i = 0; i < rg.nd; ++i, ++O) {
+                const unsigned b = (unsigned)(O & 1);
+                if (!__all_sync(0xffffffffu, mbar_wait_abort(smem_u32(&bar_acc_full[b]), (unsigned)((O >> 1) & 1),
+                                                            &abort_flag))) {
+                    live = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const unsigned base = tmem + ((unsigned)(qw * 32) << 16) + b * kAccCols;
+                float acc[NT / 16][3][16];
+#pragma unroll
+                for (int c = 0; c < NT / 16; ++c) {
+                    tmem_ld16(base + (unsigned)(c * 16), acc[c][0]);
+                    tmem_ld16(base + (unsigned)(NT + c * 16), acc[c][1]);
+                    tmem_ld16(base + (unsigned)(2 * NT + c * 16), acc[c][2]);
+                }
+                // the accumulator is in registers: hand it back to the MMA issuer
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                mbar_arrive(smem_u32(&bar_acc_empty[b]));
+                const long long v = (((long long)rg.b * D + rg.d_begin + i) * H + ho) * W + wo;
+#pragma unroll
+                for (int c = 0; c < NT / 16; ++c) {
+                    float *a0 = acc[c][0];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        a0[j] += __shfl_down_sync(0xffffffffu, acc[c][1][j], 1) +
+                                 __shfl_down_sync(0xffffffffu, acc[c][2][j], 2);
+                    const int n = n0 + c * 16;
+                    if (!out_in || n >= Nn) continue;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        float x = a0[j];
+                        if (bias) x += sBias[c * 16 + j];
+                        if (relu) x = fmaxf(x, 0.f);
+                        a0[j] = x;
+                    }
+                    if (g.mask) {
+                        if (g.mask_ca > 0)
+                            apply_relu_mask16_fused(g, Nn, rg.b, rg.d_begin + i, ho, wo, D, H, W, n, a0);
+                        else
+                            apply_relu_mask16(g.mask, v, Nn, n, a0);
+                    }
+                    if (out_f32) {
+                        float4 *dst = (float4 *)(out_f32 + v * Nn + n);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            dst[j] = make_float4(a0[4 * j], a0[4 * j + 1], a0[4 * j + 2], a0[4 * j + 3]);
+                    }
+                    if (out_bf16) {
+                        uint4 qv[2];
+                        unsigned *qq = (unsigned *)qv;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            __nv_bfloat162 p2 = __floats2bfloat162_rn(a0[2 * j], a0[2 * j + 1]);
+                            qq[j] = *(unsigned *)&p2;
+                        }
+                        // split output: channels >= mask_ca into out_b
+                        uint4 *dst = g.out_b == nullptr
+                                         ? (uint4 *)(out_bf16 + v * Nn + n)
+                                         : (n < g.mask_ca ? (uint4 *)(out_bf16 + v * g.mask_ca + n)
+                                                          : (uint4 *)((__nv_bfloat16 *)g.out_b + v * (Nn - g.mask_ca) +
+                                                                      (n - g.mask_ca)));
+                        dst[0] = qv[0];
+                        dst[1] = qv[1];
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && abort_flag) atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -918,8 +1289,12 @@ __device__ __forceinline__ void ldmatrix_x4_trans(const unsigned char *p, unsign
 // With db, the CTAs of the first input-channel tile also add the bias
 // gradient of their 16 output channels, db[co] += sum over their voxels of
 // dy[v][co], from the dy tiles they stage anyway.
+// The input may be the concatenation [upsample?(x) | xb] of the fused forward
+// (x: ca channels, at half resolution when up_a; xb: Ci - ca channels), read
+// in place; otherwise ca = Ci and xb is unused.
 __global__ void __launch_bounds__(128) conv3_wgrad_halo_kernel(const Conv3dArgs g, const __nv_bfloat16 *x,
-                                                               const __nv_bfloat16 *dy, float *dw, float *db) {
+                                                               const __nv_bfloat16 *dy, float *dw, float *db,
+                                                               int ca, int up_a, const __nv_bfloat16 *xb) {
     __shared__ __align__(16) unsigned char sX[kHalo * kRowBytes];
     __shared__ __align__(16) unsigned char sDy[kRows * kDyRowBytes];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -956,7 +1331,16 @@ __global__ void __launch_bounds__(128) conv3_wgrad_halo_kernel(const Conv3dArgs 
             const int hd = row / (kHH * kHW), hh = (row / kHW) % kHH, hw = row % kHW;
             const int d = d0 - 1 + hd, h = h0 - 1 + hh, w = w0 - 1 + hw;
             const bool ok = d >= 0 && d < D && h >= 0 && h < H && w >= 0 && w < W;
-            const __nv_bfloat16 *p = ok ? x + ((((long long)b * D + d) * H + h) * W + w) * Ci + ci0 + half * 8 : x;
+            const __nv_bfloat16 *p = x;
+            if (ok) {
+                if (ci0 >= ca)
+                    p = xb + ((((long long)b * D + d) * H + h) * W + w) * (Ci - ca) + (ci0 - ca) + half * 8;
+                else if (up_a)
+                    p = x + ((((long long)b * (D / 2) + (d >> 1)) * (H / 2) + (h >> 1)) * (W / 2) + (w >> 1)) * ca + ci0 +
+                        half * 8;
+                else
+                    p = x + ((((long long)b * D + d) * H + h) * W + w) * ca + ci0 + half * 8;
+            }
             cp_async16(sX + row * kRowBytes + half * 16, p, ok);
         }
         for (int i = tid; i < kRows * 2; i += 128) {
@@ -1439,6 +1823,46 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
     auto sb = (const __nv_bfloat16 *)src_b;
     // input channels <= 32 (the 128^3 and 64^3 levels of the network): the
     // d-walking kernel, CTAs spread over the flattened (tile, d) planes
+    if (FDC_CONV_WS && Cs <= 32 && Nn % 16 == 0) {
+        // warp-specialised d-walking kernel: ring of R >= kWsInflight + 3 slots
+        int dev = 0, sms = 0, smem_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e != cudaSuccess) return e;
+        const int S = Cs / 16;
+        const int NT = Nn % 32 == 0 ? 32 : 16;
+        const int wbytes = S * 9 * 2 * (3 * NT) * 16;
+        const int plane = S * kDwPlaneSliceBytes;
+        const int per_sm_tmem = NT == 32 ? 2 : 4;
+        const int budget = smem_sm / per_sm_tmem - 2048;
+        const int R = std::max(kWsInflight + 3, std::min(10, (budget - wbytes) / plane));
+        const int smem = wbytes + R * plane;
+        cudaFuncAttributes fa;
+        if (NT == 32) {
+            static OccCache cache;
+            e = prepare_kernel_smem(cache, conv3_ws_kernel<32>, smem);
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv3_ws_kernel<32>);
+        } else {
+            static OccCache cache;
+            e = prepare_kernel_smem(cache, conv3_ws_kernel<16>, smem);
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv3_ws_kernel<16>);
+        }
+        if (e != cudaSuccess) return e;
+        const int by_smem = smem_sm / (smem + (int)fa.sharedSizeBytes + 1024);
+        const int by_regs = 65536 / (256 * std::max(fa.numRegs, 1));
+        const int per_sm = std::max(1, std::min(per_sm_tmem, std::min(by_smem, by_regs)));
+        const int ntiles = (Nn + NT - 1) / NT;
+        const long long planes = (long long)g.batch * ((g.in_h + 7) / 8) * ((g.in_w + 13) / 14) * g.in_d;
+        long long gx = std::max(1ll, (long long)sms * per_sm / ntiles);
+        if (gx > planes) gx = planes;
+        const dim3 grid((unsigned)gx, (unsigned)ntiles);
+        if (NT == 32)
+            conv3_ws_kernel<32><<<grid, 256, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb, R);
+        else
+            conv3_ws_kernel<16><<<grid, 256, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb, R);
+        return cudaGetLastError();
+    }
     if (FDC_CONV_DWALK && Cs <= 32 && Nn % 16 == 0) {
         int dev = 0, sms = 0, smem_sm = 0;
         cudaError_t e = cudaGetDevice(&dev);
@@ -1524,6 +1948,8 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
     return cudaGetLastError();
 }
 
+bool conv_dwalk_enabled() { return FDC_CONV_WS != 0 || FDC_CONV_DWALK != 0; }
+
 cudaError_t launch_wait_timeout(long long cycles, cudaStream_t st) {
     wait_timeout_kernel<<<1, 32, 0, st>>>(cycles);
     return cudaGetLastError();
@@ -1568,7 +1994,8 @@ cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const vo
 }
 
 cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy, float *dw, float *db,
-                              cudaStream_t st) {
+                              cudaStream_t st, int ca, int up_a, const void *xb) {
+    if (ca <= 0) ca = g.c_in;
     const long long rows = (long long)g.batch * g.out_d * g.out_h * g.out_w;
     if (FDC_WGRAD_HALO && g.ksize == 3 && g.stride == 1 && g.pad == 1) {
         const long long blocks = (long long)g.batch * ((g.in_d + 1) / 2) * ((g.in_h + 7) / 8) * ((g.in_w + 7) / 8);
@@ -1578,7 +2005,7 @@ cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy
         if (per < 1) per = 1;
         dim3 grid((unsigned)per, (unsigned)(g.c_out / 16), (unsigned)(g.c_in / 16));
         conv3_wgrad_halo_kernel<<<grid, 128, 0, st>>>(g, (const __nv_bfloat16 *)x, (const __nv_bfloat16 *)dy, dw,
-                                                      db);
+                                                      db, ca, up_a, (const __nv_bfloat16 *)xb);
         return cudaGetLastError();
     }
     const int taps = g.ksize * g.ksize * g.ksize;
@@ -1710,6 +2137,10 @@ fdc::Conv3dArgs to_args(const fdc_conv3d *g) {
     a.c_in = g->c_in; a.c_out = g->c_out;
     a.ksize = g->ksize; a.stride = g->stride; a.pad = g->pad; a.relu = g->relu ? 1 : 0;
     a.mask = nullptr;
+    a.mask_b = nullptr;
+    a.mask_ca = 0;
+    a.mask_up = 0;
+    a.out_b = nullptr;
     return a;
 }
 
@@ -1754,7 +2185,32 @@ int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_
 int fdc_conv3d_backward_weights(const fdc_conv3d *g, const void *x, const void *dy, float *dw, float *db,
                                 void *stream) {
     if (!conv_ok(g) || !x || !dy || !dw) return FDC_ERR_INVALID;
-    return rc(fdc::launch_conv_wgrad(to_args(g), x, dy, dw, db, (cudaStream_t)stream));
+    return rc(fdc::launch_conv_wgrad(to_args(g), x, dy, dw, db, (cudaStream_t)stream, g->c_in, 0, nullptr));
+}
+
+int fdc_conv3d_backward_weights_fused(const fdc_conv3d *g, const void *xa, int32_t ca, int32_t upsample_a,
+                                      const void *xb, const void *dy, float *dw, float *db, void *stream) {
+    if (!conv_ok(g) || !is_k3s1p1(g) || !xa || !dy || !dw) return FDC_ERR_INVALID;
+    if (ca < 16 || ca % 16 || ca > g->c_in || (ca < g->c_in && !xb)) return FDC_ERR_INVALID;
+    if (upsample_a && (g->in_d % 2 || g->in_h % 2 || g->in_w % 2)) return FDC_ERR_INVALID;
+    return rc(fdc::launch_conv_wgrad(to_args(g), xa, dy, dw, db, (cudaStream_t)stream, ca, upsample_a ? 1 : 0, xb));
+}
+
+int fdc_conv3d_backward_data_fused(const fdc_conv3d *g, const void *dy, const void *w_t, const void *xa, int32_t ca,
+                                   int32_t upsample_a, const void *xb, void *dxa, void *dxb, void *stream) {
+    if (!conv_ok(g) || !is_k3s1p1(g) || !dy || !w_t || !xa || !dxa) return FDC_ERR_INVALID;
+    if (g->c_out > 32 || !fdc::conv_dwalk_enabled()) return FDC_ERR_INVALID;  // the d-walking kernels only
+    if (ca < 16 || ca % 16 || ca > g->c_in || (ca < g->c_in && (!xb || !dxb))) return FDC_ERR_INVALID;
+    if (upsample_a && (g->in_d % 2 || g->in_h % 2 || g->in_w % 2)) return FDC_ERR_INVALID;
+    fdc::Conv3dArgs a = to_args(g);
+    a.relu = 0;
+    a.mask = xa;
+    a.mask_b = ca < g->c_in ? xb : nullptr;
+    a.mask_ca = ca;
+    a.mask_up = upsample_a ? 1 : 0;
+    a.out_b = ca < g->c_in ? dxb : nullptr;
+    return rc(fdc::launch_conv_halo(a, dy, w_t, nullptr, dxa, nullptr, g->c_out, g->c_in, 0, (cudaStream_t)stream,
+                                    g->c_out, 0, nullptr));
 }
 
 int fdc_conv3d_transpose_weights(const fdc_conv3d *g, const void *w, void *w_t, void *stream) {

@@ -98,9 +98,10 @@ class ConvLayer:
             self.x, self.y = x, y
         return y
 
-    def forward_fused(self, xa, upsample=False, xb=None):
-        """Inference only: this 3^3 convolution applied to [upsample(xa) | xb]
-        without materialising the upsampled or concatenated input."""
+    def forward_fused(self, xa, upsample=False, xb=None, keep=False):
+        """This 3^3 convolution applied to [upsample(xa) | xb] without
+        materialising the upsampled or concatenated input; with keep, the two
+        parts are kept for the fused gradients (backward)."""
         import torch
         B, D, H, W, ca = xa.shape
         if upsample:
@@ -109,6 +110,9 @@ class ConvLayer:
         y = torch.empty(oshape, dtype=torch.bfloat16, device=self.dev)
         _ok(fdc.lib().fdc_conv3d_forward_fused(C.byref(g), _p(xa), ca, 1 if upsample else 0, _p(xb),
                                                _p(self.w16), _p(self.b32), _p(y), None, _s()), "conv forward fused")
+        if keep:
+            self.x, self.y = None, y
+            self.fused_in = (xa, bool(upsample), xb, (B, D, H, W, self.cin))
         return y
 
     def backward(self, dy, need_dx=True):
@@ -116,9 +120,28 @@ class ConvLayer:
         ReLU derivative already applied: every layer's input is the output of
         a ReLU layer, and the data gradient below masks dx by x > 0 in its
         epilogue, which is that derivative for the layer before).  Returns
-        the gradient with respect to the previous layer's pre-activation."""
+        the gradient with respect to the previous layer's pre-activation; after
+        forward_fused(keep=True), the pair (d xa, d xb) for a concatenated input
+        (d xa at full resolution when xa was upsampled), or d xa alone."""
         import torch
         L = fdc.lib()
+        if getattr(self, "fused_in", None) is not None:
+            xa, up, xb, shape = self.fused_in
+            g, _ = self.geom(shape)
+            ca = xa.shape[-1]
+            _ok(L.fdc_conv3d_backward_weights_fused(C.byref(g), _p(xa), ca, 1 if up else 0, _p(xb), _p(dy),
+                                                    _p(self.gw), _p(self.gb), _s()), "conv wgrad fused")
+            out = None
+            if need_dx:
+                dxa = torch.empty(shape[:4] + (ca,), dtype=torch.bfloat16, device=self.dev)
+                dxb = (torch.empty(shape[:4] + (self.cin - ca,), dtype=torch.bfloat16, device=self.dev)
+                       if xb is not None else None)
+                _ok(L.fdc_conv3d_backward_data_fused(C.byref(g), _p(dy), _p(self.wt16), _p(xa), ca, 1 if up else 0,
+                                                     _p(xb), _p(dxa), _p(dxb), _s()), "conv dgrad fused")
+                out = (dxa, dxb) if xb is not None else dxa
+            self.fused_in = None
+            self.y = None
+            return out
         g, _ = self.geom(tuple(self.x.shape))
         _ok(L.fdc_conv3d_backward_weights(C.byref(g), _p(self.x), _p(dy), _p(self.gw), _p(self.gb), _s()),
             "conv wgrad")
@@ -227,10 +250,10 @@ class UNet:
         e2 = self._seq(self.enc2, self.down1.forward(e1, keep), keep)
         e3 = self._seq(self.enc3, self.down2.forward(e2, keep), keep)
         b = self._seq(self.bott, self.down3.forward(e3, keep), keep)
-        if keep:  # training: the weight gradients need the materialised inputs
-            f3 = self._seq(self.dec3, _concat(self.up3.forward(_upsample(b), keep), e3), keep)
-            f2 = self._seq(self.dec2, _concat(self.up2.forward(_upsample(f3), keep), e2), keep)
-            f1 = self._seq(self.dec1, _concat(self.up1.forward(_upsample(f2), keep), e1), keep)
+        if keep:  # training
+            f3 = self._decoder_train(self.up3, self.dec3, b, e3)
+            f2 = self._decoder_train(self.up2, self.dec2, f3, e2)
+            f1 = self._decoder_train(self.up1, self.dec1, f2, e1)
         else:  # inference: upsampling and skip concatenation fused into the convolutions
             f = b
             for up, dec, skip in ((self.up3, self.dec3, e3), (self.up2, self.dec2, e2), (self.up1, self.dec1, e1)):
@@ -238,6 +261,31 @@ class UNet:
                 f = dec[1].forward(dec[0].forward_fused(u, xb=skip), False)
             f1 = f
         return self.head.forward(f1, keep)
+
+    @staticmethod
+    def _fuse_level(up):
+        """Decoder levels whose up-convolution has at most 32 output channels
+        (the 128^3 and 64^3 levels) train on the fused inputs: the fused data
+        gradient runs on the d-walking convolution kernels, which need that."""
+        return up.cout <= 32
+
+    def _decoder_train(self, up, dec, f, skip):
+        if self._fuse_level(up):  # upsampled and concatenated inputs are never materialised
+            u = up.forward_fused(f, upsample=True, keep=True)
+            h = dec[0].forward_fused(u, xb=skip, keep=True)
+        else:
+            u = up.forward(_upsample(f), True)
+            h = dec[0].forward(_concat(u, skip), True)
+        return dec[1].forward(h, True)
+
+    def _decoder_back(self, up, dec, d, c):
+        """Gradient of one decoder level: returns (d f, d skip)."""
+        d = dec[1].backward(d)
+        if self._fuse_level(up):
+            dc, dskip = dec[0].backward(d)
+        else:
+            dc, dskip = _split(dec[0].backward(d), c, c)
+        return _upsample(up.backward(dc), backward=True), dskip
 
     @staticmethod
     def _seq_back(layers, dy, need_last=True):
@@ -248,12 +296,9 @@ class UNet:
     def backward(self, dhead):
         c1, c2, c3, _ = self.channels
         d = self.head.backward(dhead)
-        dc, de1 = _split(self._seq_back(self.dec1, d), c1, c1)
-        d = _upsample(self.up1.backward(dc), backward=True)
-        dc, de2 = _split(self._seq_back(self.dec2, d), c2, c2)
-        d = _upsample(self.up2.backward(dc), backward=True)
-        dc, de3 = _split(self._seq_back(self.dec3, d), c3, c3)
-        d = _upsample(self.up3.backward(dc), backward=True)
+        d, de1 = self._decoder_back(self.up1, self.dec1, d, c1)
+        d, de2 = self._decoder_back(self.up2, self.dec2, d, c2)
+        d, de3 = self._decoder_back(self.up3, self.dec3, d, c3)
         d = self.down3.backward(self._seq_back(self.bott, d))
         d = self.down2.backward(self._seq_back(self.enc3, _add(d, de3)))
         d = self.down1.backward(self._seq_back(self.enc2, _add(d, de2)))

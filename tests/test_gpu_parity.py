@@ -448,3 +448,32 @@ def test_autotune_for_shared_tracks_is_not_slower_than_default(thorax_full):
     a = gpu_energy(eng, ph, beam, 78, n=2_000_000, track_group=32)["tally"]
     b = gpu_energy(eng, ph, beam, 78, n=2_000_000, track_group=32, schedule=default)["tally"]
     assert np.array_equal(a, b)
+
+
+def test_32_and_64_bit_step_bookkeeping_agree_bitwise():
+    """Databases whose steps all lose less than 2^32 tally units (16 MeV)
+    run the kernel that keeps a step's running deposit in 32 bits; one
+    extra energy bin that the beam never selects, holding a 20 MeV step,
+    forces the 64-bit form on otherwise identical data.  The tallies agree
+    bit for bit (with rotation, FP32 and FP64 geometry, and local deposits)."""
+    base = synth.water_database(synth.database_energies(6, 120, 180), 200, seed=2, nuclear=True)
+    extra = synth.database_from_tracks([400.0], [[[(20.0, 0.5, 0.0, 0.0, 0.0)]]])
+    n_base = base.step_begin[-1]
+    big = synth.Database(
+        energy=np.concatenate([base.energy, extra.energy]),
+        track_begin=np.concatenate([base.track_begin, base.track_begin[-1:] + 1]),
+        step_begin=np.concatenate([base.step_begin, [n_base + 1]]),
+        dE=np.concatenate([base.dE, extra.dE]), len=np.concatenate([base.len, extra.len]),
+        theta=np.concatenate([base.theta, extra.theta]), phi=np.concatenate([base.phi, extra.phi]),
+        esec=np.concatenate([base.esec, extra.esec]))
+    assert float(base.dE.max()) * (1 << 28) < 2.0 ** 32 - 4096 < 20.0 * (1 << 28)
+    ph = synth.thorax_phantom(seed=7, shape=(96, 96, 64))
+    beam = synth.field_beam(40000, energy=150.0, width=8.0, height=8.0, sigma_e_rel=0.01)
+    e32, e64 = engine(base, ph), engine(big, ph)
+    for kw in (dict(), dict(track_group=32), dict(fp64_geometry=True)):
+        a = gpu_energy(e32, ph, beam, 6, **kw)
+        b = gpu_energy(e64, ph, beam, 6, **kw)
+        assert np.array_equal(a["tally"], b["tally"]), kw
+        assert a["counters"] == b["counters"], kw
+    e32.close()
+    e64.close()

@@ -322,3 +322,57 @@ def test_unet_inference_matches_training_forward():
     b = net.forward(s.x, keep=False)
     torch.cuda.synchronize()
     assert torch.allclose(a, b, rtol=0, atol=1e-3 * float(a.abs().max()))
+
+
+@pytest.mark.parametrize("ca,cb,up,cout", [(32, 0, 1, 16), (16, 16, 0, 16), (32, 32, 0, 32), (64, 0, 1, 32)])
+def test_fused_backward_equals_materialised(ca, cb, up, cout):
+    """The gradients of the fused forward (input [upsample?(xa) | xb] never
+    materialised): the data gradient with the ReLU mask of that input, split
+    by channel, equals fdc_conv3d_backward_data on the materialised input bit
+    for bit; the weight and bias gradients agree with
+    fdc_conv3d_backward_weights to FP32 accumulation order."""
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    L = fdc.lib()
+    rng = np.random.default_rng(ca + 3 * cb + up + cout)
+    D, H, W = 6, 10, 18
+    sa = (1, D // 2, H // 2, W // 2, ca) if up else (1, D, H, W, ca)
+    xat, _ = bf16(np.maximum(rng.normal(size=sa), 0) * (rng.random(sa) < 0.8))  # ReLU outputs with zeros
+    xbt = bf16(np.maximum(rng.normal(size=(1, D, H, W, cb)), 0))[0] if cb else None
+    cin = ca + cb
+    wt, _ = bf16(rng.normal(size=(cout, 3, 3, 3, cin)) / np.sqrt(27 * cin))
+    g, oshape = geom((1, D, H, W, cin), cout, 3, 1, 1, 1)
+    dyt, _ = bf16(rng.normal(size=oshape))
+    full = torch.empty((1, D, H, W, cin), dtype=torch.bfloat16, device="cuda:0")
+    xa_full = xat
+    if up:
+        xa_full = torch.empty((1, D, H, W, ca), dtype=torch.bfloat16, device="cuda:0")
+        assert L.fdc_upsample2(ptr(xat), ptr(xa_full), 1, D // 2, H // 2, W // 2, ca, 0, None) == 0
+    if cb:
+        assert L.fdc_concat_channels(ptr(xa_full), ca, ptr(xbt), cb, ptr(full), D * H * W, 0, None) == 0
+    else:
+        full.copy_(xa_full)
+    w_t = torch.empty((cin, 3, 3, 3, cout), dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_conv3d_transpose_weights(C.byref(g), ptr(wt), ptr(w_t), None) == 0
+    dx = torch.empty((1, D, H, W, cin), dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_conv3d_backward_data(C.byref(g), ptr(dyt), ptr(w_t), ptr(full), ptr(dx), None) == 0
+    dxa = torch.empty((1, D, H, W, ca), dtype=torch.bfloat16, device="cuda:0")
+    dxb = torch.empty((1, D, H, W, cb), dtype=torch.bfloat16, device="cuda:0") if cb else None
+    assert L.fdc_conv3d_backward_data_fused(C.byref(g), ptr(dyt), ptr(w_t), ptr(xat), ca, up, ptr(xbt), ptr(dxa),
+                                            ptr(dxb), None) == 0
+    dw = torch.zeros((cout, 3, 3, 3, cin), dtype=torch.float32, device="cuda:0")
+    db = torch.zeros(cout, dtype=torch.float32, device="cuda:0")
+    assert L.fdc_conv3d_backward_weights(C.byref(g), ptr(full), ptr(dyt), ptr(dw), ptr(db), None) == 0
+    dwf, dbf = torch.zeros_like(dw), torch.zeros_like(db)
+    assert L.fdc_conv3d_backward_weights_fused(C.byref(g), ptr(xat), ca, up, ptr(xbt), ptr(dyt), ptr(dwf), ptr(dbf),
+                                               None) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(dxa, dx[..., :ca])
+    if cb:
+        assert torch.equal(dxb, dx[..., ca:])
+    torch.testing.assert_close(dwf, dw, rtol=0, atol=1e-5 * float(dw.abs().max()))
+    torch.testing.assert_close(dbf, db, rtol=0, atol=1e-5 * float(db.abs().max()))
+    # the fused data gradient needs the d-walking kernels (at most 32 output channels)
+    g2, _ = geom((1, D, H, W, cin), 64, 3, 1, 1, 1)
+    assert L.fdc_conv3d_backward_data_fused(C.byref(g2), ptr(dyt), ptr(w_t), ptr(xat), ca, up, ptr(xbt), ptr(dxa),
+                                            ptr(dxb), None) == 1
