@@ -705,9 +705,6 @@ constexpr int kDwPlaneSliceBytes = 10 * 512;  // [h 10][w-group 2][k-chunk 2][8 
 #ifndef FDC_CONV_DWALK
 #define FDC_CONV_DWALK 1
 #endif
-#ifndef FDC_CONV_WS
-#define FDC_CONV_WS 1
-#endif
 
 template <int NT>
 __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
@@ -932,331 +929,6 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
     }
     if (!ok && tid == 0) atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
     cp_async_wait<0>();
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
-    }
-}
-
-// Warp-specialised form of the d-walking convolution (same tiles, plane ring
-// and accumulators as conv3_dwalk_kernel; input channels Cs <= 32, NT = 16 or
-// 32), 256 threads in three roles joined by mbarriers instead of CTA-wide
-// barriers:
-//   producers (warps 0, 1, 3): stage the planes of the CTA's ranges into the
-//     ring with cp.async, keeping kWsInflight planes in flight per thread; a
-//     plane is published (fence.proxy.async, then an arrive on full[slot])
-//     once the thread's copies of it have landed, and a slot is reused only
-//     after empty[slot] says the MMAs that read its previous plane finished;
-//   MMA issuer (warp 2, one thread): per output plane waits for its newest
-//     input plane and a free accumulator, issues the 9 * Cs / 16 MMAs,
-//     commits to acc_full[b] and to empty[] of the plane no later output
-//     reads (the last two planes of a range at its end);
-//   epilogue (warps 4-7, TMEM lane quarters 0-3): waits for acc_full[b],
-//     loads the accumulator, releases it (acc_empty[b]) and then combines the
-//     kw columns, adds bias, applies ReLU or the ReLU mask and stores.
-// Every wait is bounded; a timeout raises a shared abort flag that every
-// other wait also watches, records FDC_ERR_TIMEOUT and the CTA winds down.
-constexpr int kWsInflight = 3;  // planes in flight per producer thread (<= ring slots - 3)
-
-__device__ __forceinline__ bool mbar_wait_abort(unsigned mbar, unsigned parity, volatile int *abort) {
-    const long long t0 = clock64();
-    for (;;) {
-        unsigned ok;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (*abort) return false;
-        if (clock64() - t0 > kTcWaitCycles) {
-            *abort = 1;
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned mbar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
-}
-
-template <int NT>
-__global__ void __launch_bounds__(256) conv3_ws_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
-                                                       const __nv_bfloat16 *wt, const float *bias,
-                                                       __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn,
-                                                       int relu, int ca, int up_a, const __nv_bfloat16 *src_b,
-                                                       int R) {
-    constexpr int N3 = 3 * NT;
-    constexpr unsigned kAccCols = N3 <= 64 ? 64 : 128;
-    constexpr unsigned kCols = 2 * kAccCols;
-    constexpr int kMaxR = 10;
-    constexpr int kProducers = 96;
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) unsigned long long bar_full[kMaxR], bar_empty[kMaxR], bar_acc_full[2],
-        bar_acc_empty[2];
-    __shared__ unsigned tmem_slot;
-    __shared__ volatile int abort_flag;
-    __shared__ float sBias[NT];  // the CTA's output channels are fixed: bias staged once
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int D = g.in_d, H = g.in_h, W = g.in_w;
-    const int S = Cs / 16;
-    const int plane_bytes = S * kDwPlaneSliceBytes;
-    const int wbytes = S * 9 * 2 * N3 * 16;
-    unsigned char *sW = smem;
-    unsigned char *sP = smem + wbytes;
-    const int tiles_w = (W + 13) / 14, tiles_h = (H + 7) / 8;
-    const long long n_cols = (long long)g.batch * tiles_h * tiles_w;
-    const long long total = n_cols * D;
-    const long long q_begin = total * blockIdx.x / gridDim.x, q_end = total * (blockIdx.x + 1) / gridDim.x;
-    const int n0 = blockIdx.y * NT;
-    const int cb = Cs - ca;
-    const int Da = up_a ? D / 2 : D, Ha = up_a ? H / 2 : H, Wa = up_a ? W / 2 : W;
-
-    if (tid == 0) {
-        for (int i = 0; i < R; ++i) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&bar_full[i])), "r"(kProducers));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar_empty[i])));
-        }
-        for (int i = 0; i < 2; ++i) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar_acc_full[i])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;\n" ::"r"(smem_u32(&bar_acc_empty[i])));
-        }
-        abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(kCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-    }
-    if (tid < NT) sBias[tid] = (bias && n0 + tid < Nn) ? bias[n0 + tid] : 0.f;
-    // resident weights (every thread helps; they land before the first plane is published)
-    {
-        constexpr int kChunks = 9 * 2 * N3;
-        for (int i = tid; i < S * kChunks; i += 256) {
-            const int sl = i / kChunks, r = i % kChunks;
-            const int n = r % N3, q = r / N3, kc = q & 1, kdh = q >> 1;
-            const int co = n0 + (n % NT), kw = n / NT;
-            const bool in = co < Nn;
-            const __nv_bfloat16 *p = in ? wt + (size_t)((co * 27 + kdh * 3 + kw) * Cs + sl * 16 + kc * 8) : wt;
-            cp_async16_ca(sW + i * 16, p, in);
-        }
-        cp_async_commit();
-        cp_async_wait<0>();
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const unsigned tmem = tmem_slot;
-
-    // the CTA's ranges: (column, first plane, number of planes), decoded identically by every role
-    struct Range {
-        int w0, h0, b, d_begin, nd;
-    };
-    auto range_at = [&](long long q, Range &r) {
-        const long long col = q / D;
-        r.d_begin = (int)(q % D);
-        r.nd = (int)(q_end - q < (long long)(D - r.d_begin) ? q_end - q : (long long)(D - r.d_begin));
-        long long t = col;
-        r.w0 = (int)(t % tiles_w) * 14; t /= tiles_w;
-        r.h0 = (int)(t % tiles_h) * 8;
-        r.b = (int)(t / tiles_h);
-    };
-
-    if (warp == 0 || warp == 1 || warp == 3) {
-        // ---------------- producers
-        const int pt = warp == 3 ? 64 + lane : tid;  // 0 .. 95
-        const int kc = pt & 1, hw = (pt >> 1) & 15, r0 = pt >> 5;
-        const unsigned hdst = (unsigned)((((hw >> 3) * 2 + kc) * 128) + (hw & 7) * 16);
-        long long P = 0;  // planes issued
-        bool live = true;
-        for (long long q = q_begin; q < q_end && live;) {
-            Range rg;
-            range_at(q, rg);
-            q += rg.nd;
-            const int w = rg.w0 - 1 + hw;
-            const bool w_in = w >= 0 && w < W;
-            for (int j = 0; j <= rg.nd + 1 && live; ++j, ++P) {
-                const int slot = (int)(P % R);
-                if (P >= R && !mbar_wait_abort(smem_u32(&bar_empty[slot]), (unsigned)((P / R - 1) & 1), &abort_flag)) {
-                    live = false;
-                    break;
-                }
-                const int d = rg.d_begin - 1 + j;
-                const bool d_in = w_in && d >= 0 && d < D;
-                unsigned char *dst = sP + slot * plane_bytes + hdst;
-                for (int r = r0; r < S * 10; r += 3) {
-                    const int sl = r / 10, hh = r - 10 * sl;
-                    const int h = rg.h0 - 1 + hh, c0 = sl * 16;
-                    const bool in = d_in && h >= 0 && h < H;
-                    const __nv_bfloat16 *p = src;
-                    if (in) {
-                        if (c0 >= ca)
-                            p = src_b + ((((long long)rg.b * D + d) * H + h) * W + w) * cb + (c0 - ca) + kc * 8;
-                        else if (up_a)
-                            p = src + ((((long long)rg.b * Da + (d >> 1)) * Ha + (h >> 1)) * Wa + (w >> 1)) * ca + c0 +
-                                kc * 8;
-                        else
-                            p = src + ((((long long)rg.b * D + d) * H + h) * W + w) * ca + c0 + kc * 8;
-                    }
-                    cp_async16(dst + r * 512, p, in);
-                }
-                cp_async_commit();
-                if (P >= kWsInflight) {  // plane P - kWsInflight has landed: publish it
-                    cp_async_wait<kWsInflight>();
-                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                    mbar_arrive(smem_u32(&bar_full[(int)((P - kWsInflight) % R)]));
-                }
-            }
-        }
-        cp_async_wait<0>();
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        if (live)  // publish the last planes still in flight
-            for (long long k = P - kWsInflight < 0 ? 0 : P - kWsInflight; k < P; ++k)
-                mbar_arrive(smem_u32(&bar_full[(int)(k % R)]));
-    } else if (warp == 2) {
-        // ---------------- MMA issuer
-        if (lane == 0) {
-            long long P = 0, O = 0;  // planes consumed, outputs issued
-            const unsigned wa = smem_u32(sW);
-            constexpr unsigned idesc = umma_idesc(128, N3);
-            bool live = true;
-            for (long long q = q_begin; q < q_end && live;) {
-                Range rg;
-                range_at(q, rg);
-                q += rg.nd;
-                const long long base = P;
-                // the first two planes of the range
-                for (int j = 0; j < 2 && live; ++j)
-                    live = mbar_wait_abort(smem_u32(&bar_full[(int)((base + j) % R)]),
-                                           (unsigned)(((base + j) / R) & 1), &abort_flag);
-                for (int i = 0; i < rg.nd && live; ++i, ++O) {
-                    const long long pn = base + i + 2;
-                    const unsigned b = (unsigned)(O & 1);
-                    if (!mbar_wait_abort(smem_u32(&bar_full[(int)(pn % R)]), (unsigned)((pn / R) & 1), &abort_flag) ||
-                        (O >= 2 && !mbar_wait_abort(smem_u32(&bar_acc_empty[b]), (unsigned)(((O >> 1) - 1) & 1),
-                                                    &abort_flag))) {
-                        live = false;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    unsigned long long ad_kd[3];
-                    const int s0 = (int)((base + i) % R);
-#pragma unroll
-                    for (int kd = 0; kd < 3; ++kd) {
-                        int sk = s0 + kd;
-                        if (sk >= R) sk -= R;
-                        ad_kd[kd] = umma_desc(smem_u32(sP) + sk * plane_bytes, 128, 256);
-                    }
-                    const unsigned long long bd0 = umma_desc(wa, N3 * 16, 128);
-#pragma unroll 1
-                    for (int sl = 0; sl < S; ++sl) {
-#pragma unroll
-                        for (int kdh = 0; kdh < 9; ++kdh) {
-                            const unsigned long long ad = ad_kd[kdh / 3] +
-                                (unsigned long long)((sl * kDwPlaneSliceBytes + (kdh % 3) * 512) >> 4);
-                            const unsigned long long bd =
-                                bd0 + (unsigned long long)(((sl * 9 + kdh) * 2 * N3 * 16) >> 4);
-                            umma_bf16(tmem + b * kAccCols, ad, bd, idesc, (sl | kdh) != 0);
-                        }
-                    }
-                    umma_commit(smem_u32(&bar_acc_full[b]));
-                    umma_commit(smem_u32(&bar_empty[(int)((base + i) % R)]));  // no later output reads plane base + i
-                }
-                if (live) {
-                    umma_commit(smem_u32(&bar_empty[(int)((base + rg.nd) % R)]));
-                    umma_commit(smem_u32(&bar_empty[(int)((base + rg.nd + 1) % R)]));
-                }
-                P = base + rg.nd + 2;
-            }
-        }
-        __syncwarp();
-    } else {
-        // ---------------- epilogue (warps 4-7: TMEM lanes 32 (warp - 4) ...)
-        const int qw = warp - 4;
-        const int m = qw * 32 + lane;
-        long long O = 0;
-        bool live = true;
-        for (long long q = q_begin; q < q_end && live;) {
-            Range rg;
-            range_at(q, rg);
-            q += rg.nd;
-            const int ho = rg.h0 + (m >> 4), wl = m & 15, wo = rg.w0 + wl;
-            const bool out_in = wl < 14 && ho < H && wo < W;
-            for (int i = 0; i < rg.nd; ++i, ++O) {
-                const unsigned b = (unsigned)(O & 1);
-                if (!__all_sync(0xffffffffu, mbar_wait_abort(smem_u32(&bar_acc_full[b]), (unsigned)((O >> 1) & 1),
-                                                            &abort_flag))) {
-                    live = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const unsigned base = tmem + ((unsigned)(qw * 32) << 16) + b * kAccCols;
-                float acc[NT / 16][3][16];
-#pragma unroll
-                for (int c = 0; c < NT / 16; ++c) {
-                    tmem_ld16(base + (unsigned)(c * 16), acc[c][0]);
-                    tmem_ld16(base + (unsigned)(NT + c * 16), acc[c][1]);
-                    tmem_ld16(base + (unsigned)(2 * NT + c * 16), acc[c][2]);
-                }
-                // the accumulator is in registers: hand it back to the MMA issuer
-                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                mbar_arrive(smem_u32(&bar_acc_empty[b]));
-                const long long v = (((long long)rg.b * D + rg.d_begin + i) * H + ho) * W + wo;
-#pragma unroll
-                for (int c = 0; c < NT / 16; ++c) {
-                    float *a0 = acc[c][0];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        a0[j] += __shfl_down_sync(0xffffffffu, acc[c][1][j], 1) +
-                                 __shfl_down_sync(0xffffffffu, acc[c][2][j], 2);
-                    const int n = n0 + c * 16;
-                    if (!out_in || n >= Nn) continue;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        float x = a0[j];
-                        if (bias) x += sBias[c * 16 + j];
-                        if (relu) x = fmaxf(x, 0.f);
-                        a0[j] = x;
-                    }
-                    if (g.mask) {
-                        if (g.mask_ca > 0)
-                            apply_relu_mask16_fused(g, Nn, rg.b, rg.d_begin + i, ho, wo, D, H, W, n, a0);
-                        else
-                            apply_relu_mask16(g.mask, v, Nn, n, a0);
-                    }
-                    if (out_f32) {
-                        float4 *dst = (float4 *)(out_f32 + v * Nn + n);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            dst[j] = make_float4(a0[4 * j], a0[4 * j + 1], a0[4 * j + 2], a0[4 * j + 3]);
-                    }
-                    if (out_bf16) {
-                        uint4 qv[2];
-                        unsigned *qq = (unsigned *)qv;
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            __nv_bfloat162 p2 = __floats2bfloat162_rn(a0[2 * j], a0[2 * j + 1]);
-                            qq[j] = *(unsigned *)&p2;
-                        }
-                        // split output: channels >= mask_ca into out_b
-                        uint4 *dst = g.out_b == nullptr
-                                         ? (uint4 *)(out_bf16 + v * Nn + n)
-                                         : (n < g.mask_ca ? (uint4 *)(out_bf16 + v * g.mask_ca + n)
-                                                          : (uint4 *)((__nv_bfloat16 *)g.out_b + v * (Nn - g.mask_ca) +
-                                                                      (n - g.mask_ca)));
-                        dst[0] = qv[0];
-                        dst[1] = qv[1];
-                    }
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if (tid == 0 && abort_flag) atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -1823,46 +1495,6 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
     auto sb = (const __nv_bfloat16 *)src_b;
     // input channels <= 32 (the 128^3 and 64^3 levels of the network): the
     // d-walking kernel, CTAs spread over the flattened (tile, d) planes
-    if (FDC_CONV_WS && Cs <= 32 && Nn % 16 == 0) {
-        // warp-specialised d-walking kernel: ring of R >= kWsInflight + 3 slots
-        int dev = 0, sms = 0, smem_sm = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        if (e != cudaSuccess) return e;
-        const int S = Cs / 16;
-        const int NT = Nn % 32 == 0 ? 32 : 16;
-        const int wbytes = S * 9 * 2 * (3 * NT) * 16;
-        const int plane = S * kDwPlaneSliceBytes;
-        const int per_sm_tmem = NT == 32 ? 2 : 4;
-        const int budget = smem_sm / per_sm_tmem - 2048;
-        const int R = std::max(kWsInflight + 3, std::min(10, (budget - wbytes) / plane));
-        const int smem = wbytes + R * plane;
-        cudaFuncAttributes fa;
-        if (NT == 32) {
-            static OccCache cache;
-            e = prepare_kernel_smem(cache, conv3_ws_kernel<32>, smem);
-            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv3_ws_kernel<32>);
-        } else {
-            static OccCache cache;
-            e = prepare_kernel_smem(cache, conv3_ws_kernel<16>, smem);
-            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv3_ws_kernel<16>);
-        }
-        if (e != cudaSuccess) return e;
-        const int by_smem = smem_sm / (smem + (int)fa.sharedSizeBytes + 1024);
-        const int by_regs = 65536 / (256 * std::max(fa.numRegs, 1));
-        const int per_sm = std::max(1, std::min(per_sm_tmem, std::min(by_smem, by_regs)));
-        const int ntiles = (Nn + NT - 1) / NT;
-        const long long planes = (long long)g.batch * ((g.in_h + 7) / 8) * ((g.in_w + 13) / 14) * g.in_d;
-        long long gx = std::max(1ll, (long long)sms * per_sm / ntiles);
-        if (gx > planes) gx = planes;
-        const dim3 grid((unsigned)gx, (unsigned)ntiles);
-        if (NT == 32)
-            conv3_ws_kernel<32><<<grid, 256, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb, R);
-        else
-            conv3_ws_kernel<16><<<grid, 256, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb, R);
-        return cudaGetLastError();
-    }
     if (FDC_CONV_DWALK && Cs <= 32 && Nn % 16 == 0) {
         int dev = 0, sms = 0, smem_sm = 0;
         cudaError_t e = cudaGetDevice(&dev);
@@ -1948,7 +1580,7 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
     return cudaGetLastError();
 }
 
-bool conv_dwalk_enabled() { return FDC_CONV_WS != 0 || FDC_CONV_DWALK != 0; }
+bool conv_dwalk_enabled() { return FDC_CONV_DWALK != 0; }
 
 cudaError_t launch_wait_timeout(long long cycles, cudaStream_t st) {
     wait_timeout_kernel<<<1, 32, 0, st>>>(cycles);

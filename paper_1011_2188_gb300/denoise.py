@@ -234,6 +234,40 @@ class UNet:
         self.head = L(c1, 16, 1, 1, 0, relu=False, f32_out=True)
         self.channels = channels
         self.t = 0
+        self._flatten()
+
+    def _flatten(self):
+        """All layers' FP32 weights and biases, their gradients, Adam moments
+        and BF16 copies become views of five flat buffers, so that one fill
+        zeroes every gradient and one Adam launch updates every parameter.
+        Every tensor holds a multiple of 16 elements, so each view starts on
+        a 64-byte (FP32) / 32-byte (BF16) boundary."""
+        import torch
+        layers = self.layers()
+        n = sum(l.w32.numel() + l.b32.numel() for l in layers)
+        dev = layers[0].dev
+        self.p32 = torch.empty(n, dtype=torch.float32, device=dev)
+        self.g32 = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.m32 = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.v32 = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.p16 = torch.empty(n, dtype=torch.bfloat16, device=dev)
+        o = 0
+        for l in layers:
+            for pn, gn, mn, vn in (("w32", "gw", "mw", "vw"), ("b32", "gb", "mb", "vb")):
+                t = getattr(l, pn)
+                k = t.numel()
+                assert k % 16 == 0 and o % 16 == 0
+                view = self.p32[o:o + k].view(t.shape)
+                view.copy_(t)
+                setattr(l, pn, view)
+                setattr(l, gn, self.g32[o:o + k].view(t.shape))
+                setattr(l, mn, self.m32[o:o + k].view(t.shape))
+                setattr(l, vn, self.v32[o:o + k].view(t.shape))
+                if pn == "w32":
+                    l.w16 = self.p16[o:o + k].view(t.shape)
+                o += k
+        for l in layers:
+            l.sync_weights()
 
     def layers(self):
         return (self.enc1 + [self.down1] + self.enc2 + [self.down2] + self.enc3 + [self.down3] + self.bott +
@@ -305,13 +339,19 @@ class UNet:
         self._seq_back(self.enc1, _add(d, de1), need_last=False)
 
     def zero_grad(self):
-        for l in self.layers():
-            l.zero_grad()
+        self.g32.zero_()
 
-    def step(self, lr):
+    def step(self, lr, b1=0.9, b2=0.999, eps=1e-8):
+        """One Adam step over every parameter (one launch on the flat
+        buffers, BF16 copies included), then each layer's data-gradient
+        weights from its new BF16 weights."""
         self.t += 1
+        L = fdc.lib()
+        _ok(L.fdc_adam(_p(self.p32), _p(self.g32), _p(self.m32), _p(self.v32), _p(self.p16), self.p32.numel(),
+                       lr, b1, b2, eps, self.t, _s()), "adam")
         for l in self.layers():
-            l.step(lr, self.t)
+            g, _ = l.geom((1, 8, 8, 8, l.cin))
+            _ok(L.fdc_conv3d_transpose_weights(C.byref(g), _p(l.w16), _p(l.wt16), _s()), "transpose")
 
     def state(self):
         return [l.state() for l in self.layers()]
