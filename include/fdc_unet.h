@@ -111,7 +111,8 @@ int fdc_add_bf16(const void *a, const void *b, void *out, int64_t n, void *strea
  * density * density_scale, channels 2..15 zero; dose_in [n] FP32 = channel 0.
  * With dose_high (a high-history dose of the same field) and target not NULL,
  * target [n] FP32 = dose_high / dose_scale - dose_in, the correction the
- * network is trained to predict. */
+ * network is trained to predict.  x must be 16-byte aligned (rows are
+ * written as 16-byte pieces); FDC_ERR_INVALID otherwise. */
 int fdc_unet_prepare(const double *dose, const float *density, const double *dose_high, int64_t n,
                      double dose_scale, float density_scale, void *x, float *dose_in, float *target,
                      void *stream);

@@ -109,17 +109,42 @@ __global__ void __launch_bounds__(128) conv_igemm_kernel(const Conv3dArgs g, con
     const int Wr = MODE == 0 ? g.out_w : g.in_w;
     const int Cs = MODE == 0 ? g.c_in : g.c_out;   // gathered channels (K per tap)
     const int Nn = MODE == 0 ? g.c_out : g.c_in;   // output channels
-    const long long rows = (long long)g.batch * Dr * Hr * Wr;
+    // Data gradient of a convolution whose kernel tiles its input (stride =
+    // ksize, no padding: the 2^3 stride-2 down-convolutions): input voxel
+    // (d, h, w) receives exactly one tap, (d, h, w) mod stride.  The rows are
+    // then the input voxels of one parity class (blockIdx.z), a sub-grid of
+    // stride^3 spacing, and K runs over that one tap's channels only.
+    const bool par = MODE == 1 && g.stride == g.ksize && g.pad == 0;
+    int pd = 0, ph = 0, pw = 0, Dq = Dr, Hq = Hr, Wq = Wr;
+    if (par) {
+        const int st = g.stride, cls = blockIdx.z;
+        pd = cls / (st * st); ph = (cls / st) % st; pw = cls % st;
+        Dq = (Dr - pd + st - 1) / st; Hq = (Hr - ph + st - 1) / st; Wq = (Wr - pw + st - 1) / st;
+    }
+    const long long rows = (long long)g.batch * Dq * Hq * Wq;
     const long long r0 = (long long)blockIdx.x * kRows;
+    if (r0 >= rows) return;  // parity classes with fewer rows than the grid
     const int n0 = blockIdx.y * NT;
     const int taps = g.ksize * g.ksize * g.ksize;
+    const int tap_par = (pd * g.ksize + ph) * g.ksize + pw;
     const int csteps = Cs / 16;
-    const int ksteps = taps * csteps;
+    const int ksteps = par ? csteps : taps * csteps;
+    // the voxel (in the D x H x W row space) of row r of this grid
+    auto row_voxel = [&](long long r, RowCoord &c) {
+        c = row_coord(r, rows, Dq, Hq, Wq);
+        if (par) {
+            c.d = c.d * g.stride + pd;
+            c.h = c.h * g.stride + ph;
+            c.w = c.w * g.stride + pw;
+        }
+        return (((long long)c.b * Dr + c.d) * Hr + c.h) * (long long)Wr + c.w;
+    };
     // this thread gathers row r0 + tid
-    const RowCoord rc = row_coord(r0 + tid, rows, Dr, Hr, Wr);
+    RowCoord rc;
+    row_voxel(r0 + tid, rc);
 
     auto load_stage = [&](int buf, int ks) {
-        const int tap = ks / csteps, c0 = (ks % csteps) * 16;
+        const int tap = par ? tap_par : ks / csteps, c0 = (ks % csteps) * 16;
         const int kd = tap / (g.ksize * g.ksize), kh = (tap / g.ksize) % g.ksize, kw = tap % g.ksize;
         const long long sv = src_voxel<MODE>(rc, kd, kh, kw, g);
         const __nv_bfloat16 *p = sv >= 0 ? src + sv * Cs + c0 : src;
@@ -176,8 +201,10 @@ __global__ void __launch_bounds__(128) conv_igemm_kernel(const Conv3dArgs g, con
     for (int mt = 0; mt < 2; ++mt) {
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
-            const long long r = r0 + warp * 32 + mt * 16 + grp + half * 8;
-            if (r >= rows) continue;
+            const long long rr = r0 + warp * 32 + mt * 16 + grp + half * 8;
+            if (rr >= rows) continue;
+            RowCoord rcv;
+            const long long r = row_voxel(rr, rcv);  // output row in the D x H x W space
 #pragma unroll
             for (int nt = 0; nt < NT / 8; ++nt) {
                 const int n = n0 + nt * 8 + tig * 2;
@@ -705,6 +732,15 @@ constexpr int kDwPlaneSliceBytes = 10 * 512;  // [h 10][w-group 2][k-chunk 2][8 
 #ifndef FDC_CONV_DWALK
 #define FDC_CONV_DWALK 1
 #endif
+// widest input (channels) that takes the d-walking kernel; wider inputs use
+// the kw-stacked kernel (the resident weights and a 5-plane ring must fit)
+#ifndef FDC_CONV_DWALK_MAXC
+#define FDC_CONV_DWALK_MAXC 32
+#endif
+// the d-walking kernel's shared memory at its smallest ring (5 planes) fits one CTA
+inline bool dwalk_fits(int S, int NT) {
+    return S * 9 * 2 * (3 * NT) * 16 + 5 * S * kDwPlaneSliceBytes <= 227 * 1024 - 1024;
+}
 
 template <int NT>
 __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
@@ -1293,15 +1329,22 @@ __global__ void concat_kernel(const __nv_bfloat16 *a, int Ca, const __nv_bfloat1
 // target[rows]; writes the BF16 gradient [rows][C] (zero outside channel 0)
 // and adds the loss to *loss (per-block partial sums).
 __global__ void mse_kernel(const float *pred, int C, const float *target, long long rows, float scale,
-                           __nv_bfloat16 *grad, float *loss) {
+                           __nv_bfloat16 *grad, float *loss, int vec) {
     __shared__ float sm[256];
     float s = 0.f;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
         const float e = pred[r * C] - target[r];
         s += e * e;
         if (grad) {
-            grad[r * C] = __float2bfloat16_rn(2.f * e * scale);
-            for (int c = 1; c < C; ++c) grad[r * C + c] = __float2bfloat16_rn(0.f);
+            if (vec) {  // whole 16-byte groups of the row (C % 8 == 0, aligned): channel 0, then zeros
+                const __nv_bfloat16 g0 = __float2bfloat16_rn(2.f * e * scale);
+                uint4 *row = (uint4 *)(grad + r * C);
+                row[0] = make_uint4((unsigned)*(const unsigned short *)&g0, 0u, 0u, 0u);
+                for (int k = 1; k < C / 8; ++k) row[k] = make_uint4(0u, 0u, 0u, 0u);
+            } else {
+                grad[r * C] = __float2bfloat16_rn(2.f * e * scale);
+                for (int c = 1; c < C; ++c) grad[r * C + c] = __float2bfloat16_rn(0.f);
+            }
         }
     }
     sm[threadIdx.x] = s;
@@ -1349,10 +1392,12 @@ __global__ void prepare_kernel(const double *dose, const float *density, const d
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float d = (float)(dose[i] * inv_scale);
         dose_in[i] = d;
-        __nv_bfloat16 *row = x + i * 16;
-        row[0] = __float2bfloat16_rn(d);
-        row[1] = __float2bfloat16_rn(density[i] * density_scale);
-        for (int c = 2; c < 16; ++c) row[c] = __float2bfloat16_rn(0.f);
+        // the 32-byte row as two 16-byte stores: channels 0 and 1, then zeros
+        const __nv_bfloat162 c01 = __floats2bfloat162_rn(d, density[i] * density_scale);
+        uint4 q0 = make_uint4(*(const unsigned *)&c01, 0u, 0u, 0u);
+        uint4 *row = (uint4 *)(x + i * 16);
+        row[0] = q0;
+        row[1] = make_uint4(0u, 0u, 0u, 0u);
         if (target) target[i] = (float)(dose_high[i] * inv_scale) - d;
     }
 }
@@ -1495,7 +1540,8 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
     auto sb = (const __nv_bfloat16 *)src_b;
     // input channels <= 32 (the 128^3 and 64^3 levels of the network): the
     // d-walking kernel, CTAs spread over the flattened (tile, d) planes
-    if (FDC_CONV_DWALK && Cs <= 32 && Nn % 16 == 0) {
+    if (FDC_CONV_DWALK && Cs <= FDC_CONV_DWALK_MAXC && Nn % 16 == 0 &&
+        dwalk_fits(Cs / 16, Nn % 32 == 0 ? 32 : 16)) {
         int dev = 0, sms = 0, smem_sm = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1609,7 +1655,14 @@ cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const vo
     const long long rows = (long long)g.batch * (mode == 0 ? (long long)g.out_d * g.out_h * g.out_w
                                                           : (long long)g.in_d * g.in_h * g.in_w);
     const int nt = Nn >= 64 ? 64 : (Nn >= 32 ? 32 : 16);
-    dim3 grid((unsigned)((rows + kRows - 1) / kRows), (unsigned)((Nn + nt - 1) / nt));
+    // data gradient of a tiling convolution: one grid layer per parity class
+    const bool par = mode == 1 && g.stride == g.ksize && g.pad == 0;
+    const int classes = par ? g.stride * g.stride * g.stride : 1;
+    long long rows_c = rows;
+    if (par)  // the largest class (parity 0 in every dimension)
+        rows_c = (long long)g.batch * ((g.in_d + g.stride - 1) / g.stride) * ((g.in_h + g.stride - 1) / g.stride) *
+                 ((g.in_w + g.stride - 1) / g.stride);
+    dim3 grid((unsigned)((rows_c + kRows - 1) / kRows), (unsigned)((Nn + nt - 1) / nt), (unsigned)classes);
     auto s = (const __nv_bfloat16 *)src;
     auto w = (const __nv_bfloat16 *)wt;
     auto ob = (__nv_bfloat16 *)out_bf16;
@@ -1686,7 +1739,9 @@ cudaError_t launch_concat(const void *a, int Ca, const void *b, int Cb, void *ou
 
 cudaError_t launch_mse(const float *pred, int C, const float *target, long long rows, void *grad, float *loss,
                        cudaStream_t st) {
-    mse_kernel<<<grid_for(rows), 256, 0, st>>>(pred, C, target, rows, 1.0f / (float)rows, (__nv_bfloat16 *)grad, loss);
+    const int vec = (C % 8 == 0 && ((uintptr_t)grad & 15) == 0) ? 1 : 0;
+    mse_kernel<<<grid_for(rows), 256, 0, st>>>(pred, C, target, rows, 1.0f / (float)rows, (__nv_bfloat16 *)grad, loss,
+                                               vec);
     return cudaGetLastError();
 }
 
@@ -1896,7 +1951,8 @@ int fdc_add_bf16(const void *a, const void *b, void *out, int64_t n, void *strea
 int fdc_unet_prepare(const double *dose, const float *density, const double *dose_high, int64_t n,
                      double dose_scale, float density_scale, void *x, float *dose_in, float *target,
                      void *stream) {
-    if (!dose || !density || !x || !dose_in || n < 1 || !(dose_scale > 0) || (target && !dose_high))
+    if (!dose || !density || !x || !dose_in || n < 1 || !(dose_scale > 0) || (target && !dose_high) ||
+        ((uintptr_t)x & 15))
         return FDC_ERR_INVALID;
     return rc(fdc::launch_prepare(dose, density, dose_high, n, 1.0 / dose_scale, density_scale, x, dose_in,
                                   target, (cudaStream_t)stream));

@@ -53,6 +53,9 @@ CASES = [
     ((2, 9, 17, 29, 32), 16, 3, 1, 1),
     ((1, 12, 9, 30, 32), 32, 3, 1, 1),
     ((1, 1, 8, 14, 16), 16, 3, 1, 1),
+    # stride-2 down-convolution on odd sizes: the last input plane of each
+    # axis reaches no output (zero data gradient), parity classes of unequal size
+    ((2, 7, 5, 9, 16), 32, 2, 2, 0),
 ]
 
 
