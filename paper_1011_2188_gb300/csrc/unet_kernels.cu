@@ -735,7 +735,7 @@ constexpr int kDwPlaneSliceBytes = 10 * 512;  // [h 10][w-group 2][k-chunk 2][8 
 // widest input (channels) that takes the d-walking kernel; wider inputs use
 // the kw-stacked kernel (the resident weights and a 5-plane ring must fit)
 #ifndef FDC_CONV_DWALK_MAXC
-#define FDC_CONV_DWALK_MAXC 32
+#define FDC_CONV_DWALK_MAXC 64
 #endif
 // the d-walking kernel's shared memory at its smallest ring (5 planes) fits one CTA
 inline bool dwalk_fits(int S, int NT) {
