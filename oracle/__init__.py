@@ -62,7 +62,7 @@ class _Opts(C.Structure):
 class _Out(C.Structure):
     _fields_ = [("edep", C.c_void_p), ("hh_sumsq", C.c_void_p), ("replayed", C.c_double),
                 ("escaped", C.c_double), ("n_histories", C.c_uint64), ("n_steps", C.c_uint64),
-                ("n_segments", C.c_uint64)]
+                ("n_segments", C.c_uint64), ("hv_sumsq", C.c_void_p)]
 
 
 SPOT_FIELDS = [("x", "<f8"), ("y", "<f8"), ("energy", "<f8"), ("sigma_e", "<f8"),
@@ -155,9 +155,10 @@ def sample(db, beam, seed, h_begin, n, track_group=1, rotate=True):
 
 
 class Result:
-    def __init__(self, edep, hh_sumsq, out):
+    def __init__(self, edep, hh_sumsq, out, hv_sumsq=None):
         self.edep = edep
         self.hh_sumsq = hh_sumsq
+        self.hv_sumsq = hv_sumsq
         self.replayed = out.replayed
         self.escaped = out.escaped
         self.n_histories = int(out.n_histories)
@@ -166,9 +167,11 @@ class Result:
 
 
 def run(db, ph, beam, seed, h_begin=0, h_end=None, track_group=1, scaling_mode=0,
-        per_layer=False, history_squares=False, rotate=True):
+        per_layer=False, history_squares=False, rotate=True, visit_squares=False):
     """Replay histories [h_begin, h_end) in FP64.  Returns a ``Result`` whose
-    ``edep`` is MeV per voxel, shape (nz, ny, nx) or (n_layers, nz, ny, nx)."""
+    ``edep`` is MeV per voxel, shape (nz, ny, nx) or (n_layers, nz, ny, nx);
+    with history_squares, ``hh_sumsq`` sums each history's squared energy per
+    voxel, with visit_squares ``hv_sumsq`` each voxel visit's (MeV^2)."""
     keep = _Keep()
     d = _db_struct(db, keep)
     p = _ph_struct(ph, keep)
@@ -180,13 +183,15 @@ def run(db, ph, beam, seed, h_begin=0, h_end=None, track_group=1, scaling_mode=0
     n_layers = int(np.max(beam["layer"])) + 1 if per_layer else 1
     edep = np.zeros((n_layers, nz, ny, nx), np.float64)
     sq = np.zeros((nz, ny, nx), np.float64) if history_squares else None
-    out = _Out(edep.ctypes.data, sq.ctypes.data if sq is not None else None, 0.0, 0.0, 0, 0, 0)
+    vq = np.zeros((nz, ny, nx), np.float64) if visit_squares else None
+    out = _Out(edep.ctypes.data, sq.ctypes.data if sq is not None else None, 0.0, 0.0, 0, 0, 0,
+               vq.ctypes.data if vq is not None else None)
     opts = _Opts(seed, h_begin, h_end, track_group, scaling_mode, 1 if per_layer else 0,
                  1 if rotate else 0)
     rc = lib().fdco_run(C.byref(d), C.byref(p), sp, ns, C.byref(opts), C.byref(out))
     if rc:
         raise RuntimeError(f"oracle run failed: {rc}")
-    return Result(edep if per_layer else edep[0], sq, out)
+    return Result(edep if per_layer else edep[0], sq, out, vq)
 
 
 def run_parallel(db, ph, beam, seed, h_begin=0, h_end=None, threads=None, **kw):
@@ -216,6 +221,8 @@ def run_parallel(db, ph, beam, seed, h_begin=0, h_end=None, threads=None, **kw):
         res.edep += r.edep
         if res.hh_sumsq is not None:
             res.hh_sumsq += r.hh_sumsq
+        if res.hv_sumsq is not None:
+            res.hv_sumsq += r.hv_sumsq
         res.replayed += r.replayed
         res.escaped += r.escaped
         res.n_histories += r.n_histories

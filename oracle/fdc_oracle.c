@@ -24,7 +24,8 @@
  *             different entry positions.
  *   Sec. 2.4  Eq. (2) history-by-history uncertainty needs per-history sums
  *             of squares; those are produced here exactly (per history, not
- *             per deposit).
+ *             per deposit), and, as a second output, per voxel visit (the
+ *             squares of what a history leaves in a voxel before moving on).
  *
  * Readings of what the paper leaves open (the engine follows the same ones):
  *   - per-step record: (dE, len, theta, phi, esec); theta/phi is the
@@ -98,6 +99,8 @@ typedef struct {
     double replayed;   /* sum over histories of the energy of the replayed steps */
     double escaped;    /* part of it that left the grid */
     uint64_t n_histories, n_steps, n_segments;
+    double *hv_sumsq;  /* optional [nvox]: sum over voxel visits of (visit's energy)^2, a visit
+                          being a maximal run of one history's consecutive deposits into v */
 } or_out;
 
 /* ------------------------------------------------------------------ */
@@ -298,6 +301,37 @@ static void hmap_flush(hmap *m, double *sumsq)
 }
 
 /* ------------------------------------------------------------------ */
+/* Per-visit squares (the reading of Sec. 2.3's second tally that squares */
+/* what one history leaves in a voxel before it moves on): the energy of  */
+/* the current visit is accumulated while deposits go to the same voxel   */
+/* and squared when the next deposit goes elsewhere or the history ends.  */
+
+typedef struct {
+    int64_t v;      /* voxel of the current visit, -1 for none */
+    double e;       /* its energy so far */
+    double *sumsq;  /* [nvox] */
+} or_visit;
+
+static void visit_add(or_visit *vs, int64_t v, double e)
+{
+    if (!vs) return;
+    if (v != vs->v) {
+        if (vs->v >= 0) vs->sumsq[vs->v] += vs->e * vs->e;
+        vs->v = v;
+        vs->e = 0.0;
+    }
+    vs->e += e;
+}
+
+static void visit_end(or_visit *vs)
+{
+    if (!vs) return;
+    if (vs->v >= 0) vs->sumsq[vs->v] += vs->e * vs->e;
+    vs->v = -1;
+    vs->e = 0.0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Direction change: rotate unit vector d by polar angle theta at azimuth */
 /* phi.  Frame attached to d = (dx,dy,dz) with p = sqrt(dx^2+dy^2) > 0:  */
 /*   e2 = (z x d)/p = (-dy, dx, 0)/p,  e1 = e2 x d = (dx dz, dy dz, -p^2)/p */
@@ -334,7 +368,7 @@ static void deflect(double d[3], double theta, double phi, double psi)
 /* Task 2: re-trace one history (Sec. 2.2, 2.3).                        */
 
 static int replay(const or_db *db, const or_phantom *ph, const or_start *st, int scaling_mode,
-                  double *edep_layer, hmap *hm, or_out *out)
+                  double *edep_layer, hmap *hm, or_visit *vs, or_out *out)
 {
     const int64_t s0 = db->step_begin[st->track];
     const int nx = ph->nx, ny = ph->ny, nz = ph->nz;
@@ -418,6 +452,7 @@ static int replay(const or_db *db, const or_phantom *ph, const or_start *st, int
                 double e = dE * rem / len;
                 edep_layer[v] += e;
                 if (hm && e != 0.0 && hmap_add(hm, v, e)) return OR_ERR_NOMEM;
+                visit_add(vs, v, e);
                 acc_k2 += rem * k2;
                 t += rem / S;
                 rem = 0.0;
@@ -427,6 +462,7 @@ static int replay(const or_db *db, const or_phantom *ph, const or_start *st, int
             double e = dE * wet / len;
             edep_layer[v] += e;
             if (hm && e != 0.0 && hmap_add(hm, v, e)) return OR_ERR_NOMEM;
+            visit_add(vs, v, e);
             acc_k2 += wet * k2;
             rem -= wet;
             t = tmax[a];
@@ -444,6 +480,7 @@ static int replay(const or_db *db, const or_phantom *ph, const or_start *st, int
         if (esec != 0.0) {
             edep_layer[v] += esec;
             if (hm && hmap_add(hm, v, esec)) return OR_ERR_NOMEM;
+            visit_add(vs, v, esec);
         }
         /* angle scaling and direction change at the end of the step */
         double theta_m = (double)db->theta[s0 + k] * sqrt(acc_k2 / len);
@@ -497,15 +534,18 @@ int fdco_run(const or_db *db, const or_phantom *ph, const or_spot *spots, int32_
     const int64_t nvox = (int64_t)ph->nx * ph->ny * ph->nz;
     hmap hm;
     int use_hm = out->hh_sumsq != NULL;
+    or_visit visit = {-1, 0.0, out->hv_sumsq};
+    or_visit *vs = out->hv_sumsq ? &visit : NULL;
     if (use_hm && hmap_init(&hm, 1 << 16)) return OR_ERR_NOMEM;
     rc = OR_OK;
     for (uint64_t hh = h_begin; hh < h_end; ++hh) {
         or_start st;
         sample_history(db, spots, n_spots, seed, hh, track_group, rotate, &st);
         double *edep = out->edep + (per_layer ? (int64_t)st.layer * nvox : 0);
-        rc = replay(db, ph, &st, scaling_mode, edep, use_hm ? &hm : NULL, out);
+        rc = replay(db, ph, &st, scaling_mode, edep, use_hm ? &hm : NULL, vs, out);
         if (rc) break;
         if (use_hm) hmap_flush(&hm, out->hh_sumsq);
+        visit_end(vs);
         out->n_histories++;
     }
     if (use_hm) hmap_free(&hm);

@@ -307,13 +307,14 @@ def test_graph_relaunch_matches_direct_launches():
 
 # ------------------------------------------------------------------ eq. (2) second tally
 
-def test_history_squares_against_exact_per_history_squares():
-    """The GPU squares each voxel visit of a history; the oracle squares each
-    history's total per voxel (exact eq. (2) input).  Visit squares can only
-    be smaller (a re-entered voxel splits one history's energy in two
-    squares) and for forward-moving protons they nearly coincide."""
+def test_history_squares_against_the_oracle_visit_squares():
+    """The GPU's second tally squares each voxel visit of a history (the
+    energy a history leaves in a voxel before it moves on): it matches the
+    oracle's per-visit squares on the same histories within 0.1 % of the
+    maximum per voxel and 1e-6 in total; the oracle's exact per-history
+    squares (eq. (2) input) are never smaller, and the eq. (2) uncertainty
+    from the GPU's squares is within 5 % of the exact one on this pencil beam."""
     import torch
-    from paper_1011_2188_gb300 import fdc
     db = synth.water_database([150.0], 300, seed=1)
     ph = synth.slab_phantom()
     beam = synth.pencil_beam(40000, energy=150.0, sigma_cm=0.3)
@@ -323,21 +324,17 @@ def test_history_squares_against_exact_per_history_squares():
     sq = torch.zeros_like(dose)
     tally = torch.zeros(shape, dtype=torch.int64, device="cuda:0")
     eng.run_ex(beam, 0, 21, dose=dose, history_sumsq=sq, tally=tally)
-    cnt = eng.sync()
-    ref = oracle.run(db, ph, beam, seed=21, history_squares=True)
+    eng.sync()
+    ref = oracle.run(db, ph, beam, seed=21, history_squares=True, visit_squares=True)
     # the squares variant leaves the dose itself unchanged
     plain = gpu_energy(eng, ph, beam, 21)
     assert np.array_equal(tally.cpu().numpy(), plain["tally"])
     mass = ph.density.astype(np.float64) * 0.2 ** 3 * 1e-3
     gy_per_mev = 1.602176634e-13 / mass
     sq_mev = sq.cpu().numpy() / gy_per_mev ** 2
-    big = ref.hh_sumsq > 1e-2 * ref.hh_sumsq.max()
-    ratio = sq_mev[big] / ref.hh_sumsq[big]
-    assert ratio.max() <= 1.0 + 1e-4, ratio.max()
-    assert ratio.min() >= 0.8, ratio.min()
-    tot = sq_mev.sum() / ref.hh_sumsq.sum()
-    assert 0.95 <= tot <= 1.0 + 1e-6, tot
-    # eq. (2) on the device vs the oracle's FP64 statistics
+    assert_parity(sq_mev, ref.hv_sumsq, "per-visit squares")
+    assert np.all(ref.hv_sumsq <= ref.hh_sumsq * (1 + 1e-12))
+    # eq. (2) on the device vs the oracle's FP64 statistics of the exact squares
     mean, sigma, rel = eng.history_stats(dose, sq, 40000)
     d_ref = oracle.dose(ph, ref.edep)
     sg_ref = stats.history_sigma(d_ref, ref.hh_sumsq * gy_per_mev ** 2, 40000)

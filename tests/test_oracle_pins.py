@@ -365,6 +365,44 @@ def test_history_squares_exact():
     np.testing.assert_allclose(r.hh_sumsq, sq, rtol=1e-12, atol=1e-12)
 
 
+def test_visit_squares_of_a_back_scattered_track():
+    """Per-visit squares by hand on the back-scattering tiny case: the track
+    deposits 2 MeV in voxel 0, 1 MeV in voxel 4, turns round, deposits
+    2 t_a more in voxel 4 (the same visit: no other voxel in between), then
+    2 (1 - t_a) and 2 t_b in voxel 0 -- a second visit of voxel 0.  The
+    per-history squares see one (summed) visit per voxel."""
+    import math
+    db, ph, beam, opts, exp = tiny_cases.CASES["backscatter"]()
+    r = oracle.run(db, ph, beam, seed=1, rotate=False, history_squares=True, visit_squares=True, **opts)
+    c = -math.cos(tiny_cases.THETA_180)
+    t_a = 0.5 / c
+    z2 = 1.0 - (1.0 - t_a) * c
+    t_b = z2 / c
+    back = 2.0 * (1.0 - t_a) + 2.0 * t_b
+    hv, hh = r.hv_sumsq.reshape(-1), r.hh_sumsq.reshape(-1)
+    assert hv[0] == pytest.approx(2.0 ** 2 + back ** 2, rel=1e-12)
+    assert hv[4] == pytest.approx((1.0 + 2.0 * t_a) ** 2, rel=1e-12)
+    assert hh[0] == pytest.approx((2.0 + back) ** 2, rel=1e-12)
+    assert hh[4] == pytest.approx(hv[4], rel=1e-12)
+    assert np.count_nonzero(hv) == 2
+
+
+def test_visit_squares_equal_history_squares_without_reentry():
+    """Straight tracks along the axis enter every voxel once: the per-visit
+    and per-history squares coincide; with scattering (voxels re-entered)
+    the visit squares are never larger, voxel by voxel (a sum of squares of
+    non-negative parts is at most the square of their sum)."""
+    db = synth.water_database([100.0], 20, seed=4, scatter=False)
+    ph = synth.slab_phantom(n=24, voxel_cm=0.4)
+    beam = synth.pencil_beam(300, energy=100.0, sigma_cm=0.5)
+    r = oracle.run(db, ph, beam, seed=3, history_squares=True, visit_squares=True)
+    np.testing.assert_allclose(r.hv_sumsq, r.hh_sumsq, rtol=1e-12, atol=0)
+    db = synth.water_database([100.0], 20, seed=4)
+    r = oracle.run(db, ph, beam, seed=3, history_squares=True, visit_squares=True)
+    assert np.all(r.hv_sumsq <= r.hh_sumsq * (1 + 1e-12))
+    assert r.hv_sumsq.sum() < r.hh_sumsq.sum()
+
+
 def test_per_layer_tallies_partition_the_run():
     """Per-layer tallies (a history scores into its spot's layer): the layers
     add up to the plain run, and each layer equals a run over exactly the
