@@ -149,6 +149,29 @@ int fdc_debug_wait_timeout(int64_t cycles, void *stream);
 int fdc_unet_finish(const float *head, const float *dose_in, int64_t n, double dose_scale, double *dose_out,
                     void *stream);
 
+/* Head of the denoiser, output channel 0 of its 1^3 convolution (the only
+ * channel the loss and the denoised dose use): for every voxel i of n,
+ * y_i = b[0] + sum_c w[c] x[i][c], with x [n][16] BF16 features (c must be 16;
+ * 16-byte aligned), w the 16 BF16 weights of that output channel (row 0 of the
+ * head's [16][16] weights) and b its FP32 bias (b[0] read on the device).
+ * Products are exact, the sum FP32.  y [n] FP32 (may be NULL) receives y_i;
+ * dose_out [n] FP64 (may be NULL; needs dose_in and dose_scale > 0) receives
+ * max(0, (y_i + dose_in[i]) * dose_scale), the denoised dose in Gy.
+ * FDC_ERR_INVALID on NULL inputs, c != 16, n < 1 or no output. */
+int fdc_unet_head(const void *x, int32_t c, const void *w, const float *b, int64_t n, const float *dose_in,
+                  double dose_scale, float *y, double *dose_out, void *stream);
+/* Loss and gradients of that head: *loss += (1/n) sum_i (y_i - target[i])^2
+ * (FP32, *loss on the device); with g_i = 2 (y_i - target[i]) / n,
+ * dx [n][16] BF16 (may be NULL; 16-byte aligned, not aliasing x) =
+ * bf16(w[c] g_i) where x[i][c] > 0, else 0 (the ReLU derivative of the layer
+ * that produced x); dw [16] FP32 += sum_i g_i x[i][c] and db[0] += sum_i g_i
+ * (both NULL, or both given).  Sums are per-block FP32 partials added with
+ * atomics: their order, and so their last bits, vary from run to run.
+ * FDC_ERR_INVALID on NULL inputs, c != 16, n < 1, misalignment, aliasing, or
+ * exactly one of dw and db. */
+int fdc_unet_head_loss(const void *x, int32_t c, const void *w, const float *b, const float *target, int64_t n,
+                       float *loss, void *dx, float *dw, float *db, void *stream);
+
 /* Gamma index (Low, Harms, Mutic & Purdy 1998) of an evaluated dose against a
  * reference dose on the same d x h x w grid (spacing sd, sh, sw cm; FP64,
  * x fastest): for every reference voxel above threshold * max(ref),

@@ -153,6 +153,10 @@ cudaError_t launch_prepare(const double *dose, const float *density, const doubl
                            cudaStream_t st);
 cudaError_t launch_finish(const float *head, const float *dose_in, long long n, double scale, double *dose_out,
                           cudaStream_t st);
+cudaError_t launch_head(const void *x, const void *w, const float *b, long long n, const float *dose_in,
+                        double scale, float *y, double *dose_out, cudaStream_t st);
+cudaError_t launch_head_loss(const void *x, const void *w, const float *b, const float *target, long long n,
+                             float *loss, void *dx, float *dw, float *db, cudaStream_t st);
 cudaError_t launch_gamma(const double *ref, const double *eval, int D, int H, int W, double sd, double sh, double sw,
                          double dd, double dta, double thr, int radius, float *gamma, unsigned long long *scratch,
                          cudaStream_t st);

@@ -1430,6 +1430,112 @@ __global__ void finish_kernel(const float *head, const float *dose_in, long long
     }
 }
 
+// ---- head of the denoiser: output channel 0 of its 1^3 convolution, the only
+// channel the loss and the denoised dose use: y = b[0] + sum_c w[c] x[c] over
+// the 16 BF16 feature channels of a voxel (exact BF16 products, FP32 sum).
+__device__ __forceinline__ void load_row16(const __nv_bfloat16 *__restrict__ x, long long i, float f[16]) {
+    const uint4 *row = (const uint4 *)(x + i * 16);
+    const uint4 q[2] = {row[0], row[1]};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const unsigned u[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 v = __bfloat1622float2(*(const __nv_bfloat162 *)&u[j]);
+            f[8 * k + 2 * j] = v.x;
+            f[8 * k + 2 * j + 1] = v.y;
+        }
+    }
+}
+
+__device__ __forceinline__ float head_dot(const float w[16], const float f[16], float b0) {
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) s = fmaf(w[c], f[c], s);
+    return s + b0;
+}
+
+// Inference: y (may be NULL) = the correction; dose_out (may be NULL) =
+// max(0, (y + dose_in) * scale).
+__global__ void head_kernel(const __nv_bfloat16 *__restrict__ x, const __nv_bfloat16 *__restrict__ w,
+                            const float *__restrict__ b, long long n, const float *__restrict__ dose_in, double scale,
+                            float *__restrict__ y, double *__restrict__ dose_out) {
+    float wf[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) wf[c] = __bfloat162float(w[c]);
+    const float b0 = b[0];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float f[16];
+        load_row16(x, i, f);
+        const float v = head_dot(wf, f, b0);
+        if (y) y[i] = v;
+        if (dose_out) {
+            const double d = ((double)v + (double)dose_in[i]) * scale;
+            dose_out[i] = d > 0.0 ? d : 0.0;
+        }
+    }
+}
+
+// Training: loss += mean over voxels of (y - target)^2; with g = 2 (y - target) / n,
+// dx (may be NULL) = bf16(w[c] g) where x[c] > 0 (the ReLU derivative of the
+// layer that produced x), else 0; dw[c] += sum g x[c] and db[0] += sum g
+// (dw NULL: no weight gradient).  Block partial sums, one FP32 atomic per
+// block and value.
+__global__ void __launch_bounds__(256) head_loss_kernel(const __nv_bfloat16 *__restrict__ x,
+                                                        const __nv_bfloat16 *__restrict__ w,
+                                                        const float *__restrict__ b, const float *__restrict__ target,
+                                                        long long n, float inv_n, float *loss,
+                                                        __nv_bfloat16 *__restrict__ dx, float *dw, float *db) {
+    __shared__ float part[8][18];
+    float wf[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) wf[c] = __bfloat162float(w[c]);
+    const float b0 = b[0];
+    float acc[18];  // 0..15: weight gradient, 16: bias gradient, 17: squared error
+#pragma unroll
+    for (int k = 0; k < 18; ++k) acc[k] = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float f[16];
+        load_row16(x, i, f);
+        const float e = head_dot(wf, f, b0) - target[i];
+        acc[17] = fmaf(e, e, acc[17]);
+        const float g = 2.f * e * inv_n;
+        if (dx) {
+            unsigned u[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * j] > 0.f ? wf[2 * j] * g : 0.f,
+                                                               f[2 * j + 1] > 0.f ? wf[2 * j + 1] * g : 0.f);
+                u[j] = *(const unsigned *)&h;
+            }
+            uint4 *row = (uint4 *)(dx + i * 16);
+            row[0] = make_uint4(u[0], u[1], u[2], u[3]);
+            row[1] = make_uint4(u[4], u[5], u[6], u[7]);
+        }
+        if (dw) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] = fmaf(g, f[c], acc[c]);
+            acc[16] += g;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+        float v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) part[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 18) {
+        float v = 0.f;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += part[q][threadIdx.x];
+        if (threadIdx.x == 17) atomicAdd(loss, v * inv_n);
+        else if (dw && threadIdx.x == 16) atomicAdd(db, v);
+        else if (dw) atomicAdd(dw + threadIdx.x, v);
+    }
+}
+
 // ---- gamma index (Low et al. 1998), global dose difference
 // gamma(v) = min over evaluated points u within the search radius of
 // sqrt(|u - v|^2 / dta^2 + (eval(u) - ref(v))^2 / (dd * ref_max)^2),
@@ -1778,6 +1884,23 @@ cudaError_t launch_finish(const float *head, const float *dose_in, long long n, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_head(const void *x, const void *w, const float *b, long long n, const float *dose_in,
+                        double scale, float *y, double *dose_out, cudaStream_t st) {
+    head_kernel<<<grid_for(n), 256, 0, st>>>((const __nv_bfloat16 *)x, (const __nv_bfloat16 *)w, b, n, dose_in, scale,
+                                             y, dose_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_head_loss(const void *x, const void *w, const float *b, const float *target, long long n,
+                             float *loss, void *dx, float *dw, float *db, cudaStream_t st) {
+    // a few voxels per thread: the block partials and their atomics stay few
+    long long blocks = (n + 256 * 4 - 1) / (256 * 4);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    head_loss_kernel<<<(int)blocks, 256, 0, st>>>((const __nv_bfloat16 *)x, (const __nv_bfloat16 *)w, b, target, n,
+                                                  1.0f / (float)n, loss, (__nv_bfloat16 *)dx, dw, db);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gamma(const double *ref, const double *eval, int D, int H, int W, double sd, double sh, double sw,
                          double dd, double dta, double thr, int radius, float *gamma, unsigned long long *scratch,
                          cudaStream_t st) {
@@ -1977,6 +2100,22 @@ int fdc_unet_finish(const float *head, const float *dose_in, int64_t n, double d
                     void *stream) {
     if (!head || !dose_in || !dose_out || n < 1 || !(dose_scale > 0)) return FDC_ERR_INVALID;
     return rc(fdc::launch_finish(head, dose_in, n, dose_scale, dose_out, (cudaStream_t)stream));
+}
+
+int fdc_unet_head(const void *x, int32_t c, const void *w, const float *b, int64_t n, const float *dose_in,
+                  double dose_scale, float *y, double *dose_out, void *stream) {
+    if (!x || !w || !b || c != 16 || n < 1 || (!y && !dose_out) || (dose_out && (!dose_in || !(dose_scale > 0))) ||
+        ((uintptr_t)x & 15))
+        return FDC_ERR_INVALID;
+    return rc(fdc::launch_head(x, w, b, n, dose_in, dose_scale, y, dose_out, (cudaStream_t)stream));
+}
+
+int fdc_unet_head_loss(const void *x, int32_t c, const void *w, const float *b, const float *target, int64_t n,
+                       float *loss, void *dx, float *dw, float *db, void *stream) {
+    if (!x || !w || !b || !target || !loss || c != 16 || n < 1 || (!dw != !db) || ((uintptr_t)x & 15) ||
+        ((uintptr_t)dx & 15) || (dx && dx == x))
+        return FDC_ERR_INVALID;
+    return rc(fdc::launch_head_loss(x, w, b, target, n, loss, dx, dw, db, (cudaStream_t)stream));
 }
 
 int fdc_gamma(const double *ref, const double *eval, int32_t d, int32_t h, int32_t w, double sd, double sh, double sw,

@@ -9,7 +9,9 @@ Network (channels-last BF16 activations, FP32 master weights):
   down (conv 2^3, stride 2) to 32 ch, 2 x conv3 -> s2; to 64 ch -> s3; to 128 ch
   bottleneck: 2 x conv3 (128)
   up: nearest x2, conv3 to half the channels, concatenate the skip, 2 x conv3
-  head: conv 1^3 to 16 ch; channel 0 is the correction added to the input dose.
+  head: conv 1^3 to 16 ch; channel 0 is the correction added to the input dose
+  (the only channel computed: a fused kernel takes it, the loss and its
+  gradients straight from the last decoder layer's output).
 All convolutions but the head apply ReLU.  Loss: mean squared error of the
 corrected dose against the high-history dose (both divided by the input
 dose's maximum).  Optimiser: Adam.
@@ -279,7 +281,9 @@ class UNet:
             x = l.forward(x, keep)
         return x
 
-    def forward(self, x, keep=True):
+    def features(self, x, keep=True):
+        """Output of the last decoder layer: the head's input, 16 BF16
+        channels per voxel (keep: store what the backward pass needs)."""
         e1 = self._seq(self.enc1, x, keep)
         e2 = self._seq(self.enc2, self.down1.forward(e1, keep), keep)
         e3 = self._seq(self.enc3, self.down2.forward(e2, keep), keep)
@@ -294,7 +298,28 @@ class UNet:
                 u = up.forward_fused(f, upsample=True)
                 f = dec[1].forward(dec[0].forward_fused(u, xb=skip), False)
             f1 = f
-        return self.head.forward(f1, keep)
+        return f1
+
+    def forward(self, x, keep=True):
+        """Correction predicted for every voxel, FP32 [1, D, H, W]: output
+        channel 0 of the 1^3 head (the other 15 feed neither the loss nor
+        the dose, so they are not computed)."""
+        import torch
+        f1 = self.features(x, keep)
+        y = torch.empty(f1.shape[:4], dtype=torch.float32, device=f1.device)
+        _ok(fdc.lib().fdc_unet_head(_p(f1), f1.shape[-1], _p(self.head.w16), _p(self.head.b32), y.numel(), None,
+                                    0.0, _p(y), None, _s()), "head")
+        return y
+
+    def head_loss(self, f1, target, loss, df1=None):
+        """Adds the mean squared error of the head's correction against the
+        target to loss; with df1, also the head's weight and bias gradients
+        and, in df1, the gradient with respect to the last decoder layer's
+        pre-activation."""
+        grad = df1 is not None
+        _ok(fdc.lib().fdc_unet_head_loss(_p(f1), f1.shape[-1], _p(self.head.w16), _p(self.head.b32), _p(target),
+                                         target.numel(), _p(loss), _p(df1), _p(self.head.gw) if grad else None,
+                                         _p(self.head.gb) if grad else None, _s()), "head loss")
 
     @staticmethod
     def _fuse_level(up):
@@ -327,10 +352,11 @@ class UNet:
             dy = l.backward(dy, need_dx=need_last or i < len(layers) - 1)
         return dy
 
-    def backward(self, dhead):
+    def backward(self, df1):
+        """Backward pass from the gradient df1 of the head's input (as
+        head_loss leaves it), after features(keep=True)."""
         c1, c2, c3, _ = self.channels
-        d = self.head.backward(dhead)
-        d, de1 = self._decoder_back(self.up1, self.dec1, d, c1)
+        d, de1 = self._decoder_back(self.up1, self.dec1, df1, c1)
         d, de2 = self._decoder_back(self.up2, self.dec2, d, c2)
         d, de3 = self._decoder_back(self.up3, self.dec3, d, c3)
         d = self.down3.backward(self._seq_back(self.bott, d))
@@ -417,32 +443,31 @@ def train_step(net, sample, lr):
     """Forward, loss, backward and Adam step; returns the loss tensor (FP32,
     device) without synchronising."""
     import torch
-    head = net.forward(sample.x)
-    n = sample.dose_in.numel()
-    dhead = torch.empty(head.shape, dtype=torch.bfloat16, device=head.device)
-    loss = torch.zeros(1, dtype=torch.float32, device=head.device)
-    _ok(fdc.lib().fdc_mse(_p(head), 16, _p(sample.target), n, _p(dhead), _p(loss), _s()), "mse")
+    f1 = net.features(sample.x)
+    loss = torch.zeros(1, dtype=torch.float32, device=f1.device)
+    df1 = torch.empty_like(f1)
     net.zero_grad()
-    net.backward(dhead)
+    net.head_loss(f1, sample.target, loss, df1)
+    net.backward(df1)
     net.step(lr)
     return loss
 
 
 def evaluate_loss(net, sample):
     import torch
-    head = net.forward(sample.x, keep=False)
-    loss = torch.zeros(1, dtype=torch.float32, device=head.device)
-    _ok(fdc.lib().fdc_mse(_p(head), 16, _p(sample.target), sample.dose_in.numel(), None, _p(loss), _s()), "mse")
+    f1 = net.features(sample.x, keep=False)
+    loss = torch.zeros(1, dtype=torch.float32, device=f1.device)
+    net.head_loss(f1, sample.target, loss)
     return loss
 
 
 def denoise(net, sample):
     """Denoised dose (Gy, FP64 on the device) of a prepared sample."""
     import torch
-    head = net.forward(sample.x, keep=False)
-    out = torch.empty(sample.shape, dtype=torch.float64, device=head.device)
-    _ok(fdc.lib().fdc_unet_finish(_p(head), _p(sample.dose_in), sample.dose_in.numel(), sample.scale, _p(out),
-                                  _s()), "finish")
+    f1 = net.features(sample.x, keep=False)
+    out = torch.empty(sample.shape, dtype=torch.float64, device=f1.device)
+    _ok(fdc.lib().fdc_unet_head(_p(f1), f1.shape[-1], _p(net.head.w16), _p(net.head.b32), out.numel(),
+                                _p(sample.dose_in), sample.scale, None, _p(out), _s()), "head")
     return out
 
 

@@ -59,6 +59,8 @@ SIGNATURES = {
     "fdc_add_bf16": (C.c_int, [_p, _p, _p, C.c_int64, _p]),
     "fdc_unet_prepare": (C.c_int, [_p, _p, _p, C.c_int64, C.c_double, C.c_float, _p, _p, _p, _p]),
     "fdc_unet_finish": (C.c_int, [_p, _p, C.c_int64, C.c_double, _p, _p]),
+    "fdc_unet_head": (C.c_int, [_p, C.c_int32, _p, _p, C.c_int64, _p, C.c_double, _p, _p, _p]),
+    "fdc_unet_head_loss": (C.c_int, [_p, C.c_int32, _p, _p, _p, C.c_int64, _p, _p, _p, _p, _p]),
     "fdc_unet_status": (C.c_int, [C.c_int32]),
     "fdc_debug_wait_timeout": (C.c_int, [C.c_int64, _p]),
     "fdc_unet_dihedral": (C.c_int, [_p, _p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _p, _p, _p]),

@@ -246,6 +246,110 @@ def test_mse_and_adam():
     np.testing.assert_allclose(pb.double().cpu().numpy(), pr, rtol=8e-3, atol=1e-6)
 
 
+@pytest.mark.parametrize("n", [1, 255, 5000 + 37, 300_000])
+def test_head_and_head_loss(n):
+    """The fused head (output channel 0 of the 1^3 convolution), its loss and
+    gradients against FP64 sums of the same BF16 values; ragged voxel counts
+    (one voxel, less than a block, several blocks with a ragged tail, more
+    voxels than the loss kernel's threads)."""
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    L = fdc.lib()
+    rng = np.random.default_rng(n)
+    xt, x = bf16(np.maximum(rng.normal(size=(n, 16)), 0.0))  # ReLU features: about half exact zeros
+    w16, w = bf16(rng.normal(size=(16, 16)) / 4)  # the head's [16][16] weights; row 0 is used
+    b = torch.tensor(rng.normal(size=16), dtype=torch.float32, device="cuda:0")
+    tgt = rng.normal(size=n).astype(np.float32)
+    din = rng.random(n).astype(np.float32)
+    tt, dt = torch.from_numpy(tgt).cuda(), torch.from_numpy(din).cuda()
+    y_ref = x @ w[0] + float(b[0])
+    y = torch.empty(n, dtype=torch.float32, device="cuda:0")
+    dose = torch.empty(n, dtype=torch.float64, device="cuda:0")
+    assert L.fdc_unet_head(ptr(xt), 16, ptr(w16), ptr(b), n, ptr(dt), 2.5, ptr(y), ptr(dose), None) == 0
+    torch.cuda.synchronize()
+    mag = np.abs(x) @ np.abs(w[0]) + abs(float(b[0]))
+    assert np.all(np.abs(y.double().cpu().numpy() - y_ref) <= 2e-6 * mag + 1e-30)
+    d_ref = np.maximum((y.double().cpu().numpy() + din) * 2.5, 0.0)  # FP64 epilogue of the FP32 correction
+    np.testing.assert_allclose(dose.cpu().numpy(), d_ref, rtol=1e-15, atol=0)
+    # loss and gradients
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda:0")
+    dx = torch.empty((n, 16), dtype=torch.bfloat16, device="cuda:0")
+    dw = torch.full((16,), 0.5, dtype=torch.float32, device="cuda:0")  # accumulated into
+    db = torch.full((1,), -0.25, dtype=torch.float32, device="cuda:0")
+    assert L.fdc_unet_head_loss(ptr(xt), 16, ptr(w16), ptr(b), ptr(tt), n, ptr(loss), ptr(dx), ptr(dw), ptr(db),
+                                None) == 0
+    torch.cuda.synchronize()
+    e = y_ref - tgt
+    assert float(loss) == pytest.approx(np.mean(e ** 2), rel=1e-4)
+    g = 2 * e / n
+    dx_ref = np.where(x > 0, w[0][None, :] * g[:, None], 0.0)
+    got = dx.double().cpu().numpy()
+    np.testing.assert_allclose(got, dx_ref, rtol=8e-3, atol=1e-3 * np.abs(dx_ref).max() / 64)
+    assert np.all(got[x == 0] == 0)
+    scale_w = (np.abs(g)[:, None] * x).sum(0)
+    assert np.all(np.abs(dw.double().cpu().numpy() - 0.5 - x.T @ g) <= 1e-4 * scale_w + 1e-7)
+    assert abs(float(db[0]) + 0.25 - g.sum()) <= 1e-4 * np.abs(g).sum() + 1e-7
+    # loss only (no gradients), accumulated onto the previous value
+    assert L.fdc_unet_head_loss(ptr(xt), 16, ptr(w16), ptr(b), ptr(tt), n, ptr(loss), None, None, None, None) == 0
+    torch.cuda.synchronize()
+    assert float(loss) == pytest.approx(2 * np.mean(e ** 2), rel=1e-4)
+    # refused: 8 channels, no output, dx aliasing x, only one of dw and db
+    assert L.fdc_unet_head(ptr(xt), 8, ptr(w16), ptr(b), n, None, 0.0, ptr(y), None, None) != 0
+    assert L.fdc_unet_head(ptr(xt), 16, ptr(w16), ptr(b), n, None, 0.0, None, None, None) != 0
+    assert L.fdc_unet_head_loss(ptr(xt), 16, ptr(w16), ptr(b), ptr(tt), n, ptr(loss), ptr(xt), None, None,
+                                None) != 0
+    assert L.fdc_unet_head_loss(ptr(xt), 16, ptr(w16), ptr(b), ptr(tt), n, ptr(loss), None, ptr(dw), None,
+                                None) != 0
+
+
+def test_head_matches_convolution_and_mse():
+    """The fused head equals channel 0 of the general 1^3 convolution with
+    FP32 output, and its loss and gradients equal fdc_mse followed by that
+    convolution's weight and data gradients."""
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    L = fdc.lib()
+    rng = np.random.default_rng(77)
+    shape = (1, 6, 9, 10, 16)
+    n = 6 * 9 * 10
+    xt, x = bf16(np.maximum(rng.normal(size=shape), 0.0))
+    w16, w = bf16(rng.normal(size=(16, 1, 1, 1, 16)) / 4)
+    b = torch.tensor(rng.normal(size=16), dtype=torch.float32, device="cuda:0")
+    g, oshape = geom(shape, 16, 1, 1, 0, 0)
+    yc = torch.empty(oshape, dtype=torch.float32, device="cuda:0")
+    assert L.fdc_conv3d_forward(C.byref(g), ptr(xt), ptr(w16), ptr(b), None, ptr(yc), None) == 0
+    y = torch.empty(n, dtype=torch.float32, device="cuda:0")
+    assert L.fdc_unet_head(ptr(xt), 16, ptr(w16), ptr(b), n, None, 0.0, ptr(y), None, None) == 0
+    tt = torch.from_numpy(rng.normal(size=n).astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    c0 = yc.reshape(n, 16)[:, 0]
+    assert torch.allclose(y, c0, rtol=0, atol=2e-6 * float(c0.abs().max()))
+    # the unfused chain: mse on channel 0, then the convolution's gradients
+    loss_a = torch.zeros(1, dtype=torch.float32, device="cuda:0")
+    dy = torch.empty(oshape, dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_mse(ptr(yc), 16, ptr(tt), n, ptr(dy), ptr(loss_a), None) == 0
+    dw_a = torch.zeros((16, 1, 1, 1, 16), dtype=torch.float32, device="cuda:0")
+    db_a = torch.zeros(16, dtype=torch.float32, device="cuda:0")
+    assert L.fdc_conv3d_backward_weights(C.byref(g), ptr(xt), ptr(dy), ptr(dw_a), ptr(db_a), None) == 0
+    wt = torch.empty_like(w16)
+    assert L.fdc_conv3d_transpose_weights(C.byref(g), ptr(w16), ptr(wt), None) == 0
+    dx_a = torch.empty(shape, dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_conv3d_backward_data(C.byref(g), ptr(dy), ptr(wt), ptr(xt), ptr(dx_a), None) == 0
+    loss_b = torch.zeros(1, dtype=torch.float32, device="cuda:0")
+    dx_b = torch.empty(shape, dtype=torch.bfloat16, device="cuda:0")
+    dw_b = torch.zeros(16, dtype=torch.float32, device="cuda:0")
+    db_b = torch.zeros(1, dtype=torch.float32, device="cuda:0")
+    assert L.fdc_unet_head_loss(ptr(xt), 16, ptr(w16), ptr(b), ptr(tt), n, ptr(loss_b), ptr(dx_b), ptr(dw_b),
+                                ptr(db_b), None) == 0
+    torch.cuda.synchronize()
+    assert float(loss_b) == pytest.approx(float(loss_a), rel=1e-5)
+    # the unfused chain rounds the loss gradient to BF16 first: one BF16 rounding apart
+    assert torch.allclose(dx_b.float(), dx_a.float(), rtol=1e-2, atol=1e-3 * float(dx_a.float().abs().max()))
+    assert torch.allclose(dw_b, dw_a.reshape(16, 16)[0], rtol=1e-2, atol=1e-3 * float(dw_a.abs().max()))
+    assert float(db_b[0]) == pytest.approx(float(db_a[0]), rel=1e-2, abs=1e-3 * float(db_a.abs().max()))
+    assert float(db_a[1:].abs().max()) == 0.0 and float(dw_a[1:].abs().max()) == 0.0
+
+
 def test_gamma_matches_oracle():
     import torch
     from paper_1011_2188_gb300 import denoise
