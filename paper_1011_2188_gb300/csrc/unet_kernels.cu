@@ -239,9 +239,6 @@ __global__ void __launch_bounds__(128) conv_igemm_kernel(const Conv3dArgs g, con
     }
 }
 
-// Halo of a 2 x 8 x 8 voxel block for a 3^3 stencil (weight gradient).
-constexpr int kHD = 4, kHH = 10, kHW = 10, kHalo = kHD * kHH * kHW;
-
 // ---------------------------------------------------------------- tcgen05
 // 3x3x3 stride-1 padding-1 convolution on the fifth-generation tensor cores:
 // a CTA of four warps owns a 1 x 16 x 8 block of output voxels (M = 128 rows,
@@ -973,156 +970,255 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
     }
 }
 
-// Weight gradient of a 3^3 stride-1 padding-1 convolution for one 16-wide
-// output-channel tile and one 16-wide input-channel slice:
-//   dW[co][tap][ci] += sum over voxels v of dy[v][co] * x[v + tap - 1][ci].
-// A CTA walks 2 x 8 x 8 voxel blocks (grid-stride); per block it stages the
-// dy tile (128 voxels x 16) and the x halo (4 x 10 x 10 x 16) in shared
-// memory, and each warp accumulates the GEMMs of its taps (M = 16 co, N = 16
-// ci, K = the block's 128 voxels) with ldmatrix.trans fragments; the CTA's
-// partial dW is added atomically at the end.
-constexpr int kDyRowBytes = 48;  // 16 BF16 padded
-#ifndef FDC_WGRAD_HALO
-#define FDC_WGRAD_HALO 1
-#endif
+// ---- weight gradient on the tcgen05 tensor cores, voxels as the reduction axis
+//   dW[co][kd][kh][kw][ci] += sum over output voxels o of dy[o][co] * x[o + (kd, kh, kw) - 1][ci]
+// (3^3, stride 1, padding 1).  K runs over (output plane d, output row h,
+// input column wx); with the output column wo = wx + 1 - kw and kw' = 2 - kw,
+//   D_kd[(kh, ci)][(kw', co)] += sum_k x[d + kd - 1][h + kh - 1][wx][ci] * dy[d][h][wx - 1 + kw'][co]
+// is one MMA per kd for 16 consecutive planes d: M = 4 kh slots (the fourth
+// discarded) x 8 CG input channels, N = 3 kw' x 16 output channels, K = 16.
+// Both operands are MN-major (8 channels contiguous; the eight K rows of a
+// core matrix are eight consecutive planes, 16 bytes apart): the input tile is
+// stored [wx][h][channel group][d] and the gradient tile [h][wo][channel
+// group][d], so every (kh, group) of A and every (kw', group) of B lies at one
+// uniform stride from the first and the taps cost no copies.
+// A CTA walks chunks of HT rows x WT columns x 16 planes (grid-stride),
+// staging chunk i + 1 with cp.async while the MMAs of chunk i run (two
+// buffers); the three accumulators (M x 48 FP32) stay in TMEM until its last
+// chunk, are then laid out [co][tap][ci] in shared memory and added to dw
+// with 16-byte vector reductions.  With db, the CTAs of the first input-channel
+// slice also sum dy over their chunks into the bias gradient.  Every wait is
+// bounded (FDC_ERR_TIMEOUT in g_tc_status on expiry).
+constexpr int kWtDt = 16;          // output planes per chunk: one K run
+constexpr int kWtDD = kWtDt + 2;   // input planes staged per chunk
 
-__device__ __forceinline__ void ldmatrix_x4_trans(const unsigned char *p, unsigned &r0, unsigned &r1, unsigned &r2,
-                                                  unsigned &r3) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(a));
+template <int CG, int HT, int WT>
+struct WgTc {
+    static constexpr int HH = HT + 2, WO = WT + 2, CGO = 2, NCO = 16;
+    static constexpr int M = 32 * CG, N = 24 * CGO;
+    static constexpr int XBytes = WT * HH * CG * kWtDD * 16;
+    static constexpr int YBytes = HT * WO * CGO * kWtDt * 16;
+    static constexpr int BufBytes = XBytes + YBytes;
+    static constexpr int Smem = 2 * BufBytes;
+    static constexpr unsigned Cols = 3 * N <= 128 ? 128u : 256u;
+    static constexpr int RedFloats = NCO * 27 * CG * 8;  // the CTA's dW block, [co][tap][ci]
+    // A's discarded fourth kh slot of the last column reads past the input
+    // tile, into the gradient tile that follows it
+    static_assert(XBytes % 128 == 0 && BufBytes % 128 == 0, "128-byte aligned tiles");
+    static_assert(YBytes >= CG * kWtDD * 16 + 512, "A's overrun stays in the buffer");
+    static_assert(RedFloats * 4 <= Smem, "reduction tile fits the buffers");
+};
+
+__host__ __device__ constexpr unsigned umma_idesc_mn(int M, int N) {
+    return umma_idesc(M, N) | (1u << 15) | (1u << 16);  // A and B MN-major
 }
 
-// With db, the CTAs of the first input-channel tile also add the bias
-// gradient of their 16 output channels, db[co] += sum over their voxels of
-// dy[v][co], from the dy tiles they stage anyway.
-// The input may be the concatenation [upsample?(x) | xb] of the fused forward
-// (x: ca channels, at half resolution when up_a; xb: Ci - ca channels), read
-// in place; otherwise ca = Ci and xb is unused.
-__global__ void __launch_bounds__(128) conv3_wgrad_halo_kernel(const Conv3dArgs g, const __nv_bfloat16 *x,
-                                                               const __nv_bfloat16 *dy, float *dw, float *db,
-                                                               int ca, int up_a, const __nv_bfloat16 *xb) {
-    __shared__ __align__(16) unsigned char sX[kHalo * kRowBytes];
-    __shared__ __align__(16) unsigned char sDy[kRows * kDyRowBytes];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int grp = lane >> 2, tig = lane & 3;
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+template <int CG, int HT, int WT>
+__global__ void __launch_bounds__(128) conv3_wgrad_tc_kernel(const Conv3dArgs g, const __nv_bfloat16 *x,
+                                                             const __nv_bfloat16 *dy, float *dw, float *db, int ca,
+                                                             int up_a, const __nv_bfloat16 *xb, int vec) {
+    using P = WgTc<CG, HT, WT>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ unsigned tmem_slot;
+    __shared__ float sBias[4][P::NCO];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = g.in_d, H = g.in_h, W = g.in_w, Ci = g.c_in, Co = g.c_out;
-    const int co0 = blockIdx.y * 16, ci0 = blockIdx.z * 16;
-    const int tiles_w = (W + 7) / 8, tiles_h = (H + 7) / 8, tiles_d = (D + 1) / 2;
-    const long long n_blocks = (long long)g.batch * tiles_d * tiles_h * tiles_w;
-    // taps of this warp: warp, warp + 4, ... (7 or 6 of the 27)
-    float acc[7][2][4];
-#pragma unroll
-    for (int i = 0; i < 7; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
-    // ldmatrix row of this lane: voxel (lane & 7) + 8 ((lane >> 3) & 1) of a
-    // 16-voxel k-step, channel offset 8 (lane >> 4)
-    const int lv = (lane & 7) + ((lane >> 3) & 1) * 8, lc = (lane >> 4) * 16;
+    const int co0 = blockIdx.y * P::NCO, ci0 = blockIdx.z * (8 * CG);
+    const int cb = Ci - ca;
+    const int Da = up_a ? D / 2 : D, Ha = up_a ? H / 2 : H, Wa = up_a ? W / 2 : W;
+    const int tw = (W + WT - 1) / WT, th = (H + HT - 1) / HT, td = (D + kWtDt - 1) / kWtDt;
+    const long long n_chunks = (long long)g.batch * td * th * tw;
     const bool do_bias = db != nullptr && blockIdx.z == 0;
-    float bsum[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) bsum[j] = 0.f;
-    // for B (x): lanes 0-15 channels 0-7 with voxels 0-15, lanes 16-31 channels 8-15
-    for (long long blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
-        long long t = blk;
-        const int tw = (int)(t % tiles_w); t /= tiles_w;
-        const int th = (int)(t % tiles_h); t /= tiles_h;
-        const int td = (int)(t % tiles_d);
-        const int b = (int)(t / tiles_d);
-        const int d0 = td * 2, h0 = th * 8, w0 = tw * 8;
-        for (int i = tid; i < kHalo * 2; i += 128) {
-            const int row = i >> 1, half = i & 1;
-            const int hd = row / (kHH * kHW), hh = (row / kHW) % kHH, hw = row % kHW;
-            const int d = d0 - 1 + hd, h = h0 - 1 + hh, w = w0 - 1 + hw;
-            const bool ok = d >= 0 && d < D && h >= 0 && h < H && w >= 0 && w < W;
+    const unsigned mb0 = smem_u32(&mbar[0]), mb1 = smem_u32(&mbar[1]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb1));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(P::Cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = tmem_slot;
+
+    // stage chunk ch into buf: input tile X[c][hh][cg][dd] (index order cg, c,
+    // hh, dd: consecutive threads read consecutive 16-byte pieces of a row) and
+    // gradient tile Y[r][wo][cgo][dd]; zero outside the grid
+    auto stage = [&](long long ch, unsigned char *buf) {
+        long long t = ch;
+        const int cw = (int)(t % tw); t /= tw;
+        const int chh = (int)(t % th); t /= th;
+        const int cd = (int)(t % td);
+        const int b = (int)(t / td);
+        const int d0 = cd * kWtDt, h0 = chh * HT, w0 = cw * WT;
+        for (int i = tid; i < WT * P::HH * CG * kWtDD; i += 128) {
+            const int cg = i % CG;
+            int q = i / CG;
+            const int c = q % WT;
+            q /= WT;
+            const int hh = q % P::HH, dd = q / P::HH;
+            const int d = d0 - 1 + dd, h = h0 - 1 + hh, w = w0 + c;
+            const bool in = d >= 0 && d < D && h >= 0 && h < H && w < W;
+            const int ch0 = ci0 + cg * 8;
             const __nv_bfloat16 *p = x;
-            if (ok) {
-                if (ci0 >= ca)
-                    p = xb + ((((long long)b * D + d) * H + h) * W + w) * (Ci - ca) + (ci0 - ca) + half * 8;
+            if (in) {
+                if (ch0 >= ca)
+                    p = xb + ((((long long)b * D + d) * H + h) * W + w) * cb + (ch0 - ca);
                 else if (up_a)
-                    p = x + ((((long long)b * (D / 2) + (d >> 1)) * (H / 2) + (h >> 1)) * (W / 2) + (w >> 1)) * ca + ci0 +
-                        half * 8;
+                    p = x + ((((long long)b * Da + (d >> 1)) * Ha + (h >> 1)) * Wa + (w >> 1)) * ca + ch0;
                 else
-                    p = x + ((((long long)b * D + d) * H + h) * W + w) * ca + ci0 + half * 8;
+                    p = x + ((((long long)b * D + d) * H + h) * W + w) * ca + ch0;
             }
-            cp_async16(sX + row * kRowBytes + half * 16, p, ok);
+            cp_async16(buf + (((c * P::HH + hh) * CG + cg) * kWtDD + dd) * 16, p, in);
         }
-        for (int i = tid; i < kRows * 2; i += 128) {
-            const int r = i >> 1, half = i & 1;
-            const int d = d0 + (r >> 6), h = h0 + ((r >> 3) & 7), w = w0 + (r & 7);
-            const bool ok = d < D && h < H && w < W;
-            const __nv_bfloat16 *p = ok ? dy + ((((long long)b * D + d) * H + h) * W + w) * Co + co0 + half * 8 : dy;
-            cp_async16(sDy + r * kDyRowBytes + half * 16, p, ok);
+        unsigned char *yb = buf + P::XBytes;
+        for (int i = tid; i < HT * P::WO * P::CGO * kWtDt; i += 128) {
+            const int cgo = i % P::CGO;
+            int q = i / P::CGO;
+            const int wo = q % P::WO;
+            q /= P::WO;
+            const int r = q % HT, dd = q / HT;
+            const int d = d0 + dd, h = h0 + r, w = w0 - 1 + wo;
+            const bool in = d < D && h < H && w >= 0 && w < W;
+            const __nv_bfloat16 *p = in ? dy + ((((long long)b * D + d) * H + h) * W + w) * Co + co0 + cgo * 8 : dy;
+            cp_async16(yb + (((r * P::WO + wo) * P::CGO + cgo) * kWtDt + dd) * 16, p, in);
         }
-        cp_async_commit();
+    };
+    float bsum[P::NCO];
+#pragma unroll
+    for (int j = 0; j < P::NCO; ++j) bsum[j] = 0.f;
+    bool ok = true;
+    int it = 0;
+    long long ch = blockIdx.x;
+    if (ch < n_chunks) stage(ch, smem);
+    cp_async_commit();
+    for (; ch < n_chunks; ch += gridDim.x, ++it) {
+        const int p = it & 1;
+        unsigned char *buf = smem + p * P::BufBytes;
         cp_async_wait<0>();
-        __syncthreads();
-        if (do_bias) {  // row tid of the dy tile (zero outside the grid)
-            const uint4 *row = (const uint4 *)(sDy + tid * kDyRowBytes);
-            const uint4 q[2] = {row[0], row[1]};
-            const __nv_bfloat162 *h2 = (const __nv_bfloat162 *)q;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float2 f = __bfloat1622float2(h2[j]);
-                bsum[2 * j] += f.x;
-                bsum[2 * j + 1] += f.y;
-            }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        // also agrees on the outcome of the previous iteration's bounded wait
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
         }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            constexpr unsigned idesc = umma_idesc_mn(P::M, P::N);
+            // LBO: 128 bytes between K groups (8 planes); SBO: between M (N) groups
+            const unsigned long long ad0 = umma_desc(smem_u32(buf), 128, kWtDD * 16);
+            const unsigned long long bd0 = umma_desc(smem_u32(buf + P::XBytes), 128, kWtDt * 16);
 #pragma unroll 1
-        for (int ks = 0; ks < 8; ++ks) {  // 16 voxels per k-step
-            // A = dy^T: rows co, k = voxels ks*16 .. +15
-            unsigned a0, a1, a2, a3;
-            {
-                const int v = ks * 16 + (lane & 7) + (lane >> 4) * 8;  // matrices: (v 0-7, co 0-7), (v 0-7, co 8-15), (v 8-15, co 0-7), (v 8-15, co 8-15)
-                ldmatrix_x4_trans(sDy + v * kDyRowBytes + ((lane >> 3) & 1) * 16, a0, a1, a2, a3);
-            }
-            const int v = ks * 16 + lv;  // this lane's voxel row for the B matrices
-            const int hidx = ((v >> 6) * kHH + ((v >> 3) & 7)) * kHW + (v & 7);
+            for (int r = 0; r < HT; ++r)
+#pragma unroll 1
+                for (int c = 0; c < WT; ++c) {
+                    const unsigned long long bd = bd0 + (unsigned long long)((((r * P::WO + c) * P::CGO) * kWtDt));
+                    const unsigned long long ad = ad0 + (unsigned long long)(((c * P::HH + r) * CG) * kWtDD);
+                    const int acc = (it > 0 || r > 0 || c > 0) ? 1 : 0;
 #pragma unroll
-            for (int i = 0; i < 7; ++i) {
-                const int tap = warp + 4 * i;
-                if (tap < 27) {
-                    const int kd = tap / 9, kh = (tap / 3) % 3, kw = tap % 3;
-                    const int off = (kd * kHH + kh) * kHW + kw;
-                    unsigned b0, b1, b2, b3;
-                    ldmatrix_x4_trans(sX + (hidx + off) * kRowBytes + lc, b0, b1, b2, b3);
-                    // b0,b1: k = voxels 0-7 / 8-15, n = ci 0-7; b2,b3: ci 8-15
-                    mma_bf16(acc[i][0], a0, a1, a2, a3, b0, b1);
-                    mma_bf16(acc[i][1], a0, a1, a2, a3, b2, b3);
+                    for (int kd = 0; kd < 3; ++kd)
+                        umma_bf16(tmem + (unsigned)(kd * P::N), ad + (unsigned long long)kd, bd, idesc, acc);
+                }
+            umma_commit(p ? mb1 : mb0);
+        }
+        if (do_bias) {  // the chunk's own columns wo = 1 .. WT of the gradient tile
+            const unsigned char *yb = buf + P::XBytes;
+            for (int i = tid; i < HT * WT * kWtDt; i += 128) {
+                const int dd = i % kWtDt, q = i / kWtDt;
+                const int c = q % WT, r = q / WT;
+#pragma unroll
+                for (int cgo = 0; cgo < P::CGO; ++cgo) {
+                    const uint4 v = *(const uint4 *)(yb + (((r * P::WO + c + 1) * P::CGO + cgo) * kWtDt + dd) * 16);
+                    const __nv_bfloat162 *h2 = (const __nv_bfloat162 *)&v;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float2 f = __bfloat1622float2(h2[j]);
+                        bsum[cgo * 8 + 2 * j] += f.x;
+                        bsum[cgo * 8 + 2 * j + 1] += f.y;
+                    }
                 }
             }
         }
-        __syncthreads();
+        // the other buffer is free once the previous chunk's MMAs are done
+        if (it >= 1) ok = mbar_wait_bounded(p ? mb0 : mb1, ((it - 1) >> 1) & 1);
+        const long long nx = ch + gridDim.x;
+        if (ok && nx < n_chunks) stage(nx, smem + (p ^ 1) * P::BufBytes);
+        cp_async_commit();
     }
+    // the last chunk's MMAs complete after all earlier ones
+    if (ok && it >= 1) ok = mbar_wait_bounded(((it - 1) & 1) ? mb1 : mb0, ((it - 1) >> 1) & 1);
+    cp_async_wait<0>();
+    ok = __syncthreads_and(ok);
+    if (ok && it >= 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        // accumulator row of this thread: M = 128, lane quadrant rows; M = 64,
+        // rows 16 warp .. 16 warp + 15 in lanes 0-15 of the warp's quadrant
+        const int m = P::M == 128 ? warp * 32 + lane : warp * 16 + lane;
+        const bool row_ok = P::M == 128 || lane < 16;
+        const int j = m >> 3, e = m & 7;
+        const int kh = j / CG, cil = (j % CG) * 8 + e;
+        const bool valid = row_ok && kh < 3;
+        float *red = (float *)smem;  // [co][tap][ci] of this CTA; the buffers are idle now
+#pragma unroll 1
+        for (int kd = 0; kd < 3; ++kd)
 #pragma unroll
-    for (int i = 0; i < 7; ++i) {
-        const int tap = warp + 4 * i;
-        if (tap >= 27) continue;
+            for (int c16 = 0; c16 < P::N; c16 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(kd * P::N + c16), v);
+                if (valid)
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-            for (int hf = 0; hf < 2; ++hf) {
-                const int co = co0 + grp + hf * 8, ci = ci0 + nt * 8 + tig * 2;
-                float *q = dw + ((long long)co * 27 + tap) * Ci + ci;
-                atomicAdd(q, acc[i][nt][hf * 2]);
-                atomicAdd(q + 1, acc[i][nt][hf * 2 + 1]);
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int n = c16 + jj, jn = n >> 3;
+                        const int co = (jn % P::CGO) * 8 + (n & 7), kw = 2 - jn / P::CGO;
+                        red[(co * 27 + (kd * 3 + kh) * 3 + kw) * (CG * 8) + cil] = v[jj];
+                    }
             }
-    }
-    if (do_bias) {  // block reduction of the 128 per-thread row sums (sX is free after the last tile)
         __syncthreads();
-        float *red = (float *)sX;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) red[j * 128 + tid] = bsum[j];
-        __syncthreads();
-        if (tid < 16) {
-            float t = 0.f;
-            for (int k = 0; k < 128; ++k) t += red[tid * 128 + k];
-            atomicAdd(db + co0 + tid, t);
+        // 16-byte pieces along ci: dw[(co0 + co) * 27 + tap][ci0 ..]
+        constexpr int pieces = P::RedFloats / 4;
+        for (int i = tid; i < pieces; i += 128) {
+            const int f = i * 4;
+            const int cil4 = f % (CG * 8), rest = f / (CG * 8);  // rest = co * 27 + tap
+            const int co = rest / 27, tap = rest % 27;
+            const float4 q = *(const float4 *)(red + f);
+            float *dst = dw + ((long long)(co0 + co) * 27 + tap) * Ci + ci0 + cil4;
+            if (vec) {
+                red_add_v4(dst, q.x, q.y, q.z, q.w);
+            } else {  // dw not 16-byte aligned
+                atomicAdd(dst, q.x);
+                atomicAdd(dst + 1, q.y);
+                atomicAdd(dst + 2, q.z);
+                atomicAdd(dst + 3, q.w);
+            }
         }
+        if (do_bias) {
+#pragma unroll
+            for (int jb = 0; jb < P::NCO; ++jb) {
+                float v = bsum[jb];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) sBias[warp][jb] = v;
+            }
+            __syncthreads();
+            if (tid < P::NCO) atomicAdd(db + co0 + tid, sBias[0][tid] + sBias[1][tid] + sBias[2][tid] + sBias[3][tid]);
+        }
+    }
+    if (!ok && tid == 0) atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(P::Cols));
     }
 }
 
@@ -1788,15 +1884,36 @@ cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy
                               cudaStream_t st, int ca, int up_a, const void *xb) {
     if (ca <= 0) ca = g.c_in;
     const long long rows = (long long)g.batch * g.out_d * g.out_h * g.out_w;
-    if (FDC_WGRAD_HALO && g.ksize == 3 && g.stride == 1 && g.pad == 1) {
-        const long long blocks = (long long)g.batch * ((g.in_d + 1) / 2) * ((g.in_h + 7) / 8) * ((g.in_w + 7) / 8);
-        const int pairs = (g.c_out / 16) * (g.c_in / 16);
-        long long per = (152ll * 8 + pairs - 1) / pairs;  // CTAs per channel-tile pair
-        if (per > blocks) per = blocks;
-        if (per < 1) per = 1;
-        dim3 grid((unsigned)per, (unsigned)(g.c_out / 16), (unsigned)(g.c_in / 16));
-        conv3_wgrad_halo_kernel<<<grid, 128, 0, st>>>(g, (const __nv_bfloat16 *)x, (const __nv_bfloat16 *)dy, dw,
-                                                      db, ca, up_a, (const __nv_bfloat16 *)xb);
+    if (g.ksize == 3 && g.stride == 1 && g.pad == 1) {  // tcgen05, voxels as K (c_in, c_out multiples of 16)
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const int vec = ((uintptr_t)dw & 15) == 0 ? 1 : 0;
+        auto X = (const __nv_bfloat16 *)x, Y = (const __nv_bfloat16 *)dy, XB = (const __nv_bfloat16 *)xb;
+        // 32-channel input slices (M = 128) where the channels allow, else 16 (M = 64);
+        // two CTAs per SM (256 TMEM columns, ~94 KB of shared memory each)
+        const bool wide = g.c_in % 32 == 0;
+        const int cg = wide ? 4 : 2, ht = wide ? 2 : 4, wt = 8;
+        const long long chunks = (long long)g.batch * ((g.in_d + kWtDt - 1) / kWtDt) * ((g.in_h + ht - 1) / ht) *
+                                 ((g.in_w + wt - 1) / wt);
+        const int ytiles = g.c_out / 16, zslices = g.c_in / (8 * cg);
+        long long gx = std::max(1ll, (long long)sms * 2 / (ytiles * zslices));
+        if (gx > chunks) gx = chunks;
+        const dim3 grid((unsigned)gx, (unsigned)ytiles, (unsigned)zslices);
+        if (wide) {
+            using P = WgTc<4, 2, 8>;
+            static OccCache cache;
+            e = prepare_kernel_smem(cache, conv3_wgrad_tc_kernel<4, 2, 8>, P::Smem);
+            if (e != cudaSuccess) return e;
+            conv3_wgrad_tc_kernel<4, 2, 8><<<grid, 128, P::Smem, st>>>(g, X, Y, dw, db, ca, up_a, XB, vec);
+        } else {
+            using P = WgTc<2, 4, 8>;
+            static OccCache cache;
+            e = prepare_kernel_smem(cache, conv3_wgrad_tc_kernel<2, 4, 8>, P::Smem);
+            if (e != cudaSuccess) return e;
+            conv3_wgrad_tc_kernel<2, 4, 8><<<grid, 128, P::Smem, st>>>(g, X, Y, dw, db, ca, up_a, XB, vec);
+        }
         return cudaGetLastError();
     }
     const int taps = g.ksize * g.ksize * g.ksize;

@@ -56,6 +56,9 @@ CASES = [
     # stride-2 down-convolution on odd sizes: the last input plane of each
     # axis reaches no output (zero data gradient), parity classes of unequal size
     ((2, 7, 5, 9, 16), 32, 2, 2, 0),
+    # weight gradient with several 16-plane chunks along d, the last ragged
+    ((1, 37, 5, 9, 16), 16, 3, 1, 1),
+    ((1, 21, 3, 10, 64), 32, 3, 1, 1),
 ]
 
 
@@ -114,6 +117,13 @@ def test_conv_backward_data_and_weights(case):
     assert torch.equal(dxm, torch.where(xt > 0, dx, torch.zeros_like(dx)))
     np.testing.assert_allclose(dw.cpu().numpy(), rdw, rtol=0, atol=2e-5 * np.abs(rdw).max())
     np.testing.assert_allclose(db.cpu().numpy(), rdb, rtol=0, atol=2e-5 * np.abs(rdb).max())
+    # accumulation into a weight gradient that is not 16-byte aligned (scalar atomics)
+    store = torch.full((dw.numel() + 1,), 0.5, dtype=torch.float32, device="cuda:0")
+    dw_odd = store[1:].view(dw.shape)
+    assert L.fdc_conv3d_backward_weights(C.byref(g), ptr(xt), ptr(dyt), ptr(dw_odd), None, None) == 0
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(dw_odd.cpu().numpy() - 0.5, rdw, rtol=0, atol=2e-5 * np.abs(rdw).max())
+    assert float(store[0]) == 0.5
 
 
 def test_elementwise_kernels():
