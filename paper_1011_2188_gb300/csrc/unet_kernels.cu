@@ -329,6 +329,35 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float v[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Three 16-column loads (the kw blocks of a kw-stacked accumulator) with one
+// wait: the loads overlap instead of each waiting in turn.
+__device__ __forceinline__ void tmem_ld16x3(unsigned t0, unsigned t1, unsigned t2, float a[16], float b[16],
+                                            float c[16]) {
+    unsigned r[48];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%48];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, "
+        "%29, %30, %31}, [%49];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, "
+        "%45, %46, %47}, [%50];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+          "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+        : "r"(t0), "r"(t1), "r"(t2)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        a[i] = __uint_as_float(r[i]);
+        b[i] = __uint_as_float(r[16 + i]);
+        c[i] = __uint_as_float(r[32 + i]);
+    }
+}
+
 // ReLU derivative of the previous layer, applied to a data-gradient output
 // row: channels [n, n + 16) of voxel v become zero where that layer's output
 // (the convolution's input, `mask`, Nn channels per voxel) is not positive.
@@ -660,9 +689,7 @@ __global__ void __launch_bounds__(128) conv3_kws_kernel(const Conv3dArgs g, cons
 #pragma unroll
         for (int c = 0; c < NT; c += 16) {
             float a0[16], a1[16], a2[16];
-            tmem_ld16(base + (unsigned)c, a0);
-            tmem_ld16(base + (unsigned)(NT + c), a1);
-            tmem_ld16(base + (unsigned)(2 * NT + c), a2);
+            tmem_ld16x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c), a0, a1, a2);
 #pragma unroll
             for (int j = 0; j < 16; ++j)
                 a0[j] += __shfl_down_sync(0xffffffffu, a1[j], 1) + __shfl_down_sync(0xffffffffu, a2[j], 2);
@@ -854,9 +881,7 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
 #pragma unroll
             for (int c = 0; c < NT; c += 16) {
                 float a0[16], a1[16], a2[16];
-                tmem_ld16(base + (unsigned)c, a0);
-                tmem_ld16(base + (unsigned)(NT + c), a1);
-                tmem_ld16(base + (unsigned)(2 * NT + c), a2);
+                tmem_ld16x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c), a0, a1, a2);
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
                     a0[j] += __shfl_down_sync(0xffffffffu, a1[j], 1) + __shfl_down_sync(0xffffffffu, a2[j], 2);
@@ -990,6 +1015,7 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
 // slice also sum dy over their chunks into the bias gradient.  Every wait is
 // bounded (FDC_ERR_TIMEOUT in g_tc_status on expiry).
 constexpr int kWtDt = 16;          // output planes per chunk: one K run
+constexpr int kWtThreads = 256;    // eight warps: staging in parallel, two CTAs per SM
 constexpr int kWtDD = kWtDt + 2;   // input planes staged per chunk
 
 template <int CG, int HT, int WT>
@@ -1019,21 +1045,21 @@ __device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, 
 }
 
 template <int CG, int HT, int WT>
-__global__ void __launch_bounds__(128) conv3_wgrad_tc_kernel(const Conv3dArgs g, const __nv_bfloat16 *x,
+__global__ void __launch_bounds__(kWtThreads) conv3_wgrad_tc_kernel(const Conv3dArgs g, const __nv_bfloat16 *x,
                                                              const __nv_bfloat16 *dy, float *dw, float *db, int ca,
                                                              int up_a, const __nv_bfloat16 *xb, int vec) {
     using P = WgTc<CG, HT, WT>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ unsigned tmem_slot;
-    __shared__ float sBias[4][P::NCO];
+    __shared__ float sBias[kWtThreads / 32][P::NCO];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = g.in_d, H = g.in_h, W = g.in_w, Ci = g.c_in, Co = g.c_out;
     const int co0 = blockIdx.y * P::NCO, ci0 = blockIdx.z * (8 * CG);
     const int cb = Ci - ca;
     const int Da = up_a ? D / 2 : D, Ha = up_a ? H / 2 : H, Wa = up_a ? W / 2 : W;
     const int tw = (W + WT - 1) / WT, th = (H + HT - 1) / HT, td = (D + kWtDt - 1) / kWtDt;
-    const long long n_chunks = (long long)g.batch * td * th * tw;
+    const int n_chunks = g.batch * td * th * tw;  // the launcher checks that it fits
     const bool do_bias = db != nullptr && blockIdx.z == 0;
     const unsigned mb0 = smem_u32(&mbar[0]), mb1 = smem_u32(&mbar[1]);
     if (tid == 0) {
@@ -1054,43 +1080,51 @@ __global__ void __launch_bounds__(128) conv3_wgrad_tc_kernel(const Conv3dArgs g,
     // stage chunk ch into buf: input tile X[c][hh][cg][dd] (index order cg, c,
     // hh, dd: consecutive threads read consecutive 16-byte pieces of a row) and
     // gradient tile Y[r][wo][cgo][dd]; zero outside the grid
-    auto stage = [&](long long ch, unsigned char *buf) {
-        long long t = ch;
-        const int cw = (int)(t % tw); t /= tw;
-        const int chh = (int)(t % th); t /= th;
-        const int cd = (int)(t % td);
-        const int b = (int)(t / td);
+    // Input tile: each thread keeps one (column c, channel group cg) pair and
+    // walks the (hh, dd) rows of it, so its source tensor, channel offset and
+    // column are fixed (consecutive threads: consecutive 16-byte pieces of a
+    // voxel row).  Gradient tile: index order cgo, wo, r, dd.
+    constexpr int kPairs = CG * WT, kStep = kWtThreads / kPairs;
+    static_assert(kWtThreads % kPairs == 0, "whole column pairs per pass");
+    const int xcg = tid % CG, xc = (tid / CG) % WT, xrow0 = tid / kPairs;
+    const int xch = ci0 + xcg * 8;
+    const bool xfromb = xch >= ca;
+    const __nv_bfloat16 *xsrc = xfromb ? xb : x;
+    const int xC = xfromb ? cb : ca, xoff = xfromb ? xch - ca : xch, xup = xfromb ? 0 : up_a;
+    const int xHs = xup ? Ha : H, xWs = xup ? Wa : W;
+    const long long xplane = (long long)(xup ? Da : D) * xHs * xWs;
+    const unsigned xdst0 = (unsigned)(((xc * P::HH) * CG + xcg) * kWtDD * 16);
+    auto stage = [&](int ch, unsigned char *buf) {
+        int t = ch;
+        const int cw = t % tw;
+        t /= tw;
+        const int chh = t % th;
+        t /= th;
+        const int cd = t % td, b = t / td;
         const int d0 = cd * kWtDt, h0 = chh * HT, w0 = cw * WT;
-        for (int i = tid; i < WT * P::HH * CG * kWtDD; i += 128) {
-            const int cg = i % CG;
-            int q = i / CG;
-            const int c = q % WT;
-            q /= WT;
-            const int hh = q % P::HH, dd = q / P::HH;
-            const int d = d0 - 1 + dd, h = h0 - 1 + hh, w = w0 + c;
-            const bool in = d >= 0 && d < D && h >= 0 && h < H && w < W;
-            const int ch0 = ci0 + cg * 8;
-            const __nv_bfloat16 *p = x;
-            if (in) {
-                if (ch0 >= ca)
-                    p = xb + ((((long long)b * D + d) * H + h) * W + w) * cb + (ch0 - ca);
-                else if (up_a)
-                    p = x + ((((long long)b * Da + (d >> 1)) * Ha + (h >> 1)) * Wa + (w >> 1)) * ca + ch0;
-                else
-                    p = x + ((((long long)b * D + d) * H + h) * W + w) * ca + ch0;
+        {
+            const int w = w0 + xc;
+            const bool w_in = w < W;
+            const __nv_bfloat16 *base = xsrc + ((long long)b * xplane + (w >> xup)) * xC + xoff;
+            for (int r = xrow0; r < P::HH * kWtDD; r += kStep) {
+                const int hh = r / kWtDD, dd = r - hh * kWtDD;
+                const int d = d0 - 1 + dd, h = h0 - 1 + hh;
+                const bool in = w_in && (unsigned)d < (unsigned)D && (unsigned)h < (unsigned)H;
+                const __nv_bfloat16 *p = in ? base + (long long)((d >> xup) * xHs + (h >> xup)) * xWs * xC : x;
+                cp_async16(buf + xdst0 + (hh * CG * kWtDD + dd) * 16, p, in);
             }
-            cp_async16(buf + (((c * P::HH + hh) * CG + cg) * kWtDD + dd) * 16, p, in);
         }
         unsigned char *yb = buf + P::XBytes;
-        for (int i = tid; i < HT * P::WO * P::CGO * kWtDt; i += 128) {
+        const __nv_bfloat16 *dyb = dy + (long long)b * D * H * W * Co + co0;
+        for (int i = tid; i < HT * P::WO * P::CGO * kWtDt; i += kWtThreads) {
             const int cgo = i % P::CGO;
             int q = i / P::CGO;
             const int wo = q % P::WO;
             q /= P::WO;
             const int r = q % HT, dd = q / HT;
             const int d = d0 + dd, h = h0 + r, w = w0 - 1 + wo;
-            const bool in = d < D && h < H && w >= 0 && w < W;
-            const __nv_bfloat16 *p = in ? dy + ((((long long)b * D + d) * H + h) * W + w) * Co + co0 + cgo * 8 : dy;
+            const bool in = d < D && h < H && (unsigned)w < (unsigned)W;
+            const __nv_bfloat16 *p = in ? dyb + ((long long)(d * H + h) * W + w) * Co + cgo * 8 : dy;
             cp_async16(yb + (((r * P::WO + wo) * P::CGO + cgo) * kWtDt + dd) * 16, p, in);
         }
     };
@@ -1099,7 +1133,7 @@ __global__ void __launch_bounds__(128) conv3_wgrad_tc_kernel(const Conv3dArgs g,
     for (int j = 0; j < P::NCO; ++j) bsum[j] = 0.f;
     bool ok = true;
     int it = 0;
-    long long ch = blockIdx.x;
+    int ch = blockIdx.x;
     if (ch < n_chunks) stage(ch, smem);
     cp_async_commit();
     for (; ch < n_chunks; ch += gridDim.x, ++it) {
@@ -1133,7 +1167,7 @@ __global__ void __launch_bounds__(128) conv3_wgrad_tc_kernel(const Conv3dArgs g,
         }
         if (do_bias) {  // the chunk's own columns wo = 1 .. WT of the gradient tile
             const unsigned char *yb = buf + P::XBytes;
-            for (int i = tid; i < HT * WT * kWtDt; i += 128) {
+            for (int i = tid; i < HT * WT * kWtDt; i += kWtThreads) {
                 const int dd = i % kWtDt, q = i / kWtDt;
                 const int c = q % WT, r = q / WT;
 #pragma unroll
@@ -1151,7 +1185,7 @@ __global__ void __launch_bounds__(128) conv3_wgrad_tc_kernel(const Conv3dArgs g,
         }
         // the other buffer is free once the previous chunk's MMAs are done
         if (it >= 1) ok = mbar_wait_bounded(p ? mb0 : mb1, ((it - 1) >> 1) & 1);
-        const long long nx = ch + gridDim.x;
+        const int nx = ch + (int)gridDim.x;
         if (ok && nx < n_chunks) stage(nx, smem + (p ^ 1) * P::BufBytes);
         cp_async_commit();
     }
@@ -1161,20 +1195,22 @@ __global__ void __launch_bounds__(128) conv3_wgrad_tc_kernel(const Conv3dArgs g,
     ok = __syncthreads_and(ok);
     if (ok && it >= 1) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        // accumulator row of this thread: M = 128, lane quadrant rows; M = 64,
-        // rows 16 warp .. 16 warp + 15 in lanes 0-15 of the warp's quadrant
-        const int m = P::M == 128 ? warp * 32 + lane : warp * 16 + lane;
+        // accumulator row of this thread (warp w reads the lanes of quadrant
+        // w % 4): M = 128, the quadrant's rows; M = 64, rows 16 q .. 16 q + 15 in
+        // lanes 0-15 of quadrant q.  Warps w and w + 4 take alternate 16-column blocks.
+        const int quad = warp & 3, half = warp >> 2;
+        const int m = P::M == 128 ? quad * 32 + lane : quad * 16 + lane;
         const bool row_ok = P::M == 128 || lane < 16;
         const int j = m >> 3, e = m & 7;
         const int kh = j / CG, cil = (j % CG) * 8 + e;
         const bool valid = row_ok && kh < 3;
         float *red = (float *)smem;  // [co][tap][ci] of this CTA; the buffers are idle now
 #pragma unroll 1
-        for (int kd = 0; kd < 3; ++kd)
-#pragma unroll
-            for (int c16 = 0; c16 < P::N; c16 += 16) {
+        for (int blk = half; blk < 3 * (P::N / 16); blk += 2) {
+            const int kd = blk / (P::N / 16), c16 = (blk % (P::N / 16)) * 16;
+            {
                 float v[16];
-                tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(kd * P::N + c16), v);
+                tmem_ld16(tmem + ((unsigned)(quad * 32) << 16) + (unsigned)(kd * P::N + c16), v);
                 if (valid)
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj) {
@@ -1183,10 +1219,11 @@ __global__ void __launch_bounds__(128) conv3_wgrad_tc_kernel(const Conv3dArgs g,
                         red[(co * 27 + (kd * 3 + kh) * 3 + kw) * (CG * 8) + cil] = v[jj];
                     }
             }
+        }
         __syncthreads();
         // 16-byte pieces along ci: dw[(co0 + co) * 27 + tap][ci0 ..]
         constexpr int pieces = P::RedFloats / 4;
-        for (int i = tid; i < pieces; i += 128) {
+        for (int i = tid; i < pieces; i += kWtThreads) {
             const int f = i * 4;
             const int cil4 = f % (CG * 8), rest = f / (CG * 8);  // rest = co * 27 + tap
             const int co = rest / 27, tap = rest % 27;
@@ -1210,7 +1247,12 @@ __global__ void __launch_bounds__(128) conv3_wgrad_tc_kernel(const Conv3dArgs g,
                 if (lane == 0) sBias[warp][jb] = v;
             }
             __syncthreads();
-            if (tid < P::NCO) atomicAdd(db + co0 + tid, sBias[0][tid] + sBias[1][tid] + sBias[2][tid] + sBias[3][tid]);
+            if (tid < P::NCO) {
+                float v = 0.f;
+#pragma unroll
+                for (int w = 0; w < kWtThreads / 32; ++w) v += sBias[w][tid];
+                atomicAdd(db + co0 + tid, v);
+            }
         }
     }
     if (!ok && tid == 0) atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
@@ -1897,6 +1939,7 @@ cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy
         const int cg = wide ? 4 : 2, ht = wide ? 2 : 4, wt = 8;
         const long long chunks = (long long)g.batch * ((g.in_d + kWtDt - 1) / kWtDt) * ((g.in_h + ht - 1) / ht) *
                                  ((g.in_w + wt - 1) / wt);
+        if (chunks >= (1ll << 31) || (long long)g.in_d * g.in_h * g.in_w >= (1ll << 31)) return cudaErrorInvalidValue;
         const int ytiles = g.c_out / 16, zslices = g.c_in / (8 * cg);
         long long gx = std::max(1ll, (long long)sms * 2 / (ytiles * zslices));
         if (gx > chunks) gx = chunks;
@@ -1906,13 +1949,13 @@ cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy
             static OccCache cache;
             e = prepare_kernel_smem(cache, conv3_wgrad_tc_kernel<4, 2, 8>, P::Smem);
             if (e != cudaSuccess) return e;
-            conv3_wgrad_tc_kernel<4, 2, 8><<<grid, 128, P::Smem, st>>>(g, X, Y, dw, db, ca, up_a, XB, vec);
+            conv3_wgrad_tc_kernel<4, 2, 8><<<grid, kWtThreads, P::Smem, st>>>(g, X, Y, dw, db, ca, up_a, XB, vec);
         } else {
             using P = WgTc<2, 4, 8>;
             static OccCache cache;
             e = prepare_kernel_smem(cache, conv3_wgrad_tc_kernel<2, 4, 8>, P::Smem);
             if (e != cudaSuccess) return e;
-            conv3_wgrad_tc_kernel<2, 4, 8><<<grid, 128, P::Smem, st>>>(g, X, Y, dw, db, ca, up_a, XB, vec);
+            conv3_wgrad_tc_kernel<2, 4, 8><<<grid, kWtThreads, P::Smem, st>>>(g, X, Y, dw, db, ca, up_a, XB, vec);
         }
         return cudaGetLastError();
     }
