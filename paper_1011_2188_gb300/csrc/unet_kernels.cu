@@ -361,19 +361,25 @@ __device__ __forceinline__ void tmem_ld16x3(unsigned t0, unsigned t1, unsigned t
 // ReLU derivative of the previous layer, applied to a data-gradient output
 // row: channels [n, n + 16) of voxel v become zero where that layer's output
 // (the convolution's input, `mask`, Nn channels per voxel) is not positive.
-__device__ __forceinline__ void apply_relu_mask16(const void *mask, long long v, int Nn, int n, float a[16]) {
+// ReLU derivative of the previous layer on CW output channels of a
+// data-gradient row (zero where that layer's output is not positive).
+template <int CW>
+__device__ __forceinline__ void apply_relu_mask(const void *mask, long long v, int Nn, int n, float a[CW]) {
     const uint4 *m = (const uint4 *)((const __nv_bfloat16 *)mask + v * Nn + n);
-    const uint4 q[2] = {__ldg(m), __ldg(m + 1)};
+    uint4 q[CW / 8];
+#pragma unroll
+    for (int k = 0; k < CW / 8; ++k) q[k] = __ldg(m + k);
     const unsigned short *h = (const unsigned short *)q;
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
+    for (int j = 0; j < CW; ++j)
         if ((short)h[j] <= 0) a[j] = 0.f;  // sign bit set, or +0: not positive
 }
 
-// Mask of output channels [n, n + 16) at voxel (b, d, h, w) of a D x H x W
+// Mask of output channels [n, n + CW) at voxel (b, d, h, w) of a D x H x W
 // grid when the layer's forward input was [upsample?(a) | b] (g.mask_ca > 0).
-__device__ __forceinline__ void apply_relu_mask16_fused(const Conv3dArgs &g, int Nn, int bb, int d, int h, int w,
-                                                        int D, int H, int W, int n, float a[16]) {
+template <int CW>
+__device__ __forceinline__ void apply_relu_mask_fused(const Conv3dArgs &g, int Nn, int bb, int d, int h, int w, int D,
+                                                      int H, int W, int n, float a[CW]) {
     const __nv_bfloat16 *m;
     if (n < g.mask_ca) {
         const long long vv = g.mask_up ? (((long long)bb * (D / 2) + (d >> 1)) * (H / 2) + (h >> 1)) * (W / 2) + (w >> 1)
@@ -383,11 +389,42 @@ __device__ __forceinline__ void apply_relu_mask16_fused(const Conv3dArgs &g, int
         const long long vv = (((long long)bb * D + d) * H + h) * W + w;
         m = (const __nv_bfloat16 *)g.mask_b + vv * (Nn - g.mask_ca) + (n - g.mask_ca);
     }
-    const uint4 q[2] = {__ldg((const uint4 *)m), __ldg((const uint4 *)m + 1)};
+    uint4 q[CW / 8];
+#pragma unroll
+    for (int k = 0; k < CW / 8; ++k) q[k] = __ldg((const uint4 *)m + k);
     const unsigned short *hh = (const unsigned short *)q;
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
+    for (int j = 0; j < CW; ++j)
         if ((short)hh[j] <= 0) a[j] = 0.f;
+}
+
+__device__ __forceinline__ void tmem_ld8x3(unsigned t0, unsigned t1, unsigned t2, float a[8], float b[8], float c[8]) {
+    unsigned r[24];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%24];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%25];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%26];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+        : "r"(t0), "r"(t1), "r"(t2)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        a[i] = __uint_as_float(r[i]);
+        b[i] = __uint_as_float(r[8 + i]);
+        c[i] = __uint_as_float(r[16 + i]);
+    }
+}
+
+__device__ __forceinline__ void apply_relu_mask16(const void *mask, long long v, int Nn, int n, float a[16]) {
+    const uint4 *m = (const uint4 *)((const __nv_bfloat16 *)mask + v * Nn + n);
+    const uint4 q[2] = {__ldg(m), __ldg(m + 1)};
+    const unsigned short *h = (const unsigned short *)q;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        if ((short)h[j] <= 0) a[j] = 0.f;  // sign bit set, or +0: not positive
 }
 
 __device__ __forceinline__ void umma_commit(unsigned mbar) {
@@ -766,8 +803,12 @@ inline bool dwalk_fits(int S, int NT) {
     return S * 9 * 2 * (3 * NT) * 16 + 5 * S * kDwPlaneSliceBytes <= 227 * 1024 - 1024;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
+// THR = 256: eight warps, warps w and w + 4 sharing an accumulator row
+// quadrant (measured faster for 32-channel tiles and two-slice inputs);
+// THR = 128 for one 16-channel input slice and 16-channel tiles (74 vs 82 us
+// at 128^3).
+template <int NT, int THR>
+__global__ void __launch_bounds__(THR) conv3_dwalk_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
                                                           const __nv_bfloat16 *wt, const float *bias,
                                                           __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn,
                                                           int relu, int ca, int up_a, const __nv_bfloat16 *src_b,
@@ -810,7 +851,7 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
     // resident weights of every input slice (through L1: all CTAs read the same)
     {
         constexpr int kChunks = 9 * 2 * N3;  // per slice
-        for (int i = tid; i < S * kChunks; i += 128) {
+        for (int i = tid; i < S * kChunks; i += THR) {
             const int sl = i / kChunks, r = i % kChunks;
             const int n = r % N3, q = r / N3, kc = q & 1, kdh = q >> 1;
             const int co = n0 + (n % NT), kw = n / NT;
@@ -826,6 +867,7 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
     const unsigned tmem = tmem_slot;
 
     // this thread's halo column and k-chunk; it walks rows r = slice * 10 + h
+    constexpr int kRowStep = THR / 32;
     const int kc = tid & 1, hw = (tid >> 1) & 15, r0 = tid >> 5;
     const unsigned hdst = (unsigned)((((hw >> 3) * 2 + kc) * 128) + (hw & 7) * 16);
     bool ok = true;
@@ -847,7 +889,7 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
                 const int d = d_begin - 1 + j;
                 unsigned char *dst = sP + (j % R) * plane_bytes + hdst;
                 const bool d_in = w_in && d >= 0 && d < D;
-                for (int r = r0; r < S * 10; r += 4) {
+                for (int r = r0; r < S * 10; r += kRowStep) {
                     const int sl = r / 10, hh = r - 10 * sl;
                     const int h = h0 - 1 + hh, c0 = sl * 16;
                     const bool in = d_in && h >= 0 && h < H;
@@ -873,22 +915,28 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
             // warp-uniform outcome (the shuffles below need every lane)
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(ab ? mb1 : mb0, ph))) return false;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const int m = warp * 32 + lane;
+            // warp w reads the accumulator rows of lane quadrant w % 4; with eight
+            // warps, w and w + 4 take output channels [0, NT/2) and [NT/2, NT)
+            constexpr int CW = NT * 128 / THR;
+            static_assert(CW == 8 || CW == 16, "8 or 16 output channels per thread");
+            const int quad = warp & 3, c = (warp >> 2) * CW;
+            const int m = quad * 32 + lane;
             const int ho = h0 + (m >> 4), wl = m & 15, wo = w0 + wl;
             const bool out_in = wl < 14 && ho < H && wo < W;
             const long long v = (((long long)b * D + d_begin + i) * H + ho) * W + wo;
-            const unsigned base = tmem + ((unsigned)(warp * 32) << 16) + ab * kAccCols;
-#pragma unroll
-            for (int c = 0; c < NT; c += 16) {
-                float a0[16], a1[16], a2[16];
+            const unsigned base = tmem + ((unsigned)(quad * 32) << 16) + ab * kAccCols;
+            float a0[CW], a1[CW], a2[CW];
+            if constexpr (CW == 16)
                 tmem_ld16x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c), a0, a1, a2);
+            else
+                tmem_ld8x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c), a0, a1, a2);
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    a0[j] += __shfl_down_sync(0xffffffffu, a1[j], 1) + __shfl_down_sync(0xffffffffu, a2[j], 2);
-                const int n = n0 + c;
-                if (!out_in || n >= Nn) continue;
+            for (int j = 0; j < CW; ++j)
+                a0[j] += __shfl_down_sync(0xffffffffu, a1[j], 1) + __shfl_down_sync(0xffffffffu, a2[j], 2);
+            const int n = n0 + c;
+            if (out_in && n < Nn) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
+                for (int j = 0; j < CW; ++j) {
                     float x = a0[j];
                     if (bias) x += sBias[c + j];
                     if (relu) x = fmaxf(x, 0.f);
@@ -896,21 +944,21 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
                 }
                 if (g.mask) {
                     if (g.mask_ca > 0)
-                        apply_relu_mask16_fused(g, Nn, b, d_begin + i, ho, wo, D, H, W, n, a0);
+                        apply_relu_mask_fused<CW>(g, Nn, b, d_begin + i, ho, wo, D, H, W, n, a0);
                     else
-                        apply_relu_mask16(g.mask, v, Nn, n, a0);
+                        apply_relu_mask<CW>(g.mask, v, Nn, n, a0);
                 }
                 if (out_f32) {
                     float4 *dst = (float4 *)(out_f32 + v * Nn + n);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
+                    for (int j = 0; j < CW / 4; ++j)
                         dst[j] = make_float4(a0[4 * j], a0[4 * j + 1], a0[4 * j + 2], a0[4 * j + 3]);
                 }
                 if (out_bf16) {
-                    uint4 qv[2];
+                    uint4 qv[CW / 8];
                     unsigned *qq = (unsigned *)qv;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
+                    for (int j = 0; j < CW / 2; ++j) {
                         __nv_bfloat162 p2 = __floats2bfloat162_rn(a0[2 * j], a0[2 * j + 1]);
                         qq[j] = *(unsigned *)&p2;
                     }
@@ -920,8 +968,8 @@ __global__ void __launch_bounds__(128) conv3_dwalk_kernel(const Conv3dArgs g, co
                                      : (n < g.mask_ca ? (uint4 *)(out_bf16 + v * g.mask_ca + n)
                                                       : (uint4 *)((__nv_bfloat16 *)g.out_b + v * (Nn - g.mask_ca) +
                                                                   (n - g.mask_ca)));
-                    dst[0] = qv[0];
-                    dst[1] = qv[1];
+#pragma unroll
+                    for (int j = 0; j < CW / 8; ++j) dst[j] = qv[j];
                 }
             }
             // every warp has read this accumulator before MMAs overwrite it
@@ -1261,6 +1309,386 @@ __global__ void __launch_bounds__(kWtThreads) conv3_wgrad_tc_kernel(const Conv3d
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(P::Cols));
+    }
+}
+
+// ---- 2^3 stride-2 convolutions (the down-convolutions) on tcgen05.
+// Output voxel v = (d, h, w) reads the 2 x 2 x 2 input block at (2d, 2h, 2w):
+// tap t = (td * 2 + th) * 2 + tw, weights [co][t][ci].  Every input voxel
+// belongs to exactly one block (the output grid is the input halved), so no
+// tile needs a halo.
+constexpr int kS2Vox = 128;      // output voxels per tile or K chunk
+constexpr int kS2Threads = 256;
+
+// Weight gradient dW[co][t][ci] += sum over v of dy[v][co] * x[2v + t][ci]:
+// M = (tap, channel group) of a 16-channel input slice = 128 rows, N = Co
+// (NCO), K = output voxels, 128 per chunk.  Both operands MN-major: A [tap][group][v][8 ch]
+// (M groups 2048 bytes apart), B [co group][v][8 ch].  Chunks are staged with
+// cp.async into two buffers (chunk i + 1 while chunk i's eight MMAs run), the
+// accumulator stays in TMEM until the CTA's last chunk and is added to dw with
+// 16-byte vector reductions; the CTAs of the first slice also sum dy into db.
+template <int NCO>
+__global__ void __launch_bounds__(kS2Threads) conv_s2_wgrad_tc_kernel(const Conv3dArgs g, const __nv_bfloat16 *x,
+                                                                      const __nv_bfloat16 *dy, float *dw, float *db,
+                                                                      int vec) {
+    constexpr int CGO = NCO / 8;
+    constexpr int ABytes = 16 * kS2Vox * 16, BBytes = CGO * kS2Vox * 16, Buf = ABytes + BBytes;
+    constexpr unsigned Cols = NCO;
+    static_assert(NCO * 8 * 16 * 4 <= 2 * Buf, "reduction tile fits the buffers");
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ unsigned tmem_slot;
+    __shared__ float sb[NCO];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int D = g.in_d, H = g.in_h, W = g.in_w, Ci = g.c_in;
+    const int D2 = g.out_d, H2 = g.out_h, W2 = g.out_w;
+    const int ci0 = blockIdx.z * 16;
+    const long long V = (long long)g.batch * D2 * H2 * W2;
+    const int n_chunks = (int)((V + kS2Vox - 1) / kS2Vox);
+    const bool do_bias = db != nullptr && blockIdx.z == 0;
+    const unsigned mb0 = smem_u32(&mbar[0]), mb1 = smem_u32(&mbar[1]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb1));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (tid < NCO) sb[tid] = 0.f;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(Cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = tmem_slot;
+    // A: thread keeps q = (tw, group) and two voxels vA, vA + 64; 8 pieces per
+    // chunk (tdh = k / 2).  B: thread keeps its co group and voxels stepping by
+    // 256 / CGO.
+    const int q = tid & 3, tw = q >> 1, cg = q & 1, vA = tid >> 2;
+    const int bcgo = tid % CGO, bv0 = tid / CGO;
+    constexpr int kBStep = kS2Threads / CGO;
+    float bsum[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) bsum[j] = 0.f;
+    auto voxel_base = [&](int v) -> const __nv_bfloat16 * {  // the launcher keeps V below 2^31
+        const int w = v % W2;
+        int t = v / W2;
+        const int h = t % H2;
+        t /= H2;
+        const int d = t % D2, b = t / D2;
+        return x + ((((long long)b * D + 2 * d) * H + 2 * h) * W + 2 * w + tw) * Ci + ci0 + cg * 8;
+    };
+    auto stage = [&](int ch, unsigned char *buf) {
+        const long long v0 = (long long)ch * kS2Vox;
+        const bool okA = v0 + vA < V, okB = v0 + vA + 64 < V;
+        const __nv_bfloat16 *pa = okA ? voxel_base((int)(v0 + vA)) : x, *pb = okB ? voxel_base((int)(v0 + vA + 64)) : x;
+        const long long sh = (long long)W * Ci, sd = (long long)H * W * Ci;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int tdh = k >> 1, vi = vA + (k & 1) * 64;
+            const bool ok = (k & 1) ? okB : okA;
+            const __nv_bfloat16 *p = (k & 1) ? pb : pa;
+            const long long off = (tdh >> 1) * sd + (tdh & 1) * sh;
+            const int tap = tdh * 2 + tw;
+            cp_async16(buf + ((tap * 2 + cg) * kS2Vox + vi) * 16, ok ? p + off : x, ok);
+        }
+        unsigned char *bb = buf + ABytes;
+#pragma unroll
+        for (int vi = bv0; vi < kS2Vox; vi += kBStep) {
+            const bool ok = v0 + vi < V;
+            cp_async16(bb + (bcgo * kS2Vox + vi) * 16, ok ? dy + (v0 + vi) * g.c_out + bcgo * 8 : dy, ok);
+        }
+    };
+    bool ok = true;
+    int it = 0;
+    int ch = blockIdx.x;
+    if (ch < n_chunks) stage(ch, smem);
+    cp_async_commit();
+    for (; ch < n_chunks; ch += gridDim.x, ++it) {
+        const int p = it & 1;
+        unsigned char *buf = smem + p * Buf;
+        cp_async_wait<0>();
+        if (do_bias) {  // this thread's own staged dy pieces (zero past the end)
+#pragma unroll
+            for (int vi = bv0; vi < kS2Vox; vi += kBStep) {
+                const uint4 u = *(const uint4 *)(buf + ABytes + (bcgo * kS2Vox + vi) * 16);
+                const __nv_bfloat162 *h2 = (const __nv_bfloat162 *)&u;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float2 f = __bfloat1622float2(h2[j]);
+                    bsum[2 * j] += f.x;
+                    bsum[2 * j + 1] += f.y;
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            constexpr unsigned idesc = umma_idesc_mn(128, NCO);
+            // LBO: 128 bytes between K groups (8 voxels); SBO: 2048 bytes between M (N) groups
+            const unsigned long long ad0 = umma_desc(smem_u32(buf), 128, kS2Vox * 16);
+            const unsigned long long bd0 = umma_desc(smem_u32(buf + ABytes), 128, kS2Vox * 16);
+#pragma unroll
+            for (int ks = 0; ks < kS2Vox / 16; ++ks)
+                umma_bf16(tmem, ad0 + (unsigned long long)(ks * 16), bd0 + (unsigned long long)(ks * 16), idesc,
+                          (it > 0 || ks > 0) ? 1 : 0);
+            umma_commit(p ? mb1 : mb0);
+        }
+        if (it >= 1) ok = mbar_wait_bounded(p ? mb0 : mb1, ((it - 1) >> 1) & 1);
+        const int nx = ch + (int)gridDim.x;
+        if (ok && nx < n_chunks) stage(nx, smem + (p ^ 1) * Buf);
+        cp_async_commit();
+    }
+    if (ok && it >= 1) ok = mbar_wait_bounded(((it - 1) & 1) ? mb1 : mb0, ((it - 1) >> 1) & 1);
+    cp_async_wait<0>();
+    ok = __syncthreads_and(ok);
+    if (ok && it >= 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const int quad = warp & 3, half = warp >> 2;
+        const int m = quad * 32 + lane;  // row (tap, group, channel)
+        const int tap = m >> 4, cil = ((m >> 3) & 1) * 8 + (m & 7);
+        float *red = (float *)smem;  // [co][tap][16 ci]
+#pragma unroll 1
+        for (int c16 = half * 16; c16 < NCO; c16 += 32) {
+            float v[16];
+            tmem_ld16(tmem + ((unsigned)(quad * 32) << 16) + (unsigned)c16, v);
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) red[((c16 + jj) * 8 + tap) * 16 + cil] = v[jj];
+        }
+        __syncthreads();
+        for (int i = tid; i < NCO * 8 * 4; i += kS2Threads) {
+            const int c4 = (i & 3) * 4, rest = i >> 2;  // rest = co * 8 + tap
+            const float4 qv = *(const float4 *)(red + i * 4);
+            float *dst = dw + (long long)rest * Ci + ci0 + c4;
+            if (vec) {
+                red_add_v4(dst, qv.x, qv.y, qv.z, qv.w);
+            } else {
+                atomicAdd(dst, qv.x);
+                atomicAdd(dst + 1, qv.y);
+                atomicAdd(dst + 2, qv.z);
+                atomicAdd(dst + 3, qv.w);
+            }
+        }
+        if (do_bias) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) atomicAdd(&sb[bcgo * 8 + j], bsum[j]);
+            __syncthreads();
+            if (tid < NCO) atomicAdd(db + tid, sb[tid]);
+        }
+    }
+    if (!ok && tid == 0) atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(Cols));
+    }
+}
+
+// Forward (MODE 0) and data gradient (MODE 1) of the 2^3 stride-2
+// convolution: M = 128 output voxels per tile, K-major operands in the
+// canonical no-swizzle layout (core matrices of 8 rows x 16 bytes), the
+// weights resident in shared memory, A tiles double-buffered with cp.async
+// and two TMEM accumulators, so that tile i's epilogue and tile i + 1's
+// staging run while tile i's MMAs execute.
+//   MODE 0: A[v][k] = x[2v + t][ci] with k = t Ci + ci (K = 8 Ci; the eight
+//           2 x 2 x 2 block values of a voxel, two contiguous 2 Ci runs per
+//           (td, th)), B[n = co][k] = w[co][t][ci]; epilogue bias, ReLU, y.
+//   MODE 1: A[v][k = co] = dy[v][co] (K = Co), B[n][co] = w[co][t][ci] for the
+//           N-tile's n = t Ci + ci (rows of w_t = [ci][t][co]); epilogue: the
+//           16 columns of one tap are channels ci .. ci + 15 of input voxel
+//           2v + t, masked by the ReLU derivative and stored.
+template <int MODE, int N, int K>
+__global__ void __launch_bounds__(128) conv_s2_tc_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
+                                                         const __nv_bfloat16 *wt, const float *bias,
+                                                         __nv_bfloat16 *out_bf16, float *out_f32) {
+    constexpr int ABytes = kS2Vox * K * 2, BBytes = N * K * 2;
+    constexpr unsigned Cols = 2 * N;
+    static_assert(Cols <= 512 && K % 16 == 0 && N % 16 == 0, "tile shape");
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ unsigned tmem_slot;
+    unsigned char *sB = smem, *sA = smem + BBytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int D = g.in_d, H = g.in_h, W = g.in_w, Ci = g.c_in, Co = g.c_out;
+    const int D2 = g.out_d, H2 = g.out_h, W2 = g.out_w;
+    const int V = g.batch * D2 * H2 * W2;  // the launcher keeps it below 2^31
+    const int n_tiles = (V + kS2Vox - 1) / kS2Vox;
+    const int n0 = blockIdx.y * N;         // MODE 1: first column (t Ci + ci) of this N-tile
+    const unsigned mb0 = smem_u32(&mbar[0]), mb1 = smem_u32(&mbar[1]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb1));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(Cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = tmem_slot;
+    // resident B: element (n, k) at ((k / 8) * (N / 8) + n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2
+    for (int i = tid; i < N * (K / 8); i += 128) {
+        const int n = i % N, kg = i / N;
+        const __nv_bfloat16 *p;
+        if (MODE == 0) {
+            p = wt + (long long)n * K + kg * 8;  // w[co][t Ci + ci]
+        } else {
+            const int col = n0 + n, t = col / Ci, ci = col % Ci;
+            p = wt + ((long long)ci * 8 + t) * Co + kg * 8;  // w_t[ci][t][co]
+        }
+        cp_async16_ca(sB + ((kg * (N / 8) + n / 8) * 8 + (n % 8)) * 16, p, true);
+    }
+    // A tile of output voxels v0 .. v0 + 127: element (v, k) at
+    // ((k / 8) * 16 + v / 8) * 128 + (v % 8) * 16 + (k % 8) * 2
+    auto stage = [&](int tile, unsigned char *buf) {
+        const int v0 = tile * kS2Vox;
+        if (MODE == 0) {
+            // per voxel and (td, th): 2 Ci contiguous values = 2 Ci / 8 pieces
+            constexpr int PV = K / 8;  // pieces per voxel
+            for (int i = tid; i < kS2Vox * PV; i += 128) {
+                const int j = i % PV, vi = i / PV;  // j = tdh * (PV / 4) + (piece within the run)
+                const int v = v0 + vi;
+                const bool ok = v < V;
+                const __nv_bfloat16 *p = src;
+                if (ok) {
+                    const int w = v % W2;
+                    int t = v / W2;
+                    const int h = t % H2;
+                    t /= H2;
+                    const int d = t % D2, b = t / D2;
+                    const int tdh = j / (PV / 4), r = j % (PV / 4);
+                    p = src + ((((long long)b * D + 2 * d + (tdh >> 1)) * H + 2 * h + (tdh & 1)) * W + 2 * w) * Ci + r * 8;
+                }
+                cp_async16(buf + ((j * 16 + vi / 8) * 8 + (vi % 8)) * 16, p, ok);
+            }
+        } else {
+            constexpr int PV = K / 8;
+            for (int i = tid; i < kS2Vox * PV; i += 128) {
+                const int j = i % PV, vi = i / PV;
+                const bool ok = v0 + vi < V;
+                cp_async16(buf + ((j * 16 + vi / 8) * 8 + (vi % 8)) * 16,
+                           ok ? src + (long long)(v0 + vi) * Co + j * 8 : src, ok);
+            }
+        }
+    };
+    // epilogue of the tile in accumulator ab: row m = this thread's voxel
+    auto epilogue = [&](int tile, unsigned ab, unsigned ph) -> bool {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(ab ? mb1 : mb0, ph))) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const int v = tile * kS2Vox + warp * 32 + lane;
+        const bool in = v < V;
+        int d = 0, h = 0, w = 0, b = 0;
+        if (in) {
+            w = v % W2;
+            int t = v / W2;
+            h = t % H2;
+            t /= H2;
+            d = t % D2;
+            b = t / D2;
+        }
+        const unsigned base = tmem + ((unsigned)(warp * 32) << 16) + ab * N;
+#pragma unroll 1
+        for (int c = 0; c < N; c += 16) {
+            float a[16];
+            tmem_ld16(base + (unsigned)c, a);
+            if (!in) continue;
+            if (MODE == 0) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float x = a[j];
+                    if (bias) x += __ldg(bias + c + j);
+                    if (g.relu) x = fmaxf(x, 0.f);
+                    a[j] = x;
+                }
+                if (out_f32) {
+                    float4 *dst = (float4 *)(out_f32 + (long long)v * Co + c);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) dst[j] = make_float4(a[4 * j], a[4 * j + 1], a[4 * j + 2], a[4 * j + 3]);
+                }
+                if (out_bf16) {
+                    uint4 qv[2];
+                    unsigned *qq = (unsigned *)qv;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        __nv_bfloat162 p2 = __floats2bfloat162_rn(a[2 * j], a[2 * j + 1]);
+                        qq[j] = *(unsigned *)&p2;
+                    }
+                    uint4 *dst = (uint4 *)(out_bf16 + (long long)v * Co + c);
+                    dst[0] = qv[0];
+                    dst[1] = qv[1];
+                }
+            } else {
+                const int col = n0 + c, t = col / Ci, ci = col % Ci;
+                const long long xv = (((long long)b * D + 2 * d + (t >> 2)) * H + 2 * h + ((t >> 1) & 1)) * W + 2 * w + (t & 1);
+                if (g.mask) apply_relu_mask<16>(g.mask, xv, Ci, ci, a);
+                uint4 qv[2];
+                unsigned *qq = (unsigned *)qv;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    __nv_bfloat162 p2 = __floats2bfloat162_rn(a[2 * j], a[2 * j + 1]);
+                    qq[j] = *(unsigned *)&p2;
+                }
+                uint4 *dst = (uint4 *)(out_bf16 + xv * Ci + ci);
+                dst[0] = qv[0];
+                dst[1] = qv[1];
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        return true;
+    };
+    bool ok = true;
+    int it = 0;
+    int tile = blockIdx.x;
+    if (tile < n_tiles) stage(tile, sA);
+    cp_async_commit();  // with the resident weights
+    for (; tile < n_tiles; tile += gridDim.x, ++it) {
+        const unsigned ab = it & 1u;
+        unsigned char *buf = sA + ab * ABytes;
+        cp_async_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        // also agrees on the outcome of the previous epilogue's bounded wait
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            constexpr unsigned idesc = umma_idesc(128, N);
+            // A: K groups 2048 bytes apart, 8-row groups 128; B: K groups N * 16 apart
+            const unsigned long long ad0 = umma_desc(smem_u32(buf), kS2Vox * 16, 128);
+            const unsigned long long bd0 = umma_desc(smem_u32(sB), N * 16, 128);
+#pragma unroll
+            for (int ks = 0; ks < K / 16; ++ks)
+                umma_bf16(tmem + ab * N, ad0 + (unsigned long long)(ks * 2 * kS2Vox), bd0 + (unsigned long long)(ks * 2 * N),
+                          idesc, ks > 0 ? 1 : 0);
+            umma_commit(ab ? mb1 : mb0);
+        }
+        // the previous tile's epilogue frees its accumulator and A buffer
+        if (it > 0) ok = epilogue(tile - (int)gridDim.x, ab ^ 1u, ((it - 1) >> 1) & 1u);
+        const int nx = tile + (int)gridDim.x;
+        if (ok && nx < n_tiles) stage(nx, sA + (ab ^ 1u) * ABytes);
+        cp_async_commit();
+    }
+    if (__syncthreads_and(ok) && it > 0)
+        ok = epilogue(blockIdx.x + (it - 1) * (int)gridDim.x, (unsigned)(it - 1) & 1u, ((it - 1) >> 1) & 1u);
+    else
+        ok = ok && it == 0;
+    if (!ok && tid == 0) atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
+    cp_async_wait<0>();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(Cols));
     }
 }
 
@@ -1806,18 +2234,23 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
         const int smem = wbytes + R * plane;
         cudaFuncAttributes fa;
         int per_sm = 0;
+        const int thr = (NT == 16 && S == 1) ? 128 : 256;
         if (NT == 32) {
             static OccCache cache;
-            e = prepare_kernel_smem(cache, conv3_dwalk_kernel<32>, smem);
-            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv3_dwalk_kernel<32>);
+            e = prepare_kernel_smem(cache, conv3_dwalk_kernel<32, 256>, smem);
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv3_dwalk_kernel<32, 256>);
+        } else if (thr == 128) {
+            static OccCache cache;
+            e = prepare_kernel_smem(cache, conv3_dwalk_kernel<16, 128>, smem);
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv3_dwalk_kernel<16, 128>);
         } else {
             static OccCache cache;
-            e = prepare_kernel_smem(cache, conv3_dwalk_kernel<16>, smem);
-            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv3_dwalk_kernel<16>);
+            e = prepare_kernel_smem(cache, conv3_dwalk_kernel<16, 256>, smem);
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv3_dwalk_kernel<16, 256>);
         }
         if (e != cudaSuccess) return e;
         const int by_smem = smem_sm / (smem + (int)fa.sharedSizeBytes + 1024);
-        const int by_regs = 65536 / (128 * std::max(fa.numRegs, 1));
+        const int by_regs = 65536 / (thr * std::max(fa.numRegs, 1));
         per_sm = std::max(1, std::min(per_sm_tmem, std::min(by_smem, by_regs)));
         const int ntiles = (Nn + NT - 1) / NT;
         const long long planes = (long long)g.batch * ((g.in_h + 7) / 8) * ((g.in_w + 13) / 14) * g.in_d;
@@ -1825,9 +2258,11 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
         if (gx > planes) gx = planes;
         const dim3 grid((unsigned)gx, (unsigned)ntiles);
         if (NT == 32)
-            conv3_dwalk_kernel<32><<<grid, 128, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb, pf);
+            conv3_dwalk_kernel<32, 256><<<grid, 256, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb, pf);
+        else if (thr == 128)
+            conv3_dwalk_kernel<16, 128><<<grid, 128, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb, pf);
         else
-            conv3_dwalk_kernel<16><<<grid, 128, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb, pf);
+            conv3_dwalk_kernel<16, 256><<<grid, 256, smem, st>>>(g, s, w, bias, ob, out_f32, Cs, Nn, relu, ca, up_a, sb, pf);
         return cudaGetLastError();
     }
     // 64-channel tiles (27 MMAs of N = 64) when they give at least one CTA per SM
@@ -1893,8 +2328,53 @@ cudaError_t launch_flip_transpose(const void *w, void *wf, int co, int k, int ci
     return cudaGetLastError();
 }
 
+// The down-convolutions on tcgen05 (2^3, stride 2, no padding): returns
+// false, launching nothing, for a shape without an instantiation.
+template <int MODE, int N, int K>
+cudaError_t launch_s2_tc(const Conv3dArgs &g, const void *src, const void *wt, const float *bias, void *out_bf16,
+                         float *out_f32, int ntiles_n, cudaStream_t st) {
+    static OccCache cache;
+    constexpr int smem = N * K * 2 + 2 * kS2Vox * K * 2;
+    int dev = 0, sms = 0, smem_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = prepare_kernel_smem(cache, conv_s2_tc_kernel<MODE, N, K>, smem);
+    if (e != cudaSuccess) return e;
+    const int per_sm = std::max(1, std::min(512 / (2 * N), smem_sm / (smem + 2048)));
+    const long long tiles = ((long long)g.batch * g.out_d * g.out_h * g.out_w + kS2Vox - 1) / kS2Vox;
+    long long gx = std::max(1ll, (long long)sms * per_sm / ntiles_n);
+    if (gx > tiles) gx = tiles;
+    conv_s2_tc_kernel<MODE, N, K><<<dim3((unsigned)gx, (unsigned)ntiles_n), 128, smem, st>>>(
+        g, (const __nv_bfloat16 *)src, (const __nv_bfloat16 *)wt, bias, (__nv_bfloat16 *)out_bf16, out_f32);
+    return cudaGetLastError();
+}
+
+bool s2_tc_shape(const Conv3dArgs &g, int mode, const float *out_f32) {
+    if (g.ksize != 2 || g.stride != 2 || g.pad != 0) return false;
+    if ((long long)g.batch * g.out_d * g.out_h * g.out_w >= (1ll << 31) - kS2Vox) return false;
+    if (mode == 0) return (g.c_in == 16 && g.c_out == 32) || (g.c_in == 32 && g.c_out == 64);
+    return out_f32 == nullptr && ((g.c_in == 16 && g.c_out == 32) || (g.c_in == 32 && g.c_out == 64) ||
+                                  (g.c_in == 64 && g.c_out == 128));
+}
+
 cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const void *wt, const float *bias,
                         void *out_bf16, float *out_f32, cudaStream_t st) {
+    if (s2_tc_shape(g, mode, out_f32)) {
+        if (mode == 0) {
+            if (g.c_in == 16) return launch_s2_tc<0, 32, 128>(g, src, wt, bias, out_bf16, out_f32, 1, st);
+            return launch_s2_tc<0, 64, 256>(g, src, wt, bias, out_bf16, out_f32, 1, st);
+        }
+        // input voxels of an odd-sized axis's last plane reach no output: zero gradient
+        if ((g.in_d | g.in_h | g.in_w) & 1) {
+            const cudaError_t e = cudaMemsetAsync(
+                out_bf16, 0, (size_t)g.batch * g.in_d * g.in_h * g.in_w * g.c_in * sizeof(__nv_bfloat16), st);
+            if (e != cudaSuccess) return e;
+        }
+        if (g.c_in == 16) return launch_s2_tc<1, 128, 32>(g, src, wt, nullptr, out_bf16, nullptr, 1, st);
+        if (g.c_in == 32) return launch_s2_tc<1, 256, 64>(g, src, wt, nullptr, out_bf16, nullptr, 1, st);
+        return launch_s2_tc<1, 256, 128>(g, src, wt, nullptr, out_bf16, nullptr, 2, st);
+    }
     const int Nn = mode == 0 ? g.c_out : g.c_in;
     const long long rows = (long long)g.batch * (mode == 0 ? (long long)g.out_d * g.out_h * g.out_w
                                                           : (long long)g.in_d * g.in_h * g.in_w);
@@ -1958,6 +2438,36 @@ cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy
             conv3_wgrad_tc_kernel<2, 4, 8><<<grid, kWtThreads, P::Smem, st>>>(g, X, Y, dw, db, ca, up_a, XB, vec);
         }
         return cudaGetLastError();
+    }
+    const long long vox2 = (long long)g.batch * g.out_d * g.out_h * g.out_w;
+    if (g.ksize == 2 && g.stride == 2 && g.pad == 0 && (g.c_out == 32 || g.c_out == 64 || g.c_out == 128) &&
+        vox2 < (1ll << 31) - kS2Vox) {  // the down-convolutions: tcgen05, voxels as K
+        int dev = 0, sms = 0, smem_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e != cudaSuccess) return e;
+        const int vec = ((uintptr_t)dw & 15) == 0 ? 1 : 0;
+        const int smem = 2 * (16 + g.c_out / 8) * kS2Vox * 16;
+        const int per_sm = std::max(1, smem_sm / (smem + 2048));
+        const long long chunks = (vox2 + kS2Vox - 1) / kS2Vox;
+        const int zs = g.c_in / 16;
+        long long gx = std::max(1ll, (long long)sms * per_sm / zs);
+        if (gx > chunks) gx = chunks;
+        const dim3 grid((unsigned)gx, 1, (unsigned)zs);
+        auto X = (const __nv_bfloat16 *)x, Y = (const __nv_bfloat16 *)dy;
+        static OccCache c32, c64, c128;
+        if (g.c_out == 32) {
+            e = prepare_kernel_smem(c32, conv_s2_wgrad_tc_kernel<32>, smem);
+            if (e == cudaSuccess) conv_s2_wgrad_tc_kernel<32><<<grid, kS2Threads, smem, st>>>(g, X, Y, dw, db, vec);
+        } else if (g.c_out == 64) {
+            e = prepare_kernel_smem(c64, conv_s2_wgrad_tc_kernel<64>, smem);
+            if (e == cudaSuccess) conv_s2_wgrad_tc_kernel<64><<<grid, kS2Threads, smem, st>>>(g, X, Y, dw, db, vec);
+        } else {
+            e = prepare_kernel_smem(c128, conv_s2_wgrad_tc_kernel<128>, smem);
+            if (e == cudaSuccess) conv_s2_wgrad_tc_kernel<128><<<grid, kS2Threads, smem, st>>>(g, X, Y, dw, db, vec);
+        }
+        return e != cudaSuccess ? e : cudaGetLastError();
     }
     const int taps = g.ksize * g.ksize * g.ksize;
     const int tiles = ((g.c_out + 63) / 64) * ((g.c_in + 63) / 64);

@@ -59,6 +59,9 @@ CASES = [
     # weight gradient with several 16-plane chunks along d, the last ragged
     ((1, 37, 5, 9, 16), 16, 3, 1, 1),
     ((1, 21, 3, 10, 64), 32, 3, 1, 1),
+    # stride-2 down-convolutions on the tensor-core path: 32 -> 64, batch 2 with odd sizes
+    ((1, 6, 8, 10, 32), 64, 2, 2, 0),
+    ((2, 5, 7, 9, 32), 64, 2, 2, 0),
 ]
 
 
