@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libfdc.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["fdc_kernels.cu", "fdc_api.cu", "unet_kernels.cu"]
-HEADERS = [os.path.join(CSRC, "fdc_internal.h"), os.path.join(INCLUDE, "fdc.h"), os.path.join(INCLUDE, "fdc_unet.h")]
+HEADERS = [os.path.join(CSRC, "fdc_internal.h"), os.path.join(CSRC, "unet_internal.h"), os.path.join(INCLUDE, "fdc.h"),
+           os.path.join(INCLUDE, "fdc_unet.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

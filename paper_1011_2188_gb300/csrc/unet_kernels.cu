@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "fdc_internal.h"
+#include "unet_internal.h"
 
 namespace fdc {
 namespace {
