@@ -57,6 +57,13 @@ int fdc_conv3d_forward_fused(const fdc_conv3d *g, const void *xa, int32_t ca, in
  * then the gradient with respect to the previous layer's pre-activation). */
 int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_t, const void *relu_mask, void *dx,
                              void *stream);
+/* The same plus a second gradient of the same activation: dx = (masked data
+ * gradient) + residual, rounded once to BF16 (the U-Net adds the skip
+ * connection's gradient this way).  residual bf16 in dx's layout, must not
+ * alias dx.  The 2^3 stride-2 convolutions add it in the tensor-core
+ * epilogue; other shapes run the data gradient, then the addition. */
+int fdc_conv3d_backward_data_add(const fdc_conv3d *g, const void *dy, const void *w_t, const void *relu_mask,
+                                 const void *residual, void *dx, void *stream);
 /* dw[co][tap][ci] += sum_o dy[o][co] x[o * stride - pad + tap][ci] and, if db is not NULL,
  * db[co] += sum_o dy[o][co]; dw, db FP32 (accumulated: zero them first). */
 int fdc_conv3d_backward_weights(const fdc_conv3d *g, const void *x, const void *dy, float *dw, float *db,
@@ -80,6 +87,11 @@ int fdc_conv3d_backward_data_fused(const fdc_conv3d *g, const void *dy, const vo
  * tap reflected (tap -> k^3 - 1 - tap) for 3^3 stride-1 padding-1 convolutions, whose data
  * gradient is then a forward convolution of dy. */
 int fdc_conv3d_transpose_weights(const fdc_conv3d *g, const void *w, void *w_t, void *stream);
+/* The same for n layers in one launch per 32 layers: g[i], w[i], w_t[i] (host
+ * arrays of geometries and device pointers) as in fdc_conv3d_transpose_weights.
+ * FDC_ERR_INVALID on n < 0, a NULL array or pointer, or a bad geometry. */
+int fdc_conv3d_transpose_weights_batch(int32_t n, const fdc_conv3d *g, const void *const *w, void *const *w_t,
+                                       void *stream);
 
 /* dx = dy where y > 0, else 0 (bf16, n elements). */
 int fdc_relu_backward(const void *y, const void *dy, void *dx, int64_t n, void *stream);

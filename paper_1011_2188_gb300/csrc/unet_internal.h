@@ -23,8 +23,9 @@ struct Conv3dArgs {
     int mask_ca, mask_up;
     void *out_b;
 };
+// residual (data gradient, mode 1, BF16 like the output, not aliasing it): added to the output
 cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const void *wt, const float *bias,
-                        void *out_bf16, float *out_f32, cudaStream_t st);
+                        void *out_bf16, float *out_f32, cudaStream_t st, const void *residual = nullptr);
 int tc_status(bool clear);
 cudaError_t launch_wait_timeout(long long cycles, cudaStream_t st);
 cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *wt, const float *bias,

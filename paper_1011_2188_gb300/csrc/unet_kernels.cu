@@ -1503,11 +1503,13 @@ __global__ void __launch_bounds__(kS2Threads) conv_s2_wgrad_tc_kernel(const Conv
 //   MODE 1: A[v][k = co] = dy[v][co] (K = Co), B[n][co] = w[co][t][ci] for the
 //           N-tile's n = t Ci + ci (rows of w_t = [ci][t][co]); epilogue: the
 //           16 columns of one tap are channels ci .. ci + 15 of input voxel
-//           2v + t, masked by the ReLU derivative and stored.
+//           2v + t, masked by the ReLU derivative, plus the residual gradient
+//           if given, and stored.
 template <int MODE, int N, int K>
 __global__ void __launch_bounds__(128) conv_s2_tc_kernel(const Conv3dArgs g, const __nv_bfloat16 *src,
                                                          const __nv_bfloat16 *wt, const float *bias,
-                                                         __nv_bfloat16 *out_bf16, float *out_f32) {
+                                                         __nv_bfloat16 *out_bf16, float *out_f32,
+                                                         const __nv_bfloat16 *residual) {
     constexpr int ABytes = kS2Vox * K * 2, BBytes = N * K * 2;
     constexpr unsigned Cols = 2 * N;
     static_assert(Cols <= 512 && K % 16 == 0 && N % 16 == 0, "tile shape");
@@ -1631,6 +1633,17 @@ __global__ void __launch_bounds__(128) conv_s2_tc_kernel(const Conv3dArgs g, con
                 const int col = n0 + c, t = col / Ci, ci = col % Ci;
                 const long long xv = (((long long)b * D + 2 * d + (t >> 2)) * H + 2 * h + ((t >> 1) & 1)) * W + 2 * w + (t & 1);
                 if (g.mask) apply_relu_mask<16>(g.mask, xv, Ci, ci, a);
+                if (residual) {  // a second gradient of the same activation, added before rounding
+                    const uint4 *rp = (const uint4 *)(residual + xv * Ci + ci);
+                    const uint4 rq[2] = {__ldg(rp), __ldg(rp + 1)};
+                    const __nv_bfloat162 *r2 = (const __nv_bfloat162 *)rq;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float2 f = __bfloat1622float2(r2[j]);
+                        a[2 * j] += f.x;
+                        a[2 * j + 1] += f.y;
+                    }
+                }
                 uint4 qv[2];
                 unsigned *qq = (unsigned *)qv;
 #pragma unroll
@@ -1825,6 +1838,34 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(const Conv3dArgs g, con
             for (int vi = 0; vi < 16; ++vi) t += red[(vi * 8 + part) * 8 + j];
             if (co < g.c_out) atomicAdd(db + co, t);
         }
+    }
+}
+
+// Several layers' data-gradient weights in one launch: entry e maps
+// w[co][tap][ci] to wt[ci][tap'][co], tap' = taps - 1 - tap when flip (3^3
+// stride-1 padding-1) else tap; element i of the batch belongs to the entry
+// whose [start[e], start[e + 1]) holds it.
+constexpr int kTrBatch = 32;
+struct TransposeBatch {
+    const __nv_bfloat16 *w[kTrBatch];
+    __nv_bfloat16 *wt[kTrBatch];
+    int co[kTrBatch], taps[kTrBatch], ci[kTrBatch], flip[kTrBatch];
+    long long start[kTrBatch + 1];
+    int n;
+};
+
+__global__ void transpose_batch_kernel(const TransposeBatch b) {
+    const long long total = b.start[b.n];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        int e = 0;
+        while (i >= b.start[e + 1]) ++e;
+        const long long j = i - b.start[e];
+        const int ci_n = b.ci[e], taps = b.taps[e], co_n = b.co[e];
+        const int ci = (int)(j % ci_n);
+        const long long q = j / ci_n;
+        const int tap = (int)(q % taps), co = (int)(q / taps);
+        const int tp = b.flip[e] ? taps - 1 - tap : tap;
+        b.wt[e][((long long)ci * taps + tp) * co_n + co] = b.w[e][j];
     }
 }
 
@@ -2333,7 +2374,7 @@ cudaError_t launch_flip_transpose(const void *w, void *wf, int co, int k, int ci
 // false, launching nothing, for a shape without an instantiation.
 template <int MODE, int N, int K>
 cudaError_t launch_s2_tc(const Conv3dArgs &g, const void *src, const void *wt, const float *bias, void *out_bf16,
-                         float *out_f32, int ntiles_n, cudaStream_t st) {
+                         float *out_f32, int ntiles_n, cudaStream_t st, const void *residual = nullptr) {
     static OccCache cache;
     constexpr int smem = N * K * 2 + 2 * kS2Vox * K * 2;
     int dev = 0, sms = 0, smem_sm = 0;
@@ -2347,7 +2388,8 @@ cudaError_t launch_s2_tc(const Conv3dArgs &g, const void *src, const void *wt, c
     long long gx = std::max(1ll, (long long)sms * per_sm / ntiles_n);
     if (gx > tiles) gx = tiles;
     conv_s2_tc_kernel<MODE, N, K><<<dim3((unsigned)gx, (unsigned)ntiles_n), 128, smem, st>>>(
-        g, (const __nv_bfloat16 *)src, (const __nv_bfloat16 *)wt, bias, (__nv_bfloat16 *)out_bf16, out_f32);
+        g, (const __nv_bfloat16 *)src, (const __nv_bfloat16 *)wt, bias, (__nv_bfloat16 *)out_bf16, out_f32,
+        (const __nv_bfloat16 *)residual);
     return cudaGetLastError();
 }
 
@@ -2360,21 +2402,23 @@ bool s2_tc_shape(const Conv3dArgs &g, int mode, const float *out_f32) {
 }
 
 cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const void *wt, const float *bias,
-                        void *out_bf16, float *out_f32, cudaStream_t st) {
+                        void *out_bf16, float *out_f32, cudaStream_t st, const void *residual) {
+    const size_t in_bytes = (size_t)g.batch * g.in_d * g.in_h * g.in_w * g.c_in * sizeof(__nv_bfloat16);
     if (s2_tc_shape(g, mode, out_f32)) {
         if (mode == 0) {
             if (g.c_in == 16) return launch_s2_tc<0, 32, 128>(g, src, wt, bias, out_bf16, out_f32, 1, st);
             return launch_s2_tc<0, 64, 256>(g, src, wt, bias, out_bf16, out_f32, 1, st);
         }
-        // input voxels of an odd-sized axis's last plane reach no output: zero gradient
+        // input voxels of an odd-sized axis's last plane reach no output: their
+        // gradient is zero, or the residual
         if ((g.in_d | g.in_h | g.in_w) & 1) {
-            const cudaError_t e = cudaMemsetAsync(
-                out_bf16, 0, (size_t)g.batch * g.in_d * g.in_h * g.in_w * g.c_in * sizeof(__nv_bfloat16), st);
+            const cudaError_t e = residual ? cudaMemcpyAsync(out_bf16, residual, in_bytes, cudaMemcpyDeviceToDevice, st)
+                                           : cudaMemsetAsync(out_bf16, 0, in_bytes, st);
             if (e != cudaSuccess) return e;
         }
-        if (g.c_in == 16) return launch_s2_tc<1, 128, 32>(g, src, wt, nullptr, out_bf16, nullptr, 1, st);
-        if (g.c_in == 32) return launch_s2_tc<1, 256, 64>(g, src, wt, nullptr, out_bf16, nullptr, 1, st);
-        return launch_s2_tc<1, 256, 128>(g, src, wt, nullptr, out_bf16, nullptr, 2, st);
+        if (g.c_in == 16) return launch_s2_tc<1, 128, 32>(g, src, wt, nullptr, out_bf16, nullptr, 1, st, residual);
+        if (g.c_in == 32) return launch_s2_tc<1, 256, 64>(g, src, wt, nullptr, out_bf16, nullptr, 1, st, residual);
+        return launch_s2_tc<1, 256, 128>(g, src, wt, nullptr, out_bf16, nullptr, 2, st, residual);
     }
     const int Nn = mode == 0 ? g.c_out : g.c_in;
     const long long rows = (long long)g.batch * (mode == 0 ? (long long)g.out_d * g.out_h * g.out_w
@@ -2400,7 +2444,10 @@ cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const vo
         else if (nt == 32) conv_igemm_kernel<1, 32><<<grid, 128, 0, st>>>(g, s, w, nullptr, ob, out_f32);
         else conv_igemm_kernel<1, 16><<<grid, 128, 0, st>>>(g, s, w, nullptr, ob, out_f32);
     }
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && residual && mode == 1)
+        e = launch_add_bf16(out_bf16, residual, out_bf16, (long long)(in_bytes / sizeof(__nv_bfloat16)), st);
+    return e;
 }
 
 cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy, float *dw, float *db,
@@ -2663,6 +2710,23 @@ int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_
     return rc(fdc::launch_conv(a, 1, dy, w_t, nullptr, dx, nullptr, (cudaStream_t)stream));
 }
 
+int fdc_conv3d_backward_data_add(const fdc_conv3d *g, const void *dy, const void *w_t, const void *relu_mask,
+                                 const void *residual, void *dx, void *stream) {
+    if (!conv_ok(g) || !dy || !w_t || !dx || !residual || residual == dx) return FDC_ERR_INVALID;
+    fdc::Conv3dArgs a = to_args(g);
+    a.relu = 0;
+    a.mask = relu_mask;
+    if (is_k3s1p1(g)) {
+        cudaError_t e = fdc::launch_conv_halo(a, dy, w_t, nullptr, dx, nullptr, g->c_out, g->c_in, 0,
+                                              (cudaStream_t)stream, g->c_out, 0, nullptr);
+        if (e == cudaSuccess)
+            e = fdc::launch_add_bf16(dx, residual, dx,
+                                     (long long)g->batch * g->in_d * g->in_h * g->in_w * g->c_in, (cudaStream_t)stream);
+        return rc(e);
+    }
+    return rc(fdc::launch_conv(a, 1, dy, w_t, nullptr, dx, nullptr, (cudaStream_t)stream, residual));
+}
+
 int fdc_conv3d_backward_weights(const fdc_conv3d *g, const void *x, const void *dy, float *dw, float *db,
                                 void *stream) {
     if (!conv_ok(g) || !x || !dy || !dw) return FDC_ERR_INVALID;
@@ -2700,6 +2764,33 @@ int fdc_conv3d_transpose_weights(const fdc_conv3d *g, const void *w, void *w_t, 
         return rc(fdc::launch_flip_transpose(w, w_t, g->c_out, 3, g->c_in, (cudaStream_t)stream));
     return rc(fdc::launch_transpose_weights(w, w_t, g->c_out, g->ksize * g->ksize * g->ksize, g->c_in,
                                             (cudaStream_t)stream));
+}
+
+int fdc_conv3d_transpose_weights_batch(int32_t n, const fdc_conv3d *g, const void *const *w, void *const *w_t,
+                                       void *stream) {
+    if (n < 0 || (n > 0 && (!g || !w || !w_t))) return FDC_ERR_INVALID;
+    for (int i = 0; i < n; ++i)
+        if (!conv_ok(&g[i]) || !w[i] || !w_t[i]) return FDC_ERR_INVALID;
+    for (int i0 = 0; i0 < n; i0 += fdc::kTrBatch) {
+        fdc::TransposeBatch b;
+        b.n = std::min(n - i0, fdc::kTrBatch);
+        b.start[0] = 0;
+        for (int e = 0; e < b.n; ++e) {
+            const fdc_conv3d &ge = g[i0 + e];
+            b.w[e] = (const __nv_bfloat16 *)w[i0 + e];
+            b.wt[e] = (__nv_bfloat16 *)w_t[i0 + e];
+            b.co[e] = ge.c_out;
+            b.taps[e] = ge.ksize * ge.ksize * ge.ksize;
+            b.ci[e] = ge.c_in;
+            b.flip[e] = is_k3s1p1(&ge) ? 1 : 0;
+            b.start[e + 1] = b.start[e] + (long long)ge.c_out * b.taps[e] * ge.c_in;
+        }
+        const long long blocks = std::min(4096ll, std::max(1ll, (b.start[b.n] + 255) / 256));
+        fdc::transpose_batch_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(b);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return rc(e);
+    }
+    return FDC_OK;
 }
 
 int fdc_relu_backward(const void *y, const void *dy, void *dx, int64_t n, void *stream) {

@@ -117,7 +117,7 @@ class ConvLayer:
             self.fused_in = (xa, bool(upsample), xb, (B, D, H, W, self.cin))
         return y
 
-    def backward(self, dy, need_dx=True):
+    def backward(self, dy, need_dx=True, residual=None):
         """dy: gradient with respect to this layer's pre-activation (its own
         ReLU derivative already applied: every layer's input is the output of
         a ReLU layer, and the data gradient below masks dx by x > 0 in its
@@ -150,8 +150,12 @@ class ConvLayer:
         dx = None
         if need_dx:
             dx = torch.empty(self.x.shape, dtype=torch.bfloat16, device=self.dev)
-            _ok(L.fdc_conv3d_backward_data(C.byref(g), _p(dy), _p(self.wt16), _p(self.x), _p(dx), _s()),
-                "conv dgrad")
+            if residual is not None:  # plus a second gradient of the same activation
+                _ok(L.fdc_conv3d_backward_data_add(C.byref(g), _p(dy), _p(self.wt16), _p(self.x), _p(residual),
+                                                   _p(dx), _s()), "conv dgrad + residual")
+            else:
+                _ok(L.fdc_conv3d_backward_data(C.byref(g), _p(dy), _p(self.wt16), _p(self.x), _p(dx), _s()),
+                    "conv dgrad")
         self.x = self.y = None
         return dx
 
@@ -359,10 +363,11 @@ class UNet:
         d, de1 = self._decoder_back(self.up1, self.dec1, df1, c1)
         d, de2 = self._decoder_back(self.up2, self.dec2, d, c2)
         d, de3 = self._decoder_back(self.up3, self.dec3, d, c3)
-        d = self.down3.backward(self._seq_back(self.bott, d))
-        d = self.down2.backward(self._seq_back(self.enc3, _add(d, de3)))
-        d = self.down1.backward(self._seq_back(self.enc2, _add(d, de2)))
-        self._seq_back(self.enc1, _add(d, de1), need_last=False)
+        # each down-convolution's data gradient adds the skip connection's gradient in its epilogue
+        d = self.down3.backward(self._seq_back(self.bott, d), residual=de3)
+        d = self.down2.backward(self._seq_back(self.enc3, d), residual=de2)
+        d = self.down1.backward(self._seq_back(self.enc2, d), residual=de1)
+        self._seq_back(self.enc1, d, need_last=False)
 
     def zero_grad(self):
         self.g32.zero_()
@@ -375,9 +380,13 @@ class UNet:
         L = fdc.lib()
         _ok(L.fdc_adam(_p(self.p32), _p(self.g32), _p(self.m32), _p(self.v32), _p(self.p16), self.p32.numel(),
                        lr, b1, b2, eps, self.t, _s()), "adam")
-        for l in self.layers():
-            g, _ = l.geom((1, 8, 8, 8, l.cin))
-            _ok(L.fdc_conv3d_transpose_weights(C.byref(g), _p(l.w16), _p(l.wt16), _s()), "transpose")
+        if getattr(self, "_tr", None) is None:  # geometries and pointers of every layer (buffers are fixed)
+            ls = self.layers()
+            self._tr = ((Conv3d * len(ls))(*[l.geom((1, 8, 8, 8, l.cin))[0] for l in ls]),
+                        (C.c_void_p * len(ls))(*[l.w16.data_ptr() for l in ls]),
+                        (C.c_void_p * len(ls))(*[l.wt16.data_ptr() for l in ls]))
+        g, w, wt = self._tr
+        _ok(L.fdc_conv3d_transpose_weights_batch(len(g), g, w, wt, _s()), "transpose")
 
     def state(self):
         return [l.state() for l in self.layers()]

@@ -45,10 +45,12 @@ SIGNATURES = {
     "fdc_conv3d_forward": (C.c_int, [_p, _p, _p, _p, _p, _p, _p]),
     "fdc_conv3d_forward_fused": (C.c_int, [_p, _p, C.c_int32, C.c_int32, _p, _p, _p, _p, _p, _p]),
     "fdc_conv3d_backward_data": (C.c_int, [_p, _p, _p, _p, _p, _p]),
+    "fdc_conv3d_backward_data_add": (C.c_int, [_p, _p, _p, _p, _p, _p, _p]),
     "fdc_conv3d_backward_weights": (C.c_int, [_p, _p, _p, _p, _p, _p]),
     "fdc_conv3d_backward_weights_fused": (C.c_int, [_p, _p, C.c_int32, C.c_int32, _p, _p, _p, _p, _p]),
     "fdc_conv3d_backward_data_fused": (C.c_int, [_p, _p, _p, _p, C.c_int32, C.c_int32, _p, _p, _p, _p]),
     "fdc_conv3d_transpose_weights": (C.c_int, [_p, _p, _p, _p]),
+    "fdc_conv3d_transpose_weights_batch": (C.c_int, [C.c_int32, _p, _p, _p, _p]),
     "fdc_relu_backward": (C.c_int, [_p, _p, _p, C.c_int64, _p]),
     "fdc_upsample2": (C.c_int, [_p, _p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _p]),
     "fdc_concat_channels": (C.c_int, [_p, C.c_int32, _p, C.c_int32, _p, C.c_int64, C.c_int32, _p]),

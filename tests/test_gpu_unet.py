@@ -118,6 +118,14 @@ def test_conv_backward_data_and_weights(case):
     rdw, rdb = ref.backward_weights(x, dy, k, stride=s, pad=p)
     np.testing.assert_allclose(dx.float().cpu().numpy(), rdx, rtol=0, atol=8e-3 * np.abs(rdx).max())
     assert torch.equal(dxm, torch.where(xt > 0, dx, torch.zeros_like(dx)))
+    # masked data gradient plus a residual gradient, rounded once
+    rest, res = bf16(rng.normal(size=shape) * np.abs(rdx).max())
+    dxr = torch.empty(shape, dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_conv3d_backward_data_add(C.byref(g), ptr(dyt), ptr(w_t), ptr(xt), ptr(rest), ptr(dxr), None) == 0
+    assert L.fdc_conv3d_backward_data_add(C.byref(g), ptr(dyt), ptr(w_t), ptr(xt), ptr(dxr), ptr(dxr), None) != 0
+    torch.cuda.synchronize()
+    rr = np.where(x > 0, rdx, 0.0) + res
+    np.testing.assert_allclose(dxr.float().cpu().numpy(), rr, rtol=0, atol=8e-3 * np.abs(rr).max())
     np.testing.assert_allclose(dw.cpu().numpy(), rdw, rtol=0, atol=2e-5 * np.abs(rdw).max())
     np.testing.assert_allclose(db.cpu().numpy(), rdb, rtol=0, atol=2e-5 * np.abs(rdb).max())
     # accumulation into a weight gradient that is not 16-byte aligned (scalar atomics)
@@ -127,6 +135,35 @@ def test_conv_backward_data_and_weights(case):
     torch.cuda.synchronize()
     np.testing.assert_allclose(dw_odd.cpu().numpy() - 0.5, rdw, rtol=0, atol=2e-5 * np.abs(rdw).max())
     assert float(store[0]) == 0.5
+
+
+def test_transpose_weights_batch_equals_single_calls():
+    """fdc_conv3d_transpose_weights_batch gives, layer by layer, the same
+    bytes as fdc_conv3d_transpose_weights (3^3 reflected, 2^3 and 1^3 plain)."""
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    from paper_1011_2188_gb300.denoise import Conv3d
+    L = fdc.lib()
+    rng = np.random.default_rng(12)
+    shapes = [(16, 16, 3, 1, 1), (32, 64, 3, 1, 1), (16, 32, 2, 2, 0), (64, 128, 2, 2, 0), (16, 16, 1, 1, 0)] * 8
+    gs, ws, wts, refs = [], [], [], []
+    for ci, co, k, st, pd in shapes:  # 40 layers: two launches of up to 32
+        g, _ = geom((1, 8, 8, 8, ci), co, k, st, pd)
+        wt_, _ = bf16(rng.normal(size=(co, k, k, k, ci)))
+        out = torch.full((ci, k, k, k, co), 7.0, dtype=torch.bfloat16, device="cuda:0")
+        ref = torch.empty_like(out)
+        assert L.fdc_conv3d_transpose_weights(C.byref(g), ptr(wt_), ptr(ref), None) == 0
+        gs.append(g); ws.append(wt_); wts.append(out); refs.append(ref)
+    n = len(gs)
+    garr = (Conv3d * n)(*gs)
+    warr = (C.c_void_p * n)(*[t.data_ptr() for t in ws])
+    tarr = (C.c_void_p * n)(*[t.data_ptr() for t in wts])
+    assert L.fdc_conv3d_transpose_weights_batch(n, garr, warr, tarr, None) == 0
+    torch.cuda.synchronize()
+    for a, b in zip(wts, refs):
+        assert torch.equal(a, b)
+    assert L.fdc_conv3d_transpose_weights_batch(-1, garr, warr, tarr, None) != 0
+    assert L.fdc_conv3d_transpose_weights_batch(0, None, None, None, None) == 0
 
 
 def test_elementwise_kernels():
