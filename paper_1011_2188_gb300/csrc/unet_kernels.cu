@@ -2308,8 +2308,9 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
         return cudaGetLastError();
     }
     // 64-channel tiles (27 MMAs of N = 64) when they give at least one CTA per SM
-    // (measured: 32^3 x 64 channels 46 vs 55 us); otherwise the kw-stacked kernel
-    // with 32-channel tiles spreads small grids wider (16^3 x 128: 43 vs 64 us)
+    // (measured: 32^3 x 64 channels 46 vs 55 us; with 128 input channels at 32^3
+    // the kw-stacked 32-channel tiles made U-Net inference 1.24 vs 1.20 ms);
+    // otherwise the kw-stacked kernel spreads small grids wider (16^3 x 128: 43 vs 64 us)
     const long long tiles64 = (long long)g.batch * g.in_d * ((g.in_h + 15) / 16) * ((g.in_w + 7) / 8);
     if (Nn % 64 == 0 && tiles64 * (Nn / 64) >= 152) {
         static OccCache cache;

@@ -481,6 +481,27 @@ def test_unet_inference_matches_training_forward():
     assert torch.allclose(a, b, rtol=0, atol=1e-3 * float(a.abs().max()))
 
 
+def test_inference_graph_replays_the_same_dose():
+    """InferenceGraph (one captured CUDA graph) gives the denoise() result bit
+    for bit, also after the sample's buffers are refilled in place."""
+    import torch
+    from paper_1011_2188_gb300 import denoise, fdc
+    rng = np.random.default_rng(13)
+    n = 32
+    dens = torch.ones((n, n, n), dtype=torch.float32, device="cuda:0")
+    s = denoise.Sample(torch.from_numpy(rng.random((n, n, n))).cuda(), dens)
+    net = denoise.UNet(seed=3)
+    ig = denoise.InferenceGraph(net, s)
+    for k in range(2):  # new doses, same scale (the graph keeps the one it was captured with)
+        dose = torch.from_numpy(rng.random((n, n, n)) * (k + 1)).cuda()
+        assert fdc.lib().fdc_unet_prepare(denoise._p(dose), denoise._p(dens), None, n ** 3, s.scale, 0.5,
+                                          denoise._p(s.x), denoise._p(s.dose_in), None, denoise._s()) == 0
+        a = ig.run().clone()
+        b = denoise.denoise(net, s)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("ca,cb,up,cout", [(32, 0, 1, 16), (16, 16, 0, 16), (32, 32, 0, 32), (64, 0, 1, 32)])
 def test_fused_backward_equals_materialised(ca, cb, up, cout):
     """The gradients of the fused forward (input [upsample?(xa) | xb] never
