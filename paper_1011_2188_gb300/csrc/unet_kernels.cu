@@ -18,8 +18,10 @@
 // run on the tcgen05 tensor cores with TMEM accumulators (conv3_tc_kernel,
 // persistent and pipelined).
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -774,6 +776,51 @@ __global__ void __launch_bounds__(128) conv3_kws_kernel(const Conv3dArgs g, cons
     }
 }
 
+// Epilogue of one output row of the d-walking kernels: CW output channels
+// [n, n + CW) of voxel v = (b, d, ho, wo): bias (staged in shared memory,
+// null for none), ReLU, the previous layer's ReLU mask of a data gradient
+// (g.mask; split over two inputs when g.mask_ca > 0), and the store (FP32
+// and/or BF16; with g.out_b, channels >= g.mask_ca go to the second output).
+template <int CW>
+__device__ __forceinline__ void dwalk_store(const Conv3dArgs &g, float a0[CW], const float *sb, int relu,
+                                            __nv_bfloat16 *out_bf16, float *out_f32, int Nn, int n, int b, int d,
+                                            int ho, int wo, long long v) {
+#pragma unroll
+    for (int j = 0; j < CW; ++j) {
+        float x = a0[j];
+        if (sb) x += sb[j];
+        if (relu) x = fmaxf(x, 0.f);
+        a0[j] = x;
+    }
+    if (g.mask) {
+        if (g.mask_ca > 0)
+            apply_relu_mask_fused<CW>(g, Nn, b, d, ho, wo, g.in_d, g.in_h, g.in_w, n, a0);
+        else
+            apply_relu_mask<CW>(g.mask, v, Nn, n, a0);
+    }
+    if (out_f32) {
+        float4 *dst = (float4 *)(out_f32 + v * Nn + n);
+#pragma unroll
+        for (int j = 0; j < CW / 4; ++j) dst[j] = make_float4(a0[4 * j], a0[4 * j + 1], a0[4 * j + 2], a0[4 * j + 3]);
+    }
+    if (out_bf16) {
+        uint4 qv[CW / 8];
+        unsigned *qq = (unsigned *)qv;
+#pragma unroll
+        for (int j = 0; j < CW / 2; ++j) {
+            __nv_bfloat162 p2 = __floats2bfloat162_rn(a0[2 * j], a0[2 * j + 1]);
+            qq[j] = *(unsigned *)&p2;
+        }
+        // split output: channels >= mask_ca into out_b
+        uint4 *dst = g.out_b == nullptr
+                         ? (uint4 *)(out_bf16 + v * Nn + n)
+                         : (n < g.mask_ca ? (uint4 *)(out_bf16 + v * g.mask_ca + n)
+                                          : (uint4 *)((__nv_bfloat16 *)g.out_b + v * (Nn - g.mask_ca) + (n - g.mask_ca)));
+#pragma unroll
+        for (int j = 0; j < CW / 8; ++j) dst[j] = qv[j];
+    }
+}
+
 // d-walking form of the kw-stacked convolution (input channels Cs <= 32,
 // NT = 16 or 32 output channels per CTA): a CTA owns a contiguous range of
 // output planes of one 8 (h) x 14 (w) column of tiles -- the flattened
@@ -935,44 +982,9 @@ __global__ void __launch_bounds__(THR) conv3_dwalk_kernel(const Conv3dArgs g, co
             for (int j = 0; j < CW; ++j)
                 a0[j] += __shfl_down_sync(0xffffffffu, a1[j], 1) + __shfl_down_sync(0xffffffffu, a2[j], 2);
             const int n = n0 + c;
-            if (out_in && n < Nn) {
-#pragma unroll
-                for (int j = 0; j < CW; ++j) {
-                    float x = a0[j];
-                    if (bias) x += sBias[c + j];
-                    if (relu) x = fmaxf(x, 0.f);
-                    a0[j] = x;
-                }
-                if (g.mask) {
-                    if (g.mask_ca > 0)
-                        apply_relu_mask_fused<CW>(g, Nn, b, d_begin + i, ho, wo, D, H, W, n, a0);
-                    else
-                        apply_relu_mask<CW>(g.mask, v, Nn, n, a0);
-                }
-                if (out_f32) {
-                    float4 *dst = (float4 *)(out_f32 + v * Nn + n);
-#pragma unroll
-                    for (int j = 0; j < CW / 4; ++j)
-                        dst[j] = make_float4(a0[4 * j], a0[4 * j + 1], a0[4 * j + 2], a0[4 * j + 3]);
-                }
-                if (out_bf16) {
-                    uint4 qv[CW / 8];
-                    unsigned *qq = (unsigned *)qv;
-#pragma unroll
-                    for (int j = 0; j < CW / 2; ++j) {
-                        __nv_bfloat162 p2 = __floats2bfloat162_rn(a0[2 * j], a0[2 * j + 1]);
-                        qq[j] = *(unsigned *)&p2;
-                    }
-                    // split output: channels >= mask_ca into out_b
-                    uint4 *dst = g.out_b == nullptr
-                                     ? (uint4 *)(out_bf16 + v * Nn + n)
-                                     : (n < g.mask_ca ? (uint4 *)(out_bf16 + v * g.mask_ca + n)
-                                                      : (uint4 *)((__nv_bfloat16 *)g.out_b + v * (Nn - g.mask_ca) +
-                                                                  (n - g.mask_ca)));
-#pragma unroll
-                    for (int j = 0; j < CW / 8; ++j) dst[j] = qv[j];
-                }
-            }
+            if (out_in && n < Nn)
+                dwalk_store<CW>(g, a0, bias ? sBias + c : nullptr, relu, out_bf16, out_f32, Nn, n, b, d_begin + i, ho,
+                                wo, v);
             // every warp has read this accumulator before MMAs overwrite it
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             return true;
@@ -1038,6 +1050,301 @@ __global__ void __launch_bounds__(THR) conv3_dwalk_kernel(const Conv3dArgs g, co
     cp_async_wait<0>();
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
+    }
+}
+
+// ---- d-walking convolution with TMA staging and warp roles
+// The tiles, resident weights, kw-stacked MMAs and two TMEM accumulators of
+// conv3_dwalk_kernel, for inputs read as stored ([a | b] at one resolution,
+// split at a 16-channel slice boundary).  Each input plane arrives by TMA: per
+// 16-channel slice one 5-D box (16 channels x 16 w x 10 h x 1 d x 1 batch,
+// zero fill outside the grid) written with the 32-byte swizzle, which is the
+// canonical SWIZZLE_32B K-major operand layout (rows of 32 B, eight-row groups
+// 256 B apart), so an MMA reads the A tile of tap kh at row 16 kh of the plane
+// directly and no thread computes a staging address.  Warp roles hand off
+// through mbarriers only (no CTA barrier inside the walk):
+//   full[s]   TMA warp -> MMA warp: the plane in ring slot s has landed
+//   empty[s]  MMA warp -> TMA warp: the MMAs that read slot s have completed
+//   accf[k]   MMA warp -> epilogue: accumulator k holds an output plane
+//   acce[k]   epilogue -> MMA warp: all EW epilogue warps have read it
+// Warps 0..EW-1 run the epilogue (TMEM lane quadrant warp % 4; with EW = 8
+// warps w and w + 4 take the two halves of the output channels), warp EW
+// issues the TMA copies, warp EW + 1 the MMAs.  Input plane j of a range is
+// read by output planes j - 2 .. j and released after output plane j.
+// Every wait is bounded: an expired wait records FDC_ERR_TIMEOUT and raises a
+// CTA-wide abort flag that ends the other roles' waits; before TMEM is freed
+// the TMA warp waits (bounded) for the copies it issued and the MMA warp for
+// its MMAs.
+constexpr int kDwtMaxRing = 12;
+#ifndef FDC_CONV_DWTMA
+#define FDC_CONV_DWTMA 1
+#endif
+
+__device__ __forceinline__ bool mbar_try(unsigned mb, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of parity `parity` of barrier mb; false when the CTA's
+// abort flag is raised or the wait expires (which raises the flag).
+__device__ __forceinline__ bool role_wait(unsigned mb, unsigned parity, volatile int *abort_flag) {
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try(mb, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kTcWaitCycles) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_5d(unsigned dst, const void *tmap, int c0, int c1, int c2, int c3, int c4,
+                                            unsigned mb) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];\n" ::"r"(dst),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mb)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major with the 32-byte swizzle: rows of
+// 32 B (16 BF16, one MMA's K), eight-row groups `sbo` bytes apart (the
+// leading offset is unused: K fits in one swizzle atom); version 1, layout 6.
+__device__ __forceinline__ unsigned long long umma_desc_sw32(unsigned saddr, unsigned sbo) {
+    return (unsigned long long)((saddr >> 4) & 0x3fffu) | (1ull << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46) | (6ull << 61);
+}
+
+template <int NT, int EW, int MINB>
+__global__ void __launch_bounds__(32 * (EW + 2), MINB)
+    conv3_dwtma_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
+                       const Conv3dArgs g, const __nv_bfloat16 *wt, const float *bias, __nv_bfloat16 *out_bf16,
+                       float *out_f32, int Cs, int Nn, int relu, int ca, int R) {
+    constexpr int N3 = 3 * NT;
+    constexpr unsigned kAccCols = N3 <= 64 ? 64 : 128;  // columns per accumulator buffer
+    constexpr unsigned kCols = 2 * kAccCols;
+    constexpr int THR = 32 * (EW + 2);
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long bars[2 * kDwtMaxRing + 5];
+    __shared__ unsigned tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ float sBias[NT];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int D = g.in_d, H = g.in_h, W = g.in_w;
+    const int S = Cs / 16;
+    const unsigned plane_bytes = (unsigned)(S * kDwPlaneSliceBytes);
+    const int wbytes = S * 9 * 2 * N3 * 16;
+    unsigned char *sW = smem;  // [slice][kd kh][k-chunk][kw NT + co][8]
+    // the plane ring starts on a 1024-byte boundary (the swizzle pattern is
+    // taken from the shared-memory address bits)
+    const unsigned sP = (smem_u32(smem) + (unsigned)wbytes + 1023u) & ~1023u;
+    const unsigned bar0 = smem_u32(&bars[0]);
+    auto full = [&](int s) { return bar0 + 8u * (unsigned)s; };
+    auto empty = [&](int s) { return bar0 + 8u * (unsigned)(kDwtMaxRing + s); };
+    auto accf = [&](unsigned k) { return bar0 + 8u * (2u * kDwtMaxRing + k); };
+    auto acce = [&](unsigned k) { return bar0 + 8u * (2u * kDwtMaxRing + 2u + k); };
+    const unsigned fin = bar0 + 8u * (2u * kDwtMaxRing + 4u);
+    volatile int *abort_v = &abort_flag;
+
+    const int tiles_w = (W + 13) / 14, tiles_h = (H + 7) / 8;
+    const long long n_cols = (long long)g.batch * tiles_h * tiles_w;
+    const long long total = n_cols * D;  // (tile column, d) output planes
+    const long long q_begin = total * blockIdx.x / gridDim.x, q_end = total * (blockIdx.x + 1) / gridDim.x;
+    const int n0 = blockIdx.y * NT;
+
+    if (tid == 0) {
+        for (int s = 0; s < R; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full(s)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(s)));
+        }
+        for (unsigned k = 0; k < 2; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(accf(k)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(acce(k)), "r"(EW));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(fin));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        abort_flag = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid < NT) sBias[tid] = (bias && n0 + tid < Nn) ? bias[n0 + tid] : 0.f;
+    {  // resident weights of every input slice (through L1: all CTAs read the same)
+        constexpr int kChunks = 9 * 2 * N3;  // per slice
+        for (int i = tid; i < S * kChunks; i += THR) {
+            const int sl = i / kChunks, r = i % kChunks;
+            const int n = r % N3, q = r / N3, kc = q & 1, kdh = q >> 1;
+            const int co = n0 + (n % NT), kw = n / NT;
+            const bool in = co < Nn;
+            const __nv_bfloat16 *p = in ? wt + (size_t)((co * 27 + kdh * 3 + kw) * Cs + sl * 16 + kc * 8) : wt;
+            cp_async16_ca(sW + i * 16, p, in);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+    }
+    // weights written by the generic proxy are read by the MMAs (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = tmem_slot;
+
+    // the (tile column, d) ranges of this CTA, identical for every role
+    auto range_at = [&](long long q, int &d_begin, int &nd, int &w0, int &h0, int &b) {
+        const long long col = q / D;
+        d_begin = (int)(q % D);
+        nd = (int)(q_end - q < (long long)(D - d_begin) ? q_end - q : (long long)(D - d_begin));
+        long long t = col;
+        w0 = (int)(t % tiles_w) * 14;
+        t /= tiles_w;
+        h0 = (int)(t % tiles_h) * 8;
+        b = (int)(t / tiles_h);
+    };
+
+    if (warp == EW) {  // ---- TMA: stage input planes d_begin - 1 .. d_begin + nd of each range
+        if (lane == 0) {
+            unsigned p = 0;  // planes issued over all ranges (ring slot p % R)
+            bool ok = true;
+            for (long long q = q_begin; q < q_end && ok;) {
+                int d_begin, nd, w0, h0, b;
+                range_at(q, d_begin, nd, w0, h0, b);
+                q += nd;
+                for (int j = 0; j < nd + 2; ++j, ++p) {
+                    const int s = (int)(p % (unsigned)R);
+                    if (p >= (unsigned)R && !role_wait(empty(s), (p / (unsigned)R - 1u) & 1u, abort_v)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full(s)),
+                                 "r"(plane_bytes)
+                                 : "memory");
+                    const int d = d_begin - 1 + j;
+                    for (int sl = 0; sl < S; ++sl) {
+                        const unsigned dst = sP + (unsigned)s * plane_bytes + (unsigned)(sl * kDwPlaneSliceBytes);
+                        if (sl * 16 < ca)
+                            tma_load_5d(dst, &tm_a, sl * 16, w0 - 1, h0 - 1, d, b, full(s));
+                        else
+                            tma_load_5d(dst, &tm_b, sl * 16 - ca, w0 - 1, h0 - 1, d, b, full(s));
+                    }
+                }
+            }
+            // copies still in flight land before the CTA exits (bounded)
+            const unsigned n_out = p < (unsigned)R ? p : (unsigned)R;
+            const long long t0 = clock64();
+            for (unsigned pp = p - n_out; pp < p; ++pp)
+                while (!mbar_try(full((int)(pp % (unsigned)R)), (pp / (unsigned)R) & 1u))
+                    if (clock64() - t0 > kTcWaitCycles) break;
+        }
+        __syncwarp();
+    } else if (warp == EW + 1) {  // ---- MMA: output planes of each range
+        if (lane == 0) {
+            constexpr unsigned idesc = umma_idesc(128, N3);
+            const unsigned long long bd0 = umma_desc(smem_u32(sW), N3 * 16, 128);
+            unsigned p = 0, it = 0;  // first plane of the range; output planes over all ranges
+            bool ok = true;
+            for (long long q = q_begin; q < q_end && ok;) {
+                int d_begin, nd, w0, h0, b;
+                range_at(q, d_begin, nd, w0, h0, b);
+                q += nd;
+                for (int i = 0; i < nd && ok; ++i, ++it) {
+                    for (int j = (i == 0 ? 0 : i + 2); j <= i + 2; ++j) {
+                        const unsigned pp = p + (unsigned)j;
+                        if (!role_wait(full((int)(pp % (unsigned)R)), (pp / (unsigned)R) & 1u, abort_v)) ok = false;
+                    }
+                    const unsigned ab = it & 1u;
+                    if (ok && it >= 2 && !role_wait(acce(ab), ((it >> 1) - 1u) & 1u, abort_v)) ok = false;
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    unsigned long long ad_kd[3];
+#pragma unroll
+                    for (int kd = 0; kd < 3; ++kd)
+                        ad_kd[kd] = umma_desc_sw32(sP + ((p + (unsigned)(i + kd)) % (unsigned)R) * plane_bytes, 256);
+#pragma unroll 1
+                    for (int sl = 0; sl < S; ++sl) {
+#pragma unroll
+                        for (int kdh = 0; kdh < 9; ++kdh) {
+                            const unsigned long long ad =
+                                ad_kd[kdh / 3] + (unsigned long long)((sl * kDwPlaneSliceBytes + (kdh % 3) * 512) >> 4);
+                            const unsigned long long bd =
+                                bd0 + (unsigned long long)(((sl * 9 + kdh) * 2 * N3 * 16) >> 4);
+                            umma_bf16(tmem + ab * kAccCols, ad, bd, idesc, (sl | kdh) != 0);
+                        }
+                    }
+                    umma_commit(accf(ab));
+                    umma_commit(empty((int)((p + (unsigned)i) % (unsigned)R)));
+                }
+                if (!ok) break;
+                // the range's last two input planes are released after its last MMAs
+                umma_commit(empty((int)((p + (unsigned)nd) % (unsigned)R)));
+                umma_commit(empty((int)((p + (unsigned)nd + 1u) % (unsigned)R)));
+                p += (unsigned)nd + 2u;
+            }
+            // every MMA issued has completed before TMEM is freed (bounded)
+            umma_commit(fin);
+            const long long t0 = clock64();
+            while (!mbar_try(fin, 0))
+                if (clock64() - t0 > kTcWaitCycles) break;
+        }
+        __syncwarp();
+    } else {  // ---- epilogue warps
+        constexpr int CW = NT * 128 / (32 * EW);
+        static_assert(CW == 8 || CW == 16, "8 or 16 output channels per thread");
+        const int quad = warp & 3, c = (warp >> 2) * CW;
+        const int m = quad * 32 + lane;
+        unsigned it = 0;
+        bool ok = true;
+        for (long long q = q_begin; q < q_end && ok;) {
+            int d_begin, nd, w0, h0, b;
+            range_at(q, d_begin, nd, w0, h0, b);
+            q += nd;
+            const int ho = h0 + (m >> 4), wl = m & 15, wo = w0 + wl;
+            const bool out_in = wl < 14 && ho < H && wo < W;
+            for (int i = 0; i < nd; ++i, ++it) {
+                const unsigned ab = it & 1u;
+                // warp-uniform outcome (the shuffles below need every lane)
+                if (!__all_sync(0xffffffffu, role_wait(accf(ab), (it >> 1) & 1u, abort_v))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const unsigned base = tmem + ((unsigned)(quad * 32) << 16) + ab * kAccCols;
+                float a0[CW], a1[CW], a2[CW];
+                if constexpr (CW == 16)
+                    tmem_ld16x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c), a0, a1,
+                                a2);
+                else
+                    tmem_ld8x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c), a0, a1,
+                               a2);
+                // the accumulator is free as soon as it is in registers
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(acce(ab)) : "memory");
+#pragma unroll
+                for (int j = 0; j < CW; ++j)
+                    a0[j] += __shfl_down_sync(0xffffffffu, a1[j], 1) + __shfl_down_sync(0xffffffffu, a2[j], 2);
+                const int n = n0 + c;
+                if (out_in && n < Nn) {
+                    const long long v = (((long long)b * D + d_begin + i) * H + ho) * W + wo;
+                    dwalk_store<CW>(g, a0, bias ? sBias + c : nullptr, relu, out_bf16, out_f32, Nn, n, b,
+                                    d_begin + i, ho, wo, v);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && *abort_v) atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
@@ -2244,10 +2551,112 @@ cudaError_t prepare_kernel_smem(OccCache &c, K kernel, int smem) {
     return cudaSuccess;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (the library links no driver stub).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// 5-D tensor map of a channels-last BF16 activation [batch][d][h][w][C] read
+// in boxes of 16 channels x 16 w x 10 h x 1 d x 1 batch with the 32-byte
+// swizzle (zero fill outside the grid); false when it cannot be made.
+bool make_plane_map(CUtensorMap *m, const void *base, int C, const Conv3dArgs &g) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || !base || ((uintptr_t)base & 15u) || C % 16) return false;
+    const cuuint64_t e = 2;  // bytes per element
+    const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)g.in_w, (cuuint64_t)g.in_h, (cuuint64_t)g.in_d,
+                                (cuuint64_t)g.batch};
+    const cuuint64_t strides[4] = {dims[0] * e, dims[0] * dims[1] * e, dims[0] * dims[1] * dims[2] * e,
+                                   dims[0] * dims[1] * dims[2] * dims[3] * e};
+    const cuuint32_t box[5] = {16, 16, 10, 1, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The TMA d-walking kernel for an input read as stored (no upsampling; the
+// split of a two-part input on a 16-channel boundary); cudaErrorNotSupported,
+// launching nothing, when its tensor maps cannot be made for this input.
+cudaError_t launch_dwtma(const Conv3dArgs &g, const __nv_bfloat16 *src, const __nv_bfloat16 *wt, const float *bias,
+                         __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn, int relu, cudaStream_t st, int ca,
+                         const __nv_bfloat16 *src_b) {
+    // boxes no larger than the grid, 16-channel slices
+    if (g.in_w < 16 || g.in_h < 10 || ca % 16 || (Cs - ca) % 16 || (ca < Cs && !src_b)) return cudaErrorNotSupported;
+    CUtensorMap tm_a, tm_b;
+    if (!make_plane_map(&tm_a, src, ca, g)) return cudaErrorNotSupported;
+    if (ca < Cs) {
+        if (!make_plane_map(&tm_b, src_b, Cs - ca, g)) return cudaErrorNotSupported;
+    } else {
+        tm_b = tm_a;
+    }
+    int dev = 0, sms = 0, smem_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e != cudaSuccess) return e;
+    const int S = Cs / 16;
+    const int NT = Nn % 32 == 0 ? 32 : 16;
+    const int wbytes = S * 9 * 2 * (3 * NT) * 16;
+    const int plane = S * kDwPlaneSliceBytes;
+    // CTAs per SM: at most what TMEM allows (two accumulators of 64 or 128 of
+    // the 512 columns), fewer when the ring would hold less than 5 planes
+    // (three in use, two in flight); one CTA per SM takes a ring of 4
+    int per_sm = NT == 32 ? 2 : 4, R = 0;
+    for (; per_sm > 1; --per_sm) {
+        R = std::min(kDwtMaxRing, (smem_sm / per_sm - 3072 - wbytes - 1024) / plane);
+        if (R >= 5) break;
+    }
+    if (per_sm == 1) R = std::min(kDwtMaxRing, (smem_sm - 3072 - wbytes - 1024) / plane);
+    if (R < 4) return cudaErrorNotSupported;
+    const int smem = wbytes + 1024 + R * plane;
+    const int ntiles = (Nn + NT - 1) / NT;
+    const long long planes = (long long)g.batch * ((g.in_h + 7) / 8) * ((g.in_w + 13) / 14) * g.in_d;
+    long long gx = std::max(1ll, (long long)sms * per_sm / ntiles);
+    if (gx > planes) gx = planes;
+    const dim3 grid((unsigned)gx, (unsigned)ntiles);
+    if (NT == 32) {
+        static OccCache cache;
+        e = prepare_kernel_smem(cache, conv3_dwtma_kernel<32, 8, 2>, smem);
+        if (e != cudaSuccess) return e;
+        conv3_dwtma_kernel<32, 8, 2><<<grid, 320, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
+                                                               relu, ca, R);
+    } else if (per_sm >= 3) {
+        static OccCache cache;
+        e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 4, 4>, smem);
+        if (e != cudaSuccess) return e;
+        conv3_dwtma_kernel<16, 4, 4><<<grid, 192, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
+                                                               relu, ca, R);
+    } else {
+        static OccCache cache;
+        e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 8, 2>, smem);
+        if (e != cudaSuccess) return e;
+        conv3_dwtma_kernel<16, 8, 2><<<grid, 320, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
+                                                               relu, ca, R);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *wt, const float *bias,
                              void *out_bf16, float *out_f32, int Cs, int Nn, int relu, cudaStream_t st,
                              int ca, int up_a, const void *src_b) {
     if (ca <= 0) ca = Cs;
+    if (FDC_CONV_DWTMA && FDC_CONV_DWALK && !up_a && Cs <= FDC_CONV_DWALK_MAXC && Cs % 16 == 0 && Nn % 16 == 0) {
+        const cudaError_t e = launch_dwtma(g, (const __nv_bfloat16 *)src, (const __nv_bfloat16 *)wt, bias,
+                                           (__nv_bfloat16 *)out_bf16, out_f32, Cs, Nn, relu, st, ca,
+                                           (const __nv_bfloat16 *)src_b);
+        if (e != cudaErrorNotSupported) return e;
+    }
     auto s = (const __nv_bfloat16 *)src;
     auto w = (const __nv_bfloat16 *)wt;
     auto ob = (__nv_bfloat16 *)out_bf16;

@@ -62,6 +62,15 @@ CASES = [
     # stride-2 down-convolutions on the tensor-core path: 32 -> 64, batch 2 with odd sizes
     ((1, 6, 8, 10, 32), 64, 2, 2, 0),
     ((2, 5, 7, 9, 32), 64, 2, 2, 0),
+    # TMA d-walking kernel (input read as stored, h >= 10, w >= 16): the
+    # smallest grid its boxes allow; walks of several planes per CTA whose
+    # ranges restart at tile columns and wrap the plane ring (16- and 32-channel
+    # tiles, one and two input slices); four input slices, one CTA per SM
+    ((1, 5, 10, 16, 16), 16, 3, 1, 1),
+    ((1, 96, 64, 60, 16), 16, 3, 1, 1),
+    ((1, 64, 40, 30, 32), 32, 3, 1, 1),
+    ((2, 40, 19, 33, 32), 16, 3, 1, 1),
+    ((1, 9, 23, 45, 64), 32, 3, 1, 1),
 ]
 
 
@@ -438,15 +447,18 @@ def test_unet_forward_backward_and_training_reduces_loss():
     assert out.shape == (n, n, n) and bool(torch.isfinite(out).all())
 
 
-@pytest.mark.parametrize("ca,cb,up", [(32, 0, 1), (16, 16, 0), (64, 64, 0), (32, 32, 1)])
-def test_fused_upsample_concat_forward(ca, cb, up):
+@pytest.mark.parametrize("ca,cb,up,dims", [(32, 0, 1, (6, 8, 10)), (16, 16, 0, (6, 8, 10)), (64, 64, 0, (6, 8, 10)),
+                                           (32, 32, 1, (6, 8, 10)), (16, 16, 0, (5, 12, 20)),
+                                           (32, 32, 0, (7, 10, 34)), (32, 16, 0, (4, 11, 16))])
+def test_fused_upsample_concat_forward(ca, cb, up, dims):
     """fdc_conv3d_forward_fused equals fdc_conv3d_forward on the materialised
-    [upsample(xa) | xb] input."""
+    [upsample(xa) | xb] input (the larger grids take the two tensor maps of
+    the TMA d-walking kernel)."""
     import torch
     from paper_1011_2188_gb300 import fdc
     L = fdc.lib()
-    rng = np.random.default_rng(ca + cb + up)
-    D, H, W = 6, 8, 10
+    rng = np.random.default_rng(ca + cb + up + sum(dims))
+    D, H, W = dims
     sa = (1, D // 2, H // 2, W // 2, ca) if up else (1, D, H, W, ca)
     xat, xa = bf16(rng.normal(size=sa))
     xbt, xb = bf16(rng.normal(size=(1, D, H, W, cb))) if cb else (None, None)
