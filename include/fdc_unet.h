@@ -47,6 +47,28 @@ int fdc_conv3d_forward(const fdc_conv3d *g, const void *x, const void *w, const 
  * Same result as fdc_conv3d_forward on the materialised input. */
 int fdc_conv3d_forward_fused(const fdc_conv3d *g, const void *xa, int32_t ca, int32_t upsample_a, const void *xb,
                              const void *w, const float *bias, void *y_bf16, float *y_f32, void *stream);
+/* The 3^3 convolution (ksize 3, stride 1, pad 1) of upsample2(xa), computed
+ * on xa's own half-resolution grid by output parity class: along each axis,
+ * output 2i + p reads the two coarse voxels i + p - 1 and i + p with the sums
+ * of the weights of the taps that land on them, 8 collapsed taps per output
+ * voxel instead of 27.  g describes the full-resolution convolution (in_d,
+ * in_h, in_w even, output = input size); xa bf16 [batch][in_d/2][in_h/2][in_w/2][c_in];
+ * w_up the collapsed weights of fdc_conv3d_collapse_up_weights; bias, relu and
+ * outputs as in fdc_conv3d_forward.  Equals fdc_conv3d_forward_fused with
+ * upsample_a = 1 up to the one BF16 rounding of each collapsed weight (unit
+ * roundoff 2^-8): per output, |difference| <= 2^-8 * sum over taps and
+ * channels of |w| |x| (plus FP32 accumulation order).  FDC_ERR_INVALID, launching nothing, for shapes
+ * without its kernel: c_in a multiple of 16 up to 64, c_out a multiple of
+ * 16, a half-resolution grid of at least 10 (h) x 16 (w), shared memory for
+ * the collapsed weights of every input channel. */
+int fdc_conv3d_forward_up(const fdc_conv3d *g, const void *xa, const void *w_up, const float *bias, void *y_bf16,
+                          float *y_f32, void *stream);
+/* Collapsed weights for fdc_conv3d_forward_up: w_up[co][pd ph][sd sh][pw sw][ci]
+ * (bf16, c_out x 64 x c_in) = the sum, in FP32 rounded once to BF16, of
+ * w[co][kd][kh][kw][ci] over the taps with (p + k - 1) >> 1 = p - 1 + s on each
+ * axis (p: output parity, s = 0, 1: the first or second coarse voxel read).
+ * g: a 3^3, stride-1, padding-1 convolution. */
+int fdc_conv3d_collapse_up_weights(const fdc_conv3d *g, const void *w, void *w_up, void *stream);
 /* dx[b][i][ci] = sum over (tap, co) with i + pad - tap = stride * o of dy[b][o][co] w[co][tap][ci]
  * (the gradient of the forward map with respect to x, without this layer's ReLU).
  * dy bf16 [batch][out...][c_out]; w_t the data-gradient weights that

@@ -31,6 +31,11 @@ cudaError_t launch_wait_timeout(long long cycles, cudaStream_t st);
 cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *wt, const float *bias,
                              void *out_bf16, float *out_f32, int Cs, int Nn, int relu, cudaStream_t st,
                              int ca, int up_a, const void *src_b);
+// the sub-pixel convolution of upsample2(xa) (cudaErrorNotSupported, nothing
+// launched, for shapes without its kernel) and its collapsed weights
+cudaError_t launch_conv_up(const Conv3dArgs &g, const void *xa, const void *w_up, const float *bias, void *out_bf16,
+                           float *out_f32, int relu, cudaStream_t st);
+cudaError_t launch_collapse_up(const void *w, void *w_up, int co, int ci, cudaStream_t st);
 cudaError_t launch_flip_transpose(const void *w, void *wf, int co, int k, int ci, cudaStream_t st);
 cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy, float *dw, float *db,
                               cudaStream_t st, int ca, int up_a, const void *xb);

@@ -332,6 +332,17 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float v[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, float v[8]) {
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                 "tcgen05.wait::ld.sync.aligned;\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Three 16-column loads (the kw blocks of a kw-stacked accumulator) with one
 // wait: the loads overlap instead of each waiting in turn.
 __device__ __forceinline__ void tmem_ld16x3(unsigned t0, unsigned t1, unsigned t2, float a[16], float b[16],
@@ -846,6 +857,14 @@ constexpr int kDwPlaneSliceBytes = 10 * 512;  // [h 10][w-group 2][k-chunk 2][8 
 #ifndef FDC_CONV_DWALK_MAXC
 #define FDC_CONV_DWALK_MAXC 64
 #endif
+// 64-channel output tiles (conv3_tc_kernel<64>) where they fill the GPU; the
+// kw-stacked kernel's output tile width (0: 32 when the channels allow, 16: always 16)
+#ifndef FDC_CONV_TC64
+#define FDC_CONV_TC64 1
+#endif
+#ifndef FDC_KWS_NT
+#define FDC_KWS_NT 0
+#endif
 // the d-walking kernel's shared memory at its smallest ring (5 planes) fits one CTA
 inline bool dwalk_fits(int S, int NT) {
     return S * 9 * 2 * (3 * NT) * 16 + 5 * S * kDwPlaneSliceBytes <= 227 * 1024 - 1024;
@@ -1079,6 +1098,7 @@ __global__ void __launch_bounds__(THR) conv3_dwalk_kernel(const Conv3dArgs g, co
 // the TMA warp waits (bounded) for the copies it issued and the MMA warp for
 // its MMAs.
 constexpr int kDwtMaxRing = 12;
+constexpr int kDwtMaxAcc = 8;   // accumulator slots
 #ifndef FDC_CONV_DWTMA
 #define FDC_CONV_DWTMA 1
 #endif
@@ -1124,26 +1144,41 @@ __device__ __forceinline__ unsigned long long umma_desc_sw32(unsigned saddr, uns
            ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46) | (6ull << 61);
 }
 
-template <int NT, int EW, int MINB>
+// MODE 1: the convolution of the nearest x2 upsampling of the input,
+// computed on the input's own (coarse) grid by output parity class
+// (sub-pixel form): along an axis, output 2i + p reads coarse voxels
+// i + p - 1 + s' (s' = 0, 1) with the weights of the taps that land there
+// summed (p = 0: tap 0 | taps 1, 2; p = 1: taps 0, 1 | tap 2), so each output
+// voxel takes 8 collapsed taps instead of 27.  A coarse output plane is four
+// units (pd, ph); a unit is 4 (sd', sh') MMAs per 16-channel slice whose N =
+// 4 NT columns hold the blocks (pw, sw') of the w axis, added in the epilogue
+// like the kw blocks of MODE 0.  Weights: fdc's collapsed layout
+// [c_out][pd ph][sd' sh'][pw sw'][c_in] (conv3_collapse_up_kernel).
+template <int NT, int EW, int MINB, int MODE>
 __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     conv3_dwtma_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
                        const Conv3dArgs g, const __nv_bfloat16 *wt, const float *bias, __nv_bfloat16 *out_bf16,
-                       float *out_f32, int Cs, int Nn, int relu, int ca, int R) {
-    constexpr int N3 = 3 * NT;
-    constexpr unsigned kAccCols = N3 <= 64 ? 64 : 128;  // columns per accumulator buffer
-    constexpr unsigned kCols = 2 * kAccCols;
+                       float *out_f32, int Cs, int Nn, int relu, int ca, int R, int NA) {
+    constexpr int NB = MODE == 0 ? 3 : 4;          // column blocks per unit (kw taps | (pw, sw'))
+    constexpr int NU = MODE == 0 ? 9 : 16;         // weight groups per slice ((kd, kh) | (pd ph, sd' sh'))
+    constexpr int NX = NB * NT;                    // MMA N
+    constexpr unsigned kAccCols = NX <= 64 ? 64 : 128;  // columns per accumulator slot
+    constexpr int UPP = MODE == 0 ? 1 : 4;         // units per (coarse) output plane
     constexpr int THR = 32 * (EW + 2);
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) unsigned long long bars[2 * kDwtMaxRing + 5];
+    __shared__ __align__(8) unsigned long long bars[2 * kDwtMaxRing + 2 * kDwtMaxAcc + 1];
     __shared__ unsigned tmem_slot;
     __shared__ int abort_flag;
     __shared__ float sBias[NT];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int D = g.in_d, H = g.in_h, W = g.in_w;
+    // the walked grid: the output grid (MODE 0) or the coarse input grid (MODE 1)
+    const int D = MODE == 0 ? g.in_d : g.in_d / 2, H = MODE == 0 ? g.in_h : g.in_h / 2,
+              W = MODE == 0 ? g.in_w : g.in_w / 2;
     const int S = Cs / 16;
     const unsigned plane_bytes = (unsigned)(S * kDwPlaneSliceBytes);
-    const int wbytes = S * 9 * 2 * N3 * 16;
-    unsigned char *sW = smem;  // [slice][kd kh][k-chunk][kw NT + co][8]
+    const int wbytes = S * NU * 2 * NX * 16;
+    const unsigned kCols = (unsigned)NA * kAccCols;
+    unsigned char *sW = smem;  // [slice][group][k-chunk][block NT + co][8]
     // the plane ring starts on a 1024-byte boundary (the swizzle pattern is
     // taken from the shared-memory address bits)
     const unsigned sP = (smem_u32(smem) + (unsigned)wbytes + 1023u) & ~1023u;
@@ -1151,8 +1186,8 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     auto full = [&](int s) { return bar0 + 8u * (unsigned)s; };
     auto empty = [&](int s) { return bar0 + 8u * (unsigned)(kDwtMaxRing + s); };
     auto accf = [&](unsigned k) { return bar0 + 8u * (2u * kDwtMaxRing + k); };
-    auto acce = [&](unsigned k) { return bar0 + 8u * (2u * kDwtMaxRing + 2u + k); };
-    const unsigned fin = bar0 + 8u * (2u * kDwtMaxRing + 4u);
+    auto acce = [&](unsigned k) { return bar0 + 8u * (2u * kDwtMaxRing + kDwtMaxAcc + k); };
+    const unsigned fin = bar0 + 8u * (2u * kDwtMaxRing + 2u * kDwtMaxAcc);
     volatile int *abort_v = &abort_flag;
 
     const int tiles_w = (W + 13) / 14, tiles_h = (H + 7) / 8;
@@ -1166,7 +1201,7 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full(s)));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(s)));
         }
-        for (unsigned k = 0; k < 2; ++k) {
+        for (unsigned k = 0; k < (unsigned)NA; ++k) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(accf(k)));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(acce(k)), "r"(EW));
         }
@@ -1181,13 +1216,15 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     }
     if (tid < NT) sBias[tid] = (bias && n0 + tid < Nn) ? bias[n0 + tid] : 0.f;
     {  // resident weights of every input slice (through L1: all CTAs read the same)
-        constexpr int kChunks = 9 * 2 * N3;  // per slice
+        constexpr int kChunks = NU * 2 * NX;  // per slice
+        constexpr int kTaps = MODE == 0 ? 27 : 64;  // weight rows per output channel
         for (int i = tid; i < S * kChunks; i += THR) {
             const int sl = i / kChunks, r = i % kChunks;
-            const int n = r % N3, q = r / N3, kc = q & 1, kdh = q >> 1;
-            const int co = n0 + (n % NT), kw = n / NT;
+            const int n = r % NX, q = r / NX, kc = q & 1, grp = q >> 1;
+            const int co = n0 + (n % NT), blk = n / NT;
             const bool in = co < Nn;
-            const __nv_bfloat16 *p = in ? wt + (size_t)((co * 27 + kdh * 3 + kw) * Cs + sl * 16 + kc * 8) : wt;
+            const __nv_bfloat16 *p =
+                in ? wt + (size_t)((co * kTaps + grp * NB + blk) * Cs + sl * 16 + kc * 8) : wt;
             cp_async16_ca(sW + i * 16, p, in);
         }
         cp_async_commit();
@@ -1247,41 +1284,63 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
                     if (clock64() - t0 > kTcWaitCycles) break;
         }
         __syncwarp();
-    } else if (warp == EW + 1) {  // ---- MMA: output planes of each range
+    } else if (warp == EW + 1) {  // ---- MMA: output units of each range
         if (lane == 0) {
-            constexpr unsigned idesc = umma_idesc(128, N3);
-            const unsigned long long bd0 = umma_desc(smem_u32(sW), N3 * 16, 128);
-            unsigned p = 0, it = 0;  // first plane of the range; output planes over all ranges
+            constexpr unsigned idesc = umma_idesc(128, NX);
+            const unsigned long long bd0 = umma_desc(smem_u32(sW), NX * 16, 128);
+            unsigned p = 0, it = 0;  // first plane of the range; units over all ranges
             bool ok = true;
             for (long long q = q_begin; q < q_end && ok;) {
                 int d_begin, nd, w0, h0, b;
                 range_at(q, d_begin, nd, w0, h0, b);
                 q += nd;
-                for (int i = 0; i < nd && ok; ++i, ++it) {
+                for (int i = 0; i < nd && ok; ++i) {
                     for (int j = (i == 0 ? 0 : i + 2); j <= i + 2; ++j) {
                         const unsigned pp = p + (unsigned)j;
                         if (!role_wait(full((int)(pp % (unsigned)R)), (pp / (unsigned)R) & 1u, abort_v)) ok = false;
                     }
-                    const unsigned ab = it & 1u;
-                    if (ok && it >= 2 && !role_wait(acce(ab), ((it >> 1) - 1u) & 1u, abort_v)) ok = false;
                     if (!ok) break;
-                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     unsigned long long ad_kd[3];
 #pragma unroll
                     for (int kd = 0; kd < 3; ++kd)
                         ad_kd[kd] = umma_desc_sw32(sP + ((p + (unsigned)(i + kd)) % (unsigned)R) * plane_bytes, 256);
-#pragma unroll 1
-                    for (int sl = 0; sl < S; ++sl) {
-#pragma unroll
-                        for (int kdh = 0; kdh < 9; ++kdh) {
-                            const unsigned long long ad =
-                                ad_kd[kdh / 3] + (unsigned long long)((sl * kDwPlaneSliceBytes + (kdh % 3) * 512) >> 4);
-                            const unsigned long long bd =
-                                bd0 + (unsigned long long)(((sl * 9 + kdh) * 2 * N3 * 16) >> 4);
-                            umma_bf16(tmem + ab * kAccCols, ad, bd, idesc, (sl | kdh) != 0);
+                    for (int u = 0; u < UPP; ++u, ++it) {
+                        const unsigned ab = it % (unsigned)NA;
+                        if (it >= (unsigned)NA && !role_wait(acce(ab), (it / (unsigned)NA - 1u) & 1u, abort_v)) {
+                            ok = false;
+                            break;
                         }
+                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll 1
+                        for (int sl = 0; sl < S; ++sl) {
+                            if constexpr (MODE == 0) {
+#pragma unroll
+                                for (int kdh = 0; kdh < 9; ++kdh) {
+                                    const unsigned long long ad =
+                                        ad_kd[kdh / 3] +
+                                        (unsigned long long)((sl * kDwPlaneSliceBytes + (kdh % 3) * 512) >> 4);
+                                    const unsigned long long bd =
+                                        bd0 + (unsigned long long)(((sl * NU + kdh) * 2 * NX * 16) >> 4);
+                                    umma_bf16(tmem + ab * kAccCols, ad, bd, idesc, (sl | kdh) != 0);
+                                }
+                            } else {
+                                // unit u = (pd, ph); combination c = (sd', sh') reads input
+                                // plane i + pd + sd' - 1 (ring index pd + sd') at row shift ph + sh'
+                                const int pd = u >> 1, ph = u & 1;
+#pragma unroll
+                                for (int c = 0; c < 4; ++c) {
+                                    const int kd = pd + (c >> 1), kh = ph + (c & 1);
+                                    const unsigned long long ad =
+                                        ad_kd[kd] + (unsigned long long)((sl * kDwPlaneSliceBytes + kh * 512) >> 4);
+                                    const unsigned long long bd =
+                                        bd0 + (unsigned long long)(((sl * NU + u * 4 + c) * 2 * NX * 16) >> 4);
+                                    umma_bf16(tmem + ab * kAccCols, ad, bd, idesc, (sl | c) != 0);
+                                }
+                            }
+                        }
+                        umma_commit(accf(ab));
                     }
-                    umma_commit(accf(ab));
+                    if (!ok) break;
                     umma_commit(empty((int)((p + (unsigned)i) % (unsigned)R)));
                 }
                 if (!ok) break;
@@ -1308,36 +1367,77 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
             int d_begin, nd, w0, h0, b;
             range_at(q, d_begin, nd, w0, h0, b);
             q += nd;
-            const int ho = h0 + (m >> 4), wl = m & 15, wo = w0 + wl;
-            const bool out_in = wl < 14 && ho < H && wo < W;
-            for (int i = 0; i < nd; ++i, ++it) {
-                const unsigned ab = it & 1u;
-                // warp-uniform outcome (the shuffles below need every lane)
-                if (!__all_sync(0xffffffffu, role_wait(accf(ab), (it >> 1) & 1u, abort_v))) {
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const unsigned base = tmem + ((unsigned)(quad * 32) << 16) + ab * kAccCols;
-                float a0[CW], a1[CW], a2[CW];
-                if constexpr (CW == 16)
-                    tmem_ld16x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c), a0, a1,
-                                a2);
-                else
-                    tmem_ld8x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c), a0, a1,
-                               a2);
-                // the accumulator is free as soon as it is in registers
-                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                __syncwarp();
-                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(acce(ab)) : "memory");
+            const int hl = h0 + (m >> 4), wl = m & 15, wc = w0 + wl;
+            const bool out_in = wl < 14 && hl < H && wc < W;
+            for (int i = 0; i < nd && ok; ++i) {
+                for (int u = 0; u < UPP; ++u, ++it) {
+                    const unsigned ab = it % (unsigned)NA;
+                    // warp-uniform outcome (the shuffles below need every lane)
+                    if (!__all_sync(0xffffffffu, role_wait(accf(ab), (it / (unsigned)NA) & 1u, abort_v))) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const unsigned base = tmem + ((unsigned)(quad * 32) << 16) + ab * kAccCols;
+                    const int n = n0 + c;
+                    if constexpr (MODE == 0) {
+                        float a0[CW], a1[CW], a2[CW];
+                        if constexpr (CW == 16)
+                            tmem_ld16x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c),
+                                        a0, a1, a2);
+                        else
+                            tmem_ld8x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c),
+                                       a0, a1, a2);
+                        // the accumulator is free as soon as it is in registers
+                        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0)
+                            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(acce(ab)) : "memory");
 #pragma unroll
-                for (int j = 0; j < CW; ++j)
-                    a0[j] += __shfl_down_sync(0xffffffffu, a1[j], 1) + __shfl_down_sync(0xffffffffu, a2[j], 2);
-                const int n = n0 + c;
-                if (out_in && n < Nn) {
-                    const long long v = (((long long)b * D + d_begin + i) * H + ho) * W + wo;
-                    dwalk_store<CW>(g, a0, bias ? sBias + c : nullptr, relu, out_bf16, out_f32, Nn, n, b,
-                                    d_begin + i, ho, wo, v);
+                        for (int j = 0; j < CW; ++j)
+                            a0[j] += __shfl_down_sync(0xffffffffu, a1[j], 1) + __shfl_down_sync(0xffffffffu, a2[j], 2);
+                        if (out_in && n < Nn) {
+                            const long long v = (((long long)b * D + d_begin + i) * H + hl) * W + wc;
+                            dwalk_store<CW>(g, a0, bias ? sBias + c : nullptr, relu, out_bf16, out_f32, Nn, n, b,
+                                            d_begin + i, hl, wc, v);
+                        }
+                    } else {
+                        // blocks (pw, sw') = (0, 0), (0, 1), (1, 0), (1, 1): output column
+                        // pw of coarse column wl adds blocks (pw, 0) of row wl + pw and
+                        // (pw, 1) of row wl + pw + 1
+                        float a0[CW], a1[CW], a2[CW], a3[CW];
+                        if constexpr (CW == 16) {
+                            tmem_ld16x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c),
+                                        a0, a1, a2);
+                            tmem_ld16(base + (unsigned)(3 * NT + c), a3);
+                        } else {
+                            tmem_ld8x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c),
+                                       a0, a1, a2);
+                            tmem_ld8(base + (unsigned)(3 * NT + c), a3);
+                        }
+                        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0)
+                            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(acce(ab)) : "memory");
+#pragma unroll
+                        for (int j = 0; j < CW; ++j) {
+                            const float b1 = __shfl_down_sync(0xffffffffu, a1[j], 1);
+                            const float b2 = __shfl_down_sync(0xffffffffu, a2[j], 1);
+                            const float b3 = __shfl_down_sync(0xffffffffu, a3[j], 2);
+                            a0[j] += b1;
+                            a2[j] = b2 + b3;
+                        }
+                        if (out_in && n < Nn) {
+                            const int pd = u >> 1, ph = u & 1;
+                            const int Do = 2 * D, Ho = 2 * H, Wo = 2 * W;
+                            const int od = 2 * (d_begin + i) + pd, oh = 2 * hl + ph, ow = 2 * wc;
+                            const long long v = (((long long)b * Do + od) * Ho + oh) * Wo + ow;
+                            dwalk_store<CW>(g, a0, bias ? sBias + c : nullptr, relu, out_bf16, out_f32, Nn, n, b, od,
+                                            oh, ow, v);
+                            dwalk_store<CW>(g, a2, bias ? sBias + c : nullptr, relu, out_bf16, out_f32, Nn, n, b, od,
+                                            oh, ow + 1, v + 1);
+                        }
+                    }
                 }
             }
         }
@@ -1348,6 +1448,35 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
+    }
+}
+
+// Collapsed weights of the upsampling convolution (MODE 1 above):
+// wc[co][pd ph][sd' sh'][pw sw'][ci] = sum of w[co][kd][kh][kw][ci] over the
+// taps k of each axis with (p + k - 1) >> 1 = p - 1 + s', summed in FP32 and
+// rounded once to BF16.
+__global__ void conv3_collapse_up_kernel(const __nv_bfloat16 *w, __nv_bfloat16 *wc, int co_n, int ci_n) {
+    const long long n = (long long)co_n * 64 * ci_n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)(i % ci_n);
+        const int t = (int)((i / ci_n) % 64);
+        const int co = (int)(i / ((long long)ci_n * 64));
+        // t = ((pd ph) * 4 + (sd' sh')) * 4 + (pw sw')
+        const int pd = (t >> 5) & 1, ph = (t >> 4) & 1, sd = (t >> 3) & 1, sh = (t >> 2) & 1, pw = (t >> 1) & 1,
+                  sw = t & 1;
+        float acc = 0.f;
+        for (int kd = 0; kd < 3; ++kd) {
+            if (((pd + kd - 1) >> 1) != pd - 1 + sd) continue;
+            for (int kh = 0; kh < 3; ++kh) {
+                if (((ph + kh - 1) >> 1) != ph - 1 + sh) continue;
+                for (int kw = 0; kw < 3; ++kw) {
+                    if (((pw + kw - 1) >> 1) != pw - 1 + sw) continue;
+                    acc += __bfloat162float(w[((long long)co * 27 + (kd * 3 + kh) * 3 + kw) * ci_n + ci]);
+                }
+            }
+        }
+        wc[i] = __float2bfloat16_rn(acc);
     }
 }
 
@@ -2570,12 +2699,11 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // 5-D tensor map of a channels-last BF16 activation [batch][d][h][w][C] read
 // in boxes of 16 channels x 16 w x 10 h x 1 d x 1 batch with the 32-byte
 // swizzle (zero fill outside the grid); false when it cannot be made.
-bool make_plane_map(CUtensorMap *m, const void *base, int C, const Conv3dArgs &g) {
+bool make_plane_map(CUtensorMap *m, const void *base, int C, int B, int D, int H, int W) {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc || !base || ((uintptr_t)base & 15u) || C % 16) return false;
+    if (!enc || !base || ((uintptr_t)base & 15u) || C % 16 || W < 16 || H < 10) return false;
     const cuuint64_t e = 2;  // bytes per element
-    const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)g.in_w, (cuuint64_t)g.in_h, (cuuint64_t)g.in_d,
-                                (cuuint64_t)g.batch};
+    const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B};
     const cuuint64_t strides[4] = {dims[0] * e, dims[0] * dims[1] * e, dims[0] * dims[1] * dims[2] * e,
                                    dims[0] * dims[1] * dims[2] * dims[3] * e};
     const cuuint32_t box[5] = {16, 16, 10, 1, 1};
@@ -2585,18 +2713,23 @@ bool make_plane_map(CUtensorMap *m, const void *base, int C, const Conv3dArgs &g
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The TMA d-walking kernel for an input read as stored (no upsampling; the
-// split of a two-part input on a 16-channel boundary); cudaErrorNotSupported,
-// launching nothing, when its tensor maps cannot be made for this input.
-cudaError_t launch_dwtma(const Conv3dArgs &g, const __nv_bfloat16 *src, const __nv_bfloat16 *wt, const float *bias,
-                         __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn, int relu, cudaStream_t st, int ca,
-                         const __nv_bfloat16 *src_b) {
-    // boxes no larger than the grid, 16-channel slices
-    if (g.in_w < 16 || g.in_h < 10 || ca % 16 || (Cs - ca) % 16 || (ca < Cs && !src_b)) return cudaErrorNotSupported;
+// The TMA d-walking kernel.  MODE 0: an input read as stored (no upsampling;
+// the split of a two-part input on a 16-channel boundary).  MODE 1: the
+// sub-pixel form of the convolution of upsample2(src), src on the coarse grid
+// with Cs channels, wt the collapsed weights.  cudaErrorNotSupported,
+// launching nothing, when the shape has no instantiation or its tensor maps
+// cannot be made.
+cudaError_t launch_dwtma(int mode, const Conv3dArgs &g, const __nv_bfloat16 *src, const __nv_bfloat16 *wt,
+                         const float *bias, __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn, int relu,
+                         cudaStream_t st, int ca, const __nv_bfloat16 *src_b) {
+    if (Cs % 16 || Cs > 64 || Nn % 16 || ca % 16 || (Cs - ca) % 16 || (ca < Cs && !src_b)) return cudaErrorNotSupported;
+    if (mode == 1 && (ca != Cs || g.in_d % 2 || g.in_h % 2 || g.in_w % 2)) return cudaErrorNotSupported;
+    // the walked (input) grid
+    const int D = mode ? g.in_d / 2 : g.in_d, H = mode ? g.in_h / 2 : g.in_h, W = mode ? g.in_w / 2 : g.in_w;
     CUtensorMap tm_a, tm_b;
-    if (!make_plane_map(&tm_a, src, ca, g)) return cudaErrorNotSupported;
+    if (!make_plane_map(&tm_a, src, ca, g.batch, D, H, W)) return cudaErrorNotSupported;
     if (ca < Cs) {
-        if (!make_plane_map(&tm_b, src_b, Cs - ca, g)) return cudaErrorNotSupported;
+        if (!make_plane_map(&tm_b, src_b, Cs - ca, g.batch, D, H, W)) return cudaErrorNotSupported;
     } else {
         tm_b = tm_a;
     }
@@ -2606,44 +2739,66 @@ cudaError_t launch_dwtma(const Conv3dArgs &g, const __nv_bfloat16 *src, const __
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e != cudaSuccess) return e;
     const int S = Cs / 16;
-    const int NT = Nn % 32 == 0 ? 32 : 16;
-    const int wbytes = S * 9 * 2 * (3 * NT) * 16;
+    const int NT = (mode == 0 && Nn % 32 == 0) ? 32 : 16;
+    const int NX = (mode == 0 ? 3 : 4) * NT, NU = mode == 0 ? 9 : 16;
+    const int wbytes = S * NU * 2 * NX * 16;
     const int plane = S * kDwPlaneSliceBytes;
-    // CTAs per SM: at most what TMEM allows (two accumulators of 64 or 128 of
-    // the 512 columns), fewer when the ring would hold less than 5 planes
-    // (three in use, two in flight); one CTA per SM takes a ring of 4
-    int per_sm = NT == 32 ? 2 : 4, R = 0;
+    // CTAs per SM: at most what TMEM allows (accumulator slots of 64 or 128 of
+    // the 512 columns: two per CTA in MODE 0, one coarse plane's four units
+    // in MODE 1), fewer when the ring would hold less than 5 planes (three in
+    // use, two in flight) or, in MODE 1, 4; one CTA per SM takes a ring of 4
+    int per_sm = mode == 1 ? 2 : (NT == 32 ? 2 : 4), R = 0;
+    const int r_min = mode == 1 ? 4 : 5;
     for (; per_sm > 1; --per_sm) {
         R = std::min(kDwtMaxRing, (smem_sm / per_sm - 3072 - wbytes - 1024) / plane);
-        if (R >= 5) break;
+        if (R >= r_min) break;
     }
     if (per_sm == 1) R = std::min(kDwtMaxRing, (smem_sm - 3072 - wbytes - 1024) / plane);
     if (R < 4) return cudaErrorNotSupported;
+    const int NA = mode == 0 ? 2 : (per_sm == 2 ? 4 : 8);
     const int smem = wbytes + 1024 + R * plane;
     const int ntiles = (Nn + NT - 1) / NT;
-    const long long planes = (long long)g.batch * ((g.in_h + 7) / 8) * ((g.in_w + 13) / 14) * g.in_d;
+    const long long planes = (long long)g.batch * ((H + 7) / 8) * ((W + 13) / 14) * D;
     long long gx = std::max(1ll, (long long)sms * per_sm / ntiles);
     if (gx > planes) gx = planes;
     const dim3 grid((unsigned)gx, (unsigned)ntiles);
-    if (NT == 32) {
+    if (mode == 1) {
         static OccCache cache;
-        e = prepare_kernel_smem(cache, conv3_dwtma_kernel<32, 8, 2>, smem);
+        e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 8, 2, 1>, smem);
         if (e != cudaSuccess) return e;
-        conv3_dwtma_kernel<32, 8, 2><<<grid, 320, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
-                                                               relu, ca, R);
+        conv3_dwtma_kernel<16, 8, 2, 1><<<grid, 320, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
+                                                                  relu, ca, R, NA);
+    } else if (NT == 32) {
+        static OccCache cache;
+        e = prepare_kernel_smem(cache, conv3_dwtma_kernel<32, 8, 2, 0>, smem);
+        if (e != cudaSuccess) return e;
+        conv3_dwtma_kernel<32, 8, 2, 0><<<grid, 320, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
+                                                                  relu, ca, R, NA);
     } else if (per_sm >= 3) {
         static OccCache cache;
-        e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 4, 4>, smem);
+        e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 4, 4, 0>, smem);
         if (e != cudaSuccess) return e;
-        conv3_dwtma_kernel<16, 4, 4><<<grid, 192, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
-                                                               relu, ca, R);
+        conv3_dwtma_kernel<16, 4, 4, 0><<<grid, 192, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
+                                                                  relu, ca, R, NA);
     } else {
         static OccCache cache;
-        e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 8, 2>, smem);
+        e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 8, 2, 0>, smem);
         if (e != cudaSuccess) return e;
-        conv3_dwtma_kernel<16, 8, 2><<<grid, 320, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
-                                                               relu, ca, R);
+        conv3_dwtma_kernel<16, 8, 2, 0><<<grid, 320, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
+                                                                  relu, ca, R, NA);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv_up(const Conv3dArgs &g, const void *xa, const void *w_up, const float *bias, void *out_bf16,
+                           float *out_f32, int relu, cudaStream_t st) {
+    return launch_dwtma(1, g, (const __nv_bfloat16 *)xa, (const __nv_bfloat16 *)w_up, bias, (__nv_bfloat16 *)out_bf16,
+                        out_f32, g.c_in, g.c_out, relu, st, g.c_in, nullptr);
+}
+
+cudaError_t launch_collapse_up(const void *w, void *w_up, int co, int ci, cudaStream_t st) {
+    const long long n = (long long)co * 64 * ci;
+    conv3_collapse_up_kernel<<<grid_for(n), 256, 0, st>>>((const __nv_bfloat16 *)w, (__nv_bfloat16 *)w_up, co, ci);
     return cudaGetLastError();
 }
 
@@ -2652,7 +2807,7 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
                              int ca, int up_a, const void *src_b) {
     if (ca <= 0) ca = Cs;
     if (FDC_CONV_DWTMA && FDC_CONV_DWALK && !up_a && Cs <= FDC_CONV_DWALK_MAXC && Cs % 16 == 0 && Nn % 16 == 0) {
-        const cudaError_t e = launch_dwtma(g, (const __nv_bfloat16 *)src, (const __nv_bfloat16 *)wt, bias,
+        const cudaError_t e = launch_dwtma(0, g, (const __nv_bfloat16 *)src, (const __nv_bfloat16 *)wt, bias,
                                            (__nv_bfloat16 *)out_bf16, out_f32, Cs, Nn, relu, st, ca,
                                            (const __nv_bfloat16 *)src_b);
         if (e != cudaErrorNotSupported) return e;
@@ -2721,7 +2876,7 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
     // the kw-stacked 32-channel tiles made U-Net inference 1.24 vs 1.20 ms);
     // otherwise the kw-stacked kernel spreads small grids wider (16^3 x 128: 43 vs 64 us)
     const long long tiles64 = (long long)g.batch * g.in_d * ((g.in_h + 15) / 16) * ((g.in_w + 7) / 8);
-    if (Nn % 64 == 0 && tiles64 * (Nn / 64) >= 152) {
+    if (FDC_CONV_TC64 && Nn % 64 == 0 && tiles64 * (Nn / 64) >= 152) {
         static OccCache cache;
         const int smem = kTcHaloBytes + 27 * 2 * 64 * 16;
         const cudaError_t e = prepare_kernel_smem(cache, conv3_tc_kernel<64>, smem);
@@ -2735,7 +2890,7 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
     // blocks per CTA: enough CTAs for a few waves, weights staged once per CTA
     const int tpc = tiles >= 8 * 152 * 4 ? 4 : (tiles >= 4 * 152 * 2 ? 2 : 1);
     const unsigned grid_x = (unsigned)((tiles + tpc - 1) / tpc);
-    if (Nn % 32 == 0) {
+    if (Nn % 32 == 0 && FDC_KWS_NT != 16) {
         constexpr int kW = 9 * 2 * 96 * 16;
         const int resw = (Cs / 16) * kW <= 56 * 1024;
         const int smem = kKwHaloBytes + (resw ? Cs / 16 : 1) * kW;
@@ -2803,6 +2958,12 @@ cudaError_t launch_s2_tc(const Conv3dArgs &g, const void *src, const void *wt, c
     return cudaGetLastError();
 }
 
+// widest output-channel tile of the mma.sync forward (its grid is small on
+// coarse levels: narrower tiles give more CTAs)
+#ifndef FDC_IGEMM_FWD_NT
+#define FDC_IGEMM_FWD_NT 64
+#endif
+
 bool s2_tc_shape(const Conv3dArgs &g, int mode, const float *out_f32) {
     if (g.ksize != 2 || g.stride != 2 || g.pad != 0) return false;
     if ((long long)g.batch * g.out_d * g.out_h * g.out_w >= (1ll << 31) - kS2Vox) return false;
@@ -2833,7 +2994,8 @@ cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const vo
     const int Nn = mode == 0 ? g.c_out : g.c_in;
     const long long rows = (long long)g.batch * (mode == 0 ? (long long)g.out_d * g.out_h * g.out_w
                                                           : (long long)g.in_d * g.in_h * g.in_w);
-    const int nt = Nn >= 64 ? 64 : (Nn >= 32 ? 32 : 16);
+    const int nt_max = mode == 0 ? FDC_IGEMM_FWD_NT : 64;
+    const int nt = Nn >= 64 && nt_max >= 64 ? 64 : (Nn >= 32 && nt_max >= 32 ? 32 : 16);
     // data gradient of a tiling convolution: one grid layer per parity class
     const bool par = mode == 1 && g.stride == g.ksize && g.pad == 0;
     const int classes = par ? g.stride * g.stride * g.stride : 1;
@@ -3106,6 +3268,20 @@ int fdc_conv3d_forward_fused(const fdc_conv3d *g, const void *xa, int32_t ca, in
     if (upsample_a && (g->in_d % 2 || g->in_h % 2 || g->in_w % 2)) return FDC_ERR_INVALID;
     return rc(fdc::launch_conv_halo(to_args(g), xa, w, bias, y_bf16, y_f32, g->c_in, g->c_out, g->relu ? 1 : 0,
                                     (cudaStream_t)stream, ca, upsample_a ? 1 : 0, xb));
+}
+
+int fdc_conv3d_forward_up(const fdc_conv3d *g, const void *xa, const void *w_up, const float *bias, void *y_bf16,
+                          float *y_f32, void *stream) {
+    if (!conv_ok(g) || !is_k3s1p1(g) || !xa || !w_up || (!y_bf16 && !y_f32)) return FDC_ERR_INVALID;
+    if (g->in_d % 2 || g->in_h % 2 || g->in_w % 2) return FDC_ERR_INVALID;
+    const cudaError_t e = fdc::launch_conv_up(to_args(g), xa, w_up, bias, y_bf16, y_f32, g->relu ? 1 : 0,
+                                              (cudaStream_t)stream);
+    return e == cudaErrorNotSupported ? FDC_ERR_INVALID : rc(e);
+}
+
+int fdc_conv3d_collapse_up_weights(const fdc_conv3d *g, const void *w, void *w_up, void *stream) {
+    if (!conv_ok(g) || !is_k3s1p1(g) || !w || !w_up) return FDC_ERR_INVALID;
+    return rc(fdc::launch_collapse_up(w, w_up, g->c_out, g->c_in, (cudaStream_t)stream));
 }
 
 int fdc_conv3d_backward_data(const fdc_conv3d *g, const void *dy, const void *w_t, const void *relu_mask, void *dx,

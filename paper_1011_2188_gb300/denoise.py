@@ -84,6 +84,21 @@ class ConvLayer:
         _ok(L.fdc_f32_to_bf16(_p(self.w32), _p(self.w16), n, _s()), "f32_to_bf16")
         g, _ = self.geom((1, 8, 8, 8, self.cin))
         _ok(L.fdc_conv3d_transpose_weights(C.byref(g), _p(self.w16), _p(self.wt16), _s()), "transpose")
+        self.collapse_up()
+
+    def enable_up(self):
+        """This layer convolves an upsampled input: keep the collapsed weights
+        of the sub-pixel form (fdc_conv3d_forward_up) next to the others."""
+        import torch
+        self.wup16 = torch.empty((self.cout, 64, self.cin), dtype=torch.bfloat16, device=self.dev)
+        self.up_ok = None  # whether fdc_conv3d_forward_up takes this layer's shape (learned at first call)
+        self.collapse_up()
+
+    def collapse_up(self):
+        if getattr(self, "wup16", None) is not None:
+            g, _ = self.geom((1, 8, 8, 8, self.cin))
+            _ok(fdc.lib().fdc_conv3d_collapse_up_weights(C.byref(g), _p(self.w16), _p(self.wup16), _s()),
+                "collapse up")
 
     def forward(self, x, keep=True):
         import torch
@@ -99,6 +114,28 @@ class ConvLayer:
         if keep:
             self.x, self.y = x, y
         return y
+
+    def forward_up(self, xa, keep=False):
+        """This 3^3 convolution of upsample2(xa): the sub-pixel kernel on xa's
+        grid (collapsed weights, see fdc_conv3d_forward_up) where it takes the
+        shape, else forward_fused; with keep, xa is kept for the gradients of
+        the exact map (backward)."""
+        import torch
+        if self.up_ok is not False:
+            B, D, H, W, ca = xa.shape
+            g, oshape = self.geom((B, 2 * D, 2 * H, 2 * W, self.cin))
+            y = torch.empty(oshape, dtype=torch.bfloat16, device=self.dev)
+            rc = fdc.lib().fdc_conv3d_forward_up(C.byref(g), _p(xa), _p(self.wup16), _p(self.b32), _p(y), None, _s())
+            if rc == 0:
+                self.up_ok = True
+                if keep:
+                    self.x, self.y = None, y
+                    self.fused_in = (xa, True, None, (B, 2 * D, 2 * H, 2 * W, self.cin))
+                return y
+            if rc != 1 or self.up_ok:  # only "no kernel for this shape" falls back
+                _ok(rc, "conv forward up")
+            self.up_ok = False
+        return self.forward_fused(xa, upsample=True, keep=keep)
 
     def forward_fused(self, xa, upsample=False, xb=None, keep=False):
         """This 3^3 convolution applied to [upsample(xa) | xb] without
@@ -241,6 +278,8 @@ class UNet:
         self.channels = channels
         self.t = 0
         self._flatten()
+        for l in (self.up1, self.up2, self.up3):
+            l.enable_up()
 
     def _flatten(self):
         """All layers' FP32 weights and biases, their gradients, Adam moments
@@ -299,7 +338,7 @@ class UNet:
         else:  # inference: upsampling and skip concatenation fused into the convolutions
             f = b
             for up, dec, skip in ((self.up3, self.dec3, e3), (self.up2, self.dec2, e2), (self.up1, self.dec1, e1)):
-                u = up.forward_fused(f, upsample=True)
+                u = up.forward_up(f)
                 f = dec[1].forward(dec[0].forward_fused(u, xb=skip), False)
             f1 = f
         return f1
@@ -334,7 +373,7 @@ class UNet:
 
     def _decoder_train(self, up, dec, f, skip):
         if self._fuse_level(up):  # upsampled and concatenated inputs are never materialised
-            u = up.forward_fused(f, upsample=True, keep=True)
+            u = up.forward_up(f, keep=True)
             h = dec[0].forward_fused(u, xb=skip, keep=True)
         else:
             u = up.forward(_upsample(f), True)
@@ -387,6 +426,8 @@ class UNet:
                         (C.c_void_p * len(ls))(*[l.wt16.data_ptr() for l in ls]))
         g, w, wt = self._tr
         _ok(L.fdc_conv3d_transpose_weights_batch(len(g), g, w, wt, _s()), "transpose")
+        for l in (self.up1, self.up2, self.up3):
+            l.collapse_up()
 
     def state(self):
         return [l.state() for l in self.layers()]

@@ -566,3 +566,73 @@ def test_fused_backward_equals_materialised(ca, cb, up, cout):
     g2, _ = geom((1, D, H, W, cin), 64, 3, 1, 1, 1)
     assert L.fdc_conv3d_backward_data_fused(C.byref(g2), ptr(dyt), ptr(w_t), ptr(xat), ca, up, ptr(xbt), ptr(dxa),
                                             ptr(dxb), None) == 1
+
+
+def _collapse_up(w):
+    """The collapsed weights of the sub-pixel upsampling convolution from
+    their definition (FP64): along each axis, output parity p and coarse
+    offset s in {0, 1} take the taps k with floor((p + k - 1) / 2) = p - 1 + s."""
+    co, ci = w.shape[0], w.shape[-1]
+    sets = {(p, s): [k for k in range(3) if (p + k - 1) // 2 == p - 1 + s] for p in (0, 1) for s in (0, 1)}
+    out = np.zeros((co, 64, ci))
+    for t in range(64):
+        pd, ph, sd, sh, pw, sw = [(t >> b) & 1 for b in (5, 4, 3, 2, 1, 0)]
+        for kd in sets[pd, sd]:
+            for kh in sets[ph, sh]:
+                for kw in sets[pw, sw]:
+                    out[:, t, :] += w[:, kd, kh, kw, :]
+    return out
+
+
+@pytest.mark.parametrize("shape,cout", [((1, 8, 20, 32, 32), 16), ((1, 4, 20, 32, 16), 16),
+                                        ((2, 12, 26, 40, 64), 32), ((1, 64, 48, 60, 32), 16)])
+@pytest.mark.parametrize("relu", [0, 1])
+def test_forward_up_subpixel(shape, cout, relu):
+    """fdc_conv3d_forward_up (the upsampling convolution on the coarse grid
+    by output parity class, 8 collapsed taps per output) against the FP64
+    convolution of the materialised upsample2(xa).  Its one extra rounding is
+    each collapsed weight's (to BF16: relative 2^-8, the unit roundoff of an
+    8-bit significand), so per output |y - ref| <= 2^-8 * sum |w| |x| + the
+    FP32 accumulation term of the other convolution tests; the collapsed
+    weights equal their FP64 definition within that rounding (after the FP32
+    sum: 2^-8 + 2^-22 relative)."""
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    L = fdc.lib()
+    B, D, H, W, ci = shape  # the full-resolution grid
+    rng = np.random.default_rng(sum(shape) + cout + relu)
+    xat, xa = bf16(rng.normal(size=(B, D // 2, H // 2, W // 2, ci)))
+    wt, w = bf16(rng.normal(size=(cout, 3, 3, 3, ci)) / np.sqrt(27 * ci))
+    b = rng.normal(size=cout).astype(np.float32)
+    bt = torch.from_numpy(b).cuda()
+    g, oshape = geom(shape, cout, 3, 1, 1, relu)
+    wup = torch.empty((cout, 64, ci), dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_conv3d_collapse_up_weights(C.byref(g), ptr(wt), ptr(wup), None) == 0
+    y32 = torch.empty(oshape, dtype=torch.float32, device="cuda:0")
+    y16 = torch.empty(oshape, dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_conv3d_forward_up(C.byref(g), ptr(xat), ptr(wup), ptr(bt), ptr(y16), ptr(y32), None) == 0
+    torch.cuda.synchronize()
+    exact = _collapse_up(w)
+    got = wup.double().cpu().numpy()
+    assert np.all(np.abs(got - exact) <= (2.0 ** -8 + 2.0 ** -22) * np.abs(exact))
+    up = ref.upsample2(xa)
+    r = ref.forward(up, w, b.astype(np.float64), relu=bool(relu))
+    bound = 2.0 ** -8 * ref.forward(np.abs(up), np.abs(w), None) + 2e-5 * np.abs(r).max()
+    err = np.abs(y32.cpu().numpy() - r)
+    assert np.all(err <= bound), float((err / bound).max())
+    assert np.all(np.abs(y16.double().cpu().numpy() - r) <= bound + 2.0 ** -8 * np.abs(r))
+
+
+def test_forward_up_refuses_shapes_without_its_kernel():
+    """FDC_ERR_INVALID, nothing launched: a coarse grid narrower than the TMA
+    box (16 w), odd sizes, more than 64 input channels."""
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    L = fdc.lib()
+    x = torch.zeros((1, 8, 16, 32, 128), dtype=torch.bfloat16, device="cuda:0")
+    wup = torch.zeros((16, 64, 128), dtype=torch.bfloat16, device="cuda:0")
+    y = torch.empty((1, 16, 32, 64, 16), dtype=torch.bfloat16, device="cuda:0")
+    for shape in [(1, 6, 20, 30, 16), (1, 7, 20, 32, 16), (1, 16, 32, 64, 128)]:
+        g, _ = geom(shape, 16, 3, 1, 1)
+        assert L.fdc_conv3d_forward_up(C.byref(g), ptr(x), ptr(wup), None, ptr(y), None, None) == 1
+    torch.cuda.synchronize()
