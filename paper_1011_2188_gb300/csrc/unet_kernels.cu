@@ -863,7 +863,7 @@ constexpr int kDwPlaneSliceBytes = 10 * 512;  // [h 10][w-group 2][k-chunk 2][8 
 #define FDC_CONV_TC64 1
 #endif
 #ifndef FDC_KWS_NT
-#define FDC_KWS_NT 0
+#define FDC_KWS_NT 16
 #endif
 // the d-walking kernel's shared memory at its smallest ring (5 planes) fits one CTA
 inline bool dwalk_fits(int S, int NT) {
@@ -1165,6 +1165,7 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     constexpr unsigned kAccCols = NX <= 64 ? 64 : 128;  // columns per accumulator slot
     constexpr int UPP = MODE == 0 ? 1 : 4;         // units per (coarse) output plane
     constexpr int THR = 32 * (EW + 2);
+    constexpr int kMmaWarp = EW + 1;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bars[2 * kDwtMaxRing + 2 * kDwtMaxAcc + 1];
     __shared__ unsigned tmem_slot;
@@ -1284,7 +1285,7 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
                     if (clock64() - t0 > kTcWaitCycles) break;
         }
         __syncwarp();
-    } else if (warp == EW + 1) {  // ---- MMA: output units of each range
+    } else if (warp == kMmaWarp) {  // ---- MMA: output units of each range
         if (lane == 0) {
             constexpr unsigned idesc = umma_idesc(128, NX);
             const unsigned long long bd0 = umma_desc(smem_u32(sW), NX * 16, 128);
@@ -2961,7 +2962,7 @@ cudaError_t launch_s2_tc(const Conv3dArgs &g, const void *src, const void *wt, c
 // widest output-channel tile of the mma.sync forward (its grid is small on
 // coarse levels: narrower tiles give more CTAs)
 #ifndef FDC_IGEMM_FWD_NT
-#define FDC_IGEMM_FWD_NT 64
+#define FDC_IGEMM_FWD_NT 32
 #endif
 
 bool s2_tc_shape(const Conv3dArgs &g, int mode, const float *out_f32) {
