@@ -74,13 +74,24 @@ def parse():
     return ap.parse_args()
 
 
-def load_peaks():
+def load_peaks(key="hbm_gbs", fallback=6800.0):
+    """A measured peak of MEASURED_PEAKS.json (HBM copy GB/s by default; bf16_tflops for the
+    dense BF16 burst), else the profiling recipe's fallback figure."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return float(d.get("hbm_gbs", 6800.0)), "measured"
-    return 6800.0, "fallback"
+        if key in d:
+            return float(d[key]), "measured"
+    return fallback, "fallback"
+
+
+def unet_forward_flops(net, g):
+    """Forward FLOPs of one g^3 sample in the direct form of every convolution
+    (2 * taps * cin * cout per output voxel; the head counted in full)."""
+    out_grid = [g, g, g // 2, g // 2, g // 2, g // 4, g // 4, g // 4, g // 8, g // 8, g // 8,
+                g // 4, g // 4, g // 4, g // 2, g // 2, g // 2, g, g, g, g]  # output grid of each layer
+    return sum(2.0 * l.k ** 3 * l.cin * l.cout * vox ** 3 for l, vox in zip(net.layers(), out_grid))
 
 
 def workload(args, world):
@@ -386,12 +397,8 @@ def denoiser_study(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t
     rows, summary = denoise.evaluate(net, eng, eval_cases, n_low, (0.2, 0.2, 0.2))
-    flops = 0.0  # forward FLOPs of one grid^3 sample: 2 * taps * cin * cout * output voxels per conv
     g = args.grid
-    out_grid = [g, g, g // 2, g // 2, g // 2, g // 4, g // 4, g // 4, g // 8, g // 8, g // 8,
-                g // 4, g // 4, g // 4, g // 2, g // 2, g // 2, g, g, g, g]  # output grid of each layer
-    for l, vox in zip(net.layers(), out_grid):
-        flops += 2.0 * l.k ** 3 * l.cin * l.cout * vox ** 3
+    flops = unet_forward_flops(net, g)
     line = {"study": "denoiser", "grid": g, "train_cases": len(train_cases), "train_phantoms": args.train_cases,
             "eval_cases": args.eval_cases,
             "epochs": args.epochs, "histories_low": n_low, "histories_high": args.high,
@@ -408,46 +415,59 @@ def denoiser_study(args):
 
 
 def unet_timing(args):
-    """Inference and training-step time of the U-Net on one grid^3 sample
-    (a Gaussian dose on a water grid; the weights do not change the cost)."""
+    print(json.dumps({"study": "unet_timing", **unet_times(args.grid, args.steps, args.warmup)}), flush=True)
+
+
+def unet_times(g, steps, warmup):
+    """Inference and training-step time of the U-Net on one g^3 sample (a
+    Gaussian dose on a water grid; the weights do not change the cost), CUDA
+    events; inference also replayed as one CUDA graph.  The tensor-core
+    roofline takes the model's FLOPs (direct form of every convolution) over
+    the graph-replayed inference time against the measured BF16 burst peak."""
     import numpy as np
     import torch
     from paper_1011_2188_gb300 import denoise
-    g = args.grid
     z, y, x = np.meshgrid(*[np.linspace(-1, 1, g)] * 3, indexing="ij")
     dose = torch.from_numpy(np.exp(-(x ** 2 + y ** 2) / 0.1) * (1 + z)).cuda()
     dens = torch.ones((g, g, g), dtype=torch.float32, device="cuda:0")
     s = denoise.Sample(dose, dens, dose)
     net = denoise.UNet(seed=0)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         denoise.denoise(net, s)
         denoise.train_step(net, s, 1e-5)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         denoise.denoise(net, s)
     e1.record()
     e1.synchronize()
-    inf = e0.elapsed_time(e1) / args.steps
+    inf = e0.elapsed_time(e1) / steps
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         denoise.train_step(net, s, 1e-5)
     e1.record()
     e1.synchronize()
-    tr = e0.elapsed_time(e1) / args.steps
+    tr = e0.elapsed_time(e1) / steps
     # the same inference replayed as one CUDA graph (no host launch gaps)
     ig = denoise.InferenceGraph(net, s)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         ig.run()
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         ig.run()
     e1.record()
     e1.synchronize()
-    infg = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"study": "unet_timing", "grid": g, "inference_ms": inf, "inference_graph_ms": infg,
-                      "train_step_ms": tr}), flush=True)
+    infg = e0.elapsed_time(e1) / steps
+    flops = unet_forward_flops(net, g)
+    peak, kind = load_peaks("bf16_tflops", 1900.0)
+    achieved = flops / (infg * 1e-3) / 1e12
+    return {"grid": g, "inference_ms": inf, "inference_graph_ms": infg, "train_step_ms": tr,
+            "forward_gflop": flops / 1e9,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "peak_source": f"{kind} bf16_tflops (burst)",
+                         "count": "model FLOPs of one inference (direct form of every convolution; the "
+                                  "upsampling convolutions compute 8/27 of theirs in sub-pixel form)"}}
 
 
 def precision_case(E, n_total, n_batches=100, n_sub=300_000, local=0):
@@ -863,6 +883,7 @@ def main():
         eng = None
         line["precision_fp32_fp64"] = precision_case(150.0, 100_000_000, local=local)
         line["denoiser"] = denoiser_eval(WEIGHTS, local=local)
+        line["denoiser"]["unet_128"] = unet_times(128, 20, 3)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if eng is not None:

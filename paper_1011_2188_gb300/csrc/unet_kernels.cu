@@ -1099,6 +1099,10 @@ __global__ void __launch_bounds__(THR) conv3_dwalk_kernel(const Conv3dArgs g, co
 // its MMAs.
 constexpr int kDwtMaxRing = 12;
 constexpr int kDwtMaxAcc = 8;   // accumulator slots
+// pair tiles (MODE 2) for inputs made of two 16-channel tensors
+#ifndef FDC_DWT_PAIR
+#define FDC_DWT_PAIR 1
+#endif
 #ifndef FDC_CONV_DWTMA
 #define FDC_CONV_DWTMA 1
 #endif
@@ -1154,16 +1158,39 @@ __device__ __forceinline__ unsigned long long umma_desc_sw32(unsigned saddr, uns
 // 4 NT columns hold the blocks (pw, sw') of the w axis, added in the epilogue
 // like the kw blocks of MODE 0.  Weights: fdc's collapsed layout
 // [c_out][pd ph][sd' sh'][pw sw'][c_in] (conv3_collapse_up_kernel).
+// MODE 2 (inputs made of 16-channel tensors, even w): pair tiles.  Each
+// 64-byte row of a plane holds two neighbouring voxels' 16 channels (one TMA
+// box per tensor: 32 values x 16 voxel pairs x 10 h, 64-byte swizzle), so a
+// box fetches 32 input columns in rows of 64 B instead of 16 columns in rows
+// of 32 B; the MMAs of a (kd, kh) tap read the even (e = 0) and the odd
+// (e = 1) voxel of every pair as two K-major A operands 32 B apart in the
+// swizzle atom, into two accumulators D_e, D_o.  A tile's first output column
+// is w0 = 30 t - 1; it loads columns w0 - 1 .. w0 + 30 and yields w0 ..
+// w0 + 29: pair P (columns w0 - 1 + 2P, w0 + 2P) gives
+//   w0 + 2P     = D_e[P] kw0 + D_o[P] kw1 + D_e[P+1] kw2,
+//   w0 + 2P + 1 = D_o[P] kw0 + D_e[P+1] kw1 + D_o[P+1] kw2.
+// The same with the 64-byte swizzle (rows of 64 B, eight-row groups `sbo`
+// bytes apart; layout 4); a start address 32 B into a row selects its second
+// 16 BF16 as the K slice.
+__device__ __forceinline__ unsigned long long umma_desc_sw64(unsigned saddr, unsigned sbo) {
+    return (unsigned long long)((saddr >> 4) & 0x3fffu) | (1ull << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46) | (4ull << 61);
+}
+
 template <int NT, int EW, int MINB, int MODE>
 __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     conv3_dwtma_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
                        const Conv3dArgs g, const __nv_bfloat16 *wt, const float *bias, __nv_bfloat16 *out_bf16,
                        float *out_f32, int Cs, int Nn, int relu, int ca, int R, int NA) {
-    constexpr int NB = MODE == 0 ? 3 : 4;          // column blocks per unit (kw taps | (pw, sw'))
-    constexpr int NU = MODE == 0 ? 9 : 16;         // weight groups per slice ((kd, kh) | (pd ph, sd' sh'))
+    constexpr int NB = MODE == 1 ? 4 : 3;          // column blocks per unit (kw taps | (pw, sw'))
+    constexpr int NU = MODE == 1 ? 16 : 9;         // weight groups per slice ((kd, kh) | (pd ph, sd' sh'))
     constexpr int NX = NB * NT;                    // MMA N
-    constexpr unsigned kAccCols = NX <= 64 ? 64 : 128;  // columns per accumulator slot
-    constexpr int UPP = MODE == 0 ? 1 : 4;         // units per (coarse) output plane
+    // columns per accumulator slot (MODE 2: D_e and D_o, 64 apart)
+    constexpr unsigned kAccCols = MODE == 2 ? 128 : (NX <= 64 ? 64 : 128);
+    constexpr int UPP = MODE == 1 ? 4 : 1;         // units per (coarse) output plane
+    constexpr int kSlice = MODE == 2 ? 2 * kDwPlaneSliceBytes : kDwPlaneSliceBytes;  // bytes per slice of a plane
+    constexpr int kTileW = MODE == 2 ? 30 : 14;    // output columns per tile
+    static_assert(MODE != 2 || (NT == 16 && EW == 8), "pair tiles: 16-channel output tiles, 8 epilogue warps");
     constexpr int THR = 32 * (EW + 2);
     constexpr int kMmaWarp = EW + 1;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1172,11 +1199,11 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     __shared__ int abort_flag;
     __shared__ float sBias[NT];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // the walked grid: the output grid (MODE 0) or the coarse input grid (MODE 1)
-    const int D = MODE == 0 ? g.in_d : g.in_d / 2, H = MODE == 0 ? g.in_h : g.in_h / 2,
-              W = MODE == 0 ? g.in_w : g.in_w / 2;
+    // the walked grid: the output grid (MODE 0, 2) or the coarse input grid (MODE 1)
+    const int D = MODE != 1 ? g.in_d : g.in_d / 2, H = MODE != 1 ? g.in_h : g.in_h / 2,
+              W = MODE != 1 ? g.in_w : g.in_w / 2;
     const int S = Cs / 16;
-    const unsigned plane_bytes = (unsigned)(S * kDwPlaneSliceBytes);
+    const unsigned plane_bytes = (unsigned)(S * kSlice);
     const int wbytes = S * NU * 2 * NX * 16;
     const unsigned kCols = (unsigned)NA * kAccCols;
     unsigned char *sW = smem;  // [slice][group][k-chunk][block NT + co][8]
@@ -1191,7 +1218,8 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     const unsigned fin = bar0 + 8u * (2u * kDwtMaxRing + 2u * kDwtMaxAcc);
     volatile int *abort_v = &abort_flag;
 
-    const int tiles_w = (W + 13) / 14, tiles_h = (H + 7) / 8;
+    // MODE 2 tiles start 2 columns before their first output (the first tile at w = -1)
+    const int tiles_w = MODE == 2 ? (W + 1 + kTileW - 1) / kTileW : (W + kTileW - 1) / kTileW, tiles_h = (H + 7) / 8;
     const long long n_cols = (long long)g.batch * tiles_h * tiles_w;
     const long long total = n_cols * D;  // (tile column, d) output planes
     const long long q_begin = total * blockIdx.x / gridDim.x, q_end = total * (blockIdx.x + 1) / gridDim.x;
@@ -1218,7 +1246,7 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     if (tid < NT) sBias[tid] = (bias && n0 + tid < Nn) ? bias[n0 + tid] : 0.f;
     {  // resident weights of every input slice (through L1: all CTAs read the same)
         constexpr int kChunks = NU * 2 * NX;  // per slice
-        constexpr int kTaps = MODE == 0 ? 27 : 64;  // weight rows per output channel
+        constexpr int kTaps = MODE == 1 ? 64 : 27;  // weight rows per output channel
         for (int i = tid; i < S * kChunks; i += THR) {
             const int sl = i / kChunks, r = i % kChunks;
             const int n = r % NX, q = r / NX, kc = q & 1, grp = q >> 1;
@@ -1244,7 +1272,7 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
         d_begin = (int)(q % D);
         nd = (int)(q_end - q < (long long)(D - d_begin) ? q_end - q : (long long)(D - d_begin));
         long long t = col;
-        w0 = (int)(t % tiles_w) * 14;
+        w0 = (int)(t % tiles_w) * kTileW - (MODE == 2 ? 1 : 0);  // first output column
         t /= tiles_w;
         h0 = (int)(t % tiles_h) * 8;
         b = (int)(t / tiles_h);
@@ -1269,8 +1297,11 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
                                  : "memory");
                     const int d = d_begin - 1 + j;
                     for (int sl = 0; sl < S; ++sl) {
-                        const unsigned dst = sP + (unsigned)s * plane_bytes + (unsigned)(sl * kDwPlaneSliceBytes);
-                        if (sl * 16 < ca)
+                        const unsigned dst = sP + (unsigned)s * plane_bytes + (unsigned)(sl * kSlice);
+                        if (MODE == 2)  // one 16-channel tensor per slice, columns w0 - 1 .. w0 + 30 as 16 pairs
+                            tma_load_5d(dst, sl == 0 ? (const void *)&tm_a : (const void *)&tm_b, 0, (w0 - 1) / 2,
+                                        h0 - 1, d, b, full(s));
+                        else if (sl * 16 < ca)
                             tma_load_5d(dst, &tm_a, sl * 16, w0 - 1, h0 - 1, d, b, full(s));
                         else
                             tma_load_5d(dst, &tm_b, sl * 16 - ca, w0 - 1, h0 - 1, d, b, full(s));
@@ -1303,8 +1334,10 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
                     if (!ok) break;
                     unsigned long long ad_kd[3];
 #pragma unroll
-                    for (int kd = 0; kd < 3; ++kd)
-                        ad_kd[kd] = umma_desc_sw32(sP + ((p + (unsigned)(i + kd)) % (unsigned)R) * plane_bytes, 256);
+                    for (int kd = 0; kd < 3; ++kd) {
+                        const unsigned a = sP + ((p + (unsigned)(i + kd)) % (unsigned)R) * plane_bytes;
+                        ad_kd[kd] = MODE == 2 ? umma_desc_sw64(a, 512) : umma_desc_sw32(a, 256);
+                    }
                     for (int u = 0; u < UPP; ++u, ++it) {
                         const unsigned ab = it % (unsigned)NA;
                         if (it >= (unsigned)NA && !role_wait(acce(ab), (it / (unsigned)NA - 1u) & 1u, abort_v)) {
@@ -1314,7 +1347,23 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
                         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll 1
                         for (int sl = 0; sl < S; ++sl) {
-                            if constexpr (MODE == 0) {
+                            if constexpr (MODE == 2) {
+                                // tap (kd, kh): the even and the odd voxel of every pair (rows of
+                                // 64 B, 16 pairs per h row: kh shifts by 1 KB, e by 32 B)
+#pragma unroll
+                                for (int kdh = 0; kdh < 9; ++kdh) {
+                                    const unsigned long long bd =
+                                        bd0 + (unsigned long long)(((sl * NU + kdh) * 2 * NX * 16) >> 4);
+#pragma unroll
+                                    for (int e = 0; e < 2; ++e) {
+                                        const unsigned long long ad =
+                                            ad_kd[kdh / 3] +
+                                            (unsigned long long)((sl * kSlice + (kdh % 3) * 1024 + e * 32) >> 4);
+                                        umma_bf16(tmem + ab * kAccCols + (unsigned)(e * 64), ad, bd, idesc,
+                                                  (sl | kdh) != 0);
+                                    }
+                                }
+                            } else if constexpr (MODE == 0) {
 #pragma unroll
                                 for (int kdh = 0; kdh < 9; ++kdh) {
                                     const unsigned long long ad =
@@ -1369,7 +1418,7 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
             range_at(q, d_begin, nd, w0, h0, b);
             q += nd;
             const int hl = h0 + (m >> 4), wl = m & 15, wc = w0 + wl;
-            const bool out_in = wl < 14 && hl < H && wc < W;
+            const bool out_in = wl < 14 && hl < H && wc < W;  // MODE 0, 1
             for (int i = 0; i < nd && ok; ++i) {
                 for (int u = 0; u < UPP; ++u, ++it) {
                     const unsigned ab = it % (unsigned)NA;
@@ -1381,7 +1430,36 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     const unsigned base = tmem + ((unsigned)(quad * 32) << 16) + ab * kAccCols;
                     const int n = n0 + c;
-                    if constexpr (MODE == 0) {
+                    if constexpr (MODE == 2) {
+                        float e0[CW], e1[CW], e2[CW], o0[CW], o1[CW], o2[CW];
+                        tmem_ld8x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c), e0,
+                                   e1, e2);
+                        tmem_ld8x3(base + 64u + (unsigned)c, base + 64u + (unsigned)(NT + c),
+                                   base + 64u + (unsigned)(2 * NT + c), o0, o1, o2);
+                        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0)
+                            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(acce(ab)) : "memory");
+                        // pair P = m & 15 gives columns w0 + 2P and w0 + 2P + 1 (w0: first output)
+#pragma unroll
+                        for (int j = 0; j < CW; ++j) {
+                            const float ne2 = __shfl_down_sync(0xffffffffu, e2[j], 1);
+                            const float ne1 = __shfl_down_sync(0xffffffffu, e1[j], 1);
+                            const float no2 = __shfl_down_sync(0xffffffffu, o2[j], 1);
+                            e0[j] = e0[j] + o1[j] + ne2;
+                            o0[j] = o0[j] + ne1 + no2;
+                        }
+                        const int wa = w0 + 2 * wl;
+                        if (wl < 15 && hl < H && n < Nn) {
+                            const long long v = (((long long)b * D + d_begin + i) * H + hl) * W + wa;
+                            if (wa >= 0 && wa < W)
+                                dwalk_store<CW>(g, e0, bias ? sBias + c : nullptr, relu, out_bf16, out_f32, Nn, n, b,
+                                                d_begin + i, hl, wa, v);
+                            if (wa + 1 < W)
+                                dwalk_store<CW>(g, o0, bias ? sBias + c : nullptr, relu, out_bf16, out_f32, Nn, n, b,
+                                                d_begin + i, hl, wa + 1, v + 1);
+                        }
+                    } else if constexpr (MODE == 0) {
                         float a0[CW], a1[CW], a2[CW];
                         if constexpr (CW == 16)
                             tmem_ld16x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c),
@@ -2714,6 +2792,21 @@ bool make_plane_map(CUtensorMap *m, const void *base, int C, int B, int D, int H
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 5-D tensor map of a 16-channel channels-last BF16 activation read as pairs
+// of neighbouring voxels (W even): 32 values x W/2 pairs x H x D x batch,
+// boxes of 16 pairs x 10 h with the 64-byte swizzle; false when it cannot be made.
+bool make_pair_map(CUtensorMap *m, const void *base, int B, int D, int H, int W) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || !base || ((uintptr_t)base & 15u) || W % 2 || W < 32 || H < 10) return false;
+    const cuuint64_t dims[5] = {32, (cuuint64_t)W / 2, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B};
+    const cuuint64_t strides[4] = {64, 64 * dims[1], 64 * dims[1] * dims[2], 64 * dims[1] * dims[2] * dims[3]};
+    const cuuint32_t box[5] = {32, 16, 10, 1, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // The TMA d-walking kernel.  MODE 0: an input read as stored (no upsampling;
 // the split of a two-part input on a 16-channel boundary).  MODE 1: the
 // sub-pixel form of the convolution of upsample2(src), src on the coarse grid
@@ -2728,11 +2821,17 @@ cudaError_t launch_dwtma(int mode, const Conv3dArgs &g, const __nv_bfloat16 *src
     // the walked (input) grid
     const int D = mode ? g.in_d / 2 : g.in_d, H = mode ? g.in_h / 2 : g.in_h, W = mode ? g.in_w / 2 : g.in_w;
     CUtensorMap tm_a, tm_b;
-    if (!make_plane_map(&tm_a, src, ca, g.batch, D, H, W)) return cudaErrorNotSupported;
-    if (ca < Cs) {
-        if (!make_plane_map(&tm_b, src_b, Cs - ca, g.batch, D, H, W)) return cudaErrorNotSupported;
-    } else {
+    // pair tiles when the input is two 16-channel tensors and w is even (measured at 128^3:
+    // [16 | 16] -> 16 94 vs 118 us; for one 16-channel tensor the two CTAs per SM that their
+    // accumulators leave were slower than four with plain tiles, 66 vs 62 us)
+    if (mode == 0 && FDC_DWT_PAIR && ca == 16 && Cs == 32 && make_pair_map(&tm_a, src, g.batch, D, H, W) &&
+        make_pair_map(&tm_b, src_b, g.batch, D, H, W))
+        mode = 2;
+    if (mode != 2 && !make_plane_map(&tm_a, src, ca, g.batch, D, H, W)) return cudaErrorNotSupported;
+    if (ca == Cs) {
         tm_b = tm_a;
+    } else if (mode != 2 && !make_plane_map(&tm_b, src_b, Cs - ca, g.batch, D, H, W)) {
+        return cudaErrorNotSupported;
     }
     int dev = 0, sms = 0, smem_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -2741,29 +2840,36 @@ cudaError_t launch_dwtma(int mode, const Conv3dArgs &g, const __nv_bfloat16 *src
     if (e != cudaSuccess) return e;
     const int S = Cs / 16;
     const int NT = (mode == 0 && Nn % 32 == 0) ? 32 : 16;
-    const int NX = (mode == 0 ? 3 : 4) * NT, NU = mode == 0 ? 9 : 16;
+    const int NX = (mode == 1 ? 4 : 3) * NT, NU = mode == 1 ? 16 : 9;
     const int wbytes = S * NU * 2 * NX * 16;
-    const int plane = S * kDwPlaneSliceBytes;
+    const int plane = S * kDwPlaneSliceBytes * (mode == 2 ? 2 : 1);
     // CTAs per SM: at most what TMEM allows (accumulator slots of 64 or 128 of
     // the 512 columns: two per CTA in MODE 0, one coarse plane's four units
     // in MODE 1), fewer when the ring would hold less than 5 planes (three in
     // use, two in flight) or, in MODE 1, 4; one CTA per SM takes a ring of 4
-    int per_sm = mode == 1 ? 2 : (NT == 32 ? 2 : 4), R = 0;
-    const int r_min = mode == 1 ? 4 : 5;
+    int per_sm = mode != 0 ? 2 : (NT == 32 ? 2 : 4), R = 0;
+    const int r_min = mode != 0 ? 4 : 5;
     for (; per_sm > 1; --per_sm) {
         R = std::min(kDwtMaxRing, (smem_sm / per_sm - 3072 - wbytes - 1024) / plane);
         if (R >= r_min) break;
     }
     if (per_sm == 1) R = std::min(kDwtMaxRing, (smem_sm - 3072 - wbytes - 1024) / plane);
     if (R < 4) return cudaErrorNotSupported;
-    const int NA = mode == 0 ? 2 : (per_sm == 2 ? 4 : 8);
+    const int NA = mode != 1 ? 2 : (per_sm == 2 ? 4 : 8);
     const int smem = wbytes + 1024 + R * plane;
     const int ntiles = (Nn + NT - 1) / NT;
-    const long long planes = (long long)g.batch * ((H + 7) / 8) * ((W + 13) / 14) * D;
+    const long long planes =
+        (long long)g.batch * ((H + 7) / 8) * (mode == 2 ? (W + 30) / 30 : (W + 13) / 14) * D;
     long long gx = std::max(1ll, (long long)sms * per_sm / ntiles);
     if (gx > planes) gx = planes;
     const dim3 grid((unsigned)gx, (unsigned)ntiles);
-    if (mode == 1) {
+    if (mode == 2) {
+        static OccCache cache;
+        e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 8, 2, 2>, smem);
+        if (e != cudaSuccess) return e;
+        conv3_dwtma_kernel<16, 8, 2, 2><<<grid, 320, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
+                                                                  relu, ca, R, NA);
+    } else if (mode == 1) {
         static OccCache cache;
         e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 8, 2, 1>, smem);
         if (e != cudaSuccess) return e;

@@ -71,6 +71,10 @@ CASES = [
     ((1, 64, 40, 30, 32), 32, 3, 1, 1),
     ((2, 40, 19, 33, 32), 16, 3, 1, 1),
     ((1, 9, 23, 45, 64), 32, 3, 1, 1),
+    # one 16-channel tensor, even w >= 32: ragged last tile, two 16-channel
+    # output tiles, batch 2 at the smallest width
+    ((1, 12, 21, 70, 16), 32, 3, 1, 1),
+    ((2, 7, 10, 32, 16), 16, 3, 1, 1),
 ]
 
 
@@ -449,7 +453,8 @@ def test_unet_forward_backward_and_training_reduces_loss():
 
 @pytest.mark.parametrize("ca,cb,up,dims", [(32, 0, 1, (6, 8, 10)), (16, 16, 0, (6, 8, 10)), (64, 64, 0, (6, 8, 10)),
                                            (32, 32, 1, (6, 8, 10)), (16, 16, 0, (5, 12, 20)),
-                                           (32, 32, 0, (7, 10, 34)), (32, 16, 0, (4, 11, 16))])
+                                           (32, 32, 0, (7, 10, 34)), (32, 16, 0, (4, 11, 16)),
+                                           (16, 16, 0, (6, 12, 36)), (16, 16, 0, (96, 40, 62))])
 def test_fused_upsample_concat_forward(ca, cb, up, dims):
     """fdc_conv3d_forward_fused equals fdc_conv3d_forward on the materialised
     [upsample(xa) | xb] input (the larger grids take the two tensor maps of
@@ -514,8 +519,10 @@ def test_inference_graph_replays_the_same_dose():
         assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("ca,cb,up,cout", [(32, 0, 1, 16), (16, 16, 0, 16), (32, 32, 0, 32), (64, 0, 1, 32)])
-def test_fused_backward_equals_materialised(ca, cb, up, cout):
+@pytest.mark.parametrize("ca,cb,up,cout,dims", [(32, 0, 1, 16, (6, 10, 18)), (16, 16, 0, 16, (6, 10, 18)),
+                                                (32, 32, 0, 32, (6, 10, 18)), (64, 0, 1, 32, (6, 10, 18)),
+                                                (16, 16, 0, 16, (6, 10, 34)), (32, 0, 1, 16, (4, 12, 64))])
+def test_fused_backward_equals_materialised(ca, cb, up, cout, dims):
     """The gradients of the fused forward (input [upsample?(xa) | xb] never
     materialised): the data gradient with the ReLU mask of that input, split
     by channel, equals fdc_conv3d_backward_data on the materialised input bit
@@ -524,8 +531,8 @@ def test_fused_backward_equals_materialised(ca, cb, up, cout):
     import torch
     from paper_1011_2188_gb300 import fdc
     L = fdc.lib()
-    rng = np.random.default_rng(ca + 3 * cb + up + cout)
-    D, H, W = 6, 10, 18
+    rng = np.random.default_rng(ca + 3 * cb + up + cout + sum(dims))
+    D, H, W = dims
     sa = (1, D // 2, H // 2, W // 2, ca) if up else (1, D, H, W, ca)
     xat, _ = bf16(np.maximum(rng.normal(size=sa), 0) * (rng.random(sa) < 0.8))  # ReLU outputs with zeros
     xbt = bf16(np.maximum(rng.normal(size=(1, D, H, W, cb)), 0))[0] if cb else None
