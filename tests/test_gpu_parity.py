@@ -375,6 +375,36 @@ def test_autotune_picks_a_valid_schedule_and_results_do_not_change():
     eng.close()
 
 
+def test_autotune_for_shared_tracks_is_never_slower_than_the_default():
+    """fdc_autotune with the run's own options (32 histories per track, the
+    benchmark's scheme) on a thorax case: the schedule it picks replays no
+    slower than the default (5 % allowance for timing noise; replay kernel
+    time from CUDA events, median of five launches after one warm-up) and
+    gives the same tally bit for bit."""
+    import torch
+    db = synth.water_database(synth.database_energies(24), 4000, seed=2)
+    ph = synth.thorax_phantom(seed=7)
+    n = 2_000_000
+    beam = synth.field_beam(n, energy=150.0, width=10.0, height=10.0, sigma_e_rel=0.01)
+    eng = engine(db, ph)
+    eng.set_timing(True)
+    tally = torch.empty(ph.shape[::-1], dtype=torch.int64, device="cuda:0")
+
+    def timed(schedule):
+        ms = []
+        for _ in range(6):
+            eng.run_ex(beam, 0, 11, track_group=32, schedule=schedule, tally=tally)
+            ms.append(eng.last_kernel_ms()[0])
+        return float(np.median(ms[1:])), tally.cpu().numpy().copy()
+
+    t_def, a = timed(None)
+    sched = eng.autotune(beam, n, 11, track_group=32)
+    t_tun, b = timed(sched)
+    assert np.array_equal(a, b)
+    assert t_tun <= 1.05 * t_def, (t_tun, t_def, sched)
+    eng.close()
+
+
 @pytest.fixture(scope="module")
 def thorax_full():
     """The benchmark's workload at full size: 24 x 10^5-track database
