@@ -150,6 +150,21 @@ int fdc_add_bf16(const void *a, const void *b, void *out, int64_t n, void *strea
 int fdc_unet_prepare(const double *dose, const float *density, const double *dose_high, int64_t n,
                      double dose_scale, float density_scale, void *x, float *dose_in, float *target,
                      void *stream);
+/* The same steps with the dose scale in device memory, so that a whole
+ * denoising pass (scale, input, network, head) can be captured in one CUDA
+ * graph without a device-to-host read of the scale:
+ *   fdc_unet_dose_scale: *scale (FP64, device) = max of dose[n] (dose values are
+ *     non-negative; 0 when all are 0);
+ *   fdc_unet_prepare_dev: fdc_unet_prepare without the training target, the
+ *     scale read from *scale on the device (a scale <= 0 counts as 1);
+ *   fdc_unet_head_dev: fdc_unet_head's dose_out with the scale read likewise.
+ * The results equal those of the host-scale calls given the same scale.
+ * FDC_ERR_INVALID on NULL pointers, n < 1, c != 16 or misaligned x. */
+int fdc_unet_dose_scale(const double *dose, int64_t n, double *scale, void *stream);
+int fdc_unet_prepare_dev(const double *dose, const float *density, int64_t n, const double *scale,
+                         float density_scale, void *x, float *dose_in, void *stream);
+int fdc_unet_head_dev(const void *x, int32_t c, const void *w, const float *b, int64_t n, const float *dose_in,
+                      const double *scale, double *dose_out, void *stream);
 /* Training augmentation by a lateral symmetry of a field along +z (the
  * physics is unchanged by mirroring x or y or exchanging them, so a transformed
  * pair is another valid low/high-history pair): for every voxel of the d x h x w

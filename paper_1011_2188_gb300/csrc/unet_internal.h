@@ -52,13 +52,15 @@ cudaError_t launch_adam(float *p, const float *g, float *m, float *v, void *p_bf
                         float b2, float eps, float bc1, float bc2, cudaStream_t st);
 cudaError_t launch_f32_to_bf16(const float *x, void *y, long long n, cudaStream_t st);
 cudaError_t launch_add_bf16(const void *a, const void *b, void *out, long long n, cudaStream_t st);
+// scale_dev (may be null): the dose scale read on the device instead of inv_scale / scale
 cudaError_t launch_prepare(const double *dose, const float *density, const double *dose_high, long long n,
                            double inv_scale, float density_scale, void *x, float *dose_in, float *target,
-                           cudaStream_t st);
+                           cudaStream_t st, const double *scale_dev);
+cudaError_t launch_dose_scale(const double *dose, long long n, double *scale, cudaStream_t st);
 cudaError_t launch_finish(const float *head, const float *dose_in, long long n, double scale, double *dose_out,
                           cudaStream_t st);
 cudaError_t launch_head(const void *x, const void *w, const float *b, long long n, const float *dose_in,
-                        double scale, float *y, double *dose_out, cudaStream_t st);
+                        double scale, float *y, double *dose_out, cudaStream_t st, const double *scale_dev);
 cudaError_t launch_head_loss(const void *x, const void *w, const float *b, const float *target, long long n,
                              float *loss, void *dx, float *dw, float *db, cudaStream_t st);
 cudaError_t launch_gamma(const double *ref, const double *eval, int D, int H, int W, double sd, double sh, double sw,

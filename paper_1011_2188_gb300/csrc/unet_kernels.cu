@@ -2511,7 +2511,9 @@ __global__ void add_bf16_kernel(const __nv_bfloat16 *a, const __nv_bfloat16 *b, 
 // predicts the correction to its input).
 __global__ void prepare_kernel(const double *dose, const float *density, const double *dose_high, long long n,
                                double inv_scale, float density_scale, __nv_bfloat16 *x, float *dose_in,
-                               float *target) {
+                               float *target, const double *scale_dev) {
+    // scale_dev: the dose scale in device memory (a non-positive scale counts as 1)
+    if (scale_dev) inv_scale = 1.0 / (*scale_dev > 0.0 ? *scale_dev : 1.0);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float d = (float)(dose[i] * inv_scale);
         dose_in[i] = d;
@@ -2582,7 +2584,8 @@ __device__ __forceinline__ float head_dot(const float w[16], const float f[16], 
 // max(0, (y + dose_in) * scale).
 __global__ void head_kernel(const __nv_bfloat16 *__restrict__ x, const __nv_bfloat16 *__restrict__ w,
                             const float *__restrict__ b, long long n, const float *__restrict__ dose_in, double scale,
-                            float *__restrict__ y, double *__restrict__ dose_out) {
+                            float *__restrict__ y, double *__restrict__ dose_out, const double *scale_dev) {
+    if (scale_dev) scale = *scale_dev > 0.0 ? *scale_dev : 1.0;
     float wf[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) wf[c] = __bfloat162float(w[c]);
@@ -3262,9 +3265,20 @@ cudaError_t launch_add_bf16(const void *a, const void *b, void *out, long long n
 
 cudaError_t launch_prepare(const double *dose, const float *density, const double *dose_high, long long n,
                            double inv_scale, float density_scale, void *x, float *dose_in, float *target,
-                           cudaStream_t st) {
+                           cudaStream_t st, const double *scale_dev) {
     prepare_kernel<<<grid_for(n), 256, 0, st>>>(dose, density, dose_high, n, inv_scale, density_scale,
-                                                (__nv_bfloat16 *)x, dose_in, target);
+                                                (__nv_bfloat16 *)x, dose_in, target, scale_dev);
+    return cudaGetLastError();
+}
+
+// The dose scale on the device: max(dose) into *scale (FP64 bits, atomic max
+// of non-negative values; 0 when every voxel is 0).
+cudaError_t launch_dose_scale(const double *dose, long long n, double *scale, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(scale, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    long long blocks = (n + 1023) / 1024;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    max_kernel<<<(int)blocks, 256, 0, st>>>(dose, n, (unsigned long long *)scale);
     return cudaGetLastError();
 }
 
@@ -3282,9 +3296,9 @@ cudaError_t launch_finish(const float *head, const float *dose_in, long long n, 
 }
 
 cudaError_t launch_head(const void *x, const void *w, const float *b, long long n, const float *dose_in,
-                        double scale, float *y, double *dose_out, cudaStream_t st) {
+                        double scale, float *y, double *dose_out, cudaStream_t st, const double *scale_dev) {
     head_kernel<<<grid_for(n), 256, 0, st>>>((const __nv_bfloat16 *)x, (const __nv_bfloat16 *)w, b, n, dose_in, scale,
-                                             y, dose_out);
+                                             y, dose_out, scale_dev);
     return cudaGetLastError();
 }
 
@@ -3533,7 +3547,19 @@ int fdc_unet_prepare(const double *dose, const float *density, const double *dos
         ((uintptr_t)x & 15))
         return FDC_ERR_INVALID;
     return rc(fdc::launch_prepare(dose, density, dose_high, n, 1.0 / dose_scale, density_scale, x, dose_in,
-                                  target, (cudaStream_t)stream));
+                                  target, (cudaStream_t)stream, nullptr));
+}
+
+int fdc_unet_dose_scale(const double *dose, int64_t n, double *scale, void *stream) {
+    if (!dose || !scale || n < 1) return FDC_ERR_INVALID;
+    return rc(fdc::launch_dose_scale(dose, n, scale, (cudaStream_t)stream));
+}
+
+int fdc_unet_prepare_dev(const double *dose, const float *density, int64_t n, const double *scale,
+                         float density_scale, void *x, float *dose_in, void *stream) {
+    if (!dose || !density || !scale || !x || !dose_in || n < 1 || ((uintptr_t)x & 15)) return FDC_ERR_INVALID;
+    return rc(fdc::launch_prepare(dose, density, nullptr, n, 1.0, density_scale, x, dose_in, nullptr,
+                                  (cudaStream_t)stream, scale));
 }
 
 int fdc_unet_dihedral(const void *x, const float *target, int32_t d, int32_t h, int32_t w, int32_t code,
@@ -3562,7 +3588,14 @@ int fdc_unet_head(const void *x, int32_t c, const void *w, const float *b, int64
     if (!x || !w || !b || c != 16 || n < 1 || (!y && !dose_out) || (dose_out && (!dose_in || !(dose_scale > 0))) ||
         ((uintptr_t)x & 15))
         return FDC_ERR_INVALID;
-    return rc(fdc::launch_head(x, w, b, n, dose_in, dose_scale, y, dose_out, (cudaStream_t)stream));
+    return rc(fdc::launch_head(x, w, b, n, dose_in, dose_scale, y, dose_out, (cudaStream_t)stream, nullptr));
+}
+
+int fdc_unet_head_dev(const void *x, int32_t c, const void *w, const float *b, int64_t n, const float *dose_in,
+                      const double *scale, double *dose_out, void *stream) {
+    if (!x || !w || !b || c != 16 || n < 1 || !dose_in || !scale || !dose_out || ((uintptr_t)x & 15))
+        return FDC_ERR_INVALID;
+    return rc(fdc::launch_head(x, w, b, n, dose_in, 1.0, nullptr, dose_out, (cudaStream_t)stream, scale));
 }
 
 int fdc_unet_head_loss(const void *x, int32_t c, const void *w, const float *b, const float *target, int64_t n,

@@ -542,6 +542,61 @@ class InferenceGraph:
         return self.out
 
 
+class DenoisedPath:
+    """The denoised path on fixed device buffers: the engine's low-history
+    run writes its dose into `dose`, then one CUDA graph computes the dose
+    scale on the device (fdc_unet_dose_scale), the network input, the network
+    and the head's denoised dose (no host read of the scale, no launch from
+    the host between them).  Same result as denoise(net, Sample(dose,
+    density)).  `density` is copied in by set_density (e.g. per phantom)."""
+
+    def __init__(self, net, shape, density_scale=0.5, device="cuda:0"):
+        import torch
+        self.net, self.shape, self.density_scale = net, tuple(shape), density_scale
+        n = int(np.prod(shape))
+        self.n = n
+        self.dose = torch.zeros(self.shape, dtype=torch.float64, device=device)
+        self.density = torch.ones(self.shape, dtype=torch.float32, device=device)
+        self.scale = torch.zeros(1, dtype=torch.float64, device=device)
+        self.x = torch.empty((1,) + self.shape + (16,), dtype=torch.bfloat16, device=device)
+        self.dose_in = torch.empty(self.shape, dtype=torch.float32, device=device)
+        self._graph = None
+
+    def set_density(self, density):
+        self.density.copy_(density)
+
+    def _pass(self):
+        import torch
+        L = fdc.lib()
+        _ok(L.fdc_unet_dose_scale(_p(self.dose), self.n, _p(self.scale), _s()), "dose scale")
+        _ok(L.fdc_unet_prepare_dev(_p(self.dose), _p(self.density), self.n, _p(self.scale), self.density_scale,
+                                   _p(self.x), _p(self.dose_in), _s()), "prepare")
+        f1 = self.net.features(self.x, keep=False)
+        out = torch.empty(self.shape, dtype=torch.float64, device=f1.device)
+        _ok(L.fdc_unet_head_dev(_p(f1), f1.shape[-1], _p(self.net.head.w16), _p(self.net.head.b32), self.n,
+                                _p(self.dose_in), _p(self.scale), _p(out), _s()), "head")
+        return out
+
+    def denoise(self):
+        """Denoised dose (Gy, FP64 on the device) of the dose now in `dose`;
+        the graph is captured at the first call (after one pass outside it)."""
+        import torch
+        if self._graph is None:
+            self._pass()
+            torch.cuda.synchronize()
+            self._graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self._graph):
+                self.out = self._pass()
+        self._graph.replay()
+        return self.out
+
+    def run(self, eng, beam, seed, stream=None):
+        """Low-history run of `beam` (engine with the case's phantom loaded)
+        into `dose`, then the denoising graph; returns the denoised dose."""
+        eng.run_ex(beam, 0, seed, dose=self.dose, stream=stream)
+        return self.denoise()
+
+
 def gamma_pass_rate(ref, ev, spacing, dose_frac=0.02, dta=0.2, threshold=0.1, gamma_out=None):
     """Gamma pass rate (fraction of voxels above threshold * max(ref) with
     gamma <= 1) of an evaluated dose against a reference (FP64 device grids
@@ -664,29 +719,35 @@ def evaluate(net, eng, cases, n_low, spacing, dose_frac=0.02, dta=0.2, threshold
     """Per held-out case: gamma pass rate (dose_frac / dta) against the
     high-history plain dose of the denoised low-history dose and of the raw
     low-history dose; device time of the denoised path (low-history run +
-    network) and of the plain method run to ``target_sigma`` mean batch
-    uncertainty (eq. (1), voxels above half the maximum).  With host_timing,
-    also the host wall time of both from the beam in host memory to the dose
-    in (pinned) host memory, copies included: the denoised path as a run,
-    the network and one dose download; the plain method as one
-    fdc_run_host call of the history count it needs for target_sigma."""
+    network, as DenoisedPath runs it: the run, then one CUDA graph from the
+    dose scale to the denoised dose; timed after a warm pass) and of the
+    plain method run to ``target_sigma`` mean batch uncertainty (eq. (1),
+    voxels above half the maximum).  With host_timing, also the host wall
+    time of both from the beam in host memory to the dose in (pinned) host
+    memory, copies included: the denoised path as that run, graph and one
+    dose download; the plain method as one fdc_run_host call of the history
+    count it needs for target_sigma."""
     import time
     import torch
     from .measure import time_to_sigma
     rows = []
+    path = None
     for c in cases:
         eng.load_phantom(c.phantom)
         shape = c.phantom.shape[::-1]
+        if path is None or path.shape != tuple(shape):
+            path = DenoisedPath(net, shape, device=c.density.device)
+        path.set_density(c.density)
         # denoised path, timed from the start of the low-history run to the dose
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        eng.run(c.beam_low, 0, 7 + c.seed)  # warm
+        path.run(eng, c.beam_low, 7 + c.seed)  # warm (the first case also captures the graph)
         e0.record()
-        low = eng.run(c.beam_low, 0, 7 + c.seed)
-        s = Sample(low, c.density)
-        out = denoise(net, s)
+        out = path.run(eng, c.beam_low, 7 + c.seed)
         e1.record()
         e1.synchronize()
         t_den = e0.elapsed_time(e1) * 1e-3
+        low = path.dose.clone()
+        out = out.clone()
         g_den = gamma_pass_rate(c.high, out, spacing, dose_frac, dta, threshold)
         g_raw = gamma_pass_rate(c.high, low, spacing, dose_frac, dta, threshold)
         plain = time_to_sigma(eng, case_beam(c.seed, 100_000_000), shape, 11 + c.seed, target_sigma)
@@ -705,9 +766,7 @@ def evaluate(net, eng, cases, n_low, spacing, dose_frac=0.02, dta=0.2, threshold
             for rep in range(3):
                 torch.cuda.synchronize()
                 t = time.perf_counter()
-                low = eng.run(c.beam_low, 0, 17 + c.seed + rep)
-                out = denoise(net, Sample(low, c.density))
-                host.copy_(out)
+                host.copy_(path.run(eng, c.beam_low, 17 + c.seed + rep))
                 torch.cuda.synchronize()
                 walls.append(time.perf_counter() - t)
             row["wall_seconds_denoised"] = min(walls[1:])

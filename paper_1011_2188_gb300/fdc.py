@@ -63,6 +63,9 @@ SIGNATURES = {
     "fdc_add_bf16": (C.c_int, [_p, _p, _p, C.c_int64, _p]),
     "fdc_unet_prepare": (C.c_int, [_p, _p, _p, C.c_int64, C.c_double, C.c_float, _p, _p, _p, _p]),
     "fdc_unet_finish": (C.c_int, [_p, _p, C.c_int64, C.c_double, _p, _p]),
+    "fdc_unet_dose_scale": (C.c_int, [_p, C.c_int64, _p, _p]),
+    "fdc_unet_prepare_dev": (C.c_int, [_p, _p, C.c_int64, _p, C.c_float, _p, _p, _p]),
+    "fdc_unet_head_dev": (C.c_int, [_p, C.c_int32, _p, _p, C.c_int64, _p, _p, _p, _p]),
     "fdc_unet_head": (C.c_int, [_p, C.c_int32, _p, _p, C.c_int64, _p, C.c_double, _p, _p, _p]),
     "fdc_unet_head_loss": (C.c_int, [_p, C.c_int32, _p, _p, _p, C.c_int64, _p, _p, _p, _p, _p]),
     "fdc_unet_status": (C.c_int, [C.c_int32]),

@@ -519,6 +519,35 @@ def test_inference_graph_replays_the_same_dose():
         assert torch.equal(a, b)
 
 
+def test_denoised_path_graph_equals_denoise():
+    """DenoisedPath (dose scale on the device, one CUDA graph from the scale to
+    the denoised dose) gives denoise(net, Sample(dose, density)) bit for bit,
+    for several doses refilled in place (different scales), and the
+    device-scale calls refuse bad arguments."""
+    import torch
+    from paper_1011_2188_gb300 import denoise, fdc
+    rng = np.random.default_rng(17)
+    n = 32
+    net = denoise.UNet(seed=4)
+    path = denoise.DenoisedPath(net, (n, n, n))
+    dens = torch.from_numpy(rng.uniform(0.2, 1.9, (n, n, n)).astype(np.float32)).cuda()
+    path.set_density(dens)
+    for k in range(3):
+        dose = torch.from_numpy(rng.random((n, n, n)) * 10.0 ** (k - 1)).cuda()
+        path.dose.copy_(dose)
+        a = path.denoise().clone()
+        b = denoise.denoise(net, denoise.Sample(dose, dens))
+        torch.cuda.synchronize()
+        assert float(path.scale) == float(dose.max())
+        assert torch.equal(a, b)
+    L = fdc.lib()
+    assert L.fdc_unet_dose_scale(None, 8, ptr(path.scale), None) == 1
+    assert L.fdc_unet_prepare_dev(ptr(path.dose), ptr(dens), n ** 3, None, 0.5, ptr(path.x), ptr(path.dose_in),
+                                  None) == 1
+    assert L.fdc_unet_head_dev(ptr(path.x), 8, ptr(net.head.w16), ptr(net.head.b32), n ** 3, ptr(path.dose_in),
+                               ptr(path.scale), ptr(path.dose), None) == 1
+
+
 @pytest.mark.parametrize("ca,cb,up,cout,dims", [(32, 0, 1, 16, (6, 10, 18)), (16, 16, 0, 16, (6, 10, 18)),
                                                 (32, 32, 0, 32, (6, 10, 18)), (64, 0, 1, 32, (6, 10, 18)),
                                                 (16, 16, 0, 16, (6, 10, 34)), (32, 0, 1, 16, (4, 12, 64))])
