@@ -82,6 +82,7 @@ struct fdc_ctx {
     long long nvox = 0;
     DevBuf<float2> vox;
     DevBuf<float> density;
+    DevBuf<double> dfac;  // per-voxel dose factor of the finalize step (set at phantom load)
     // run scratch
     DevBuf<long long> tally, accum, sumsq;
     DevBuf<fdc_spot> spots;
@@ -332,6 +333,7 @@ void fdc_destroy(fdc_ctx *c) {
     c->bin_track_begin.release();
     c->vox.release();
     c->density.release();
+    c->dfac.release();
     c->tally.release();
     c->accum.release();
     c->sumsq.release();
@@ -510,6 +512,11 @@ int fdc_load_phantom(fdc_ctx *c, const fdc_phantom *ph) {
     c->dx = ph->dx;
     c->dy = ph->dy;
     c->dz = ph->dz;
+    FDC_CUDA(c, c->dfac.ensure(nvox));
+    FDC_CUDA(c, fdc::launch_dose_factor(c->density.p,
+                                        fdc::kMeVToJ / (fdc::kTallyUnitsPerMeV * c->dx * c->dy * c->dz * 1e-3), nvox,
+                                        c->dfac.p, nullptr));
+    FDC_CUDA(c, cudaStreamSynchronize(nullptr));
     c->x0 = ph->x0;
     c->y0 = ph->y0;
     c->z0 = ph->z0;
@@ -606,6 +613,7 @@ int run_impl(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t se
                 f.n_tallies = n_tallies;
                 f.nvox = c->nvox;
                 f.density = c->density.p;
+                f.factor = c->dfac.p;
                 f.scale = scale;
                 f.batch_sum = out.batch_sum;
                 f.batch_sumsq = out.batch_sumsq;
@@ -625,6 +633,7 @@ int run_impl(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint64_t se
             f.n_tallies = n_tallies;
             f.nvox = c->nvox;
             f.density = c->density.p;
+            f.factor = c->dfac.p;
             f.scale = scale;
             f.dose = out.dose;
             f.layer_dose = out.layer_dose;
@@ -723,6 +732,7 @@ int fdc_dose_from_tally(fdc_ctx *c, const int64_t *tally, double *dose_out, void
     f.n_tallies = 1;
     f.nvox = c->nvox;
     f.density = c->density.p;
+    f.factor = c->dfac.p;
     f.scale = fdc::kMeVToJ / (fdc::kTallyUnitsPerMeV * c->dx * c->dy * c->dz * 1e-3);
     f.dose = dose_out;
     FDC_CUDA(c, fdc::launch_finalize(f, c->sm_count, (cudaStream_t)stream));
@@ -977,6 +987,7 @@ int fdc_run_noalloc(fdc_ctx *c, const fdc_beam *beam, uint64_t n_histories, uint
     f.n_tallies = 1;
     f.nvox = c->nvox;
     f.density = c->density.p;
+    f.factor = c->dfac.p;
     f.scale = fdc::kMeVToJ / (fdc::kTallyUnitsPerMeV * c->dx * c->dy * c->dz * 1e-3);
     f.dose = dose_out;
     FDC_CUDA(c, fdc::launch_finalize(f, c->sm_count, st));

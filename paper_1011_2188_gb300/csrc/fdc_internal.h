@@ -75,6 +75,7 @@ struct FinalizeArgs {
     long long nvox;
     const float *density;
     double scale;            // Gy per tally unit per (g/cm^3)
+    const double *factor;    // [nvox] or null: scale / density (0 where density is 0), precomputed
     double *dose;            // [nvox] or null: dose of the summed tally
     double *layer_dose;      // [n_tallies][nvox] or null
     long long *tally_out;    // [nvox] or null: summed tally
@@ -89,6 +90,8 @@ struct FinalizeArgs {
 cudaError_t launch_replay(const ReplayArgs &a, const fdc_schedule &s, int fp64, int sm_count,
                           cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeArgs &a, int sm_count, cudaStream_t st);
+// factor[v] = scale / density[v] (0 where the density is 0), the finalize step's per-voxel factor
+cudaError_t launch_dose_factor(const float *density, double scale, long long nvox, double *factor, cudaStream_t st);
 // mode 0: eq. (1) from n batch sums; mode 1: eq. (2) from sums over n histories
 cudaError_t launch_batch_stats(const double *sum, const double *sumsq, long long n, int mode, long long nvox,
                                double frac, double *mean, double *sigma, double *partials,

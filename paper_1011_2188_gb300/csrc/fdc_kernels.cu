@@ -621,8 +621,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MINB : 2)
 __global__ void finalize_kernel(const FinalizeArgs A) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < A.nvox; v += stride) {
-        const double rho = (double)A.density[v];
-        const double f = rho > 0.0 ? A.scale / rho : 0.0;
+        // the per-voxel factor, precomputed at phantom load when available (an
+        // FP64 division per voxel costs more than the rest of this kernel on GB300)
+        double f;
+        if (A.factor) {
+            f = A.factor[v];
+        } else {
+            const double rho = (double)A.density[v];
+            f = rho > 0.0 ? A.scale / rho : 0.0;
+        }
         long long tot = 0;
         for (int l = 0; l < A.n_tallies; ++l) {
             const long long t = A.tally[l * A.nvox + v];
@@ -869,6 +876,22 @@ cudaError_t noalloc_scratch(int device, NoallocScratch *out) {
     out->spots = (fdc_spot *)(base + kNoallocSpotsOff);
     out->spot_cum = (unsigned long long *)(base + kNoallocCumOff);
     return cudaSuccess;
+}
+
+__global__ void dose_factor_kernel(const float *density, double scale, long long nvox, double *factor) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += stride) {
+        const double rho = (double)density[v];
+        factor[v] = rho > 0.0 ? scale / rho : 0.0;
+    }
+}
+
+cudaError_t launch_dose_factor(const float *density, double scale, long long nvox, double *factor, cudaStream_t st) {
+    long long blocks = (nvox + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    dose_factor_kernel<<<(int)blocks, 256, 0, st>>>(density, scale, nvox, factor);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pack_deflections(uint4 *rec, long long n, cudaStream_t st) {
