@@ -1099,6 +1099,10 @@ __global__ void __launch_bounds__(THR) conv3_dwalk_kernel(const Conv3dArgs g, co
 // its MMAs.
 constexpr int kDwtMaxRing = 12;
 constexpr int kDwtMaxAcc = 8;   // accumulator slots
+// the K dimension of inputs wider than 64 channels split over CTAs
+#ifndef FDC_DWT_KSPLIT
+#define FDC_DWT_KSPLIT 1
+#endif
 // pair tiles (MODE 2) for inputs made of two 16-channel tensors
 #ifndef FDC_DWT_PAIR
 #define FDC_DWT_PAIR 1
@@ -1181,7 +1185,12 @@ template <int NT, int EW, int MINB, int MODE>
 __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     conv3_dwtma_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
                        const Conv3dArgs g, const __nv_bfloat16 *wt, const float *bias, __nv_bfloat16 *out_bf16,
-                       float *out_f32, int Cs, int Nn, int relu, int ca, int R, int NA) {
+                       float *out_f32, int Cs, int Nn, int relu, int ca, int R, int NA, int cw,
+                       long long split_stride) {
+    // K split over blockIdx.z: this CTA's input channels are [c_off, c_off + Cs) of
+    // the cw channels of the weights; its FP32 partial sums go to out_f32 + z * split_stride
+    const int c_off = (int)blockIdx.z * Cs;
+    if (gridDim.z > 1) out_f32 += (long long)blockIdx.z * split_stride;
     constexpr int NB = MODE == 1 ? 4 : 3;          // column blocks per unit (kw taps | (pw, sw'))
     constexpr int NU = MODE == 1 ? 16 : 9;         // weight groups per slice ((kd, kh) | (pd ph, sd' sh'))
     constexpr int NX = NB * NT;                    // MMA N
@@ -1253,7 +1262,7 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
             const int co = n0 + (n % NT), blk = n / NT;
             const bool in = co < Nn;
             const __nv_bfloat16 *p =
-                in ? wt + (size_t)((co * kTaps + grp * NB + blk) * Cs + sl * 16 + kc * 8) : wt;
+                in ? wt + (size_t)((co * kTaps + grp * NB + blk) * cw + c_off + sl * 16 + kc * 8) : wt;
             cp_async16_ca(sW + i * 16, p, in);
         }
         cp_async_commit();
@@ -1298,13 +1307,14 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
                     const int d = d_begin - 1 + j;
                     for (int sl = 0; sl < S; ++sl) {
                         const unsigned dst = sP + (unsigned)s * plane_bytes + (unsigned)(sl * kSlice);
+                        const int cg = c_off + sl * 16;  // the slice's first channel of [a | b]
                         if (MODE == 2)  // one 16-channel tensor per slice, columns w0 - 1 .. w0 + 30 as 16 pairs
                             tma_load_5d(dst, sl == 0 ? (const void *)&tm_a : (const void *)&tm_b, 0, (w0 - 1) / 2,
                                         h0 - 1, d, b, full(s));
-                        else if (sl * 16 < ca)
-                            tma_load_5d(dst, &tm_a, sl * 16, w0 - 1, h0 - 1, d, b, full(s));
+                        else if (cg < ca)
+                            tma_load_5d(dst, &tm_a, cg, w0 - 1, h0 - 1, d, b, full(s));
                         else
-                            tma_load_5d(dst, &tm_b, sl * 16 - ca, w0 - 1, h0 - 1, d, b, full(s));
+                            tma_load_5d(dst, &tm_b, cg - ca, w0 - 1, h0 - 1, d, b, full(s));
                     }
                 }
             }
@@ -2816,19 +2826,105 @@ bool make_pair_map(CUtensorMap *m, const void *base, int B, int D, int H, int W)
 // with Cs channels, wt the collapsed weights.  cudaErrorNotSupported,
 // launching nothing, when the shape has no instantiation or its tensor maps
 // cannot be made.
+// FP32 partial sums of a K-split convolution, per device: grown on demand,
+// never while the stream is being captured into a graph, and a buffer once
+// handed out is never freed (a captured graph may hold its address), so the
+// buffers stay allocated until the process exits.
+struct SplitScratch {
+    float *p[16] = {};
+    size_t n[16] = {};
+    std::mutex mu;
+};
+
+cudaError_t split_scratch(size_t floats, cudaStream_t st, float **out) {
+    static SplitScratch sc;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 16) return cudaErrorNotSupported;
+    std::lock_guard<std::mutex> lock(sc.mu);
+    if (sc.n[dev] < floats) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(st, &cs);
+        if (e != cudaSuccess) return e;
+        if (cs != cudaStreamCaptureStatusNone) return cudaErrorNotSupported;  // no allocation inside a capture
+        float *q = nullptr;
+        e = cudaMalloc((void **)&q, floats * sizeof(float));
+        if (e != cudaSuccess) return e;
+        sc.p[dev] = q;  // the smaller buffer stays allocated (graphs may use it)
+        sc.n[dev] = floats;
+    }
+    *out = sc.p[dev];
+    return cudaSuccess;
+}
+
+// out[i] = act(bias[i % Nn] + sum over the splits of part[s][i]), in split order;
+// with mask (a data gradient: the layer's forward input, the output's layout),
+// zero where mask[i] is not positive.
+__global__ void split_combine_kernel(const float *part, int splits, long long n, const float *bias, int Nn, int relu,
+                                     const __nv_bfloat16 *mask, __nv_bfloat16 *out_bf16, float *out_f32) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n / 4; q += stride) {
+        float4 a = ((const float4 *)part)[q];
+        for (int sp = 1; sp < splits; ++sp) {
+            const float4 b = ((const float4 *)(part + (long long)sp * n))[q];
+            a.x += b.x;
+            a.y += b.y;
+            a.z += b.z;
+            a.w += b.w;
+        }
+        float v[4] = {a.x, a.y, a.z, a.w};
+        const int c0 = (int)((4 * q) % Nn);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (bias) v[j] += bias[c0 + j];
+            if (relu) v[j] = fmaxf(v[j], 0.f);
+        }
+        if (mask) {
+            const uint2 mq = ((const uint2 *)mask)[q];
+            const unsigned short mh[4] = {(unsigned short)(mq.x & 0xffffu), (unsigned short)(mq.x >> 16),
+                                          (unsigned short)(mq.y & 0xffffu), (unsigned short)(mq.y >> 16)};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if ((short)mh[j] <= 0) v[j] = 0.f;  // sign bit set, or +0: not positive
+        }
+        if (out_f32) ((float4 *)out_f32)[q] = make_float4(v[0], v[1], v[2], v[3]);
+        if (out_bf16) {
+            const __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
+            uint2 u;
+            u.x = *(const unsigned *)&p0;
+            u.y = *(const unsigned *)&p1;
+            ((uint2 *)out_bf16)[q] = u;
+        }
+    }
+}
+
+// The TMA d-walking kernel.  MODE 0: an input read as stored (no upsampling;
+// the split of a two-part input on a 16-channel boundary).  MODE 1: the
+// sub-pixel form of the convolution of upsample2(src), src on the coarse grid
+// with Cs channels, wt the collapsed weights.  splits > 1: the Cs input
+// channels are split into `splits` equal parts of at most 64 over
+// blockIdx.z, each part's FP32 partial sums written to scratch, and one
+// combine pass adds them in order with the bias, the ReLU and a data
+// gradient's plain ReLU mask (g.mask with g.mask_ca = 0; no split output).
+// cudaErrorNotSupported, launching nothing, when the shape has no
+// instantiation or its tensor maps cannot be made.
 cudaError_t launch_dwtma(int mode, const Conv3dArgs &g, const __nv_bfloat16 *src, const __nv_bfloat16 *wt,
                          const float *bias, __nv_bfloat16 *out_bf16, float *out_f32, int Cs, int Nn, int relu,
-                         cudaStream_t st, int ca, const __nv_bfloat16 *src_b) {
-    if (Cs % 16 || Cs > 64 || Nn % 16 || ca % 16 || (Cs - ca) % 16 || (ca < Cs && !src_b)) return cudaErrorNotSupported;
+                         cudaStream_t st, int ca, const __nv_bfloat16 *src_b, int splits = 1) {
+    if (splits < 1 || Cs % splits || (Cs / splits) % 16 || Cs / splits > 64 || Nn % 16 || ca % 16 ||
+        (Cs - ca) % 16 || (ca < Cs && !src_b))
+        return cudaErrorNotSupported;
     if (mode == 1 && (ca != Cs || g.in_d % 2 || g.in_h % 2 || g.in_w % 2)) return cudaErrorNotSupported;
+    if (splits > 1 && (g.mask_ca > 0 || g.out_b)) return cudaErrorNotSupported;
     // the walked (input) grid
     const int D = mode ? g.in_d / 2 : g.in_d, H = mode ? g.in_h / 2 : g.in_h, W = mode ? g.in_w / 2 : g.in_w;
     CUtensorMap tm_a, tm_b;
     // pair tiles when the input is two 16-channel tensors and w is even (measured at 128^3:
     // [16 | 16] -> 16 94 vs 118 us; for one 16-channel tensor the two CTAs per SM that their
     // accumulators leave were slower than four with plain tiles, 66 vs 62 us)
-    if (mode == 0 && FDC_DWT_PAIR && ca == 16 && Cs == 32 && make_pair_map(&tm_a, src, g.batch, D, H, W) &&
-        make_pair_map(&tm_b, src_b, g.batch, D, H, W))
+    if (mode == 0 && splits == 1 && FDC_DWT_PAIR && ca == 16 && Cs == 32 &&
+        make_pair_map(&tm_a, src, g.batch, D, H, W) && make_pair_map(&tm_b, src_b, g.batch, D, H, W))
         mode = 2;
     if (mode != 2 && !make_plane_map(&tm_a, src, ca, g.batch, D, H, W)) return cudaErrorNotSupported;
     if (ca == Cs) {
@@ -2841,7 +2937,8 @@ cudaError_t launch_dwtma(int mode, const Conv3dArgs &g, const __nv_bfloat16 *src
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e != cudaSuccess) return e;
-    const int S = Cs / 16;
+    const int Cp = Cs / splits;  // input channels per CTA
+    const int S = Cp / 16;
     const int NT = (mode == 0 && Nn % 32 == 0) ? 32 : 16;
     const int NX = (mode == 1 ? 4 : 3) * NT, NU = mode == 1 ? 16 : 9;
     const int wbytes = S * NU * 2 * NX * 16;
@@ -2863,47 +2960,68 @@ cudaError_t launch_dwtma(int mode, const Conv3dArgs &g, const __nv_bfloat16 *src
     const int ntiles = (Nn + NT - 1) / NT;
     const long long planes =
         (long long)g.batch * ((H + 7) / 8) * (mode == 2 ? (W + 30) / 30 : (W + 13) / 14) * D;
-    long long gx = std::max(1ll, (long long)sms * per_sm / ntiles);
+    long long gx = std::max(1ll, (long long)sms * per_sm / (ntiles * splits));
     if (gx > planes) gx = planes;
-    const dim3 grid((unsigned)gx, (unsigned)ntiles);
+    const dim3 grid((unsigned)gx, (unsigned)ntiles, (unsigned)splits);
+    // split partial sums: [splits][output voxels][Nn] FP32
+    const long long n_out = (long long)g.batch * g.in_d * g.in_h * g.in_w * Nn;
+    float *part = nullptr;
+    if (splits > 1) {
+        e = split_scratch((size_t)n_out * splits, st, &part);
+        if (e != cudaSuccess) return e;
+    }
+    Conv3dArgs gk = g;  // the split partials carry no mask: the combine pass applies it
+    if (splits > 1) gk.mask = nullptr;
+    const float *kb = splits > 1 ? nullptr : bias;
+    __nv_bfloat16 *kob = splits > 1 ? nullptr : out_bf16;
+    float *kof = splits > 1 ? part : out_f32;
+    const int krelu = splits > 1 ? 0 : relu;
     if (mode == 2) {
         static OccCache cache;
         e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 8, 2, 2>, smem);
         if (e != cudaSuccess) return e;
-        conv3_dwtma_kernel<16, 8, 2, 2><<<grid, 320, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
-                                                                  relu, ca, R, NA);
+        conv3_dwtma_kernel<16, 8, 2, 2><<<grid, 320, smem, st>>>(tm_a, tm_b, gk, wt, kb, kob, kof, Cp, Nn, krelu, ca,
+                                                                  R, NA, Cs, n_out);
     } else if (mode == 1) {
         static OccCache cache;
         e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 8, 2, 1>, smem);
         if (e != cudaSuccess) return e;
-        conv3_dwtma_kernel<16, 8, 2, 1><<<grid, 320, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
-                                                                  relu, ca, R, NA);
+        conv3_dwtma_kernel<16, 8, 2, 1><<<grid, 320, smem, st>>>(tm_a, tm_b, gk, wt, kb, kob, kof, Cp, Nn, krelu, ca,
+                                                                  R, NA, Cs, n_out);
     } else if (NT == 32) {
         static OccCache cache;
         e = prepare_kernel_smem(cache, conv3_dwtma_kernel<32, 8, 2, 0>, smem);
         if (e != cudaSuccess) return e;
-        conv3_dwtma_kernel<32, 8, 2, 0><<<grid, 320, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
-                                                                  relu, ca, R, NA);
+        conv3_dwtma_kernel<32, 8, 2, 0><<<grid, 320, smem, st>>>(tm_a, tm_b, gk, wt, kb, kob, kof, Cp, Nn, krelu, ca,
+                                                                  R, NA, Cs, n_out);
     } else if (per_sm >= 3) {
         static OccCache cache;
         e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 4, 4, 0>, smem);
         if (e != cudaSuccess) return e;
-        conv3_dwtma_kernel<16, 4, 4, 0><<<grid, 192, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
-                                                                  relu, ca, R, NA);
+        conv3_dwtma_kernel<16, 4, 4, 0><<<grid, 192, smem, st>>>(tm_a, tm_b, gk, wt, kb, kob, kof, Cp, Nn, krelu, ca,
+                                                                  R, NA, Cs, n_out);
     } else {
         static OccCache cache;
         e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 8, 2, 0>, smem);
         if (e != cudaSuccess) return e;
-        conv3_dwtma_kernel<16, 8, 2, 0><<<grid, 320, smem, st>>>(tm_a, tm_b, g, wt, bias, out_bf16, out_f32, Cs, Nn,
-                                                                  relu, ca, R, NA);
+        conv3_dwtma_kernel<16, 8, 2, 0><<<grid, 320, smem, st>>>(tm_a, tm_b, gk, wt, kb, kob, kof, Cp, Nn, krelu, ca,
+                                                                  R, NA, Cs, n_out);
     }
+    e = cudaGetLastError();
+    if (e != cudaSuccess || splits == 1) return e;
+    long long blocks = (n_out / 4 + 255) / 256;
+    if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
+    split_combine_kernel<<<(int)blocks, 256, 0, st>>>(part, splits, n_out, bias, Nn, relu,
+                                                      (const __nv_bfloat16 *)g.mask, out_bf16, out_f32);
     return cudaGetLastError();
 }
 
 cudaError_t launch_conv_up(const Conv3dArgs &g, const void *xa, const void *w_up, const float *bias, void *out_bf16,
                            float *out_f32, int relu, cudaStream_t st) {
+    // more than 64 input channels: K split into 32-channel parts (their collapsed weights fit)
+    const int splits = g.c_in > 64 && FDC_DWT_KSPLIT ? g.c_in / 32 : 1;
     return launch_dwtma(1, g, (const __nv_bfloat16 *)xa, (const __nv_bfloat16 *)w_up, bias, (__nv_bfloat16 *)out_bf16,
-                        out_f32, g.c_in, g.c_out, relu, st, g.c_in, nullptr);
+                        out_f32, g.c_in, g.c_out, relu, st, g.c_in, nullptr, splits);
 }
 
 cudaError_t launch_collapse_up(const void *w, void *w_up, int co, int ci, cudaStream_t st) {
@@ -2920,6 +3038,16 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
         const cudaError_t e = launch_dwtma(0, g, (const __nv_bfloat16 *)src, (const __nv_bfloat16 *)wt, bias,
                                            (__nv_bfloat16 *)out_bf16, out_f32, Cs, Nn, relu, st, ca,
                                            (const __nv_bfloat16 *)src_b);
+        if (e != cudaErrorNotSupported) return e;
+    }
+    // wider inputs (the 32^3 and 16^3 levels' 128 channels): the K dimension split into
+    // 64-channel parts on the same kernel, FP32 partial sums combined in order (with a plain
+    // ReLU mask for a data gradient)
+    if (FDC_CONV_DWTMA && FDC_DWT_KSPLIT && !up_a && g.mask_ca == 0 && !g.out_b && Cs > FDC_CONV_DWALK_MAXC &&
+        Cs % 64 == 0 && Cs <= 8 * 64 && Nn % 16 == 0) {
+        const cudaError_t e = launch_dwtma(0, g, (const __nv_bfloat16 *)src, (const __nv_bfloat16 *)wt, bias,
+                                           (__nv_bfloat16 *)out_bf16, out_f32, Cs, Nn, relu, st, ca,
+                                           (const __nv_bfloat16 *)src_b, Cs / 64);
         if (e != cudaErrorNotSupported) return e;
     }
     auto s = (const __nv_bfloat16 *)src;

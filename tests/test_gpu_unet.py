@@ -75,6 +75,11 @@ CASES = [
     # output tiles, batch 2 at the smallest width
     ((1, 12, 21, 70, 16), 32, 3, 1, 1),
     ((2, 7, 10, 32, 16), 16, 3, 1, 1),
+    # 128 input channels, forward: the K dimension split into two 64-channel
+    # parts over CTAs, FP32 partials combined with bias and ReLU (the 16^3
+    # bottleneck shape; a ragged 32^3-level shape with two output tiles)
+    ((1, 16, 16, 16, 128), 128, 3, 1, 1),
+    ((1, 9, 20, 36, 128), 64, 3, 1, 1),
 ]
 
 
@@ -454,7 +459,8 @@ def test_unet_forward_backward_and_training_reduces_loss():
 @pytest.mark.parametrize("ca,cb,up,dims", [(32, 0, 1, (6, 8, 10)), (16, 16, 0, (6, 8, 10)), (64, 64, 0, (6, 8, 10)),
                                            (32, 32, 1, (6, 8, 10)), (16, 16, 0, (5, 12, 20)),
                                            (32, 32, 0, (7, 10, 34)), (32, 16, 0, (4, 11, 16)),
-                                           (16, 16, 0, (6, 12, 36)), (16, 16, 0, (96, 40, 62))])
+                                           (16, 16, 0, (6, 12, 36)), (16, 16, 0, (96, 40, 62)),
+                                           (64, 64, 0, (8, 20, 34))])
 def test_fused_upsample_concat_forward(ca, cb, up, dims):
     """fdc_conv3d_forward_fused equals fdc_conv3d_forward on the materialised
     [upsample(xa) | xb] input (the larger grids take the two tensor maps of
@@ -621,7 +627,8 @@ def _collapse_up(w):
 
 
 @pytest.mark.parametrize("shape,cout", [((1, 8, 20, 32, 32), 16), ((1, 4, 20, 32, 16), 16),
-                                        ((2, 12, 26, 40, 64), 32), ((1, 64, 48, 60, 32), 16)])
+                                        ((2, 12, 26, 40, 64), 32), ((1, 64, 48, 60, 32), 16),
+                                        ((1, 8, 20, 32, 128), 64)])
 @pytest.mark.parametrize("relu", [0, 1])
 def test_forward_up_subpixel(shape, cout, relu):
     """fdc_conv3d_forward_up (the upsampling convolution on the coarse grid
@@ -661,14 +668,15 @@ def test_forward_up_subpixel(shape, cout, relu):
 
 def test_forward_up_refuses_shapes_without_its_kernel():
     """FDC_ERR_INVALID, nothing launched: a coarse grid narrower than the TMA
-    box (16 w), odd sizes, more than 64 input channels."""
+    box (16 w), odd sizes, more than 64 input channels that do not split into
+    16-channel parts of at most 32."""
     import torch
     from paper_1011_2188_gb300 import fdc
     L = fdc.lib()
     x = torch.zeros((1, 8, 16, 32, 128), dtype=torch.bfloat16, device="cuda:0")
     wup = torch.zeros((16, 64, 128), dtype=torch.bfloat16, device="cuda:0")
     y = torch.empty((1, 16, 32, 64, 16), dtype=torch.bfloat16, device="cuda:0")
-    for shape in [(1, 6, 20, 30, 16), (1, 7, 20, 32, 16), (1, 16, 32, 64, 128)]:
+    for shape in [(1, 6, 20, 30, 16), (1, 7, 20, 32, 16), (1, 16, 32, 64, 80)]:
         g, _ = geom(shape, 16, 3, 1, 1)
         assert L.fdc_conv3d_forward_up(C.byref(g), ptr(x), ptr(wup), None, ptr(y), None, None) == 1
     torch.cuda.synchronize()
