@@ -69,6 +69,28 @@ int fdc_conv3d_forward_up(const fdc_conv3d *g, const void *xa, const void *w_up,
  * axis (p: output parity, s = 0, 1: the first or second coarse voxel read).
  * g: a 3^3, stride-1, padding-1 convolution. */
 int fdc_conv3d_collapse_up_weights(const fdc_conv3d *g, const void *w, void *w_up, void *stream);
+/* The data gradient of fdc_conv3d_forward_up with respect to its coarse input
+ * xa, computed on the coarse grid (the adjoint of the sub-pixel form): along
+ * each axis, coarse voxel m receives the gradients dy[2m - 1 .. 2m + 2] of the
+ * outputs that read it, each through its collapsed weight, so
+ * dxa = upsample2-adjoint of the full-resolution data gradient without
+ * forming the latter.  g as for fdc_conv3d_forward_up; dy bf16
+ * [batch][in_d][in_h][in_w][c_out]; w_up_t from
+ * fdc_conv3d_collapse_up_weights_t; relu_mask (may be NULL): xa, bf16
+ * [batch][in_d/2][in_h/2][in_w/2][c_in], dxa written as zero where it is not
+ * positive; dxa bf16 in xa's layout.  Equals the adjoint of the direct form up
+ * to the BF16 rounding of each collapsed weight (|difference| <= 2^-8 * the
+ * same sum with |w| and |dy|) and FP32 accumulation order.  FDC_ERR_INVALID,
+ * launching nothing, without a kernel for the shape (full-resolution grid of
+ * at least 20 (h) x 32 (w), even sizes). */
+int fdc_conv3d_backward_data_up(const fdc_conv3d *g, const void *dy, const void *w_up_t, const void *relu_mask,
+                                void *dxa, void *stream);
+/* Transposed collapsed weights for fdc_conv3d_backward_data_up: w_up_t[ci][t][co]
+ * (bf16, c_in x 64 x c_out), t = (q_d, q_h, q_w, i_d, i_h, i_w) as bits from the
+ * highest, = the FP32 sum (rounded once to BF16) of w[co][kd][kh][kw][ci] over the
+ * taps of each axis with (q + k - 1) >> 1 = q - i: the collapsed weight of output
+ * parity q and coarse offset s = 1 - i. */
+int fdc_conv3d_collapse_up_weights_t(const fdc_conv3d *g, const void *w, void *w_up_t, void *stream);
 /* dx[b][i][ci] = sum over (tap, co) with i + pad - tap = stride * o of dy[b][o][co] w[co][tap][ci]
  * (the gradient of the forward map with respect to x, without this layer's ReLU).
  * dy bf16 [batch][out...][c_out]; w_t the data-gradient weights that

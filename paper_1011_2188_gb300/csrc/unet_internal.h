@@ -36,6 +36,10 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
 cudaError_t launch_conv_up(const Conv3dArgs &g, const void *xa, const void *w_up, const float *bias, void *out_bf16,
                            float *out_f32, int relu, cudaStream_t st);
 cudaError_t launch_collapse_up(const void *w, void *w_up, int co, int ci, cudaStream_t st);
+// the data gradient of that convolution on the coarse grid (g.mask: the plain ReLU mask xa)
+// and its transposed collapsed weights
+cudaError_t launch_conv_up_dgrad(const Conv3dArgs &g, const void *dy, const void *w_up_t, void *dxa, cudaStream_t st);
+cudaError_t launch_collapse_up_t(const void *w, void *w_up_t, int co, int ci, cudaStream_t st);
 cudaError_t launch_flip_transpose(const void *w, void *wf, int co, int k, int ci, cudaStream_t st);
 cudaError_t launch_conv_wgrad(const Conv3dArgs &g, const void *x, const void *dy, float *dw, float *db,
                               cudaStream_t st, int ca, int up_a, const void *xb);

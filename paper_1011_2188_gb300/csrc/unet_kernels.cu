@@ -1181,6 +1181,18 @@ __device__ __forceinline__ unsigned long long umma_desc_sw64(unsigned saddr, uns
            ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46) | (4ull << 61);
 }
 
+// MODE 3: the data gradient of the MODE 1 convolution, on the coarse grid:
+// da[m] = sum over output parities q and coarse offsets of Wc^T dy[2 (m + o) + q],
+// o in {0, +1} for q = 0 and {-1, 0} for q = 1 per axis (the adjoint of the
+// collapse: the offset index idx = o for q = 0, o + 1 for q = 1 takes the
+// collapsed weights of s' = 1 - idx).  The ring holds full-resolution dy planes,
+// each as four boxes of its (h, w) parity classes (TMA element stride 2 in w
+// and h: 16 coarse columns x 10 coarse rows); coarse output plane i reads
+// full-resolution planes 2i - 1 .. 2i + 2 (two new ones per output).  Per
+// (q, idx_d, idx_h) one MMA of N = 2 NT (the two w offsets) into the
+// accumulator half of q_w; the epilogue adds the four w blocks with lane
+// shuffles and applies the ReLU mask of a (coarse).  Weights: the transposed
+// collapsed layout [c_a][64][c_out] (conv3_collapse_up_t_kernel).
 template <int NT, int EW, int MINB, int MODE>
 __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     conv3_dwtma_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
@@ -1191,13 +1203,19 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     // the cw channels of the weights; its FP32 partial sums go to out_f32 + z * split_stride
     const int c_off = (int)blockIdx.z * Cs;
     if (gridDim.z > 1) out_f32 += (long long)blockIdx.z * split_stride;
-    constexpr int NB = MODE == 1 ? 4 : 3;          // column blocks per unit (kw taps | (pw, sw'))
-    constexpr int NU = MODE == 1 ? 16 : 9;         // weight groups per slice ((kd, kh) | (pd ph, sd' sh'))
+    // column blocks per MMA: kw taps | (pw, sw') | kw taps | the two w offsets of a parity
+    constexpr int NB = MODE == 1 ? 4 : (MODE == 3 ? 2 : 3);
+    // weight groups per slice: (kd, kh) | (pd ph, sd' sh') | (kd, kh) | (q, idx_d, idx_h)
+    constexpr int NU = MODE == 1 ? 16 : (MODE == 3 ? 32 : 9);
     constexpr int NX = NB * NT;                    // MMA N
-    // columns per accumulator slot (MODE 2: D_e and D_o, 64 apart)
-    constexpr unsigned kAccCols = MODE == 2 ? 128 : (NX <= 64 ? 64 : 128);
+    // columns per accumulator slot (MODE 2: D_e and D_o, 64 apart; MODE 3: the two w parities)
+    constexpr unsigned kAccCols = MODE == 2 ? 128 : (MODE == 3 ? 4 * NT : (NX <= 64 ? 64 : 128));
     constexpr int UPP = MODE == 1 ? 4 : 1;         // units per (coarse) output plane
-    constexpr int kSlice = MODE == 2 ? 2 * kDwPlaneSliceBytes : kDwPlaneSliceBytes;  // bytes per slice of a plane
+    constexpr int kPPO = MODE == 3 ? 2 : 1;        // new input planes per output plane
+    constexpr int kSpan = MODE == 3 ? 4 : 3;       // input planes one output plane reads
+    constexpr int kBoxes = MODE == 3 ? 4 : 1;      // boxes per slice of an input plane
+    // bytes per slice of a plane (all of its boxes)
+    constexpr int kSlice = MODE == 2 ? 2 * kDwPlaneSliceBytes : kBoxes * kDwPlaneSliceBytes;
     constexpr int kTileW = MODE == 2 ? 30 : 14;    // output columns per tile
     static_assert(MODE != 2 || (NT == 16 && EW == 8), "pair tiles: 16-channel output tiles, 8 epilogue warps");
     constexpr int THR = 32 * (EW + 2);
@@ -1208,9 +1226,10 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     __shared__ int abort_flag;
     __shared__ float sBias[NT];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // the walked grid: the output grid (MODE 0, 2) or the coarse input grid (MODE 1)
-    const int D = MODE != 1 ? g.in_d : g.in_d / 2, H = MODE != 1 ? g.in_h : g.in_h / 2,
-              W = MODE != 1 ? g.in_w : g.in_w / 2;
+    // the walked grid: the output grid (MODE 0, 2) or the coarse grid (MODE 1, 3)
+    constexpr bool kCoarse = MODE == 1 || MODE == 3;
+    const int D = kCoarse ? g.in_d / 2 : g.in_d, H = kCoarse ? g.in_h / 2 : g.in_h,
+              W = kCoarse ? g.in_w / 2 : g.in_w;
     const int S = Cs / 16;
     const unsigned plane_bytes = (unsigned)(S * kSlice);
     const int wbytes = S * NU * 2 * NX * 16;
@@ -1255,7 +1274,7 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     if (tid < NT) sBias[tid] = (bias && n0 + tid < Nn) ? bias[n0 + tid] : 0.f;
     {  // resident weights of every input slice (through L1: all CTAs read the same)
         constexpr int kChunks = NU * 2 * NX;  // per slice
-        constexpr int kTaps = MODE == 1 ? 64 : 27;  // weight rows per output channel
+        constexpr int kTaps = MODE == 1 || MODE == 3 ? 64 : 27;  // weight rows per output channel
         for (int i = tid; i < S * kChunks; i += THR) {
             const int sl = i / kChunks, r = i % kChunks;
             const int n = r % NX, q = r / NX, kc = q & 1, grp = q >> 1;
@@ -1295,7 +1314,7 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
                 int d_begin, nd, w0, h0, b;
                 range_at(q, d_begin, nd, w0, h0, b);
                 q += nd;
-                for (int j = 0; j < nd + 2; ++j, ++p) {
+                for (int j = 0; j < kPPO * nd + kSpan - kPPO; ++j, ++p) {
                     const int s = (int)(p % (unsigned)R);
                     if (p >= (unsigned)R && !role_wait(empty(s), (p / (unsigned)R - 1u) & 1u, abort_v)) {
                         ok = false;
@@ -1304,17 +1323,28 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full(s)),
                                  "r"(plane_bytes)
                                  : "memory");
-                    const int d = d_begin - 1 + j;
-                    for (int sl = 0; sl < S; ++sl) {
-                        const unsigned dst = sP + (unsigned)s * plane_bytes + (unsigned)(sl * kSlice);
-                        const int cg = c_off + sl * 16;  // the slice's first channel of [a | b]
-                        if (MODE == 2)  // one 16-channel tensor per slice, columns w0 - 1 .. w0 + 30 as 16 pairs
-                            tma_load_5d(dst, sl == 0 ? (const void *)&tm_a : (const void *)&tm_b, 0, (w0 - 1) / 2,
-                                        h0 - 1, d, b, full(s));
-                        else if (cg < ca)
-                            tma_load_5d(dst, &tm_a, cg, w0 - 1, h0 - 1, d, b, full(s));
-                        else
-                            tma_load_5d(dst, &tm_b, cg - ca, w0 - 1, h0 - 1, d, b, full(s));
+                    // MODE 3: full-resolution planes 2 d_begin - 1 + j, four parity boxes per slice
+                    const int d = MODE == 3 ? 2 * d_begin - 1 + j : d_begin - 1 + j;
+                    if constexpr (MODE == 3) {
+                        for (int bx = 0; bx < 4; ++bx)
+                            for (int sl = 0; sl < S; ++sl) {
+                                const unsigned dst =
+                                    sP + (unsigned)s * plane_bytes + (unsigned)((bx * S + sl) * kDwPlaneSliceBytes);
+                                tma_load_5d(dst, &tm_a, c_off + sl * 16, 2 * (w0 - 1) + (bx & 1),
+                                            2 * (h0 - 1) + (bx >> 1), d, b, full(s));
+                            }
+                    } else {
+                        for (int sl = 0; sl < S; ++sl) {
+                            const unsigned dst = sP + (unsigned)s * plane_bytes + (unsigned)(sl * kSlice);
+                            const int cg = c_off + sl * 16;  // the slice's first channel of [a | b]
+                            if (MODE == 2)  // one 16-channel tensor per slice, columns w0 - 1 .. w0 + 30 as pairs
+                                tma_load_5d(dst, sl == 0 ? (const void *)&tm_a : (const void *)&tm_b, 0,
+                                            (w0 - 1) / 2, h0 - 1, d, b, full(s));
+                            else if (cg < ca)
+                                tma_load_5d(dst, &tm_a, cg, w0 - 1, h0 - 1, d, b, full(s));
+                            else
+                                tma_load_5d(dst, &tm_b, cg - ca, w0 - 1, h0 - 1, d, b, full(s));
+                        }
                     }
                 }
             }
@@ -1337,15 +1367,16 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
                 range_at(q, d_begin, nd, w0, h0, b);
                 q += nd;
                 for (int i = 0; i < nd && ok; ++i) {
-                    for (int j = (i == 0 ? 0 : i + 2); j <= i + 2; ++j) {
+                    // output plane i reads input planes kPPO i .. kPPO i + kSpan - 1 of the range
+                    for (int j = (i == 0 ? 0 : kPPO * i + kSpan - kPPO); j < kPPO * i + kSpan; ++j) {
                         const unsigned pp = p + (unsigned)j;
                         if (!role_wait(full((int)(pp % (unsigned)R)), (pp / (unsigned)R) & 1u, abort_v)) ok = false;
                     }
                     if (!ok) break;
-                    unsigned long long ad_kd[3];
+                    unsigned long long ad_kd[kSpan];
 #pragma unroll
-                    for (int kd = 0; kd < 3; ++kd) {
-                        const unsigned a = sP + ((p + (unsigned)(i + kd)) % (unsigned)R) * plane_bytes;
+                    for (int kd = 0; kd < kSpan; ++kd) {
+                        const unsigned a = sP + ((p + (unsigned)(kPPO * i + kd)) % (unsigned)R) * plane_bytes;
                         ad_kd[kd] = MODE == 2 ? umma_desc_sw64(a, 512) : umma_desc_sw32(a, 256);
                     }
                     for (int u = 0; u < UPP; ++u, ++it) {
@@ -1357,7 +1388,24 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
                         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll 1
                         for (int sl = 0; sl < S; ++sl) {
-                            if constexpr (MODE == 2) {
+                            if constexpr (MODE == 3) {
+                                // parity q = (qd, qh, qw), offsets (idx_d, idx_h): full-resolution plane
+                                // 2i + 2 idx_d + 1 - qd of the range, row shift idx_h + 1 - qh,
+                                // accumulator half qw
+#pragma unroll
+                                for (int grp = 0; grp < 32; ++grp) {
+                                    const int qd = grp >> 4, qh = (grp >> 3) & 1, qw = (grp >> 2) & 1,
+                                              idd = (grp >> 1) & 1, idh = grp & 1;
+                                    const int f = 2 * idd + 1 - qd, kh = idh + 1 - qh, bx = qh * 2 + qw;
+                                    const unsigned long long ad =
+                                        ad_kd[f] +
+                                        (unsigned long long)(((bx * S + sl) * kDwPlaneSliceBytes + kh * 512) >> 4);
+                                    const unsigned long long bd =
+                                        bd0 + (unsigned long long)(((sl * NU + grp) * 2 * NX * 16) >> 4);
+                                    umma_bf16(tmem + ab * kAccCols + (unsigned)(qw * NX), ad, bd, idesc,
+                                              (sl | qd | qh | idd | idh) != 0);
+                                }
+                            } else if constexpr (MODE == 2) {
                                 // tap (kd, kh): the even and the odd voxel of every pair (rows of
                                 // 64 B, 16 pairs per h row: kh shifts by 1 KB, e by 32 B)
 #pragma unroll
@@ -1401,13 +1449,14 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
                         umma_commit(accf(ab));
                     }
                     if (!ok) break;
-                    umma_commit(empty((int)((p + (unsigned)i) % (unsigned)R)));
+                    for (int j = 0; j < kPPO; ++j)  // input planes this output plane read last
+                        umma_commit(empty((int)((p + (unsigned)(kPPO * i + j)) % (unsigned)R)));
                 }
                 if (!ok) break;
-                // the range's last two input planes are released after its last MMAs
-                umma_commit(empty((int)((p + (unsigned)nd) % (unsigned)R)));
-                umma_commit(empty((int)((p + (unsigned)nd + 1u) % (unsigned)R)));
-                p += (unsigned)nd + 2u;
+                // the range's last input planes are released after its last MMAs
+                for (int j = kPPO * nd; j < kPPO * nd + kSpan - kPPO; ++j)
+                    umma_commit(empty((int)((p + (unsigned)j) % (unsigned)R)));
+                p += (unsigned)(kPPO * nd + kSpan - kPPO);
             }
             // every MMA issued has completed before TMEM is freed (bounded)
             umma_commit(fin);
@@ -1428,7 +1477,7 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
             range_at(q, d_begin, nd, w0, h0, b);
             q += nd;
             const int hl = h0 + (m >> 4), wl = m & 15, wc = w0 + wl;
-            const bool out_in = wl < 14 && hl < H && wc < W;  // MODE 0, 1
+            const bool out_in = wl < 14 && hl < H && wc < W;  // MODE 0, 1, 3
             for (int i = 0; i < nd && ok; ++i) {
                 for (int u = 0; u < UPP; ++u, ++it) {
                     const unsigned ab = it % (unsigned)NA;
@@ -1440,7 +1489,27 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     const unsigned base = tmem + ((unsigned)(quad * 32) << 16) + ab * kAccCols;
                     const int n = n0 + c;
-                    if constexpr (MODE == 2) {
+                    if constexpr (MODE == 3) {
+                        // w blocks: parity 0 offsets 0, +1 (rows wl + 1, wl + 2), parity 1
+                        // offsets -1, 0 (rows wl, wl + 1)
+                        static_assert(CW == 16, "16 output channels per thread");
+                        float a0[16], a1[16], b0[16], b1[16];
+                        tmem_ld16x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c), a0,
+                                    a1, b0);
+                        tmem_ld16(base + (unsigned)(3 * NT + c), b1);
+                        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0)
+                            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(acce(ab)) : "memory");
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            b0[j] += __shfl_down_sync(0xffffffffu, a0[j], 1) + __shfl_down_sync(0xffffffffu, a1[j], 2) +
+                                     __shfl_down_sync(0xffffffffu, b1[j], 1);
+                        if (out_in && n < Nn) {
+                            const long long v = (((long long)b * D + d_begin + i) * H + hl) * W + wc;
+                            dwalk_store<16>(g, b0, nullptr, 0, out_bf16, out_f32, Nn, n, b, d_begin + i, hl, wc, v);
+                        }
+                    } else if constexpr (MODE == 2) {
                         float e0[CW], e1[CW], e2[CW], o0[CW], o1[CW], o2[CW];
                         tmem_ld8x3(base + (unsigned)c, base + (unsigned)(NT + c), base + (unsigned)(2 * NT + c), e0,
                                    e1, e2);
@@ -1537,6 +1606,35 @@ __global__ void __launch_bounds__(32 * (EW + 2), MINB)
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
+    }
+}
+
+// Collapsed weights of the data gradient of the upsampling convolution (MODE 3
+// above): wt[ci][t][co], t = (((((qd qh qw) idx_d) idx_h) idx_w), the sum in FP32
+// (rounded once to BF16) of w[co][kd][kh][kw][ci] over the taps of each axis
+// with (q + k - 1) >> 1 = q - 1 + s', s' = 1 - idx (the collapse of the forward
+// form, transposed).
+__global__ void conv3_collapse_up_t_kernel(const __nv_bfloat16 *w, __nv_bfloat16 *wt, int co_n, int ci_n) {
+    const long long n = (long long)co_n * 64 * ci_n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int co = (int)(i % co_n);
+        const int t = (int)((i / co_n) % 64);
+        const int ci = (int)(i / ((long long)co_n * 64));
+        const int qd = (t >> 5) & 1, qh = (t >> 4) & 1, qw = (t >> 3) & 1;
+        const int sd = 1 - ((t >> 2) & 1), sh = 1 - ((t >> 1) & 1), sw = 1 - (t & 1);
+        float acc = 0.f;
+        for (int kd = 0; kd < 3; ++kd) {
+            if (((qd + kd - 1) >> 1) != qd - 1 + sd) continue;
+            for (int kh = 0; kh < 3; ++kh) {
+                if (((qh + kh - 1) >> 1) != qh - 1 + sh) continue;
+                for (int kw = 0; kw < 3; ++kw) {
+                    if (((qw + kw - 1) >> 1) != qw - 1 + sw) continue;
+                    acc += __bfloat162float(w[((long long)co * 27 + (kd * 3 + kh) * 3 + kw) * ci_n + ci]);
+                }
+            }
+        }
+        wt[i] = __float2bfloat16_rn(acc);
     }
 }
 
@@ -2820,12 +2918,6 @@ bool make_pair_map(CUtensorMap *m, const void *base, int B, int D, int H, int W)
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The TMA d-walking kernel.  MODE 0: an input read as stored (no upsampling;
-// the split of a two-part input on a 16-channel boundary).  MODE 1: the
-// sub-pixel form of the convolution of upsample2(src), src on the coarse grid
-// with Cs channels, wt the collapsed weights.  cudaErrorNotSupported,
-// launching nothing, when the shape has no instantiation or its tensor maps
-// cannot be made.
 // FP32 partial sums of a K-split convolution, per device: grown on demand,
 // never while the stream is being captured into a graph, and a buffer once
 // handed out is never freed (a captured graph may hold its address), so the
@@ -2899,10 +2991,30 @@ __global__ void split_combine_kernel(const float *part, int splits, long long n,
     }
 }
 
+// 5-D tensor map of a full-resolution channels-last BF16 tensor read by parity
+// class: boxes of 16 channels x 16 w x 10 h taken every second voxel along w
+// and h (element strides 2), 32-byte swizzle; false when it cannot be made.
+bool make_parity_map(CUtensorMap *m, const void *base, int C, int B, int D, int H, int W) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || !base || ((uintptr_t)base & 15u) || C % 16 || W < 32 || H < 20) return false;
+    const cuuint64_t e = 2;
+    const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B};
+    const cuuint64_t strides[4] = {dims[0] * e, dims[0] * dims[1] * e, dims[0] * dims[1] * dims[2] * e,
+                                   dims[0] * dims[1] * dims[2] * dims[3] * e};
+    const cuuint32_t box[5] = {16, 32, 20, 1, 1};
+    const cuuint32_t estr[5] = {1, 2, 2, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // The TMA d-walking kernel.  MODE 0: an input read as stored (no upsampling;
 // the split of a two-part input on a 16-channel boundary).  MODE 1: the
 // sub-pixel form of the convolution of upsample2(src), src on the coarse grid
-// with Cs channels, wt the collapsed weights.  splits > 1: the Cs input
+// with Cs channels, wt the collapsed weights.  MODE 3: the data gradient of
+// that convolution on the coarse grid, src = dy at full resolution with Cs
+// channels, wt the transposed collapsed weights, Nn = the coarse input's
+// channels.  splits > 1: the Cs input
 // channels are split into `splits` equal parts of at most 64 over
 // blockIdx.z, each part's FP32 partial sums written to scratch, and one
 // combine pass adds them in order with the bias, the ReLU and a data
@@ -2915,7 +3027,8 @@ cudaError_t launch_dwtma(int mode, const Conv3dArgs &g, const __nv_bfloat16 *src
     if (splits < 1 || Cs % splits || (Cs / splits) % 16 || Cs / splits > 64 || Nn % 16 || ca % 16 ||
         (Cs - ca) % 16 || (ca < Cs && !src_b))
         return cudaErrorNotSupported;
-    if (mode == 1 && (ca != Cs || g.in_d % 2 || g.in_h % 2 || g.in_w % 2)) return cudaErrorNotSupported;
+    if ((mode == 1 || mode == 3) && (ca != Cs || g.in_d % 2 || g.in_h % 2 || g.in_w % 2))
+        return cudaErrorNotSupported;
     if (splits > 1 && (g.mask_ca > 0 || g.out_b)) return cudaErrorNotSupported;
     // the walked (input) grid
     const int D = mode ? g.in_d / 2 : g.in_d, H = mode ? g.in_h / 2 : g.in_h, W = mode ? g.in_w / 2 : g.in_w;
@@ -2926,7 +3039,11 @@ cudaError_t launch_dwtma(int mode, const Conv3dArgs &g, const __nv_bfloat16 *src
     if (mode == 0 && splits == 1 && FDC_DWT_PAIR && ca == 16 && Cs == 32 &&
         make_pair_map(&tm_a, src, g.batch, D, H, W) && make_pair_map(&tm_b, src_b, g.batch, D, H, W))
         mode = 2;
-    if (mode != 2 && !make_plane_map(&tm_a, src, ca, g.batch, D, H, W)) return cudaErrorNotSupported;
+    if (mode == 3) {
+        if (!make_parity_map(&tm_a, src, Cs, g.batch, g.in_d, g.in_h, g.in_w)) return cudaErrorNotSupported;
+    } else if (mode != 2 && !make_plane_map(&tm_a, src, ca, g.batch, D, H, W)) {
+        return cudaErrorNotSupported;
+    }
     if (ca == Cs) {
         tm_b = tm_a;
     } else if (mode != 2 && !make_plane_map(&tm_b, src_b, Cs - ca, g.batch, D, H, W)) {
@@ -2939,22 +3056,22 @@ cudaError_t launch_dwtma(int mode, const Conv3dArgs &g, const __nv_bfloat16 *src
     if (e != cudaSuccess) return e;
     const int Cp = Cs / splits;  // input channels per CTA
     const int S = Cp / 16;
-    const int NT = (mode == 0 && Nn % 32 == 0) ? 32 : 16;
-    const int NX = (mode == 1 ? 4 : 3) * NT, NU = mode == 1 ? 16 : 9;
+    const int NT = ((mode == 0 || mode == 3) && Nn % 32 == 0) ? 32 : 16;
+    const int NX = (mode == 1 ? 4 : (mode == 3 ? 2 : 3)) * NT, NU = mode == 1 ? 16 : (mode == 3 ? 32 : 9);
     const int wbytes = S * NU * 2 * NX * 16;
-    const int plane = S * kDwPlaneSliceBytes * (mode == 2 ? 2 : 1);
+    const int plane = S * kDwPlaneSliceBytes * (mode == 2 ? 2 : (mode == 3 ? 4 : 1));
     // CTAs per SM: at most what TMEM allows (accumulator slots of 64 or 128 of
     // the 512 columns: two per CTA in MODE 0, one coarse plane's four units
     // in MODE 1), fewer when the ring would hold less than 5 planes (three in
     // use, two in flight) or, in MODE 1, 4; one CTA per SM takes a ring of 4
     int per_sm = mode != 0 ? 2 : (NT == 32 ? 2 : 4), R = 0;
-    const int r_min = mode != 0 ? 4 : 5;
+    const int r_min = mode == 3 ? 6 : (mode != 0 ? 4 : 5);  // MODE 3: four planes in use, two in flight
     for (; per_sm > 1; --per_sm) {
         R = std::min(kDwtMaxRing, (smem_sm / per_sm - 3072 - wbytes - 1024) / plane);
         if (R >= r_min) break;
     }
     if (per_sm == 1) R = std::min(kDwtMaxRing, (smem_sm - 3072 - wbytes - 1024) / plane);
-    if (R < 4) return cudaErrorNotSupported;
+    if (R < (mode == 3 ? 6 : 4)) return cudaErrorNotSupported;
     const int NA = mode != 1 ? 2 : (per_sm == 2 ? 4 : 8);
     const int smem = wbytes + 1024 + R * plane;
     const int ntiles = (Nn + NT - 1) / NT;
@@ -2964,7 +3081,7 @@ cudaError_t launch_dwtma(int mode, const Conv3dArgs &g, const __nv_bfloat16 *src
     if (gx > planes) gx = planes;
     const dim3 grid((unsigned)gx, (unsigned)ntiles, (unsigned)splits);
     // split partial sums: [splits][output voxels][Nn] FP32
-    const long long n_out = (long long)g.batch * g.in_d * g.in_h * g.in_w * Nn;
+    const long long n_out = (long long)g.batch * (mode == 3 ? (long long)D * H * W : (long long)g.in_d * g.in_h * g.in_w) * Nn;
     float *part = nullptr;
     if (splits > 1) {
         e = split_scratch((size_t)n_out * splits, st, &part);
@@ -2976,7 +3093,19 @@ cudaError_t launch_dwtma(int mode, const Conv3dArgs &g, const __nv_bfloat16 *src
     __nv_bfloat16 *kob = splits > 1 ? nullptr : out_bf16;
     float *kof = splits > 1 ? part : out_f32;
     const int krelu = splits > 1 ? 0 : relu;
-    if (mode == 2) {
+    if (mode == 3 && NT == 32) {
+        static OccCache cache;
+        e = prepare_kernel_smem(cache, conv3_dwtma_kernel<32, 8, 1, 3>, smem);
+        if (e != cudaSuccess) return e;
+        conv3_dwtma_kernel<32, 8, 1, 3><<<grid, 320, smem, st>>>(tm_a, tm_b, gk, wt, kb, kob, kof, Cp, Nn, krelu, ca,
+                                                                  R, NA, Cs, n_out);
+    } else if (mode == 3) {
+        static OccCache cache;
+        e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 4, 2, 3>, smem);
+        if (e != cudaSuccess) return e;
+        conv3_dwtma_kernel<16, 4, 2, 3><<<grid, 192, smem, st>>>(tm_a, tm_b, gk, wt, kb, kob, kof, Cp, Nn, krelu, ca,
+                                                                  R, NA, Cs, n_out);
+    } else if (mode == 2) {
         static OccCache cache;
         e = prepare_kernel_smem(cache, conv3_dwtma_kernel<16, 8, 2, 2>, smem);
         if (e != cudaSuccess) return e;
@@ -3022,6 +3151,27 @@ cudaError_t launch_conv_up(const Conv3dArgs &g, const void *xa, const void *w_up
     const int splits = g.c_in > 64 && FDC_DWT_KSPLIT ? g.c_in / 32 : 1;
     return launch_dwtma(1, g, (const __nv_bfloat16 *)xa, (const __nv_bfloat16 *)w_up, bias, (__nv_bfloat16 *)out_bf16,
                         out_f32, g.c_in, g.c_out, relu, st, g.c_in, nullptr, splits);
+}
+
+// the data gradient of the sub-pixel upsampling convolution: dy (full resolution,
+// g.c_out channels) to dxa (coarse, g.c_in channels, masked by relu_mask = xa > 0)
+cudaError_t launch_conv_up_dgrad(const Conv3dArgs &g, const void *dy, const void *w_up_t, void *dxa, cudaStream_t st) {
+    // K split into 16-channel parts when the collapsed weights of all dy channels do not fit
+    const int cs = g.c_out;
+    cudaError_t e = cudaErrorNotSupported;
+    for (int splits = 1; splits <= cs / 16 && e == cudaErrorNotSupported; splits *= 2) {
+        if (cs % splits || (cs / splits) % 16) break;
+        e = launch_dwtma(3, g, (const __nv_bfloat16 *)dy, (const __nv_bfloat16 *)w_up_t, nullptr,
+                         (__nv_bfloat16 *)dxa, nullptr, cs, g.c_in, 0, st, cs, nullptr, splits);
+    }
+    return e;
+}
+
+cudaError_t launch_collapse_up_t(const void *w, void *w_up_t, int co, int ci, cudaStream_t st) {
+    const long long n = (long long)co * 64 * ci;
+    conv3_collapse_up_t_kernel<<<grid_for(n), 256, 0, st>>>((const __nv_bfloat16 *)w, (__nv_bfloat16 *)w_up_t, co,
+                                                            ci);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_collapse_up(const void *w, void *w_up, int co, int ci, cudaStream_t st) {
@@ -3526,6 +3676,22 @@ int fdc_conv3d_forward_up(const fdc_conv3d *g, const void *xa, const void *w_up,
     const cudaError_t e = fdc::launch_conv_up(to_args(g), xa, w_up, bias, y_bf16, y_f32, g->relu ? 1 : 0,
                                               (cudaStream_t)stream);
     return e == cudaErrorNotSupported ? FDC_ERR_INVALID : rc(e);
+}
+
+int fdc_conv3d_backward_data_up(const fdc_conv3d *g, const void *dy, const void *w_up_t, const void *relu_mask,
+                                void *dxa, void *stream) {
+    if (!conv_ok(g) || !is_k3s1p1(g) || !dy || !w_up_t || !dxa) return FDC_ERR_INVALID;
+    if (g->in_d % 2 || g->in_h % 2 || g->in_w % 2) return FDC_ERR_INVALID;
+    fdc::Conv3dArgs a = to_args(g);
+    a.relu = 0;
+    a.mask = relu_mask;
+    const cudaError_t e = fdc::launch_conv_up_dgrad(a, dy, w_up_t, dxa, (cudaStream_t)stream);
+    return e == cudaErrorNotSupported ? FDC_ERR_INVALID : rc(e);
+}
+
+int fdc_conv3d_collapse_up_weights_t(const fdc_conv3d *g, const void *w, void *w_up_t, void *stream) {
+    if (!conv_ok(g) || !is_k3s1p1(g) || !w || !w_up_t) return FDC_ERR_INVALID;
+    return rc(fdc::launch_collapse_up_t(w, w_up_t, g->c_out, g->c_in, (cudaStream_t)stream));
 }
 
 int fdc_conv3d_collapse_up_weights(const fdc_conv3d *g, const void *w, void *w_up, void *stream) {

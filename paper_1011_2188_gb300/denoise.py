@@ -91,7 +91,9 @@ class ConvLayer:
         of the sub-pixel form (fdc_conv3d_forward_up) next to the others."""
         import torch
         self.wup16 = torch.empty((self.cout, 64, self.cin), dtype=torch.bfloat16, device=self.dev)
+        self.wupt16 = torch.empty((self.cin, 64, self.cout), dtype=torch.bfloat16, device=self.dev)
         self.up_ok = None  # whether fdc_conv3d_forward_up takes this layer's shape (learned at first call)
+        self.up_dgrad_ok = None  # the same for fdc_conv3d_backward_data_up
         self.collapse_up()
 
     def collapse_up(self):
@@ -99,6 +101,8 @@ class ConvLayer:
             g, _ = self.geom((1, 8, 8, 8, self.cin))
             _ok(fdc.lib().fdc_conv3d_collapse_up_weights(C.byref(g), _p(self.w16), _p(self.wup16), _s()),
                 "collapse up")
+            _ok(fdc.lib().fdc_conv3d_collapse_up_weights_t(C.byref(g), _p(self.w16), _p(self.wupt16), _s()),
+                "collapse up (data gradient)")
 
     def forward(self, x, keep=True):
         import torch
@@ -161,9 +165,12 @@ class ConvLayer:
         epilogue, which is that derivative for the layer before).  Returns
         the gradient with respect to the previous layer's pre-activation; after
         forward_fused(keep=True), the pair (d xa, d xb) for a concatenated input
-        (d xa at full resolution when xa was upsampled), or d xa alone."""
+        (d xa at full resolution when xa was upsampled), or d xa alone; an
+        up-convolution with collapsed weights returns d xa on xa's own coarse
+        grid where its kernel takes the shape (then self.dx_coarse is True)."""
         import torch
         L = fdc.lib()
+        self.dx_coarse = False
         if getattr(self, "fused_in", None) is not None:
             xa, up, xb, shape = self.fused_in
             g, _ = self.geom(shape)
@@ -171,6 +178,19 @@ class ConvLayer:
             _ok(L.fdc_conv3d_backward_weights_fused(C.byref(g), _p(xa), ca, 1 if up else 0, _p(xb), _p(dy),
                                                     _p(self.gw), _p(self.gb), _s()), "conv wgrad fused")
             out = None
+            if need_dx and up and xb is None and getattr(self, "wupt16", None) is not None and \
+                    self.up_dgrad_ok is not False:
+                # the gradient of xa itself, on its coarse grid (no full-resolution gradient)
+                dxa = torch.empty(xa.shape, dtype=torch.bfloat16, device=self.dev)
+                rc = L.fdc_conv3d_backward_data_up(C.byref(g), _p(dy), _p(self.wupt16), _p(xa), _p(dxa), _s())
+                if rc == 0:
+                    self.up_dgrad_ok, self.dx_coarse = True, True
+                    self.fused_in = None
+                    self.y = None
+                    return dxa
+                if rc != 1 or self.up_dgrad_ok:
+                    _ok(rc, "conv dgrad up")
+                self.up_dgrad_ok = False
             if need_dx:
                 dxa = torch.empty(shape[:4] + (ca,), dtype=torch.bfloat16, device=self.dev)
                 dxb = (torch.empty(shape[:4] + (self.cin - ca,), dtype=torch.bfloat16, device=self.dev)
@@ -387,7 +407,8 @@ class UNet:
             dc, dskip = dec[0].backward(d)
         else:
             dc, dskip = _split(dec[0].backward(d), c, c)
-        return _upsample(up.backward(dc), backward=True), dskip
+        dx = up.backward(dc)
+        return (dx if getattr(up, "dx_coarse", False) else _upsample(dx, backward=True)), dskip
 
     @staticmethod
     def _seq_back(layers, dy, need_last=True):

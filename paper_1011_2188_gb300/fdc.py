@@ -46,6 +46,8 @@ SIGNATURES = {
     "fdc_conv3d_forward_fused": (C.c_int, [_p, _p, C.c_int32, C.c_int32, _p, _p, _p, _p, _p, _p]),
     "fdc_conv3d_forward_up": (C.c_int, [_p, _p, _p, _p, _p, _p, _p]),
     "fdc_conv3d_collapse_up_weights": (C.c_int, [_p, _p, _p, _p]),
+    "fdc_conv3d_backward_data_up": (C.c_int, [_p, _p, _p, _p, _p, _p]),
+    "fdc_conv3d_collapse_up_weights_t": (C.c_int, [_p, _p, _p, _p]),
     "fdc_conv3d_backward_data": (C.c_int, [_p, _p, _p, _p, _p, _p]),
     "fdc_conv3d_backward_data_add": (C.c_int, [_p, _p, _p, _p, _p, _p, _p]),
     "fdc_conv3d_backward_weights": (C.c_int, [_p, _p, _p, _p, _p, _p]),

@@ -680,3 +680,69 @@ def test_forward_up_refuses_shapes_without_its_kernel():
         g, _ = geom(shape, 16, 3, 1, 1)
         assert L.fdc_conv3d_forward_up(C.byref(g), ptr(x), ptr(wup), None, ptr(y), None, None) == 1
     torch.cuda.synchronize()
+
+
+def _collapse_up_t(w):
+    """Transposed collapsed weights of the coarse data gradient from their
+    definition (FP64): [ci][t][co], t = (q_d, q_h, q_w, i_d, i_h, i_w), the
+    forward collapse of output parity q and coarse offset s = 1 - i."""
+    fw = _collapse_up(w)  # [co][(pd ph)(sd sh)(pw sw)][ci]
+    co, ci = w.shape[0], w.shape[-1]
+    out = np.zeros((ci, 64, co))
+    for t in range(64):
+        qd, qh, qw, idd, idh, idw = [(t >> b) & 1 for b in (5, 4, 3, 2, 1, 0)]
+        tf = ((qd * 2 + qh) * 4 + (1 - idd) * 2 + (1 - idh)) * 4 + qw * 2 + (1 - idw)
+        out[:, t, :] = fw[:, tf, :].T
+    return out
+
+
+@pytest.mark.parametrize("full,cin,cout", [((1, 8, 20, 32), 32, 16), ((1, 6, 20, 34), 16, 16),
+                                           ((2, 8, 24, 40), 64, 32), ((1, 4, 20, 32), 128, 64),
+                                           ((1, 64, 40, 64), 32, 16)])
+def test_backward_data_up_coarse(full, cin, cout):
+    """fdc_conv3d_backward_data_up (the data gradient of the sub-pixel
+    up-convolution, on the coarse grid) against the FP64 adjoint of the direct
+    form: upsample2-adjoint of the full-resolution data gradient, masked where
+    xa is not positive.  Bound: the collapsed weights' BF16 rounding (2^-8 of
+    the same sums with |w| and |dy|), FP32 accumulation and the output's BF16
+    rounding; the transposed collapsed weights within one BF16 rounding of
+    their definition."""
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    L = fdc.lib()
+    B, D, H, W = full
+    rng = np.random.default_rng(B + D + H + W + cin + cout)
+    coarse = (B, D // 2, H // 2, W // 2, cin)
+    xat, xa = bf16(np.maximum(rng.normal(size=coarse), 0) * (rng.random(coarse) < 0.8))
+    wt, w = bf16(rng.normal(size=(cout, 3, 3, 3, cin)) / np.sqrt(27 * cin))
+    dyt, dy = bf16(rng.normal(size=(B, D, H, W, cout)))
+    g, _ = geom((B, D, H, W, cin), cout, 3, 1, 1)
+    wupt = torch.empty((cin, 64, cout), dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_conv3d_collapse_up_weights_t(C.byref(g), ptr(wt), ptr(wupt), None) == 0
+    dxa = torch.full(coarse, 7.0, dtype=torch.bfloat16, device="cuda:0")
+    assert L.fdc_conv3d_backward_data_up(C.byref(g), ptr(dyt), ptr(wupt), ptr(xat), ptr(dxa), None) == 0
+    torch.cuda.synchronize()
+    exact = _collapse_up_t(w)
+    assert np.all(np.abs(wupt.double().cpu().numpy() - exact) <= (2.0 ** -8 + 2.0 ** -22) * np.abs(exact))
+    shape = (B, D, H, W, cin)
+    r = ref.upsample2_adjoint(ref.backward_data(dy, w, shape))
+    r = np.where(xa > 0, r, 0.0)
+    bound = 2.0 ** -8 * ref.upsample2_adjoint(ref.backward_data(np.abs(dy), np.abs(w), shape)) + \
+        2e-5 * np.abs(r).max() + 2.0 ** -8 * np.abs(r)
+    err = np.abs(dxa.double().cpu().numpy() - r)
+    assert np.all(err <= bound), float((err / bound).max())
+
+
+def test_backward_data_up_refuses_shapes_without_its_kernel():
+    """FDC_ERR_INVALID, nothing launched: a full-resolution grid narrower than
+    32 columns, odd sizes."""
+    import torch
+    from paper_1011_2188_gb300 import fdc
+    L = fdc.lib()
+    dy = torch.zeros((1, 8, 20, 32, 16), dtype=torch.bfloat16, device="cuda:0")
+    wupt = torch.zeros((16, 64, 16), dtype=torch.bfloat16, device="cuda:0")
+    dxa = torch.zeros((1, 4, 10, 16, 16), dtype=torch.bfloat16, device="cuda:0")
+    for shape in [(1, 8, 20, 30, 16), (1, 7, 20, 32, 16)]:
+        g, _ = geom(shape, 16, 3, 1, 1)
+        assert L.fdc_conv3d_backward_data_up(C.byref(g), ptr(dy), ptr(wupt), None, ptr(dxa), None) == 1
+    torch.cuda.synchronize()
