@@ -48,6 +48,7 @@ __device__ __forceinline__ void cp_async16_ca(void *smem, const void *gmem, bool
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(n));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
 
@@ -132,6 +133,12 @@ __global__ void __launch_bounds__(128) conv_igemm_kernel(const Conv3dArgs g, con
     const int tap_par = (pd * g.ksize + ph) * g.ksize + pw;
     const int csteps = Cs / 16;
     const int ksteps = par ? csteps : taps * csteps;
+    // forward with a K split (blockIdx.z: the coarse layers, whose few row
+    // tiles would leave most SMs idle): this CTA's K steps [k_lo, k_hi), its
+    // FP32 partial sums stored without bias or activation to out_f32's slice z
+    const int nsplit = MODE == 0 ? (int)gridDim.z : 1;
+    const int k_lo = (int)((long long)ksteps * (MODE == 0 ? blockIdx.z : 0) / nsplit);
+    const int k_hi = (int)((long long)ksteps * ((MODE == 0 ? blockIdx.z : 0) + 1) / nsplit);
     // the voxel (in the D x H x W row space) of row r of this grid
     auto row_voxel = [&](long long r, RowCoord &c) {
         c = row_coord(r, rows, Dq, Hq, Wq);
@@ -170,11 +177,11 @@ __global__ void __launch_bounds__(128) conv_igemm_kernel(const Conv3dArgs g, con
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
 
-    load_stage(0, 0);
+    load_stage(0, k_lo);
     cp_async_commit();
-    for (int ks = 0; ks < ksteps; ++ks) {
-        const int buf = ks & 1;
-        if (ks + 1 < ksteps) load_stage(buf ^ 1, ks + 1);
+    for (int ks = k_lo; ks < k_hi; ++ks) {
+        const int buf = (ks - k_lo) & 1;
+        if (ks + 1 < k_hi) load_stage(buf ^ 1, ks + 1);
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
@@ -198,8 +205,9 @@ __global__ void __launch_bounds__(128) conv_igemm_kernel(const Conv3dArgs g, con
         __syncthreads();
     }
     cp_async_wait<0>();
+    if (nsplit > 1) out_f32 += (long long)blockIdx.z * rows * Nn;
 
-    // epilogue: bias, ReLU, store
+    // epilogue: bias, ReLU, store (a split's partials: neither)
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
 #pragma unroll
@@ -2178,22 +2186,34 @@ __global__ void __launch_bounds__(128) conv_s2_tc_kernel(const Conv3dArgs g, con
     auto stage = [&](int tile, unsigned char *buf) {
         const int v0 = tile * kS2Vox;
         if (MODE == 0) {
-            // per voxel and (td, th): 2 Ci contiguous values = 2 Ci / 8 pieces
+            // per voxel and (td, th): 2 Ci contiguous values = 2 Ci / 8 pieces.
+            // Piece i = tid + 128 m (m < PV) is piece i % PV of voxel i / PV: a
+            // warp instruction covers 32 / PV whole voxels (contiguous runs),
+            // and a warp's PV instructions cover 32 voxels, whose corner
+            // addresses (2d, 2h, 2w) its lanes compute once, one voxel per
+            // lane, and pass by shuffle.
             constexpr int PV = K / 8;  // pieces per voxel
-            for (int i = tid; i < kS2Vox * PV; i += 128) {
+            static_assert(PV <= 32 && 32 % PV == 0 && kS2Vox == 128, "staging map");
+            constexpr int VPI = 32 / PV;  // voxels per warp instruction
+            const int vl = (32 * warp) / PV + (lane / VPI) * (128 / PV) + lane % VPI;  // this lane's voxel
+            long long corner = -1;  // element offset of the voxel's (2d, 2h, 2w) input, -1 past the end
+            if (v0 + vl < V) {
+                const int v = v0 + vl;
+                const int w = v % W2;
+                int t = v / W2;
+                const int h = t % H2;
+                t /= H2;
+                const int d = t % D2, b = t / D2;
+                corner = ((((long long)b * D + 2 * d) * H + 2 * h) * W + 2 * w) * Ci;
+            }
+#pragma unroll 4
+            for (int m = 0; m < PV; ++m) {
+                const int i = tid + 128 * m;
                 const int j = i % PV, vi = i / PV;  // j = tdh * (PV / 4) + (piece within the run)
-                const int v = v0 + vi;
-                const bool ok = v < V;
-                const __nv_bfloat16 *p = src;
-                if (ok) {
-                    const int w = v % W2;
-                    int t = v / W2;
-                    const int h = t % H2;
-                    t /= H2;
-                    const int d = t % D2, b = t / D2;
-                    const int tdh = j / (PV / 4), r = j % (PV / 4);
-                    p = src + ((((long long)b * D + 2 * d + (tdh >> 1)) * H + 2 * h + (tdh & 1)) * W + 2 * w) * Ci + r * 8;
-                }
+                const long long c = __shfl_sync(0xffffffffu, corner, m * VPI + lane / PV);
+                const int tdh = j / (PV / 4), r = j % (PV / 4);
+                const bool ok = c >= 0;
+                const __nv_bfloat16 *p = ok ? src + c + ((long long)(tdh >> 1) * H + (tdh & 1)) * W * Ci + r * 8 : src;
                 cp_async16(buf + ((j * 16 + vi / 8) * 8 + (vi % 8)) * 16, p, ok);
             }
         } else {
@@ -2206,10 +2226,15 @@ __global__ void __launch_bounds__(128) conv_s2_tc_kernel(const Conv3dArgs g, con
             }
         }
     };
-    // epilogue of the tile in accumulator ab: row m = this thread's voxel
-    auto epilogue = [&](int tile, unsigned ab, unsigned ph) -> bool {
+    // the MMAs of the tile in accumulator ab have completed (bounded wait;
+    // the warp agrees on the outcome)
+    auto acc_ready = [&](unsigned ab, unsigned ph) -> bool {
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(ab ? mb1 : mb0, ph))) return false;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        return true;
+    };
+    // epilogue of the tile in accumulator ab (after acc_ready): row m = this thread's voxel
+    auto epilogue = [&](int tile, unsigned ab) {
         const int v = tile * kS2Vox + warp * 32 + lane;
         const bool in = v < V;
         int d = 0, h = 0, w = 0, b = 0;
@@ -2222,6 +2247,18 @@ __global__ void __launch_bounds__(128) conv_s2_tc_kernel(const Conv3dArgs g, con
             b = t / D2;
         }
         const unsigned base = tmem + ((unsigned)(warp * 32) << 16) + ab * N;
+        if (MODE == 1 && in && (g.mask || residual)) {
+            // the chunks below read the mask and residual rows one after the
+            // other: ask L2 for all of them first, so that their DRAM latencies
+            // overlap
+#pragma unroll 1
+            for (int c = 0; c < N; c += 16) {
+                const int col = n0 + c, t = col / Ci, ci = col % Ci;
+                const long long xv = (((long long)b * D + 2 * d + (t >> 2)) * H + 2 * h + ((t >> 1) & 1)) * W + 2 * w + (t & 1);
+                if (g.mask) prefetch_l2((const __nv_bfloat16 *)g.mask + xv * Ci + ci);
+                if (residual) prefetch_l2(residual + xv * Ci + ci);
+            }
+        }
 #pragma unroll 1
         for (int c = 0; c < N; c += 16) {
             float a[16];
@@ -2280,7 +2317,6 @@ __global__ void __launch_bounds__(128) conv_s2_tc_kernel(const Conv3dArgs g, con
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        return true;
     };
     bool ok = true;
     int it = 0;
@@ -2309,16 +2345,20 @@ __global__ void __launch_bounds__(128) conv_s2_tc_kernel(const Conv3dArgs g, con
                           idesc, ks > 0 ? 1 : 0);
             umma_commit(ab ? mb1 : mb0);
         }
-        // the previous tile's epilogue frees its accumulator and A buffer
-        if (it > 0) ok = epilogue(tile - (int)gridDim.x, ab ^ 1u, ((it - 1) >> 1) & 1u);
+        // once the previous tile's MMAs are done its A buffer takes the next
+        // tile (the copies then run under that tile's epilogue)
+        if (it > 0) ok = acc_ready(ab ^ 1u, ((it - 1) >> 1) & 1u);
         const int nx = tile + (int)gridDim.x;
         if (ok && nx < n_tiles) stage(nx, sA + (ab ^ 1u) * ABytes);
         cp_async_commit();
+        if (it > 0 && ok) epilogue(tile - (int)gridDim.x, ab ^ 1u);
     }
-    if (__syncthreads_and(ok) && it > 0)
-        ok = epilogue(blockIdx.x + (it - 1) * (int)gridDim.x, (unsigned)(it - 1) & 1u, ((it - 1) >> 1) & 1u);
-    else
+    if (__syncthreads_and(ok) && it > 0) {
+        ok = acc_ready((unsigned)(it - 1) & 1u, ((it - 1) >> 1) & 1u);
+        if (ok) epilogue(blockIdx.x + (it - 1) * (int)gridDim.x, (unsigned)(it - 1) & 1u);
+    } else {
         ok = ok && it == 0;
+    }
     if (!ok && tid == 0) atomicExch(&g_tc_status, (int)FDC_ERR_TIMEOUT);
     cp_async_wait<0>();
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -3396,6 +3436,41 @@ cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const vo
     auto w = (const __nv_bfloat16 *)wt;
     auto ob = (__nv_bfloat16 *)out_bf16;
     if (mode == 0) {
+        // a grid of fewer than two CTAs per SM (the 32^3 -> 16^3 down-convolution,
+        // 64 -> 128 channels: 128 CTAs, each a chain of 32 K steps whose
+        // operand loads wait on memory one after the other): K split over
+        // grid.z into about four CTAs per SM of at least two K steps each, FP32
+        // partials summed in split order by the combine pass, which adds bias
+        // and ReLU
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const long long ctas = (long long)grid.x * grid.y;
+        const int ksteps = g.ksize * g.ksize * g.ksize * (g.c_in / 16);
+        int splits = 1;
+        if (ctas < 2ll * sms && Nn % 4 == 0)
+            splits = (int)std::min<long long>(ksteps / 2, (4ll * sms + ctas - 1) / ctas);
+        if (splits < 1) splits = 1;
+        if (splits > 1) {
+            const long long n_out = rows * Nn;
+            float *part = nullptr;
+            e = split_scratch((size_t)n_out * splits, st, &part);
+            if (e != cudaSuccess) return e;
+            Conv3dArgs gk = g;
+            gk.relu = 0;
+            grid.z = (unsigned)splits;
+            if (nt == 64) conv_igemm_kernel<0, 64><<<grid, 128, 0, st>>>(gk, s, w, nullptr, nullptr, part);
+            else if (nt == 32) conv_igemm_kernel<0, 32><<<grid, 128, 0, st>>>(gk, s, w, nullptr, nullptr, part);
+            else conv_igemm_kernel<0, 16><<<grid, 128, 0, st>>>(gk, s, w, nullptr, nullptr, part);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            long long blocks = (n_out / 4 + 255) / 256;
+            if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
+            split_combine_kernel<<<(int)blocks, 256, 0, st>>>(part, splits, n_out, bias, Nn, g.relu, nullptr,
+                                                              ob, out_f32);
+            return cudaGetLastError();
+        }
         if (nt == 64) conv_igemm_kernel<0, 64><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32);
         else if (nt == 32) conv_igemm_kernel<0, 32><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32);
         else conv_igemm_kernel<0, 16><<<grid, 128, 0, st>>>(g, s, w, bias, ob, out_f32);

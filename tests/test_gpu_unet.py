@@ -42,6 +42,11 @@ CASES = [
     ((2, 5, 6, 7, 32), 64, 3, 1, 1),
     ((1, 8, 6, 10, 16), 32, 2, 2, 0),
     ((1, 6, 4, 8, 64), 128, 2, 2, 0),
+    # the network's 32^3 -> 16^3 down-convolution (128 CTAs, K split five
+    # ways over 32 K steps: uneven split ranges) and a 16^3 input (16 CTAs,
+    # sixteen splits of two K steps)
+    ((1, 32, 32, 32, 64), 128, 2, 2, 0),
+    ((1, 16, 16, 16, 64), 128, 2, 2, 0),
     ((1, 9, 5, 6, 32), 16, 1, 1, 0),
     ((1, 4, 4, 6, 128), 64, 3, 1, 1),
     ((1, 16, 16, 16, 16), 16, 3, 1, 1),
