@@ -1111,6 +1111,10 @@ constexpr int kDwtMaxAcc = 8;   // accumulator slots
 #ifndef FDC_DWT_KSPLIT
 #define FDC_DWT_KSPLIT 1
 #endif
+// input channels per K part of a split layer (32 or 64)
+#ifndef FDC_DWT_KSPLIT_CH
+#define FDC_DWT_KSPLIT_CH 64
+#endif
 // pair tiles (MODE 2) for inputs made of two 16-channel tensors
 #ifndef FDC_DWT_PAIR
 #define FDC_DWT_PAIR 1
@@ -3234,10 +3238,10 @@ cudaError_t launch_conv_halo(const Conv3dArgs &g, const void *src, const void *w
     // 64-channel parts on the same kernel, FP32 partial sums combined in order (with a plain
     // ReLU mask for a data gradient)
     if (FDC_CONV_DWTMA && FDC_DWT_KSPLIT && !up_a && g.mask_ca == 0 && !g.out_b && Cs > FDC_CONV_DWALK_MAXC &&
-        Cs % 64 == 0 && Cs <= 8 * 64 && Nn % 16 == 0) {
+        Cs % FDC_DWT_KSPLIT_CH == 0 && Cs <= 8 * 64 && Nn % 16 == 0) {
         const cudaError_t e = launch_dwtma(0, g, (const __nv_bfloat16 *)src, (const __nv_bfloat16 *)wt, bias,
                                            (__nv_bfloat16 *)out_bf16, out_f32, Cs, Nn, relu, st, ca,
-                                           (const __nv_bfloat16 *)src_b, Cs / 64);
+                                           (const __nv_bfloat16 *)src_b, Cs / FDC_DWT_KSPLIT_CH);
         if (e != cudaErrorNotSupported) return e;
     }
     auto s = (const __nv_bfloat16 *)src;
@@ -3386,6 +3390,11 @@ cudaError_t launch_s2_tc(const Conv3dArgs &g, const void *src, const void *wt, c
     return cudaGetLastError();
 }
 
+// CTAs per SM that the K split of a small mma.sync forward grid aims at
+#ifndef FDC_IGEMM_SPLIT_CTAS
+#define FDC_IGEMM_SPLIT_CTAS 4
+#endif
+
 // widest output-channel tile of the mma.sync forward (its grid is small on
 // coarse levels: narrower tiles give more CTAs)
 #ifndef FDC_IGEMM_FWD_NT
@@ -3450,7 +3459,7 @@ cudaError_t launch_conv(const Conv3dArgs &g, int mode, const void *src, const vo
         const int ksteps = g.ksize * g.ksize * g.ksize * (g.c_in / 16);
         int splits = 1;
         if (ctas < 2ll * sms && Nn % 4 == 0)
-            splits = (int)std::min<long long>(ksteps / 2, (4ll * sms + ctas - 1) / ctas);
+            splits = (int)std::min<long long>(ksteps / 2, ((long long)FDC_IGEMM_SPLIT_CTAS * sms + ctas - 1) / ctas);
         if (splits < 1) splits = 1;
         if (splits > 1) {
             const long long n_out = rows * Nn;
